@@ -1,0 +1,458 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+The paper prints no per-particle values, so the oracle is pinned by closed
+forms (tests/golden/closed_forms.json), brute force on tiny inputs, an
+independent kernel implementation (numpy's sinc with a scipy quadrature for
+B_n), lattice sums, IAD exactness for linear fields, conservation laws,
+symmetry and the integrator's order.  Each test names the passage it pins.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import sph_inputs
+from oracle import Box, Params
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")))
+
+
+# ---------------------------------------------------------------- helpers --
+def B_indep(n):
+    """B_n by scipy's adaptive quadrature (independent of the oracle's
+    Gauss-Legendre): 4 pi B_n int_0^2 sinc(pi v/2)^n v^2 dv = 1."""
+    from scipy.integrate import quad
+    val, _ = quad(lambda v: np.sinc(v / 2.0) ** n * v * v, 0.0, 2.0, epsabs=0.0, epsrel=2e-14,
+                  limit=400)
+    return 1.0 / (4.0 * math.pi * val)
+
+
+def W_indep(v, h, n=6, B=None):
+    """Eq. 6 kernel through numpy's sinc (np.sinc(x) = sin(pi x)/(pi x))."""
+    B = B_indep(n) if B is None else B
+    v = np.asarray(v, dtype=np.float64)
+    return np.where(v < 2.0, B / h ** 3 * np.sinc(v / 2.0) ** n, 0.0)
+
+
+def box_of(s):
+    return Box(s["lo"], s["hi"], s["periodic"])
+
+
+def min_image(d, box):
+    d = d.copy()
+    for ax in range(3):
+        if box.periodic[ax]:
+            L = box.hi[ax] - box.lo[ax]
+            d[..., ax] -= L * np.round(d[..., ax] / L)
+    return d
+
+
+def brute_numpy(s, box):
+    """Neighbour matrix by vectorised brute force with np.round minimum image."""
+    P = np.stack([s["x"], s["y"], s["z"]], 1)
+    d = min_image(P[None, :, :] - P[:, None, :], box)   # d[a, b] = x_b - x_a
+    r2 = (d ** 2).sum(-1)
+    lim = (2.0 * s["h"][:, None]) ** 2
+    nb = r2 < lim
+    np.fill_diagonal(nb, False)
+    border = np.abs(r2 - lim) <= 1e-12 * lim
+    return nb, border
+
+
+def lattice_state(side, h_over_dx=1.4397, rho0=1.0, u=1.0):
+    s = sph_inputs.jittered_box(side, jitter=0.0, vel_sigma=0.0, shuffle=True)
+    dx = 1.0 / side
+    s["h"][:] = h_over_dx * dx
+    s["m"][:] = rho0 / side ** 3
+    s["u"][:] = u
+    return s
+
+
+def all_outputs(oracle_mod, s, params=None, brute=False):
+    params = params or Params(ng_target=0)
+    rc, out = oracle_mod.outputs(box_of(s), s, params, brute=brute)
+    assert rc == 0, rc
+    return out
+
+
+# ------------------------------------------------------------ kernel (Eq. 6) --
+def test_kernel_norm_closed_forms(oracle_mod):
+    assert oracle_mod.kernel_norm(1.0) == pytest.approx(math.pi / 32, rel=1e-14)
+    assert oracle_mod.kernel_norm(2.0) == pytest.approx(math.pi / 16, rel=1e-14)
+
+
+@pytest.mark.parametrize("n", [3.0, 5.0, 6.0, 7.0, 4.5])
+def test_kernel_norm_vs_independent_quadrature(oracle_mod, n):
+    assert oracle_mod.kernel_norm(n) == pytest.approx(B_indep(n), rel=1e-13)
+
+
+def test_kernel_values(oracle_mod):
+    B = oracle_mod.kernel_norm(6.0)
+    for h in (0.5, 1.0, 0.0123):
+        assert oracle_mod.kernel_W(0.0, h, 6.0, B) == pytest.approx(B / h ** 3, rel=1e-15)
+        assert oracle_mod.kernel_W(1.0, h, 6.0, B) / oracle_mod.kernel_W(0.0, h, 6.0, B) == \
+            pytest.approx((2 / math.pi) ** 6, rel=1e-14)
+        assert oracle_mod.kernel_W(2.0000001, h, 6.0, B) == 0.0
+    v = np.linspace(0, 1.999, 97)
+    ref = W_indep(v, 0.7)
+    got = np.array([oracle_mod.kernel_W(t, 0.7, 6.0, B) for t in v])
+    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-300)
+
+
+# ------------------------------------------------------- neighbour search --
+def _tiny_cases():
+    rng = np.random.default_rng(7)
+    cases = []
+    # periodic, varying h
+    s = sph_inputs.jittered_box(10, seed_index=11)
+    s["h"] *= rng.uniform(0.7, 1.3, s["h"].shape[0])
+    cases.append(s)
+    # two cells per dimension (2 h_max just under L/2 after rescale)
+    s = sph_inputs.jittered_box(5, seed_index=12)
+    s["h"][:] = 0.24
+    cases.append(s)
+    # open x, y; periodic z (square patch layout)
+    s = sph_inputs.square_patch(7)
+    s["h"] *= rng.uniform(0.8, 1.2, s["h"].shape[0])
+    cases.append(s)
+    # fully open
+    s = sph_inputs.jittered_box(7, seed_index=13)
+    s["periodic"] = (0, 0, 0)
+    cases.append(s)
+    return cases
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_neighbors_brute_vs_numpy_and_cells(oracle_mod, case):
+    s = _tiny_cases()[case]
+    box = box_of(s)
+    rc_b, nn_b, nbr_b = oracle_mod.find_neighbors(box, s["x"], s["y"], s["z"], s["h"], brute=True,
+                                                  max_nb=400)
+    rc_c, nn_c, nbr_c = oracle_mod.find_neighbors(box, s["x"], s["y"], s["z"], s["h"], brute=False,
+                                                  max_nb=400)
+    assert rc_b == 0 and rc_c == 0
+    np.testing.assert_array_equal(nn_b, nn_c)
+    np.testing.assert_array_equal(nbr_b, nbr_c)
+    nb, border = brute_numpy(s, box)
+    assert not border.any(), "tiny case has a pair on the 2h boundary"
+    np.testing.assert_array_equal(nn_b, nb.sum(1))
+    for a in range(len(nn_b)):
+        np.testing.assert_array_equal(nbr_b[a, :nn_b[a]], np.nonzero(nb[a])[0])
+    # subset of targets gives the same rows
+    t = np.array([0, 5, len(nn_b) - 1, 17])
+    rc, nn_t, nbr_t = oracle_mod.find_neighbors(box, s["x"], s["y"], s["z"], s["h"], targets=t,
+                                                max_nb=400)
+    np.testing.assert_array_equal(nn_t, nn_c[t])
+    np.testing.assert_array_equal(nbr_t, nbr_c[t])
+
+
+def test_neighbors_overflow_and_invalid(oracle_mod):
+    s = sph_inputs.jittered_box(6, seed_index=11)
+    box = box_of(s)
+    rc, nn, nbr = oracle_mod.find_neighbors(box, s["x"], s["y"], s["z"], s["h"], max_nb=10)
+    assert rc == oracle_mod.NB_OVERFLOW and nn.max() > 10
+    h = np.full_like(s["h"], 0.26)   # 2h >= L/2 on a periodic axis
+    rc, _, _ = oracle_mod.find_neighbors(box, s["x"], s["y"], s["z"], h, max_nb=400)
+    assert rc == oracle_mod.INVALID_ARG
+
+
+def test_lattice_neighbor_counts(oracle_mod):
+    for key, expect in GOLDEN["lattice_neighbor_counts"]["values"].items():
+        s = lattice_state(12, h_over_dx=float(key) / 2)
+        rc, nn, _ = oracle_mod.find_neighbors(box_of(s), s["x"], s["y"], s["z"], s["h"], max_nb=200)
+        assert rc == 0 and (nn == expect).all()
+
+
+# --------------------------------------------------------- density (Eq. 1) --
+def test_density_lattice_sum(oracle_mod):
+    """Uniform lattice: rho_a = m sum_k W(|k| D / h_a, h_a) over the lattice
+    vectors k (self included), each particle with its own h_a."""
+    side = 12
+    s = lattice_state(side)
+    rng = np.random.default_rng(3)
+    s["h"] *= rng.uniform(0.85, 1.15, s["h"].shape[0])
+    out = all_outputs(oracle_mod, s)
+    dx = 1.0 / side
+    ks = np.array(list(itertools.product(range(-5, 6), repeat=3)), dtype=np.float64)
+    r = np.sqrt((ks ** 2).sum(1)) * dx
+    B = B_indep(6)
+    m = s["m"][0]
+    ref = np.array([m * W_indep(r / h, h, B=B)[r < 2 * h].sum() for h in s["h"]])
+    np.testing.assert_allclose(out["rho"], ref, rtol=1e-13)
+
+
+def test_density_approximates_rho0(oracle_mod):
+    for rho0 in (1.0, 3.0):
+        s = lattice_state(16, rho0=rho0)
+        out = all_outputs(oracle_mod, s)
+        assert np.abs(out["rho"] / rho0 - 1).max() < 2e-4
+
+
+def test_eos_closed_form(oracle_mod):
+    s = sph_inputs.jittered_box(8, seed_index=5)
+    out = all_outputs(oracle_mod, s)
+    np.testing.assert_allclose(out["c"], math.sqrt(10.0 / 9.0), rtol=1e-14)
+
+
+# --------------------------------------------------------------------- IAD --
+def _iad_case():
+    s = sph_inputs.jittered_box(9, seed_index=21, jitter=0.25)
+    rng = np.random.default_rng(4)
+    s["m"] *= rng.uniform(0.5, 1.5, s["m"].shape[0])      # density varies
+    s["h"] *= rng.uniform(0.9, 1.1, s["h"].shape[0])
+    return s
+
+
+def test_iad_tau_independent_and_inverse(oracle_mod):
+    s = _iad_case()
+    box = box_of(s)
+    out = all_outputs(oracle_mod, s)
+    B = B_indep(6)
+    P = np.stack([s["x"], s["y"], s["z"]], 1)
+    for a in range(0, P.shape[0], 7):
+        nb = out["nbr"][a, :out["nn"][a]]
+        d = min_image(P[nb] - P[a], box)
+        r = np.sqrt((d ** 2).sum(1))
+        w = s["m"][nb] / out["rho"][nb] * W_indep(r / s["h"][a], s["h"][a], B=B)
+        tau = (w[:, None, None] * d[:, :, None] * d[:, None, :]).sum(0)
+        t6 = out["tau"][a]
+        tau_o = np.array([[t6[0], t6[1], t6[2]], [t6[1], t6[3], t6[4]], [t6[2], t6[4], t6[5]]])
+        np.testing.assert_allclose(tau_o, tau, rtol=1e-12, atol=1e-14 * np.abs(tau).max())
+        c6 = out["iad"][a]
+        Cm = np.array([[c6[0], c6[1], c6[2]], [c6[1], c6[3], c6[4]], [c6[2], c6[4], c6[5]]])
+        np.testing.assert_allclose(Cm @ tau, np.eye(3), atol=1e-12)
+
+
+def test_iad_linear_exactness(oracle_mod):
+    """sum_b (m_b/rho_b) (f_b - f_a) A_ab(h_a) = grad f for linear f."""
+    s = _iad_case()
+    box = box_of(s)
+    out = all_outputs(oracle_mod, s)
+    B = B_indep(6)
+    g = np.array([0.3, -1.7, 2.2])
+    P = np.stack([s["x"], s["y"], s["z"]], 1)
+    for a in range(0, P.shape[0], 5):
+        nb = out["nbr"][a, :out["nn"][a]]
+        d = min_image(P[nb] - P[a], box)
+        r = np.sqrt((d ** 2).sum(1))
+        W = W_indep(r / s["h"][a], s["h"][a], B=B)
+        c6 = out["iad"][a]
+        Cm = np.array([[c6[0], c6[1], c6[2]], [c6[1], c6[3], c6[4]], [c6[2], c6[4], c6[5]]])
+        A = (Cm @ d.T).T * W[:, None]
+        grad = ((s["m"][nb] / out["rho"][nb] * (d @ g))[:, None] * A).sum(0)
+        np.testing.assert_allclose(grad, g, rtol=0, atol=1e-11)
+
+
+def test_iad_singular_flag(oracle_mod):
+    # a lone particle far from the rest has no neighbours -> tau = 0 -> singular
+    s = sph_inputs.jittered_box(6, seed_index=3)
+    s["periodic"] = (0, 0, 0)
+    s["x"][0] = 5.0
+    rc, out = oracle_mod.outputs(box_of(s), s, Params(ng_target=0))
+    assert rc == oracle_mod.SINGULAR_IAD
+    assert (out["iad"][0] == 0).all()
+
+
+# ----------------------------------------------------- momentum / energy --
+def _conservation_case(seed=31, side=9, vel=0.3):
+    s = sph_inputs.jittered_box(side, seed_index=seed, jitter=0.2, vel_sigma=vel)
+    rng = np.random.default_rng(seed)
+    s["u"] *= rng.uniform(0.5, 1.5, s["u"].shape[0])
+    s["m"] *= rng.uniform(0.8, 1.2, s["m"].shape[0])
+    return s   # common h: symmetric neighbour lists
+
+
+def test_momentum_and_energy_conservation(oracle_mod):
+    """Pair antisymmetry of Eqs. 2-4: sum m a = 0 and sum m (v.a + du) = 0."""
+    s = _conservation_case()
+    out = all_outputs(oracle_mod, s)
+    m = s["m"]
+    a = np.stack([out["ax"], out["ay"], out["az"]], 1)
+    scale = (m * out["sa"]).sum()
+    assert np.abs((m[:, None] * a).sum(0)).max() < 1e-13 * scale
+    v = np.stack([s["vx"], s["vy"], s["vz"]], 1)
+    power = (m * ((v * a).sum(1) + out["du"])).sum()
+    escale = (m * (np.linalg.norm(v, axis=1) * out["sa"] + out["sdu"])).sum()
+    assert abs(power) < 1e-13 * escale
+    # the viscous term is active in this case
+    assert np.abs(out["du"]).max() > 0
+
+
+def test_uniform_lattice_no_force(oracle_mod):
+    s = lattice_state(10)
+    out = all_outputs(oracle_mod, s)
+    assert np.abs(out["ax"]).max() < 1e-12 * out["sa"].max()
+    assert np.abs(out["du"]).max() == 0.0
+
+
+def test_galilean_invariance(oracle_mod):
+    s = _conservation_case(seed=33, side=8)
+    o1 = all_outputs(oracle_mod, s)
+    s2 = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+    s2["vx"] += 0.7
+    s2["vz"] -= 1.3
+    o2 = all_outputs(oracle_mod, s2)
+    for k in ("rho", "ax", "ay", "az"):
+        np.testing.assert_allclose(o2[k], o1[k], rtol=0, atol=1e-11 * o1["sa"].max() + 1e-14)
+    np.testing.assert_allclose(o2["du"], o1["du"], rtol=0, atol=1e-11 * o1["sdu"].max() + 1e-14)
+
+
+def test_viscosity_dissipates_and_vanishes_when_receding(oracle_mod):
+    base = _conservation_case(seed=35, side=9, vel=0.0)
+    P = np.stack([base["x"], base["y"], base["z"]], 1) - 0.5
+    for sign in (-1.0, +1.0):     # converging / diverging flow (in the box interior)
+        s = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in base.items()}
+        s["periodic"] = (0, 0, 0)
+        s["vx"], s["vy"], s["vz"] = (sign * 0.5 * P[:, k] for k in range(3))
+        o_av = all_outputs(oracle_mod, s, Params(ng_target=0, alpha=1.0))
+        o_0 = all_outputs(oracle_mod, s, Params(ng_target=0, alpha=0.0))
+        heat = s["m"] * (o_av["du"] - o_0["du"])
+        if sign < 0:
+            assert heat.sum() > 0 and (heat >= -1e-12 * np.abs(heat).max()).all()
+        else:
+            assert np.array_equal(o_av["du"], o_0["du"]) and np.array_equal(o_av["ax"], o_0["ax"])
+
+
+def test_pressure_gradient_magnitude_and_sign(oracle_mod):
+    """Smooth pressure on a uniform lattice: a ~ -grad P / rho.  This fixes the
+    sign of Eq. 2 and the P/rho^2 prefactor (rho0 = 8 separates rho from rho^2)."""
+    side, rho0, eps = 24, 8.0, 0.1
+    s = lattice_state(side, rho0=rho0)
+    s["u"] = 1.0 + eps * np.sin(2 * np.pi * s["x"])
+    out = all_outputs(oracle_mod, s)
+    gamma = 5.0 / 3.0
+    # P = (gamma-1) rho u  ->  -dP/dx / rho = -(gamma-1) eps 2 pi cos(2 pi x)
+    expect = -(gamma - 1) * eps * 2 * np.pi * np.cos(2 * np.pi * s["x"])
+    err = np.abs(out["ax"] - expect).max() / np.abs(expect).max()
+    assert err < 0.05, err
+    assert np.abs(out["ay"]).max() < 1e-10 * np.abs(expect).max()
+
+
+def test_square_patch_symmetry(oracle_mod):
+    """Section 4.6 square patch: rotating by pi about z maps the lattice to
+    itself, so a(-x,-y) = -a(x,y) in x, y and du is invariant; free-surface
+    particles are pushed outward."""
+    s = sph_inputs.square_patch(12, shuffle=False)
+    params = Params(ng_target=0)
+    rc, out = oracle_mod.outputs(box_of(s), s, params)
+    assert rc == 0
+    n = 12
+    idx = np.arange(n ** 3).reshape(n, n, n)           # [k, j, i]
+    rot = idx[:, ::-1, ::-1].ravel()                   # (x, y) -> (-x, -y)
+    tol = 1e-12 * out["sa"].max()
+    np.testing.assert_allclose(out["ax"][rot], -out["ax"], atol=tol)
+    np.testing.assert_allclose(out["ay"][rot], -out["ay"], atol=tol)
+    np.testing.assert_allclose(out["az"][rot], out["az"], atol=tol)
+    np.testing.assert_allclose(out["du"][rot], out["du"], atol=1e-12 * out["sdu"].max() + 1e-300)
+    edge = s["x"] > 0.45
+    assert (out["ax"][edge] > 0).all()
+
+
+# ------------------------------------------------------------- time step --
+def test_timestep_rule(oracle_mod):
+    h = np.array([0.1, 0.2, 0.05])
+    c = np.array([1.0, 1.0, 2.0])
+    p = Params(courant=0.2, dt_growth=1.1)
+    assert oracle_mod.timestep(h, c, p, 0.0) == pytest.approx(0.2 * 0.025, rel=1e-15)
+    assert oracle_mod.timestep(h, c, p, 0.004) == pytest.approx(0.0044, rel=1e-15)
+    assert oracle_mod.timestep(h, c, p, 0.1) == pytest.approx(0.005, rel=1e-15)
+
+
+# ------------------------------------------------------------- integrator --
+def _blank_state(n):
+    rng = np.random.default_rng(9)
+    s = {k: rng.uniform(0.2, 0.8, n) for k in ("x", "y", "z")}
+    for k in ("vx", "vy", "vz"):
+        s[k] = rng.normal(0, 0.1, n)
+    s["vxh"], s["vyh"], s["vzh"] = s["vx"].copy(), s["vy"].copy(), s["vz"].copy()
+    s["u"] = np.ones(n)
+    s["du_prev"] = np.zeros(n)
+    s["h"] = np.full(n, 0.05)
+    s["m"] = np.ones(n)
+    return s
+
+
+def test_integrator_exact_for_constant_acceleration_and_linear_du(oracle_mod):
+    n = 5
+    s = _blank_state(n)
+    x0 = {k: s[k].copy() for k in ("x", "y", "z", "vx", "vy", "vz", "u")}
+    box = Box((0, 0, 0), (1, 1, 1), (0, 0, 0))
+    a = np.array([0.3, -0.2, 0.1])
+    alpha_u, beta_u = 0.5, 2.0
+    dts = [0.01, 0.012, 0.009, 0.011]
+    t, dt_prev = 0.0, 0.0
+    nn = np.full(n, 100, dtype=np.int32)
+    for dt in dts:
+        du = np.full(n, alpha_u + beta_u * t)
+        oracle_mod.update(box, s, np.full(n, a[0]), np.full(n, a[1]), np.full(n, a[2]), du, nn, dt,
+                          dt_prev, 100)
+        t += dt
+        dt_prev = dt
+    for k, ax in zip(("x", "y", "z"), a):
+        vk = "v" + k
+        np.testing.assert_allclose(s[k], x0[k] + x0[vk] * t + 0.5 * ax * t * t, rtol=1e-14)
+        np.testing.assert_allclose(s[vk], x0[vk] + ax * t, rtol=1e-13)
+    # AB2 is exact for linear du after the forward-Euler first step
+    expect_u = 1.0 + alpha_u * t + 0.5 * beta_u * t * t - 0.5 * beta_u * dts[0] ** 2
+    np.testing.assert_allclose(s["u"], expect_u, rtol=1e-14)
+    np.testing.assert_allclose(s["h"], 0.05, rtol=1e-15)   # nn = target: h unchanged
+
+
+def test_h_update_and_periodic_wrap(oracle_mod):
+    n = 3
+    s = _blank_state(n)
+    s["x"][:] = [0.995, 0.5, 0.002]
+    s["vx"][:] = s["vxh"][:] = [1.0, 0.0, -1.0]
+    box = Box((0, 0, 0), (1, 1, 1), (1, 1, 1))
+    z3 = np.zeros(n)
+    nn = np.array([800, 100, 0], dtype=np.int32)
+    oracle_mod.update(box, s, z3, z3, z3, z3, nn, 0.01, 0.0, 100)
+    np.testing.assert_allclose(s["x"], [0.005, 0.5, 0.992], atol=1e-15)
+    np.testing.assert_allclose(s["h"], [0.05 * 0.75, 0.05, 0.05 * 0.5 * (1 + 100 ** (1 / 3))],
+                               rtol=1e-15)
+
+
+def test_diagnostics_vs_fsum(oracle_mod):
+    s = sph_inputs.jittered_box(10, seed_index=8, vel_sigma=0.5)
+    d = oracle_mod.diagnostics(s)
+    m = s["m"]
+    assert d[0] == pytest.approx(math.fsum(m * s["vx"]), abs=1e-17)
+    ek = math.fsum(0.5 * m * (s["vx"] ** 2 + s["vy"] ** 2 + s["vz"] ** 2))
+    assert d[3] == pytest.approx(ek, rel=1e-14)
+    assert d[4] == pytest.approx(math.fsum(m * s["u"]), rel=1e-14)
+    lz = math.fsum(m * (s["x"] * s["vy"] - s["y"] * s["vx"]))
+    assert d[7] == pytest.approx(lz, rel=1e-12, abs=1e-16)
+
+
+def _run_fixed_dt(oracle_mod, s, steps, dt, params):
+    box = box_of(s)
+    dt_prev = 0.0
+    for _ in range(steps):
+        rc, out = oracle_mod.outputs(box, s, params)
+        assert rc == 0
+        oracle_mod.update(box, s, out["ax"], out["ay"], out["az"], out["du"], out["nn"], dt,
+                          dt_prev, params.ng_target)
+        dt_prev = dt
+    return s
+
+
+def test_energy_error_second_order(oracle_mod):
+    """Section 4.1's second-order integrators: the total-energy error at a
+    fixed end time falls ~4x when dt halves; momentum stays at roundoff.  The
+    viscosity is off here: its switch at x_ab . v_ab = 0 has a kink that masks
+    the asymptotic order (its exact conservation is pinned above)."""
+    params = Params(ng_target=0, alpha=0.0)
+    T = 0.16
+    errs = []
+    for k in (16, 32, 64):
+        s = _conservation_case(seed=41, side=8, vel=0.4)
+        d0 = oracle_mod.diagnostics(s)
+        s = _run_fixed_dt(oracle_mod, s, k, T / k, params)
+        d1 = oracle_mod.diagnostics(s)
+        errs.append(abs((d1[3] + d1[4]) - (d0[3] + d0[4])))
+        assert np.abs(d1[:3] - d0[:3]).max() < 1e-13
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.6 < r1 < 4.8 and 3.6 < r2 < 4.6, (errs, r1, r2)
