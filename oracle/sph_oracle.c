@@ -405,8 +405,9 @@ static void sym_mul(const double* C6, const double* d, double* out) {
 /* plus sign would accelerate approaching particles toward each other).  The  */
 /* viscous energy term is Eq. 3's 1/2 sum_b v_ab . a^AV with a^AV the pair    */
 /* term of the corrected Eq. 4.                                               */
-/* Outputs per target: a (3), du, and the normalisation scales               */
-/* sa = sum_b |pair acceleration term| (Euclidean), sdu = sum_b |pair du term|. */
+/* Outputs per target: a (3), du, and the normalisation scales sa and sdu:   */
+/* the pair terms with every factor in magnitude (|X| |A|, |Pi| |Abar|,       */
+/* |v_ab| |A|), the scale of the rounding error of the sums.                  */
 /* ------------------------------------------------------------------------- */
 void oracle_momentum_energy(const oracle_box* box, const double* x, const double* y,
                             const double* z, const double* vx, const double* vy, const double* vz,
@@ -449,8 +450,14 @@ void oracle_momentum_energy(const oracle_box* box, const double* x, const double
       double eterm = Xa * m[b] * vA + 0.25 * m[b] * Pi * vAbar;
       for (int i = 0; i < 3; ++i) acc[i] += term[i];
       energy += eterm;
-      sacc += sqrt(term[0] * term[0] + term[1] * term[1] + term[2] * term[2]);
-      sen += fabs(eterm);
+      /* error-analysis scales: each product's factors taken in magnitude, so
+       * that cancellation inside a dot product does not shrink the scale */
+      double nAa = sqrt(Aa[0] * Aa[0] + Aa[1] * Aa[1] + Aa[2] * Aa[2]);
+      double nAb = sqrt(Ab[0] * Ab[0] + Ab[1] * Ab[1] + Ab[2] * Ab[2]);
+      double nv = sqrt(vab[0] * vab[0] + vab[1] * vab[1] + vab[2] * vab[2]);
+      double nAbar = nAa / rho[a] + nAb / rho[b];
+      sacc += m[b] * (fabs(Xa) * nAa + fabs(Xb) * nAb) + 0.5 * m[b] * fabs(Pi) * nAbar;
+      sen += m[b] * fabs(Xa) * nv * nAa + 0.25 * m[b] * fabs(Pi) * nv * nAbar;
     }
     ax[t] = acc[0];
     ay[t] = acc[1];
