@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Throughput of one SPH step (the per-step neighbour pipeline of arXiv
+2005.02656, section 4) on GB300: particle-updates/s and neighbour-pairs/s,
+FP32-mixed (headline) and FP64, on the 8.4M-particle Kelvin-Helmholtz box.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one sph_step: cell grid + Morton sort, neighbour search, density +
+EOS, IAD, momentum/energy, global dt, update.  The state and the neighbour
+lists (~7 GB) are far larger than L2, so no flush is needed between steps.
+Rank 0 prints one JSON line.  Under torchrun each rank advances its own
+independent box (replicas: the path has no data exchange between boxes).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-updates/s & neighbor-pairs/s per SPH step, FP32-mixed vs FP64, 1 GB300"
+UNIT = "particle-updates/s"
+KH_NX = 224            # 224x112x112 + 282x141x141 = 8,416,298 particles
+SAMPLE_NX = 112        # the same recipe at 1/8 scale for the CPU oracle (1,067,054 particles)
+
+# Flop model per directed neighbour pair (add/sub/mul = 1, FMA = 2,
+# rsqrt/div = 1), counted on the operations of each pair loop; the neighbour
+# search counts per (target, candidate) test.  See the design doc.
+FLOPS = {"find": 14, "density": 37, "iad": 57, "momentum": 140}
+# Derived non-tensor peaks: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz, and
+# the FP64 pipe at 1/64 of that rate.
+SM, LANES, MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SM * LANES * 2 * MHZ * 1e6 / 1e12
+FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--nx", type=int, default=KH_NX, help="outer lattice of the KH box")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def source_hash(name):
+    h = hashlib.sha256()
+    h.update(open(os.path.join(ROOT, "paper_2005_02656_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel_key):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, or
+    None when the kernel's source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        t = json.load(open(path))[kernel_key]
+    except Exception:
+        return None
+    if t.get("source_sha") != source_hash(t["source"]):
+        return None
+    return t["bytes_per_launch"]
+
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import sph_inputs
+    from paper_2005_02656_gb300 import HostStepper, Params, SphSim
+
+    dev = f"cuda:{local}"
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    state = sph_inputs.kelvin_helmholtz(args.nx, seed_index=2)
+    n = int(state["x"].shape[0])
+
+    def timed(precision):
+        sim = SphSim(state, precision=precision, device=dev)
+        stream = torch.cuda.current_stream()
+        for _ in range(args.warmup):
+            sim.step()
+        torch.cuda.synchronize()
+        sim.profile(True)
+        sim.stage_times()
+        st0 = sim.stats()
+        l0 = sim.launch_count()
+        clocks = Clocks(local)
+        barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            sim.step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ck = clocks.stop()
+        ms = e0.elapsed_time(e1) / args.steps
+        stages, nsteps = sim.stage_times()
+        st1 = sim.stats()
+        launches = sim.launch_count() - l0
+        flags = sim.error_word()
+        diag = sim.last_diagnostics()
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        pairs = (st1["pairs"] - st0["pairs"]) / args.steps
+        cands = (st1["candidates"] - st0["candidates"]) / args.steps
+        exact = (st1["exact_tests"] - st0["exact_tests"]) / args.steps
+        return {"ms": ms, "stages": {k: v / max(nsteps, 1) for k, v in stages.items()},
+                "pairs": pairs, "candidates": cands, "exact_tests": exact, "launches": launches,
+                "flags": flags, "clocks": ck, "dt": float(diag[8])}
+
+    r32 = timed("fp32_mixed")
+    r64 = None if args.no_fp64 else timed("fp64")
+
+    e2e = None
+    if not args.no_e2e:
+        hs = HostStepper(state, Params(box_lo=state["lo"], box_hi=state["hi"],
+                                       periodic=state["periodic"], precision="fp32_mixed"),
+                         device=dev)
+        for _ in range(args.warmup):
+            hs.step()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hs.step()                      # H2D state, step, D2H new state, sync
+        t1 = time.perf_counter()
+        barrier()
+        h2d, d2h = hs.bytes_per_step()
+        hs.close()
+        ms_e2e = max_over_ranks((t1 - t0) * 1e3 / args.steps)
+        e2e = {"value": n * world / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "path": "sph_step_host (pinned host state, FP32-mixed)"}
+
+    ms32 = max_over_ranks(r32["ms"])
+    res = {"n": n, "r32": r32, "r64": r64, "ms32": ms32, "e2e": e2e}
+    if r64 is not None:
+        res["ms64"] = max_over_ranks(r64["ms"])
+    if dist is not None:
+        dist.destroy_process_group()
+    return res
+
+
+def roofline(r, n, precision):
+    """Dominant kernel's achieved vs peak under the flop model above."""
+    st = r["stages"]
+    units = {"find": r["candidates"], "density": r["pairs"], "iad": r["pairs"],
+             "momentum": r["pairs"]}
+    kern = max(("find", "density", "iad", "momentum"), key=lambda k: st[k])
+    flops = FLOPS[kern] * units[kern]
+    ms = st[kern]
+    achieved = flops / (ms * 1e-3) / 1e12
+    if precision == "fp64" and kern != "find":
+        peak, pk = FP64_PEAK_TFLOPS, "fp64 pipe, derived: 1/64 of 152 SMs x 128 lanes x 2 x 2070 MHz"
+    else:
+        peak, pk = FP32_PEAK_TFLOPS, "fp32 pipe, derived: 152 SMs x 128 lanes x 2 x 2070 MHz"
+    src = {"find": "sph_neighbors.cu", "density": "sph_pairs_fp32.cu", "iad": "sph_pairs_fp32.cu",
+           "momentum": "sph_pairs_fp32.cu"}[kern]
+    if precision == "fp64" and kern != "find":
+        src = "sph_pairs_fp64.cu"
+    return {"kernel": f"{kern} ({precision})", "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": pk,
+            "flops_per_launch": flops, "ms_per_launch": ms,
+            "traffic": traffic_for(f"{kern}_{precision}") if src else None}
+
+
+def cpu_baseline(max_seconds=20.0, max_steps=5):
+    """The FP64 oracle, as it stands, on the host cores: full steps of the KH
+    recipe at 1/8 scale, as many as fit in about max_seconds."""
+    import numpy as np
+
+    import oracle
+    import sph_inputs
+    s = sph_inputs.kelvin_helmholtz(SAMPLE_NX, seed_index=2, shuffle=False)
+    box = oracle.Box(s["lo"], s["hi"], s["periodic"])
+    p = oracle.Params()
+    n = s["x"].shape[0]
+    dt_prev, steps, t0 = 0.0, 0, time.perf_counter()
+    pairs = 0
+    while True:
+        rc, dt_prev, out = oracle.step(box, s, p, dt_prev)
+        steps += 1
+        pairs += int(np.asarray(out["nn"]).sum())
+        el = time.perf_counter() - t0
+        if el >= max_seconds or steps >= max_steps:
+            break
+    return {"value": n * steps / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "neighbor_pairs_per_s": pairs / el, "seconds": el,
+            "sample": f"{steps} full oracle step(s) of the Kelvin-Helmholtz recipe at 1/8 scale "
+                      f"(outer lattice {SAMPLE_NX}, {n} particles), FP64, OpenMP"}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        return reference_arm(args, world)
+    res = run_gpu(args, world, rank, local)
+    if rank != 0:
+        return 0
+    n = res["n"]
+    r32, r64 = res["r32"], res["r64"]
+    ms = res["ms32"]
+    value = n * world / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"kelvin_helmholtz_{n}", "n_particles": n,
+                   "box": "[0,1]x[0,1]x[0,0.5] periodic", "precision": "fp32_mixed",
+                   "neighbors_target": 100, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "no flush: state + lists ~7 GB >> 129 MB L2"},
+        "neighbor_pairs_per_s": r32["pairs"] * world / (ms * 1e-3),
+        "stages_ms": r32["stages"],
+        "roofline": roofline(r32, n, "fp32_mixed"),
+        "gpu_launches": r32["launches"],
+        "clocks": r32["clocks"],
+        "error_flags": r32["flags"],
+        "search": {"candidates_per_step": r32["candidates"], "exact_tests_per_step": r32["exact_tests"],
+                   "pairs_per_step": r32["pairs"]},
+    }
+    if r64 is not None:
+        ms64 = res["ms64"]
+        line["fp64"] = {"value": n * world / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                        "neighbor_pairs_per_s": r64["pairs"] * world / (ms64 * 1e-3),
+                        "stages_ms": r64["stages"], "roofline": roofline(r64, n, "fp64"),
+                        "gpu_launches": r64["launches"], "error_flags": r64["flags"],
+                        "clocks": r64["clocks"]}
+        line["fp32_mixed_over_fp64"] = ms64 / ms
+    line["e2e"] = res["e2e"]
+    if not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def reference_arm(args, world):
+    """--impl reference: the FP64 oracle on the host cores, each step a full
+    oracle step of the KH recipe at 1/8 scale."""
+    import numpy as np
+
+    import oracle
+    import sph_inputs
+    s = sph_inputs.kelvin_helmholtz(SAMPLE_NX, seed_index=2, shuffle=False)
+    box = oracle.Box(s["lo"], s["hi"], s["periodic"])
+    p = oracle.Params()
+    n = s["x"].shape[0]
+    dt_prev = 0.0
+    for _ in range(args.warmup):
+        rc, dt_prev, _ = oracle.step(box, s, p, dt_prev)
+    t0 = time.perf_counter()
+    pairs = 0
+    for _ in range(args.steps):
+        rc, dt_prev, out = oracle.step(box, s, p, dt_prev)
+        pairs += int(np.asarray(out["nn"]).sum())
+    el = time.perf_counter() - t0
+    ms = el * 1e3 / args.steps
+    value = n / (ms * 1e-3)
+    sample = (f"full oracle steps of the Kelvin-Helmholtz recipe at 1/8 scale "
+              f"(outer lattice {SAMPLE_NX}, {n} particles), FP64, OpenMP")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"kelvin_helmholtz_{n}", "n_particles": n,
+                       "note": "CPU oracle on a 1/8-scale sample of the GPU arm's workload"},
+            "neighbor_pairs_per_s": pairs / el,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,241 @@
+/*
+ * sph.h -- C ABI of the GB300 SPH neighbour-pipeline library (libsph.so).
+ *
+ * The library advances a particle state by the per-step pipeline of
+ * Cavelan et al., "A Smoothed Particle Hydrodynamics Mini-App for Exascale"
+ * (arXiv 2005.02656): neighbour search, density (section 4.1, Eq. 1) with an
+ * ideal-gas equation of state, the IAD matrix (section 4.1, A_ab terms),
+ * momentum and energy with artificial viscosity (Eqs. 2-5), the global
+ * minimum time step (section 4.2) and the position/velocity/energy update
+ * (section 4.1, second-order Press and Adams-Bashforth integrators).  Every
+ * step runs in the library's own CUDA kernels for sm_103a.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: SPH_OK (0) or a negative SPH_ERR_* code.  A non-zero code
+ *    leaves a message readable with sph_last_error().
+ *  - All work is enqueued asynchronously on `stream` (a cudaStream_t passed as
+ *    void*; NULL means the legacy default stream) unless stated otherwise.
+ *    Faults found on the device (overflowing neighbour lists, a singular IAD
+ *    matrix, a non-finite value, an invalid box) do not fail the call: they
+ *    set bits of the context's error word, read with sph_error_word().
+ *  - Pointers inside sph_state are caller-owned DEVICE memory (except for
+ *    sph_step_host).  The library never frees caller memory.  Every array
+ *    has state.n elements (iad has 6*n) and is contiguous.
+ *  - A context is bound to the CUDA device that was current at sph_init();
+ *    calls must be made with that device current.  A context may be used
+ *    from one host thread at a time; calls on one context must be ordered
+ *    (same stream, or synchronised).
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SPH_API __attribute__((visibility("default")))
+#else
+#define SPH_API
+#endif
+
+typedef struct sph_ctx sph_ctx;
+typedef void* sph_stream_t; /* cudaStream_t */
+
+/* Return codes. */
+enum {
+  SPH_OK = 0,
+  SPH_ERR_INVALID_ARG = -1, /* bad pointer, size or parameter               */
+  SPH_ERR_CUDA = -2,        /* a CUDA runtime call failed                   */
+  SPH_ERR_NB_OVERFLOW = -3, /* (error-word bit) a list exceeded max_nb      */
+  SPH_ERR_SINGULAR_IAD = -4,/* (error-word bit) tau_a not invertible        */
+  SPH_ERR_NONFINITE = -5,   /* (error-word bit) NaN/inf in a result         */
+  SPH_ERR_TIMEOUT = -6,     /* a bounded device wait gave up                */
+  SPH_ERR_OOM = -7,         /* device allocation failed                     */
+  SPH_ERR_ORDER = -8        /* a stage was called before its inputs exist   */
+};
+
+/* Bits of the device error word (sph_error_word). */
+#define SPH_FLAG_NB_OVERFLOW 0x1u   /* some particle had more than max_nb neighbours; its
+                                       list was truncated (nn keeps the true count)       */
+#define SPH_FLAG_SINGULAR_IAD 0x2u  /* |det tau_a| <= 1e-12 max|tau_a|^3; C_a set to 0   */
+#define SPH_FLAG_NONFINITE 0x4u     /* a density, acceleration, du or dt was NaN/inf      */
+#define SPH_FLAG_BAD_BOX 0x8u       /* 2 h_max >= L/2 on a periodic axis (minimum image
+                                       undefined); the step's results are not valid       */
+#define SPH_FLAG_CELL_OVERFLOW 0x10u/* more than 65535 particles in one cell stencil      */
+#define SPH_FLAG_TIMEOUT 0x20u      /* a bounded device-side wait expired                 */
+
+/* Arithmetic of the pair sums. */
+enum {
+  SPH_FP64 = 0,       /* every step in FP64                                          */
+  SPH_FP32_MIXED = 1  /* pair separations, kernel values and the density, IAD and
+                         force sums in FP32; positions, integration, dt and the
+                         conservation sums in FP64                                    */
+};
+
+/* Kernel evaluation (section 4.5 of the paper mentions a 20,000-entry lookup
+ * table; SPH_KERNEL_EXACT evaluates sinc by a polynomial).                     */
+enum { SPH_KERNEL_EXACT = 0 };
+
+/* Particle state: structure of arrays of caller-owned device memory.
+ *  inputs (persistent state): x y z (positions), vx vy vz (velocity at integer
+ *    time, v^n), vxh vyh vzh (half-step velocity v^{n-1/2}; set equal to v
+ *    before the first step), h (smoothing length), m (mass), u (specific
+ *    internal energy), du_prev (du/dt of the previous step; 0 before the first
+ *    step), id (caller's particle ids, permuted with the state).
+ *  outputs of a step (valid for the state as it was before the update):
+ *    rho, p, c (density, pressure, sound speed), iad (6 per particle: the
+ *    symmetric IAD matrix C = tau^{-1} as xx xy xz yy yz zz, particle-major),
+ *    ax ay az (acceleration), du (du/dt).
+ * The library reorders every array of the state in place (particles are kept
+ * sorted by cell in Morton order), so callers identify particles by id. */
+typedef struct {
+  double *x, *y, *z, *vx, *vy, *vz, *h, *m, *u;
+  double *vxh, *vyh, *vzh, *du_prev;
+  double *rho, *p, *c, *iad, *ax, *ay, *az, *du;
+  int64_t* id;
+  int64_t n;
+} sph_state;
+
+/* Parameters.  Defaults in brackets (sph_default_params). */
+typedef struct {
+  double box_lo[3], box_hi[3]; /* box corners; used on periodic axes            */
+  int periodic[3];             /* 1 periodic, 0 open (open axes take their extent
+                                  from the particles every step)                */
+  double gamma;                /* adiabatic index of the ideal gas [5/3]        */
+  double alpha;                /* viscosity coefficient of Eq. 5 [1]            */
+  double courant;              /* Courant factor of the time step [0.2]         */
+  double dt_growth;            /* max dt_n / dt_{n-1} [1.1]                     */
+  int ng_target;               /* target neighbour count for h adaptation [100];
+                                  0 keeps h fixed                               */
+  int max_nb;                  /* neighbour-list capacity per particle [160]    */
+  double sinc_n;               /* exponent n of the sinc kernel, integer 1..12 [6] */
+  int precision;               /* SPH_FP64 or SPH_FP32_MIXED [SPH_FP64]         */
+  int kernel_mode;             /* SPH_KERNEL_EXACT                              */
+  int gradh;                   /* 0: Omega = 1 (the only supported value)       */
+} sph_params;
+
+/* Fills *p with the defaults above and a periodic unit box. */
+SPH_API void sph_default_params(sph_params* p);
+
+/* Creates a context for states of up to n_max particles on the current
+ * device, allocating the library-owned scratch (sort buffers, cell tables,
+ * neighbour lists of n_max * max_nb int32, per-particle work arrays and
+ * reduction buffers).  Computes B_n (the kernel normalisation of Eq. 6) on
+ * the host.  Returns SPH_ERR_INVALID_ARG for a bad parameter, SPH_ERR_OOM if
+ * an allocation fails.  Synchronous. */
+SPH_API int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out);
+
+/* Frees the context and its scratch (synchronises the device first). */
+SPH_API void sph_destroy(sph_ctx* ctx);
+
+/* Replaces the physical parameters (gamma, alpha, courant, dt_growth,
+ * ng_target, precision, box).  max_nb and sinc_n must not change. */
+SPH_API int sph_set_params(sph_ctx* ctx, const sph_params* params);
+
+/* The normalisation constant B_n in use (section 4.1, Eq. 6). */
+SPH_API double sph_kernel_norm(const sph_ctx* ctx);
+
+/* Neighbour search (section 4.1: b runs over the neighbours of a, the
+ * kernel's support being |x_a - x_b| <= 2 h_a; section 4.3: particles kept in
+ * space-filling-curve order).  Computes the cell grid (cell side >= 2 h_max;
+ * open axes from the particles' extent), sorts the state in place by cell
+ * Morton code (ties by previous position), and builds for every particle a
+ * the list of b != a with r_ab^2 < (2 h_a)^2, where r_ab is the minimum-image
+ * separation on periodic axes and r^2 = (dx*dx + dy*dy) + dz*dz is evaluated
+ * in FP64 without fused multiply-adds (bit-identical to that definition).
+ * Must precede sph_density/sph_iad/sph_momentum_energy on the same state. */
+SPH_API int sph_find_neighbors(sph_ctx* ctx, sph_state* state, sph_stream_t stream);
+
+/* Exports the lists of the last sph_find_neighbors/sph_step in id space:
+ * counts[p] = number of neighbours of the particle at (current) position p,
+ * ids[p*max_nb + k], k < min(counts[p], max_nb) = ids of its neighbours in
+ * ascending order.  Both are caller device arrays of n and n*max_nb entries. */
+SPH_API int sph_get_neighbors(sph_ctx* ctx, const sph_state* state, int32_t* counts, int64_t* ids,
+                      sph_stream_t stream);
+
+/* Density (Eq. 1, self term included) and the ideal-gas equation of state
+ * P = (gamma-1) rho u, c = sqrt(gamma P / rho).  Writes rho, p, c. */
+SPH_API int sph_density(sph_ctx* ctx, sph_state* state, sph_stream_t stream);
+
+/* IAD matrix: tau_a = sum_b (m_b/rho_b) (x_b-x_a)(x_b-x_a)^T W_ab(h_a),
+ * C_a = tau_a^{-1}.  Writes iad (6 per particle). */
+SPH_API int sph_iad(sph_ctx* ctx, sph_state* state, sph_stream_t stream);
+
+/* Momentum and energy equations with IAD and artificial viscosity (Eqs. 2-5,
+ * Omega = 1; the energy prefactor read as P_a/rho_a^2 and the viscous
+ * acceleration entering with a minus sign).  Writes ax, ay, az, du. */
+SPH_API int sph_momentum_energy(sph_ctx* ctx, sph_state* state, sph_stream_t stream);
+
+/* One full step: neighbour search, density + EOS, IAD, momentum/energy, the
+ * global time step dt_n = min(courant * min_a h_a/c_a, dt_growth * dt_{n-1})
+ * (no cap when dt_{n-1} = 0), and the update (half-step velocity kick by
+ * (dt_n + dt_{n-1})/2, drift, predicted velocity, Adams-Bashforth energy,
+ * periodic wrap, h <- h (1 + (ng_target/max(nn,1))^(1/3)) / 2).
+ * dt_inout: DEVICE pointer to one double holding dt_{n-1} on entry (0 before
+ * the first step) and dt_n on return.  Also accumulates the conservation
+ * sums of the new state (sph_last_diagnostics). */
+SPH_API int sph_step(sph_ctx* ctx, sph_state* state, double* dt_inout, sph_stream_t stream);
+
+/* sph_step for callers whose state lives in HOST memory (pinned or pageable):
+ * copies the state in, steps, copies the new state and the outputs back and
+ * synchronises the stream.  dt_inout is a HOST pointer.  Uses device mirrors
+ * owned by the context (allocated on first use). */
+SPH_API int sph_step_host(sph_ctx* ctx, sph_state* host_state, double* dt_inout, sph_stream_t stream);
+
+/* Conservation sums of a state {Px, Py, Pz, E_kin, E_int, Lx, Ly, Lz}
+ * (section 4.2: total momentum and energy), FP64 with compensated block
+ * sums.  out: HOST array of 8.  Synchronises the stream. */
+SPH_API int sph_diagnostics(sph_ctx* ctx, const sph_state* state, double* out, sph_stream_t stream);
+
+/* Conservation sums accumulated by the last sph_step (of its new state) and
+ * its dt, without a separate pass: out[0..7] as sph_diagnostics, out[8] = dt,
+ * out[9] = min nn, out[10] = max nn, out[11] = sum nn.  HOST array of 12;
+ * synchronises the stream. */
+SPH_API int sph_last_diagnostics(sph_ctx* ctx, double* out, sph_stream_t stream);
+
+/* Reads and clears the device error word (SPH_FLAG_* bits).  Synchronous. */
+SPH_API int sph_error_word(sph_ctx* ctx, uint32_t* flags);
+
+/* Message of the last failing call on this context ("" if none). */
+SPH_API const char* sph_last_error(const sph_ctx* ctx);
+
+/* Stages of sph_step timed by sph_profile. */
+enum {
+  SPH_STAGE_SORT = 0,     /* grid, Morton counting sort, gather          */
+  SPH_STAGE_FIND = 1,     /* neighbour lists                             */
+  SPH_STAGE_DENSITY = 2,  /* density + EOS                               */
+  SPH_STAGE_IAD = 3,      /* IAD matrix                                  */
+  SPH_STAGE_MOMENTUM = 4, /* momentum and energy                         */
+  SPH_STAGE_DT = 5,       /* global time step                            */
+  SPH_STAGE_UPDATE = 6,   /* integrator, h, conservation sums            */
+  SPH_NSTAGE = 7
+};
+
+/* Enables (1) or disables (0) per-stage timing of sph_step with CUDA events
+ * recorded on the step's stream (the events add no synchronisation). */
+SPH_API int sph_profile(sph_ctx* ctx, int enable);
+
+/* Accumulated milliseconds per stage (ms[SPH_NSTAGE], HOST) over the steps
+ * timed since the last call, and their number in *steps; then resets.
+ * Synchronises on the last recorded event. */
+SPH_API int sph_stage_times(sph_ctx* ctx, double* ms, int64_t* steps);
+
+/* Cumulative device counters since sph_init (synchronous read):
+ * out[0] (target, candidate) pairs tested by the neighbour search,
+ * out[1] of which decided by the exact FP64 criterion (inside the FP32
+ *        prefilter's error margin),
+ * out[2] neighbour pairs found by sph_step (sum over steps of sum_a nn_a),
+ * out[3] particle updates done by sph_step (sum over steps of n). */
+SPH_API int sph_stats(sph_ctx* ctx, uint64_t* out);
+
+/* Number of kernels the library launched on this context so far. */
+SPH_API int64_t sph_launch_count(const sph_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_H */

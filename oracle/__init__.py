@@ -73,6 +73,8 @@ def _load():
         lib.oracle_diagnostics.restype = None
         lib.oracle_diagnostics.argtypes = [i64] + [P] * 9
         lib.oracle_any_nonfinite.restype = cint
+        lib.oracle_num_threads.argtypes = []
+        lib.oracle_num_threads.restype = cint
         lib.oracle_any_nonfinite.argtypes = [i64, P]
         _lib = lib
     return _lib
@@ -111,6 +113,11 @@ class Params:
     sinc_n: float = 6.0
     ng_target: int = 100
     max_nb: int = 160
+
+
+def num_threads() -> int:
+    """Threads the oracle's per-particle loops run on."""
+    return int(_load().oracle_num_threads())
 
 
 def kernel_norm(sinc_n: float = 6.0) -> float:

@@ -33,6 +33,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORACLE_OK 0
 #define ORACLE_INVALID_ARG (-1)
@@ -569,6 +572,15 @@ void oracle_diagnostics(int64_t n, const double* x, const double* y, const doubl
     }
   }
   for (int k = 0; k < 8; ++k) out[k] = s[k];
+}
+
+/* Threads the per-particle loops use (the OpenMP default of this process). */
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 /* Non-finite scan helper: returns 1 if any of the n values is NaN or inf. */

@@ -1,0 +1,577 @@
+// C ABI of libsph (declared in include/sph.h): context management, argument
+// checks, scratch allocation and the order of kernel launches of each stage.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "sph_device.cuh"
+#include "sph_internal.cuh"
+
+using sph::OutView;
+using sph::StateView;
+
+namespace sph {
+
+int set_error(sph_ctx* ctx, int code, const char* fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->last_error, sizeof(ctx->last_error), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+int cuda_fail(sph_ctx* ctx, cudaError_t e, const char* what) {
+  return set_error(ctx, e == cudaErrorMemoryAllocation ? SPH_ERR_OOM : SPH_ERR_CUDA, "%s: %s",
+                   what, cudaGetErrorString(e));
+}
+
+}  // namespace sph
+
+namespace {
+
+// B_n of Eq. 6 from 4 pi B_n int_0^2 S(v)^n v^2 dv = 1: composite Simpson rule
+// with 2^16 panels and a compensated sum (host, once per context).
+double kernel_norm_host(double n) {
+  const int N = 1 << 16;
+  const double hstep = 2.0 / N;
+  auto f = [n](double v) {
+    if (v == 0.0) return 0.0;
+    const double x = 1.5707963267948966192 * v;
+    return pow(sin(x) / x, n) * v * v;
+  };
+  double s = 0.0, comp = 0.0;
+  for (int i = 0; i <= N; ++i) {
+    const double w = (i == 0 || i == N) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+    const double y = w * f(i * hstep) - comp;
+    const double t = s + y;
+    comp = (t - s) - y;
+    s = t;
+  }
+  const double integral = s * hstep / 3.0;
+  return 1.0 / (4.0 * 3.14159265358979323846 * integral);
+}
+
+int check_params(sph_ctx* ctx, const sph_params* p) {
+  if (!p) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "params is NULL");
+  for (int k = 0; k < 3; ++k) {
+    if (p->periodic[k] && !(p->box_hi[k] > p->box_lo[k]))
+      return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "periodic axis %d needs box_hi > box_lo", k);
+  }
+  if (!(p->gamma > 1.0)) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "gamma must be > 1");
+  if (!(p->alpha >= 0.0)) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "alpha must be >= 0");
+  if (!(p->courant > 0.0)) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "courant must be > 0");
+  if (!(p->dt_growth >= 1.0))
+    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "dt_growth must be >= 1");
+  if (p->ng_target < 0) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "ng_target < 0");
+  if (p->max_nb < 1 || p->max_nb > 4096)
+    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "max_nb must be in [1, 4096]");
+  if (!(p->sinc_n >= 1.0 && p->sinc_n <= 12.0) || p->sinc_n != floor(p->sinc_n))
+    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "sinc_n must be an integer in [1, 12]");
+  if (p->precision != SPH_FP64 && p->precision != SPH_FP32_MIXED)
+    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "unknown precision %d", p->precision);
+  if (p->kernel_mode != SPH_KERNEL_EXACT)
+    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "unknown kernel_mode %d", p->kernel_mode);
+  if (p->gradh != 0) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "gradh must be 0");
+  return SPH_OK;
+}
+
+int check_state(sph_ctx* ctx, const sph_state* s, bool need_outputs) {
+  if (!ctx) return SPH_ERR_INVALID_ARG;
+  if (!s) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "state is NULL");
+  if (s->n < 0 || s->n > ctx->n_max)
+    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "n = %lld outside [0, n_max = %lld]",
+                          (long long)s->n, (long long)ctx->n_max);
+  if (s->n == 0) return SPH_OK;  // empty arrays may be NULL
+  const void* req[] = {s->x, s->y, s->z, s->vx, s->vy, s->vz, s->h, s->m, s->u,
+                       s->vxh, s->vyh, s->vzh, s->du_prev, s->id};
+  for (const void* q : req)
+    if (!q) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "a state array is NULL");
+  if (need_outputs) {
+    const void* outs[] = {s->rho, s->p, s->c, s->iad, s->ax, s->ay, s->az, s->du};
+    for (const void* q : outs)
+      if (!q) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "an output array is NULL");
+  }
+  return SPH_OK;
+}
+
+StateView view_of(const sph_state* s) {
+  StateView v;
+  v.x = s->x;
+  v.y = s->y;
+  v.z = s->z;
+  v.vx = s->vx;
+  v.vy = s->vy;
+  v.vz = s->vz;
+  v.vxh = s->vxh;
+  v.vyh = s->vyh;
+  v.vzh = s->vzh;
+  v.h = s->h;
+  v.m = s->m;
+  v.u = s->u;
+  v.du_prev = s->du_prev;
+  v.id = s->id;
+  return v;
+}
+
+OutView outs_of(const sph_state* s) {
+  OutView o;
+  o.rho = s->rho;
+  o.p = s->p;
+  o.c = s->c;
+  o.iad = s->iad;
+  o.ax = s->ax;
+  o.ay = s->ay;
+  o.az = s->az;
+  o.du = s->du;
+  return o;
+}
+
+int finish(sph_ctx* ctx, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return sph::cuda_fail(ctx, e, what);
+  return SPH_OK;
+}
+
+template <typename T>
+int dalloc(sph_ctx* ctx, T** p, size_t count, size_t* total) {
+  size_t b = count * sizeof(T);
+  if (b == 0) b = sizeof(T);
+  cudaError_t e = cudaMalloc((void**)p, b);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return sph::cuda_fail(ctx, e, "cudaMalloc");
+  }
+  *total += b;
+  return SPH_OK;
+}
+
+void free_all(sph_ctx* ctx) {
+  void* ptrs[] = {ctx->grid, ctx->err, ctx->dt_dev, ctx->diag, ctx->code, ctx->slot,
+                  ctx->perm_tmp, ctx->perm, ctx->tbl_count, ctx->tbl_start, ctx->occ,
+                  ctx->scan_part, ctx->cell_of, ctx->s.x, ctx->s_id_buf, ctx->pos32,
+                  ctx->cell3, ctx->nn, ctx->nbr, ctx->vol, ctx->vel32, ctx->q32, ctx->xc32,
+                  ctx->cA32, ctx->cB32, ctx->red.part, ctx->red.counter, ctx->stats, ctx->hm_buf, ctx->hm_id};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+int run_find(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st) {
+  sph::launch_grid(ctx, in, n, st);
+  sph::launch_sort_gather(ctx, in, n, st);
+  sph::launch_find_neighbors(ctx, ctx->s, n, st);
+  return finish(ctx, "neighbour search launch");
+}
+
+void run_density(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n, cudaStream_t st) {
+  if (ctx->prm.precision == SPH_FP32_MIXED)
+    sph::launch_density_f32(ctx, s, o, n, st);
+  else
+    sph::launch_density_f64(ctx, s, o, n, st);
+}
+
+void run_iad(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n, cudaStream_t st) {
+  if (ctx->prm.precision == SPH_FP32_MIXED)
+    sph::launch_iad_f32(ctx, s, o, n, st);
+  else
+    sph::launch_iad_f64(ctx, s, o, n, st);
+}
+
+void run_momentum(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
+                  cudaStream_t st) {
+  if (ctx->prm.precision == SPH_FP32_MIXED)
+    sph::launch_momentum_f32(ctx, s, o, n, st);
+  else
+    sph::launch_momentum_f64(ctx, s, o, n, st);
+}
+
+inline void prof_mark(sph_ctx* ctx, int k, cudaStream_t st) {
+  if (ctx->prof) cudaEventRecord(ctx->prof_ev[ctx->prof_slot * (SPH_NSTAGE + 1) + k], st);
+}
+
+// Folds the recorded event sets into prof_ms (synchronises on them).
+int prof_fold(sph_ctx* ctx) {
+  for (int slot = 0; slot < ctx->prof_slot; ++slot) {
+    cudaEvent_t* e = ctx->prof_ev + slot * (SPH_NSTAGE + 1);
+    cudaError_t err = cudaEventSynchronize(e[SPH_NSTAGE]);
+    if (err != cudaSuccess) return sph::cuda_fail(ctx, err, "profile events");
+    for (int k = 0; k < SPH_NSTAGE; ++k) {
+      float ms = 0.0f;
+      err = cudaEventElapsedTime(&ms, e[k], e[k + 1]);
+      if (err != cudaSuccess) return sph::cuda_fail(ctx, err, "profile events");
+      ctx->prof_ms[k] += ms;
+    }
+    ctx->prof_steps += 1;
+  }
+  ctx->prof_slot = 0;
+  return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sph_default_params(sph_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  for (int k = 0; k < 3; ++k) {
+    p->box_lo[k] = 0.0;
+    p->box_hi[k] = 1.0;
+    p->periodic[k] = 1;
+  }
+  p->gamma = 5.0 / 3.0;
+  p->alpha = 1.0;
+  p->courant = 0.2;
+  p->dt_growth = 1.1;
+  p->ng_target = 100;
+  p->max_nb = 160;
+  p->sinc_n = 6.0;
+  p->precision = SPH_FP64;
+  p->kernel_mode = SPH_KERNEL_EXACT;
+  p->gradh = 0;
+}
+
+int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {
+  if (!out) return SPH_ERR_INVALID_ARG;
+  *out = nullptr;
+  sph_ctx* ctx = (sph_ctx*)calloc(1, sizeof(sph_ctx));
+  if (!ctx) return SPH_ERR_OOM;
+  int rc = check_params(ctx, params);
+  if (rc != SPH_OK || n_max < 1 || n_max > (int64_t)1 << 31) {
+    free(ctx);
+    return rc != SPH_OK ? rc : SPH_ERR_INVALID_ARG;
+  }
+  ctx->prm = *params;
+  ctx->n_max = n_max;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e != cudaSuccess) {
+    free(ctx);
+    return SPH_ERR_CUDA;
+  }
+  ctx->Bn = kernel_norm_host(params->sinc_n);
+  size_t total = 0;
+  const int64_t n = n_max;
+  const int mb = params->max_nb;
+  rc = SPH_OK;
+#define ALLOC(ptr, cnt) \
+  if (rc == SPH_OK) rc = dalloc(ctx, &(ptr), (size_t)(cnt), &total)
+  ALLOC(ctx->grid, 1);
+  ALLOC(ctx->err, 1);
+  ALLOC(ctx->dt_dev, 1);
+  ALLOC(ctx->diag, 32);
+  ALLOC(ctx->code, n);
+  ALLOC(ctx->slot, n);
+  ALLOC(ctx->perm_tmp, n);
+  ALLOC(ctx->perm, n);
+  ALLOC(ctx->tbl_count, sph::kMaxTable);
+  ALLOC(ctx->tbl_start, sph::kMaxTable);
+  ALLOC(ctx->occ, n);
+  ALLOC(ctx->scan_part, 2 * (sph::kMaxTable / sph::kScanItems));
+  ALLOC(ctx->cell_of, n);
+  double* sbuf = nullptr;
+  ALLOC(sbuf, 13 * n);
+  ALLOC(ctx->s_id_buf, n);
+  ALLOC(ctx->pos32, n);
+  ALLOC(ctx->cell3, n);
+  ALLOC(ctx->nn, n);
+  ALLOC(ctx->nbr, (size_t)mb * n);
+  ALLOC(ctx->vol, 5 * n);
+  ALLOC(ctx->vel32, n);
+  ALLOC(ctx->q32, n);
+  ALLOC(ctx->xc32, n);
+  ALLOC(ctx->cA32, n);
+  ALLOC(ctx->cB32, n);
+  ALLOC(ctx->red.part, sph::kReduceBlocks * 16);
+  ALLOC(ctx->red.counter, 8);
+  ALLOC(ctx->stats, 4);
+#undef ALLOC
+  if (sbuf) {
+    double** f[13] = {&ctx->s.x, &ctx->s.y, &ctx->s.z, &ctx->s.vx, &ctx->s.vy, &ctx->s.vz,
+                      &ctx->s.vxh, &ctx->s.vyh, &ctx->s.vzh, &ctx->s.h, &ctx->s.m, &ctx->s.u,
+                      &ctx->s.du_prev};
+    for (int k = 0; k < 13; ++k) *f[k] = sbuf + (size_t)k * n;
+    ctx->s.id = ctx->s_id_buf;
+  }
+  if (ctx->vol) {
+    ctx->X = ctx->vol + n;
+    ctx->inv_rho = ctx->vol + 2 * n;
+  }
+  if (rc == SPH_OK) {
+    e = cudaMemset(ctx->err, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(ctx->red.counter, 0, 8 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->diag, 0, 32 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(ctx->stats, 0, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->tbl_count, 0, sph::kMaxTable * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = sph::cuda_fail(ctx, e, "init");
+  }
+  if (rc != SPH_OK) {
+    free_all(ctx);
+    free(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return SPH_OK;
+}
+
+void sph_destroy(sph_ctx* ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  if (ctx->prof_ev) {
+    for (int k = 0; k < sph::kProfRing * (SPH_NSTAGE + 1); ++k)
+      if (ctx->prof_ev[k]) cudaEventDestroy(ctx->prof_ev[k]);
+    free(ctx->prof_ev);
+  }
+  free_all(ctx);
+  free(ctx);
+}
+
+int sph_set_params(sph_ctx* ctx, const sph_params* params) {
+  if (!ctx) return SPH_ERR_INVALID_ARG;
+  int rc = check_params(ctx, params);
+  if (rc != SPH_OK) return rc;
+  if (params->max_nb != ctx->prm.max_nb || params->sinc_n != ctx->prm.sinc_n)
+    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "max_nb and sinc_n are fixed at sph_init");
+  ctx->prm = *params;
+  ctx->have_density = ctx->have_iad = 0;
+  return SPH_OK;
+}
+
+double sph_kernel_norm(const sph_ctx* ctx) { return ctx ? ctx->Bn : 0.0; }
+
+int sph_find_neighbors(sph_ctx* ctx, sph_state* state, sph_stream_t stream) {
+  int rc = check_state(ctx, state, false);
+  if (rc != SPH_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const StateView in = view_of(state);
+  if (state->n == 0) {
+    ctx->have_lists = 1;
+    ctx->have_density = ctx->have_iad = 0;
+    return SPH_OK;
+  }
+  sph::launch_grid(ctx, in, state->n, st);
+  sph::launch_sort_gather(ctx, in, state->n, st);
+  sph::launch_copy_state(in, ctx->s, state->n, st, ctx);
+  sph::launch_find_neighbors(ctx, in, state->n, st);
+  rc = finish(ctx, "sph_find_neighbors");
+  ctx->have_lists = rc == SPH_OK;
+  ctx->have_density = ctx->have_iad = 0;
+  return rc;
+}
+
+int sph_get_neighbors(sph_ctx* ctx, const sph_state* state, int32_t* counts, int64_t* ids,
+                      sph_stream_t stream) {
+  int rc = check_state(ctx, state, false);
+  if (rc != SPH_OK) return rc;
+  if (!counts || !ids) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "NULL output");
+  if (!ctx->have_lists)
+    return sph::set_error(ctx, SPH_ERR_ORDER, "no neighbour lists: call sph_find_neighbors");
+  sph::launch_export_neighbors(ctx, view_of(state), state->n, counts, ids,
+                               (cudaStream_t)stream);
+  return finish(ctx, "sph_get_neighbors");
+}
+
+int sph_density(sph_ctx* ctx, sph_state* state, sph_stream_t stream) {
+  int rc = check_state(ctx, state, true);
+  if (rc != SPH_OK) return rc;
+  if (!ctx->have_lists)
+    return sph::set_error(ctx, SPH_ERR_ORDER, "no neighbour lists: call sph_find_neighbors");
+  run_density(ctx, view_of(state), outs_of(state), state->n, (cudaStream_t)stream);
+  rc = finish(ctx, "sph_density");
+  ctx->have_density = rc == SPH_OK;
+  ctx->have_iad = 0;
+  return rc;
+}
+
+int sph_iad(sph_ctx* ctx, sph_state* state, sph_stream_t stream) {
+  int rc = check_state(ctx, state, true);
+  if (rc != SPH_OK) return rc;
+  if (!ctx->have_density) return sph::set_error(ctx, SPH_ERR_ORDER, "call sph_density first");
+  run_iad(ctx, view_of(state), outs_of(state), state->n, (cudaStream_t)stream);
+  rc = finish(ctx, "sph_iad");
+  ctx->have_iad = rc == SPH_OK;
+  return rc;
+}
+
+int sph_momentum_energy(sph_ctx* ctx, sph_state* state, sph_stream_t stream) {
+  int rc = check_state(ctx, state, true);
+  if (rc != SPH_OK) return rc;
+  if (!ctx->have_iad) return sph::set_error(ctx, SPH_ERR_ORDER, "call sph_iad first");
+  run_momentum(ctx, view_of(state), outs_of(state), state->n, (cudaStream_t)stream);
+  return finish(ctx, "sph_momentum_energy");
+}
+
+int sph_step(sph_ctx* ctx, sph_state* state, double* dt_inout, sph_stream_t stream) {
+  int rc = check_state(ctx, state, true);
+  if (rc != SPH_OK) return rc;
+  if (!dt_inout) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "dt_inout is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = state->n;
+  if (n == 0) return SPH_OK;  // nothing to advance; dt is left unchanged
+  const StateView in = view_of(state);
+  const OutView o = outs_of(state);
+  if (ctx->prof && ctx->prof_slot == sph::kProfRing) {
+    rc = prof_fold(ctx);
+    if (rc != SPH_OK) return rc;
+  }
+  prof_mark(ctx, 0, st);
+  sph::launch_grid(ctx, in, n, st);
+  sph::launch_sort_gather(ctx, in, n, st);
+  prof_mark(ctx, 1, st);
+  sph::launch_find_neighbors(ctx, ctx->s, n, st);
+  prof_mark(ctx, 2, st);
+  run_density(ctx, ctx->s, o, n, st);
+  prof_mark(ctx, 3, st);
+  run_iad(ctx, ctx->s, o, n, st);
+  prof_mark(ctx, 4, st);
+  run_momentum(ctx, ctx->s, o, n, st);
+  prof_mark(ctx, 5, st);
+  sph::launch_timestep(ctx, ctx->s, o, n, dt_inout, st);
+  prof_mark(ctx, 6, st);
+  sph::launch_update(ctx, ctx->s, o, in, n, dt_inout, st);
+  prof_mark(ctx, 7, st);
+  if (ctx->prof) ctx->prof_slot += 1;
+  rc = finish(ctx, "sph_step");
+  // the lists index the pre-update positions, which are now overwritten
+  ctx->have_lists = 0;
+  ctx->have_density = ctx->have_iad = 0;
+  return rc;
+}
+
+int sph_step_host(sph_ctx* ctx, sph_state* hs, double* dt_inout, sph_stream_t stream) {
+  int rc = check_state(ctx, hs, false);
+  if (rc != SPH_OK) return rc;
+  if (!dt_inout) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "dt_inout is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = hs->n;
+  const int64_t nm = ctx->n_max;
+  cudaError_t e = cudaSuccess;
+  if (!ctx->hm_buf) {
+    e = cudaMalloc((void**)&ctx->hm_buf, sizeof(double) * (size_t)nm * 26);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->hm_id, sizeof(int64_t) * (size_t)nm);
+    if (e != cudaSuccess) return sph::cuda_fail(ctx, e, "sph_step_host mirrors");
+  }
+  sph_state ds;
+  double* base = ctx->hm_buf;
+  double** dfields[21] = {&ds.x, &ds.y, &ds.z, &ds.vx, &ds.vy, &ds.vz, &ds.h, &ds.m, &ds.u,
+                          &ds.vxh, &ds.vyh, &ds.vzh, &ds.du_prev, &ds.rho, &ds.p, &ds.c,
+                          &ds.ax, &ds.ay, &ds.az, &ds.du, &ds.iad};
+  for (int k = 0; k < 20; ++k) *dfields[k] = base + (size_t)k * nm;
+  ds.iad = base + (size_t)20 * nm;  // 6 * nm
+  ds.id = ctx->hm_id;
+  ds.n = n;
+  double* hin[13] = {hs->x, hs->y, hs->z, hs->vx, hs->vy, hs->vz, hs->h, hs->m, hs->u,
+                     hs->vxh, hs->vyh, hs->vzh, hs->du_prev};
+  double* din[13] = {ds.x, ds.y, ds.z, ds.vx, ds.vy, ds.vz, ds.h, ds.m, ds.u,
+                     ds.vxh, ds.vyh, ds.vzh, ds.du_prev};
+  const size_t b = sizeof(double) * (size_t)n;
+  for (int k = 0; k < 13 && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync(din[k], hin[k], b, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ds.id, hs->id, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->dt_dev, dt_inout, sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return sph::cuda_fail(ctx, e, "sph_step_host copy in");
+  rc = sph_step(ctx, &ds, ctx->dt_dev, stream);
+  if (rc != SPH_OK) return rc;
+  for (int k = 0; k < 13 && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync(hin[k], din[k], b, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hs->id, ds.id, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, st);
+  double* hout[7] = {hs->rho, hs->p, hs->c, hs->ax, hs->ay, hs->az, hs->du};
+  double* dout[7] = {ds.rho, ds.p, ds.c, ds.ax, ds.ay, ds.az, ds.du};
+  for (int k = 0; k < 7 && e == cudaSuccess; ++k)
+    if (hout[k]) e = cudaMemcpyAsync(hout[k], dout[k], b, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && hs->iad)
+    e = cudaMemcpyAsync(hs->iad, ds.iad, 6 * b, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dt_inout, ctx->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return sph::cuda_fail(ctx, e, "sph_step_host copy out");
+  return SPH_OK;
+}
+
+int sph_diagnostics(sph_ctx* ctx, const sph_state* state, double* out, sph_stream_t stream) {
+  int rc = check_state(ctx, state, false);
+  if (rc != SPH_OK) return rc;
+  if (!out) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "out is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  sph::launch_diagnostics(ctx, view_of(state), state->n, st);
+  cudaError_t e = cudaMemcpyAsync(out, ctx->diag + 16, 8 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return sph::cuda_fail(ctx, e, "sph_diagnostics");
+  return SPH_OK;
+}
+
+int sph_last_diagnostics(sph_ctx* ctx, double* out, sph_stream_t stream) {
+  if (!ctx || !out) return SPH_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(out, ctx->diag, 12 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return sph::cuda_fail(ctx, e, "sph_last_diagnostics");
+  return SPH_OK;
+}
+
+int sph_error_word(sph_ctx* ctx, uint32_t* flags) {
+  if (!ctx || !flags) return SPH_ERR_INVALID_ARG;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(flags, ctx->err, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(ctx->err, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return sph::cuda_fail(ctx, e, "sph_error_word");
+  return SPH_OK;
+}
+
+const char* sph_last_error(const sph_ctx* ctx) { return ctx ? ctx->last_error : "no context"; }
+
+int64_t sph_launch_count(const sph_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int sph_stats(sph_ctx* ctx, uint64_t* out) {
+  if (!ctx || !out) return SPH_ERR_INVALID_ARG;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(out, ctx->stats, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return sph::cuda_fail(ctx, e, "sph_stats");
+  return SPH_OK;
+}
+
+int sph_profile(sph_ctx* ctx, int enable) {
+  if (!ctx) return SPH_ERR_INVALID_ARG;
+  if (enable && !ctx->prof_ev) {
+    const int total = sph::kProfRing * (SPH_NSTAGE + 1);
+    ctx->prof_ev = (cudaEvent_t*)calloc(total, sizeof(cudaEvent_t));
+    if (!ctx->prof_ev) return sph::set_error(ctx, SPH_ERR_OOM, "profile events");
+    for (int k = 0; k < total; ++k) {
+      cudaError_t e = cudaEventCreate(&ctx->prof_ev[k]);
+      if (e != cudaSuccess) return sph::cuda_fail(ctx, e, "cudaEventCreate");
+    }
+  }
+  if (!enable && ctx->prof) {
+    int rc = prof_fold(ctx);
+    if (rc != SPH_OK) return rc;
+  }
+  ctx->prof = enable ? 1 : 0;
+  return SPH_OK;
+}
+
+int sph_stage_times(sph_ctx* ctx, double* ms, int64_t* steps) {
+  if (!ctx || !ms || !steps) return SPH_ERR_INVALID_ARG;
+  int rc = prof_fold(ctx);
+  if (rc != SPH_OK) return rc;
+  for (int k = 0; k < SPH_NSTAGE; ++k) {
+    ms[k] = ctx->prof_ms[k];
+    ctx->prof_ms[k] = 0.0;
+  }
+  *steps = ctx->prof_steps;
+  ctx->prof_steps = 0;
+  return SPH_OK;
+}
+
+}  // extern "C"

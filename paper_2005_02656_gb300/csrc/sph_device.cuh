@@ -1,0 +1,166 @@
+// Device helpers shared by the kernels: the sinc kernel of Eq. 6 evaluated by
+// a truncated Taylor series, the FP64 neighbour criterion, error flags and
+// warp/block reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+// ---------------------------------------------------------------------------
+// Sinc kernel (section 4.1, Eq. 6): W(v, h) = B_n / h^3 * S(v)^n with
+// S(v) = sin(pi v / 2) / (pi v / 2).  S is even in v, so it is evaluated as a
+// polynomial in t = v^2 (no square root): the Maclaurin series of sin(x)/x,
+//   S = sum_k (-1)^k x^(2k) / (2k+1)!,  x^2 = (pi/2)^2 t,
+// truncated where the next term is below the working precision on t in [0, 4]
+// (v in [0, 2]): 15 terms in FP64 (next term < 1.1e-19), 9 in FP32 (< 1.7e-10).
+// Coefficients are computed at compile time from their definition.
+// ---------------------------------------------------------------------------
+constexpr double kHalfPi2 = 2.4674011002723396547;  // (pi/2)^2
+
+constexpr double sinc_coef(int k) {
+  double c = 1.0;
+  for (int i = 1; i <= k; ++i) c *= -kHalfPi2 / ((2.0 * i) * (2.0 * i + 1.0));
+  return c;
+}
+
+template <int K>
+struct SincCoefs {
+  double c[K];
+  constexpr SincCoefs() : c() {
+    for (int k = 0; k < K; ++k) c[k] = sinc_coef(k);
+  }
+};
+
+constexpr int kSincTerms64 = 15;
+constexpr int kSincTerms32 = 9;
+
+__device__ __forceinline__ double sinc_poly64(double t) {
+  constexpr SincCoefs<kSincTerms64> C{};
+  double s = C.c[kSincTerms64 - 1];
+#pragma unroll
+  for (int k = kSincTerms64 - 2; k >= 0; --k) s = fma(s, t, C.c[k]);
+  return s;
+}
+
+__device__ __forceinline__ float sinc_poly32(float t) {
+  constexpr SincCoefs<kSincTerms32> C{};
+  float s = (float)C.c[kSincTerms32 - 1];
+#pragma unroll
+  for (int k = kSincTerms32 - 2; k >= 0; --k) s = fmaf(s, t, (float)C.c[k]);
+  return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T ipow(T s, int n) {
+  if (n == 6) {
+    T s2 = s * s;
+    return s2 * s2 * s2;
+  }
+  T r = s;
+  for (int i = 1; i < n; ++i) r *= s;
+  return r;
+}
+
+// W for t = v^2 < 4 (caller guarantees the neighbour criterion), norm = B_n/h^3.
+__device__ __forceinline__ double kernel_w64(double t, double norm, int n) {
+  return norm * ipow(sinc_poly64(t), n);
+}
+__device__ __forceinline__ float kernel_w32(float t, float norm, int n) {
+  // t can exceed 4 by rounding for pairs on the support edge; clamp so that the
+  // truncated series does not grow there (S(2) = 0).
+  t = fminf(t, 4.0f);
+  return norm * ipow(sinc_poly32(t), n);
+}
+
+// ---------------------------------------------------------------------------
+// Minimum-image component b - a on one axis (the reading of section 4.1's
+// pair separation on periodic axes) and the FP64 neighbour criterion
+// r^2 < (2 h_a)^2 with r^2 = (dx*dx + dy*dy) + dz*dz, evaluated with
+// explicitly rounded operations so no multiply-add is fused.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double min_image(double d, double L, double halfL, int periodic) {
+  if (periodic) {
+    if (d > halfL)
+      d = __dsub_rn(d, L);
+    else if (d < -halfL)
+      d = __dadd_rn(d, L);
+  }
+  return d;
+}
+
+__device__ __forceinline__ bool exact_neighbor(const Grid& g, double xa, double ya, double za,
+                                               double ha, double xb, double yb, double zb) {
+  double dx = min_image(__dsub_rn(xb, xa), g.Lbox[0], g.halfL[0], g.periodic[0]);
+  double dy = min_image(__dsub_rn(yb, ya), g.Lbox[1], g.halfL[1], g.periodic[1]);
+  double dz = min_image(__dsub_rn(zb, za), g.Lbox[2], g.halfL[2], g.periodic[2]);
+  double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  double two_h = __dmul_rn(2.0, ha);
+  return r2 < __dmul_rn(two_h, two_h);
+}
+
+__device__ __forceinline__ void raise_flag(uint32_t* err, uint32_t f) { atomicOr(err, f); }
+
+// Packed cell coordinates: 10 bits per axis.
+__device__ __forceinline__ int32_t pack_cell(int ix, int iy, int iz) {
+  return ix | (iy << 10) | (iz << 20);
+}
+__device__ __forceinline__ void unpack_cell(int32_t c, int& ix, int& iy, int& iz) {
+  ix = c & 1023;
+  iy = (c >> 10) & 1023;
+  iz = (c >> 20) & 1023;
+}
+
+// FP32 separation b - a along one axis from cell-relative offsets:
+// (off_b - off_a) + (cell_b - cell_a) * cs, with the cell difference taken
+// modulo the period and a final FP32 minimum image for grids of < 3 cells.
+__device__ __forceinline__ float sep32(float ob, float oa, int cb, int ca, const Grid& g, int ax) {
+  int dc = cb - ca;
+  if (g.periodic[ax]) {
+    int nc = g.nc[ax];
+    if (dc > nc / 2)
+      dc -= nc;
+    else if (dc < -(nc / 2))
+      dc += nc;
+  }
+  float d = fmaf((float)dc, g.cs32[ax], ob - oa);
+  if (g.periodic[ax]) {
+    if (d > g.halfL32[ax])
+      d -= g.L32[ax];
+    else if (d < -g.halfL32[ax])
+      d += g.L32[ax];
+  }
+  return d;
+}
+
+// Morton code of a cell: bit i of ix at 3i, iy at 3i+1, iz at 3i+2.
+__host__ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+__host__ __device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+  return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+
+// --- reductions ---
+__device__ __forceinline__ double warp_min(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace sph

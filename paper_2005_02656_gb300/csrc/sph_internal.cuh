@@ -1,0 +1,172 @@
+// Internal declarations of libsph: the context, the device-side grid
+// description and the kernel launchers of each translation unit.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sph.h"
+
+namespace sph {
+
+constexpr int kMaxCellBits = 8;                 // up to 256 cells per axis
+constexpr uint32_t kMaxTable = 1u << (3 * kMaxCellBits);
+constexpr int kReduceBlocks = 1024;             // partial slots of grid reductions
+constexpr int kScanItems = 4096;                // cell-table entries per scan block
+constexpr int kProfRing = 64;                   // step event sets kept before folding
+
+// Cell grid of the current step, computed on the device from the particles'
+// extent and h_max, read by every later kernel of the step.
+struct Grid {
+  double lo[3];      // origin of cell (0,0,0)
+  double cs[3];      // cell side per axis (>= 2 h_max)
+  double inv_cs[3];
+  double Lbox[3];    // period on periodic axes (box_hi - box_lo), 0 on open axes
+  double halfL[3];   // 0.5 * Lbox
+  float cs32[3];
+  float L32[3];
+  float halfL32[3];
+  float err32[3];    // bound on the FP32 error of a cell-relative separation
+  int nc[3];
+  int periodic[3];
+  int bits;          // Morton bits per axis
+  uint32_t tbl_size; // 2^(3 bits)
+  uint32_t n_occ;    // occupied cells (written by the scan)
+  double hmax;
+};
+
+// Sorted-state view passed to kernels by value.
+struct StateView {
+  double *x, *y, *z, *vx, *vy, *vz, *vxh, *vyh, *vzh, *h, *m, *u, *du_prev;
+  int64_t* id;
+};
+
+struct OutView {
+  double *rho, *p, *c, *iad, *ax, *ay, *az, *du;
+};
+
+// Block-reduction partials (per block) and finalisation counters.
+struct Reduce {
+  double* part;          // kReduceBlocks * 16 doubles
+  unsigned int* counter; // last-block-done counters (4)
+};
+
+}  // namespace sph
+
+struct sph_ctx {
+  sph_params prm;
+  int64_t n_max;
+  int device;
+  double Bn;
+  int sm_count;
+  int64_t launches;
+  int have_lists;     // lists valid for the current order
+  int have_density;
+  int have_iad;
+  char last_error[512];
+
+  // device scalars
+  sph::Grid* grid;
+  uint32_t* err;
+  double* dt_dev;       // scratch dt (host-step path)
+  double* diag;         // 16 doubles: [0..7] sums of the new state, [8] dt,
+                        // [9] min nn, [10] max nn, [11] sum nn, [12] dt_prev
+
+  // sort
+  uint32_t* code;       // Morton cell code per particle (input order)
+  uint32_t* slot;       // arrival slot within the cell
+  int32_t* perm_tmp;
+  int32_t* perm;        // sorted position -> source index
+  uint32_t* tbl_count;  // per Morton code
+  uint32_t* tbl_start;
+  uint32_t* occ;        // occupied cells in Morton order
+  uint32_t* scan_part;  // per scan block: particle sum, occupied sum (2 x)
+  uint32_t* cell_of;    // occupied-cell index of each sorted particle
+
+  // sorted state scratch (FP64) + ids
+  sph::StateView s;
+  int64_t* s_id_buf;
+
+  // per-particle FP32 cell-relative data (sorted order)
+  float4* pos32;        // offset from the cell origin (x, y, z) and h
+  int32_t* cell3;       // packed cell coordinates (10 bits per axis)
+
+  // neighbour lists: nn[n], nbr[k * n_max + p]
+  int32_t* nn;
+  int32_t* nbr;
+
+  // FP64 per-particle helpers: one block of 5 * n_max doubles
+  double* vol;          // m / rho          (vol + 0 n_max)
+  double* X;            // P / rho^2        (vol + 1 n_max)
+  double* inv_rho;      // 1 / rho          (vol + 2 n_max)
+                        // 1 / h^2          (vol + 3 n_max)
+                        // B_n / h^3        (vol + 4 n_max)
+
+  // FP32 mixed-path per-particle arrays (sorted order)
+  float4* vel32;        // vx, vy, vz, m (written by the gather)
+  float4* q32;          // 1/h^2, B_n/h^3, m/rho, 1/rho
+  float2* xc32;         // P/rho^2, c
+  float4* cA32;         // C00 C01 C02 C11
+  float4* cB32;         // C12 C22 P/rho^2 c
+
+  // reductions
+  sph::Reduce red;
+  unsigned long long* stats;  // 4 cumulative counters (sph_stats)
+
+  // per-stage timing (sph_profile): a ring of event sets, one per step
+  int prof;
+  int prof_slot;
+  cudaEvent_t* prof_ev;   // kProfRing * (SPH_NSTAGE + 1)
+  double prof_ms[SPH_NSTAGE];
+  int64_t prof_steps;
+
+  // host-step mirrors
+  double* hm_buf;       // device mirror storage for sph_step_host
+  int64_t* hm_id;
+  int64_t hm_n;
+};
+
+namespace sph {
+
+// --- error helpers (sph_api.cu) ---
+int set_error(sph_ctx* ctx, int code, const char* fmt, ...);
+int cuda_fail(sph_ctx* ctx, cudaError_t e, const char* what);
+
+// --- sph_sort.cu ---
+// Grid from the particles' extent + h_max; zero the cell table.
+void launch_grid(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st);
+// Counting sort by Morton cell code, deterministic order within cells; gathers
+// `in` into the sorted scratch ctx->s and builds pos32 / cell3 / cell_of.
+void launch_sort_gather(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st);
+// Recompute pos32 / cell3 for an already-sorted state (no permutation).
+void launch_copy_state(const StateView& dst, const StateView& src, int64_t n, cudaStream_t st,
+                       sph_ctx* ctx);
+
+// --- sph_neighbors.cu ---
+void launch_find_neighbors(sph_ctx* ctx, const StateView& s, int64_t n, cudaStream_t st);
+void launch_export_neighbors(sph_ctx* ctx, const StateView& s, int64_t n, int32_t* counts,
+                             int64_t* ids, cudaStream_t st);
+
+// --- sph_pairs_fp64.cu ---
+void launch_density_f64(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
+                        cudaStream_t st);
+void launch_iad_f64(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n, cudaStream_t st);
+void launch_momentum_f64(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
+                         cudaStream_t st);
+
+// --- sph_pairs_fp32.cu ---
+void launch_density_f32(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
+                        cudaStream_t st);
+void launch_iad_f32(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n, cudaStream_t st);
+void launch_momentum_f32(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
+                         cudaStream_t st);
+
+// --- sph_update.cu ---
+void launch_timestep(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n, double* dt_io,
+                     cudaStream_t st);
+// Update from the sorted scratch `s` into the caller's state `dst`.
+void launch_update(sph_ctx* ctx, const StateView& s, const OutView& o, const StateView& dst,
+                   int64_t n, const double* dt_io, cudaStream_t st);
+void launch_diagnostics(sph_ctx* ctx, const StateView& s, int64_t n, cudaStream_t st);
+
+}  // namespace sph

@@ -1,0 +1,227 @@
+// FP64 pair sums: density + EOS (Eq. 1), the IAD matrix, and momentum/energy
+// with artificial viscosity (Eqs. 2-5).  One thread per target particle a,
+// walking its neighbour list (coalesced, transposed layout) and gathering the
+// neighbours' fields through L1/L2; particles are in Morton cell order so the
+// neighbours of a warp's targets share cache lines.  On this part the FP64
+// pipe bounds these kernels, so per-pair divisions are hoisted into
+// per-particle arrays (m/rho, P/rho^2, 1/rho, 1/h^2, B_n/h^3).
+#include <cuda_runtime.h>
+
+#include "sph_device.cuh"
+#include "sph_internal.cuh"
+
+namespace sph {
+
+namespace {
+
+struct Aux64 {
+  double* vol;     // m / rho
+  double* X;       // P / rho^2
+  double* inv_rho;
+  double* hinv2;   // 1 / h^2
+  double* wnorm;   // B_n / h^3
+};
+
+__device__ __forceinline__ void sep64(const Grid& g, double xa, double ya, double za, double xb,
+                                      double yb, double zb, double& dx, double& dy, double& dz) {
+  dx = min_image(xb - xa, g.Lbox[0], g.halfL[0], g.periodic[0]);
+  dy = min_image(yb - ya, g.Lbox[1], g.halfL[1], g.periodic[1]);
+  dz = min_image(zb - za, g.Lbox[2], g.halfL[2], g.periodic[2]);
+}
+
+__global__ void __launch_bounds__(256) k_density64(const Grid* gp, StateView s, OutView o,
+                                                   Aux64 aux, const int32_t* nn,
+                                                   const int32_t* nbr, int64_t stride, int64_t n,
+                                                   int max_nb, double Bn, int sinc_n,
+                                                   double gamma, uint32_t* err) {
+  const Grid g = *gp;
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    const double xa = s.x[a], ya = s.y[a], za = s.z[a], ha = s.h[a];
+    const double hinv2 = 1.0 / (ha * ha);
+    const double norm = Bn * hinv2 / ha;
+    double rho = s.m[a] * norm;  // self term: W(0, h_a) = B_n / h_a^3
+    int cnt = nn[a];
+    cnt = cnt < max_nb ? cnt : max_nb;
+    for (int k = 0; k < cnt; ++k) {
+      const int64_t b = nbr[(int64_t)k * stride + a];
+      double dx, dy, dz;
+      sep64(g, xa, ya, za, s.x[b], s.y[b], s.z[b], dx, dy, dz);
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double t = fmin(r2 * hinv2, 4.0);
+      rho += s.m[b] * kernel_w64(t, norm, sinc_n);
+    }
+    const double p = (gamma - 1.0) * rho * s.u[a];
+    const double c = sqrt(gamma * p / rho);
+    o.rho[a] = rho;
+    o.p[a] = p;
+    o.c[a] = c;
+    const double inv_rho = 1.0 / rho;
+    aux.inv_rho[a] = inv_rho;
+    aux.vol[a] = s.m[a] * inv_rho;
+    aux.X[a] = p * inv_rho * inv_rho;
+    aux.hinv2[a] = hinv2;
+    aux.wnorm[a] = norm;
+    if (!isfinite(rho) || !isfinite(c)) raise_flag(err, SPH_FLAG_NONFINITE);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_iad64(const Grid* gp, StateView s, OutView o, Aux64 aux,
+                                               const int32_t* nn, const int32_t* nbr,
+                                               int64_t stride, int64_t n, int max_nb,
+                                               int sinc_n, uint32_t* err) {
+  const Grid g = *gp;
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    const double xa = s.x[a], ya = s.y[a], za = s.z[a];
+    const double hinv2 = aux.hinv2[a], norm = aux.wnorm[a];
+    double t00 = 0, t01 = 0, t02 = 0, t11 = 0, t12 = 0, t22 = 0;
+    int cnt = nn[a];
+    cnt = cnt < max_nb ? cnt : max_nb;
+    for (int k = 0; k < cnt; ++k) {
+      const int64_t b = nbr[(int64_t)k * stride + a];
+      double dx, dy, dz;
+      sep64(g, xa, ya, za, s.x[b], s.y[b], s.z[b], dx, dy, dz);
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double w = aux.vol[b] * kernel_w64(fmin(r2 * hinv2, 4.0), norm, sinc_n);
+      const double wx = w * dx, wy = w * dy, wz = w * dz;
+      t00 += wx * dx;
+      t01 += wx * dy;
+      t02 += wx * dz;
+      t11 += wy * dy;
+      t12 += wy * dz;
+      t22 += wz * dz;
+    }
+    // inverse of the symmetric matrix by cofactors
+    const double c00 = t11 * t22 - t12 * t12;
+    const double c01 = t02 * t12 - t01 * t22;
+    const double c02 = t01 * t12 - t02 * t11;
+    const double c11 = t00 * t22 - t02 * t02;
+    const double c12 = t01 * t02 - t00 * t12;
+    const double c22 = t00 * t11 - t01 * t01;
+    const double det = t00 * c00 + t01 * c01 + t02 * c02;
+    double tmax = fmax(fmax(fabs(t00), fabs(t01)), fmax(fabs(t02), fabs(t11)));
+    tmax = fmax(tmax, fmax(fabs(t12), fabs(t22)));
+    double* out = o.iad + 6 * a;
+    if (!isfinite(det) || fabs(det) <= 1e-12 * tmax * tmax * tmax) {
+      raise_flag(err, SPH_FLAG_SINGULAR_IAD);
+      for (int j = 0; j < 6; ++j) out[j] = 0.0;
+    } else {
+      const double id = 1.0 / det;
+      out[0] = c00 * id;
+      out[1] = c01 * id;
+      out[2] = c02 * id;
+      out[3] = c11 * id;
+      out[4] = c12 * id;
+      out[5] = c22 * id;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_momentum64(const Grid* gp, StateView s, OutView o,
+                                                    Aux64 aux, const int32_t* nn,
+                                                    const int32_t* nbr, int64_t stride,
+                                                    int64_t n, int max_nb, int sinc_n,
+                                                    double alpha, uint32_t* err) {
+  const Grid g = *gp;
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    const double xa = s.x[a], ya = s.y[a], za = s.z[a];
+    const double vxa = s.vx[a], vya = s.vy[a], vza = s.vz[a];
+    const double hinv2a = aux.hinv2[a], norma = aux.wnorm[a];
+    const double Xa = aux.X[a], ira = aux.inv_rho[a], ca = o.c[a];
+    const double* Ca = o.iad + 6 * a;
+    const double a00 = Ca[0], a01 = Ca[1], a02 = Ca[2], a11 = Ca[3], a12 = Ca[4], a22 = Ca[5];
+    double accx = 0, accy = 0, accz = 0, du = 0;
+    int cnt = nn[a];
+    cnt = cnt < max_nb ? cnt : max_nb;
+    for (int k = 0; k < cnt; ++k) {
+      const int64_t b = nbr[(int64_t)k * stride + a];
+      double dx, dy, dz;
+      sep64(g, xa, ya, za, s.x[b], s.y[b], s.z[b], dx, dy, dz);
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double Wa = kernel_w64(fmin(r2 * hinv2a, 4.0), norma, sinc_n);
+      const double tb = r2 * aux.hinv2[b];
+      const double Wb = tb < 4.0 ? kernel_w64(tb, aux.wnorm[b], sinc_n) : 0.0;
+      // C_a d and C_b d, d = x_b - x_a
+      const double Cadx = a00 * dx + a01 * dy + a02 * dz;
+      const double Cady = a01 * dx + a11 * dy + a12 * dz;
+      const double Cadz = a02 * dx + a12 * dy + a22 * dz;
+      const double* Cb = o.iad + 6 * b;
+      const double b00 = Cb[0], b01 = Cb[1], b02 = Cb[2], b11 = Cb[3], b12 = Cb[4], b22 = Cb[5];
+      const double Cbdx = b00 * dx + b01 * dy + b02 * dz;
+      const double Cbdy = b01 * dx + b11 * dy + b12 * dz;
+      const double Cbdz = b02 * dx + b12 * dy + b22 * dz;
+      const double vabx = vxa - s.vx[b], vaby = vya - s.vy[b], vabz = vza - s.vz[b];
+      const double xv = -(dx * vabx + dy * vaby + dz * vabz);  // x_ab . v_ab
+      const double irb = aux.inv_rho[b];
+      double Pi = 0.0;
+      if (xv < 0.0) {
+        const double w = xv * rsqrt(r2);
+        const double vsig = ca + o.c[b] - 3.0 * w;
+        Pi = -0.5 * alpha * vsig * w;
+      }
+      const double mb = s.m[b];
+      const double fa = mb * Wa * (Xa + 0.5 * Pi * ira);
+      const double fb = mb * Wb * (aux.X[b] + 0.5 * Pi * irb);
+      accx -= fa * Cadx + fb * Cbdx;
+      accy -= fa * Cady + fb * Cbdy;
+      accz -= fa * Cadz + fb * Cbdz;
+      const double vCa = vabx * Cadx + vaby * Cady + vabz * Cadz;
+      const double vCb = vabx * Cbdx + vaby * Cbdy + vabz * Cbdz;
+      du += mb * (Wa * (Xa + 0.25 * Pi * ira) * vCa + 0.25 * Pi * irb * Wb * vCb);
+    }
+    o.ax[a] = accx;
+    o.ay[a] = accy;
+    o.az[a] = accz;
+    o.du[a] = du;
+    if (!isfinite(accx) || !isfinite(accy) || !isfinite(accz) || !isfinite(du))
+      raise_flag(err, SPH_FLAG_NONFINITE);
+  }
+}
+
+inline int blocks_for(int64_t n, int sm) {
+  int64_t b = (n + 255) / 256;
+  int64_t cap = (int64_t)sm * 64;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+inline Aux64 aux_of(sph_ctx* ctx) {
+  Aux64 a;
+  a.vol = ctx->vol;
+  a.X = ctx->X;
+  a.inv_rho = ctx->inv_rho;
+  a.hinv2 = ctx->vol + 3 * ctx->n_max;
+  a.wnorm = ctx->vol + 4 * ctx->n_max;
+  return a;
+}
+
+}  // namespace
+
+void launch_density_f64(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
+                        cudaStream_t st) {
+  k_density64<<<blocks_for(n, ctx->sm_count), 256, 0, st>>>(
+      ctx->grid, s, o, aux_of(ctx), ctx->nn, ctx->nbr, ctx->n_max, n, ctx->prm.max_nb, ctx->Bn,
+      (int)ctx->prm.sinc_n, ctx->prm.gamma, ctx->err);
+  ctx->launches += 1;
+}
+
+void launch_iad_f64(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
+                    cudaStream_t st) {
+  k_iad64<<<blocks_for(n, ctx->sm_count), 256, 0, st>>>(ctx->grid, s, o, aux_of(ctx), ctx->nn,
+                                                        ctx->nbr, ctx->n_max, n, ctx->prm.max_nb,
+                                                        (int)ctx->prm.sinc_n, ctx->err);
+  ctx->launches += 1;
+}
+
+void launch_momentum_f64(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
+                         cudaStream_t st) {
+  k_momentum64<<<blocks_for(n, ctx->sm_count), 256, 0, st>>>(
+      ctx->grid, s, o, aux_of(ctx), ctx->nn, ctx->nbr, ctx->n_max, n, ctx->prm.max_nb,
+      (int)ctx->prm.sinc_n, ctx->prm.alpha, ctx->err);
+  ctx->launches += 1;
+}
+
+}  // namespace sph

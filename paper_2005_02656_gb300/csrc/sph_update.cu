@@ -1,0 +1,272 @@
+// Global time step, integrator update and conservation sums, all FP64.
+//
+// k_timestep  dt_n = min(courant * min_a h_a / c_a, dt_growth * dt_{n-1})
+//             (section 4.2: the global minimum time step; the paper's
+//             MPI_Allreduce becomes a block reduction plus a last-block
+//             finalisation, so the result never leaves the device)
+// k_update    section 4.1's second-order integrators, read as a variable-step
+//             leapfrog for x and v and Adams-Bashforth for u; smoothing length
+//             adapted toward the target neighbour count; periodic wrap; block
+//             partial sums of momentum, energies, angular momentum and
+//             neighbour-count statistics of the new state (section 4.2: the
+//             optional conservation reduction)
+// k_diag      the same sums for any state
+// Cross-block totals are summed in block order with compensation, so every
+// reduction here is deterministic.
+#include <cuda_runtime.h>
+
+#include "sph_device.cuh"
+#include "sph_internal.cuh"
+
+namespace sph {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kParts = 16;  // doubles per block partial
+
+__device__ __forceinline__ bool block_last(unsigned int* counter) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned int done = atomicAdd(counter, 1u);
+    last = (done == gridDim.x - 1);
+  }
+  __syncthreads();
+  return last;
+}
+
+// Block sum of NV doubles per thread into part[blockIdx.x * kParts + k].
+template <int NV>
+__device__ __forceinline__ void block_sums(double (&v)[NV], double* part) {
+  __shared__ double sh[kThreads / 32][NV];
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+    for (int k = 0; k < NV; ++k) sh[w][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int ww = 0; ww < kThreads / 32; ++ww) s += sh[ww][threadIdx.x];
+    part[blockIdx.x * kParts + threadIdx.x] = s;
+  }
+}
+
+__device__ void finalize_sums(const double* part, int nblocks, int nv, double* out) {
+  // thread k < nv: compensated sum over blocks in block order
+  int k = threadIdx.x;
+  if (k >= nv) return;
+  double s = 0.0, comp = 0.0;
+  for (int b = 0; b < nblocks; ++b) {
+    double y = ((const volatile double*)part)[b * kParts + k] - comp;
+    double t = s + y;
+    comp = (t - s) - y;
+    s = t;
+  }
+  out[k] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_timestep(const double* h, const double* c, int64_t n,
+                                                       double courant, double growth,
+                                                       double* dt_io, double* diag, double* part,
+                                                       unsigned int* counter, uint32_t* err) {
+  double mn = INFINITY;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    mn = fmin(mn, h[i] / c[i]);
+  mn = warp_min(mn);
+  __shared__ double sh[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kThreads / 32; ++w) mn = fmin(mn, sh[w]);
+    part[blockIdx.x * kParts] = mn;
+  }
+  if (!block_last(counter)) return;
+  if (threadIdx.x == 0) {
+    double m = INFINITY;
+    for (unsigned int b = 0; b < gridDim.x; ++b)
+      m = fmin(m, ((const volatile double*)part)[b * kParts]);
+    const double prev = *dt_io;
+    double dt = courant * m;
+    if (prev > 0.0) dt = fmin(dt, growth * prev);
+    if (!isfinite(dt) || !(dt > 0.0)) raise_flag(err, SPH_FLAG_NONFINITE);
+    diag[12] = prev;
+    diag[8] = dt;
+    *dt_io = dt;
+    *counter = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_update(StateView s, OutView o, StateView d,
+                                                     const int32_t* nn, int64_t n,
+                                                     sph_params prm, double* diag, double* part,
+                                                     unsigned int* counter,
+                                                     unsigned long long* stats) {
+  const double dt = diag[8], dt_prev = diag[12];
+  const double delta = 0.5 * (dt + dt_prev);
+  const double q = dt_prev > 0.0 ? dt / (2.0 * dt_prev) : 0.0;
+  double acc[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double nmin = INFINITY, nmax = -INFINITY;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const double a3[3] = {o.ax[p], o.ay[p], o.az[p]};
+    const double x3[3] = {s.x[p], s.y[p], s.z[p]};
+    const double vh3[3] = {s.vxh[p], s.vyh[p], s.vzh[p]};
+    double xn[3], vn[3], vhn[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      vhn[k] = vh3[k] + a3[k] * delta;
+      double xk = x3[k] + dt * vhn[k];
+      if (prm.periodic[k]) {
+        const double L = prm.box_hi[k] - prm.box_lo[k];
+        if (xk >= prm.box_hi[k])
+          xk -= L;
+        else if (xk < prm.box_lo[k])
+          xk += L;
+      }
+      xn[k] = xk;
+      vn[k] = vhn[k] + 0.5 * dt * a3[k];
+    }
+    const double du = o.du[p];
+    const double u = s.u[p];
+    const double un = dt_prev > 0.0 ? u + dt * ((1.0 + q) * du - q * s.du_prev[p]) : u + dt * du;
+    const int cnt = nn[p];
+    double h = s.h[p];
+    if (prm.ng_target > 0) {
+      const int kk = cnt > 1 ? cnt : 1;
+      h = h * 0.5 * (1.0 + cbrt((double)prm.ng_target / (double)kk));
+    }
+    const double m = s.m[p];
+    d.x[p] = xn[0];
+    d.y[p] = xn[1];
+    d.z[p] = xn[2];
+    d.vx[p] = vn[0];
+    d.vy[p] = vn[1];
+    d.vz[p] = vn[2];
+    d.vxh[p] = vhn[0];
+    d.vyh[p] = vhn[1];
+    d.vzh[p] = vhn[2];
+    d.u[p] = un;
+    d.du_prev[p] = du;
+    d.h[p] = h;
+    d.m[p] = m;
+    d.id[p] = s.id[p];
+    acc[0] += m * vn[0];
+    acc[1] += m * vn[1];
+    acc[2] += m * vn[2];
+    acc[3] += 0.5 * m * (vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
+    acc[4] += m * un;
+    acc[5] += m * (xn[1] * vn[2] - xn[2] * vn[1]);
+    acc[6] += m * (xn[2] * vn[0] - xn[0] * vn[2]);
+    acc[7] += m * (xn[0] * vn[1] - xn[1] * vn[0]);
+    acc[10] += (double)cnt;
+    nmin = fmin(nmin, (double)cnt);
+    nmax = fmax(nmax, (double)cnt);
+  }
+  acc[8] = 0.0;
+  acc[9] = 0.0;
+  nmin = warp_min(nmin);
+  nmax = warp_max(nmax);
+  __shared__ double shm[kThreads / 32][2];
+  if ((threadIdx.x & 31) == 0) {
+    shm[threadIdx.x >> 5][0] = nmin;
+    shm[threadIdx.x >> 5][1] = nmax;
+  }
+  block_sums<11>(acc, part);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kThreads / 32; ++w) {
+      nmin = fmin(nmin, shm[w][0]);
+      nmax = fmax(nmax, shm[w][1]);
+    }
+    part[blockIdx.x * kParts + 8] = nmin;
+    part[blockIdx.x * kParts + 9] = nmax;
+  }
+  if (!block_last(counter)) return;
+  __threadfence();
+  double tmp[11];
+  __shared__ double res[11];
+  if (threadIdx.x < 11) {
+    finalize_sums(part, gridDim.x, 11, res);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 8; ++k) diag[k] = res[k];
+    double mn = INFINITY, mx = -INFINITY;
+    for (unsigned int b = 0; b < gridDim.x; ++b) {
+      mn = fmin(mn, ((const volatile double*)part)[b * kParts + 8]);
+      mx = fmax(mx, ((const volatile double*)part)[b * kParts + 9]);
+    }
+    diag[9] = mn;
+    diag[10] = mx;
+    diag[11] = res[10];
+    stats[2] += (unsigned long long)res[10];
+    stats[3] += (unsigned long long)n;
+    *counter = 0;
+  }
+  (void)tmp;
+}
+
+__global__ void __launch_bounds__(kThreads) k_diag(StateView s, int64_t n, double* diag,
+                                                   double* part, unsigned int* counter) {
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const double m = s.m[p], x = s.x[p], y = s.y[p], z = s.z[p];
+    const double vx = s.vx[p], vy = s.vy[p], vz = s.vz[p];
+    acc[0] += m * vx;
+    acc[1] += m * vy;
+    acc[2] += m * vz;
+    acc[3] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+    acc[4] += m * s.u[p];
+    acc[5] += m * (y * vz - z * vy);
+    acc[6] += m * (z * vx - x * vz);
+    acc[7] += m * (x * vy - y * vx);
+  }
+  block_sums<8>(acc, part);
+  if (!block_last(counter)) return;
+  __threadfence();
+  __shared__ double res[8];
+  if (threadIdx.x < 8) finalize_sums(part, gridDim.x, 8, res);
+  __syncthreads();
+  if (threadIdx.x < 8) diag[threadIdx.x] = res[threadIdx.x];
+  if (threadIdx.x == 0) *counter = 0;
+}
+
+inline int red_blocks(int64_t n, int sm) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  int64_t cap = (int64_t)sm * 4;
+  if (cap > kReduceBlocks) cap = kReduceBlocks;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+void launch_timestep(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n, double* dt_io,
+                     cudaStream_t st) {
+  k_timestep<<<red_blocks(n, ctx->sm_count), kThreads, 0, st>>>(
+      s.h, o.c, n, ctx->prm.courant, ctx->prm.dt_growth, dt_io, ctx->diag, ctx->red.part,
+      ctx->red.counter + 1, ctx->err);
+  ctx->launches += 1;
+}
+
+void launch_update(sph_ctx* ctx, const StateView& s, const OutView& o, const StateView& dst,
+                   int64_t n, const double* dt_io, cudaStream_t st) {
+  (void)dt_io;
+  k_update<<<red_blocks(n, ctx->sm_count), kThreads, 0, st>>>(
+      s, o, dst, ctx->nn, n, ctx->prm, ctx->diag, ctx->red.part, ctx->red.counter + 2,
+      ctx->stats);
+  ctx->launches += 1;
+}
+
+void launch_diagnostics(sph_ctx* ctx, const StateView& s, int64_t n, cudaStream_t st) {
+  k_diag<<<red_blocks(n, ctx->sm_count), kThreads, 0, st>>>(s, n, ctx->diag + 16, ctx->red.part,
+                                                            ctx->red.counter + 3);
+  ctx->launches += 1;
+}
+
+}  // namespace sph

@@ -1,0 +1,147 @@
+"""GPU parity: the CUDA library against the FP64 oracle on identical inputs.
+
+Neighbour sets must match bit-exactly (sorted id lists).  FP64 fields must
+match within 1e-12 (normalised errors, tests/helpers.py).  FP32-mixed fields
+must match within density 1e-5, acceleration 1e-4 and du 1e-4 (normalised).
+Cases span many cells and warps with ragged tails: periodic jittered boxes,
+open axes (square patch), varying h, two cells per axis, and a small
+Kelvin-Helmholtz box with two densities.
+"""
+import numpy as np
+import pytest
+
+import sph_inputs
+from helpers import by_id, field_errors, oracle_outputs
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MAX_NB = 256          # room for the +-30% smoothing-length case
+FP32_TOL = {"rho": 1e-5, "a": 1e-4, "du": 1e-4}
+
+
+def _cases():
+    rng = np.random.default_rng(99)
+    c = {}
+    c["box20"] = sph_inputs.jittered_box(20)
+    c["box17_ragged"] = sph_inputs.jittered_box(17, seed_index=5)
+    s = sph_inputs.jittered_box(16, seed_index=6)
+    s["h"] *= rng.uniform(0.7, 1.3, s["h"].shape[0])
+    c["box16_varh"] = s
+    s = sph_inputs.jittered_box(6, seed_index=7)
+    s["h"][:] = 0.24                     # two cells per axis
+    c["box6_2cells"] = s
+    c["patch20"] = sph_inputs.square_patch(20)
+    c["kh32"] = sph_inputs.kelvin_helmholtz(32)
+    return c
+
+
+CASES = _cases()
+
+
+def _gpu(s, precision="fp64", **kw):
+    from paper_2005_02656_gb300 import SphSim
+    sim = SphSim(s, precision=precision, max_nb=MAX_NB, **kw)
+    sim.find_neighbors()
+    sim.density()
+    sim.iad()
+    sim.momentum_energy()
+    counts, ids = sim.get_neighbors()
+    got = sim.to_numpy(by_id=False)
+    flags = sim.error_word()
+    sim.close()
+    order = np.argsort(got["id"], kind="stable")
+    got = {k: v[order] for k, v in got.items()}
+    return got, counts.cpu().numpy()[order], ids.cpu().numpy()[order], flags
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_neighbors_bit_exact(name):
+    s = CASES[name]
+    rc, ref_s, ref = oracle_outputs(s, ng_target=0, max_nb=MAX_NB)
+    assert rc == 0
+    got, counts, ids, flags = _gpu(s)
+    assert flags == 0
+    np.testing.assert_array_equal(counts, ref["nn"])
+    mb = ids.shape[1]
+    for a in range(counts.shape[0]):
+        k = counts[a]
+        np.testing.assert_array_equal(ids[a, :k], ref["nbr"][a, :k])
+    assert counts.sum() == ref["nn"].sum()
+    assert mb == ref["nbr"].shape[1]
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp64_fields(name):
+    s = CASES[name]
+    rc, ref_s, ref = oracle_outputs(s, ng_target=0, max_nb=MAX_NB)
+    assert rc == 0
+    got, _, _, flags = _gpu(s)
+    assert flags == 0
+    e = field_errors(got, ref)
+    for k in ("rho", "p", "c", "iad", "a", "du"):
+        assert e[k] <= FP64_TOL, (k, e)
+
+
+@pytest.mark.parametrize("name", ["box20", "patch20", "kh32", "box16_varh"])
+def test_fp32_mixed_fields(name):
+    s = CASES[name]
+    rc, ref_s, ref = oracle_outputs(s, ng_target=0, max_nb=MAX_NB)
+    assert rc == 0
+    got, counts, _, flags = _gpu(s, precision="fp32_mixed")
+    assert flags == 0
+    np.testing.assert_array_equal(counts, ref["nn"])   # lists are exact in both precisions
+    e = field_errors(got, ref)
+    for k, tol in FP32_TOL.items():
+        assert e[k] <= tol, (k, e)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+def test_full_step_matches_oracle(precision):
+    """One sph_step (sort, search, sums, dt, update, h) against the oracle step."""
+    import oracle
+    from paper_2005_02656_gb300 import SphSim
+    s = sph_inputs.jittered_box(18, seed_index=9, vel_sigma=0.2)
+    sim = SphSim(s, precision=precision)
+    sim.step()
+    got = sim.to_numpy()
+    dt_gpu = float(sim.dt.cpu()[0])
+    assert sim.error_word() == 0
+    sim.close()
+    ref = by_id(s)
+    box = oracle.Box(s["lo"], s["hi"], s["periodic"])
+    rc, dt, out = oracle.step(box, ref, oracle.Params(), 0.0)
+    assert rc == 0
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    assert abs(dt_gpu - dt) <= tol * dt
+    # the update propagates the force errors: |dx| <= dt^2 |da|, |dv| <= dt |da|
+    ta = FP64_TOL if precision == "fp64" else FP32_TOL["a"]
+    da = ta * out["sa"].max()
+    ddu = ta * out["sdu"].max()
+    for k in ("x", "y", "z"):
+        d = np.abs(got[k] - ref[k])
+        d = np.minimum(d, 1.0 - d)          # periodic unit box
+        assert d.max() <= dt * dt * da + 1e-15, k
+    for k in ("vx", "vy", "vz", "vxh", "vyh", "vzh"):
+        assert np.abs(got[k] - ref[k]).max() <= dt * da + 1e-15, k
+    assert np.abs(got["u"] - ref["u"]).max() <= dt * ddu + 1e-15
+    assert np.abs(got["du_prev"] - ref["du_prev"]).max() <= ddu + 1e-15
+    # h depends only on the exact counts; cbrt may differ from libm by an ulp
+    np.testing.assert_allclose(got["h"], ref["h"], rtol=1e-15, atol=0)
+
+
+def test_empty_and_single_particle():
+    from paper_2005_02656_gb300 import SphSim
+    s = sph_inputs.jittered_box(10)
+    one = {k: (v[:1].copy() if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+    sim = SphSim(one, ng_target=0)
+    sim.step()
+    from paper_2005_02656_gb300 import _lib
+    flags = sim.error_word()
+    assert flags & _lib.FLAG_SINGULAR_IAD      # no neighbours: tau = 0
+    sim.close()
+    empty = {k: (v[:0].copy() if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+    sim = SphSim(empty, n_max=8)
+    sim.step()
+    assert sim.error_word() == 0
+    sim.close()
