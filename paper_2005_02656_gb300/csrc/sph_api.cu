@@ -154,8 +154,7 @@ void free_all(sph_ctx* ctx) {
   void* ptrs[] = {ctx->grid, ctx->err, ctx->dt_dev, ctx->diag, ctx->code, ctx->slot,
                   ctx->perm_tmp, ctx->perm, ctx->tbl_count, ctx->tbl_start, ctx->occ,
                   ctx->scan_part, ctx->cell_of, ctx->s.x, ctx->s_id_buf, ctx->pos32,
-                  ctx->cell3, ctx->nn, ctx->nbr, ctx->vol, ctx->vel32, ctx->q32, ctx->xc32,
-                  ctx->cA32, ctx->cB32, ctx->red.part, ctx->red.counter, ctx->stats, ctx->hm_buf, ctx->hm_id};
+                  ctx->cell3, ctx->nn, ctx->nbr, ctx->vol, ctx->rec_d, ctx->rec_i, ctx->rec_m, ctx->red.part, ctx->red.counter, ctx->stats, ctx->hm_buf, ctx->hm_id};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -282,11 +281,9 @@ int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {
   ALLOC(ctx->nn, n);
   ALLOC(ctx->nbr, (size_t)mb * n);
   ALLOC(ctx->vol, 5 * n);
-  ALLOC(ctx->vel32, n);
-  ALLOC(ctx->q32, n);
-  ALLOC(ctx->xc32, n);
-  ALLOC(ctx->cA32, n);
-  ALLOC(ctx->cB32, n);
+  ALLOC(ctx->rec_d, n);
+  ALLOC(ctx->rec_i, n);
+  ALLOC(ctx->rec_m, 5 * n);
   ALLOC(ctx->red.part, sph::kReduceBlocks * 16);
   ALLOC(ctx->red.counter, 8);
   ALLOC(ctx->stats, 4);

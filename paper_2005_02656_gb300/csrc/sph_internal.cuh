@@ -27,6 +27,7 @@ struct Grid {
   float L32[3];
   float halfL32[3];
   float err32[3];    // bound on the FP32 error of a cell-relative separation
+  int wrap32;        // a periodic axis has < 3 cells: FP32 separations need a wrap
   int nc[3];
   int periodic[3];
   int bits;          // Morton bits per axis
@@ -91,9 +92,9 @@ struct sph_ctx {
   float4* pos32;        // offset from the cell origin (x, y, z) and h
   int32_t* cell3;       // packed cell coordinates (10 bits per axis)
 
-  // neighbour lists: nn[n], nbr[k * n_max + p]
+  // neighbour lists: nn[n], nbr[p * max_nb + k] = stencil slot (sph_tile.cuh)
   int32_t* nn;
-  int32_t* nbr;
+  uint16_t* nbr;
 
   // FP64 per-particle helpers: one block of 5 * n_max doubles
   double* vol;          // m / rho          (vol + 0 n_max)
@@ -102,12 +103,10 @@ struct sph_ctx {
                         // 1 / h^2          (vol + 3 n_max)
                         // B_n / h^3        (vol + 4 n_max)
 
-  // FP32 mixed-path per-particle arrays (sorted order)
-  float4* vel32;        // vx, vy, vz, m (written by the gather)
-  float4* q32;          // 1/h^2, B_n/h^3, m/rho, 1/rho
-  float2* xc32;         // P/rho^2, c
-  float4* cA32;         // C00 C01 C02 C11
-  float4* cB32;         // C12 C22 P/rho^2 c
+  // FP32 mixed-path per-particle records (sorted order, sph_pairs_fp32.cu)
+  float4* rec_d;        // offset x, y, z, m               (gather)
+  float4* rec_i;        // offset x, y, z, m/rho           (density)
+  float4* rec_m;        // 5 float4 per particle           (gather, density, IAD)
 
   // reductions
   sph::Reduce red;

@@ -1,210 +1,271 @@
-// findNeighbors (section 4.1: b runs over the neighbours of a, i.e. the
-// particles inside the kernel support |x_a - x_b| < 2 h_a).
+// findNeighbors (section 4.1: b runs over the neighbours of a, the particles
+// inside the kernel support |x_a - x_b| < 2 h_a).
 //
-// One warp per occupied cell; each lane owns one target particle of the cell
-// (32 at a time).  The warp walks the distinct cells of the 3x3x3 stencil and,
-// for every candidate b (read once per warp and broadcast to all lanes), each
-// lane decides b in N_a:
-//   1. FP32 prefilter on cell-relative offsets: r2_32 is compared with
-//      (2 h_a)^2 within a margin M_a that bounds the FP32 rounding error of
-//      the separation (Grid::err32) and of the squares;
-//   2. only candidates inside the margin are decided by the exact FP64
-//      criterion (sph_device.cuh: exact_neighbor), so the lists are
-//      bit-identical to r^2 < (2h)^2 evaluated in FP64 without FMA.
-// Lists are stored transposed, nbr[k * stride + a], so that the per-particle
-// pair kernels read them with coalesced loads.
+// One warp per occupied cell (warps of a CTA work independently, each with
+// its own shared-memory window, so no CTA barrier is involved).  The cell's
+// stencil particles are staged in shared memory as FP32 positions relative to
+// the cell's origin (offset to their own cell + the stencil shift).  Lane t
+// owns target t of the cell (32 at a time) and walks the staged candidates in
+// blocks of 64, all lanes reading the same candidate pair (broadcast loads,
+// paired FP32 arithmetic on candidates j and j + 32 of the block):
+//   1. FP32 prefilter: r2_32 against (2 h_a)^2 within a margin M_a that
+//      bounds the FP32 rounding of the separation (Grid::err32) and of the
+//      squares; outside the margin the FP32 decision is exact;
+//   2. inside the margin, the exact FP64 criterion (exact_neighbor), so lists
+//      are bit-identical to r^2 < (2h)^2 evaluated in FP64 without FMA;
+//   3. each lane appends its hits of the block, in slot order, from a 64-bit
+//      hit mask.
+// Lists are uint16 entry codes (sph_tile.cuh), row-major per particle:
+// nbr[a * max_nb + k], ascending.
 #include <cuda_runtime.h>
 
 #include "sph_device.cuh"
 #include "sph_internal.cuh"
+#include "sph_tile.cuh"
 
 namespace sph {
 
 namespace {
 
-struct AxisCells {
-  int cell[3];
-  int shift[3];
-  int cnt;
-};
+constexpr int kFindWarps = 4;
+constexpr int kFindThreads = 32 * kFindWarps;
+constexpr int kFindWindow = 768;   // staged candidates per warp and pass (9 KB)
+constexpr float kFar = 1.0e18f;    // position of padding slots (never a neighbour)
 
-__device__ __forceinline__ AxisCells axis_cells(const Grid& g, int ax, int ic) {
-  AxisCells r;
-  int nc = g.nc[ax];
-  r.cnt = 0;
-  if (g.periodic[ax]) {
-    if (nc >= 3) {
-      for (int d = -1; d <= 1; ++d) {
-        int c = ic + d;
-        c = c < 0 ? c + nc : (c >= nc ? c - nc : c);
-        r.cell[r.cnt] = c;
-        r.shift[r.cnt] = d;
-        ++r.cnt;
-      }
-    } else if (nc == 2) {
-      r.cell[0] = ic;
-      r.shift[0] = 0;
-      r.cell[1] = 1 - ic;
-      r.shift[1] = ic == 0 ? 1 : -1;
-      r.cnt = 2;
-    } else {
-      r.cell[0] = ic;
-      r.shift[0] = 0;
-      r.cnt = 1;
-    }
-  } else {
-    for (int d = -1; d <= 1; ++d) {
-      int c = ic + d;
-      if (c < 0 || c >= nc) continue;
-      r.cell[r.cnt] = c;
-      r.shift[r.cnt] = d;
-      ++r.cnt;
-    }
-  }
-  return r;
-}
-
-__device__ __forceinline__ float wrap32(float d, const Grid& g, int ax) {
-  if (g.periodic[ax]) {
-    if (d > g.halfL32[ax])
-      d -= g.L32[ax];
-    else if (d < -g.halfL32[ax])
-      d += g.L32[ax];
-  }
+__device__ __forceinline__ float wrap_axis(float d, const Grid& g, int ax) {
+  if (d > g.halfL32[ax])
+    d -= g.L32[ax];
+  else if (d < -g.halfL32[ax])
+    d += g.L32[ax];
   return d;
 }
 
-__global__ void __launch_bounds__(128) k_find(const Grid* gp, StateView s, const float4* pos32,
-                                              const uint32_t* occ, const uint32_t* tbl_start,
-                                              const uint32_t* tbl_count, int32_t* nn,
-                                              int32_t* nbr, int64_t stride, int max_nb,
-                                              uint32_t* err, unsigned long long* stats) {
+// Shared-memory layout of a window: per block of 64 slots, the x (y, z)
+// coordinates as 32 float2 pairs (slot q, slot q + 32), so one 8-byte load
+// gives the pair processed by one paired FP32 instruction.
+__device__ __forceinline__ int pair_index(int i) {
+  const int blk = i >> 6, r = i & 63;
+  return (blk << 6) + ((r & 31) << 1) + (r >> 5);
+}
+
+struct FindWarpSmem {
+  Stencil S;
+  // 16-byte aligned: the candidate arrays are read as float2 pairs
+  alignas(16) float cx[kFindWindow];
+  alignas(16) float cy[kFindWindow];
+  alignas(16) float cz[kFindWindow];
+  uint16_t code[kFindWindow];  // list entry of each staged slot
+};
+static_assert(sizeof(FindWarpSmem) % 16 == 0, "per-warp window must keep 16-byte alignment");
+
+// Hit and margin masks of one block of 64 staged candidates for one target.
+// The decisions r2 < lo and r2 < hi are read from the sign bits of r2 - lo and
+// r2 - hi, with the limit folded into the first fused multiply-add (the margin
+// is twice the error bound, so a strict "< hi" is as safe as "<= hi").
+template <bool WRAP>
+__device__ __forceinline__ void block_masks(const Grid& g, const float* cx, const float* cy,
+                                            const float* cz, float2 npx, float2 npy, float2 npz,
+                                            float lo_lim, float hi_lim, uint64_t& hit,
+                                            uint64_t& unc) {
+  const float2* X = reinterpret_cast<const float2*>(cx);
+  const float2* Y = reinterpret_cast<const float2*>(cy);
+  const float2* Z = reinterpret_cast<const float2*>(cz);
+  const float2 nlo = make_float2(-lo_lim, -lo_lim);
+  const float2 dlh = make_float2(lo_lim - hi_lim, lo_lim - hi_lim);
+  uint32_t hA = 0, hB = 0, uA = 0, uB = 0;
+#pragma unroll 8
+  for (int q = 0; q < 32; ++q) {
+    float2 dx = __fadd2_rn(X[q], npx);
+    float2 dy = __fadd2_rn(Y[q], npy);
+    float2 dz = __fadd2_rn(Z[q], npz);
+    if (WRAP) {
+      if (g.periodic[0]) dx = make_float2(wrap_axis(dx.x, g, 0), wrap_axis(dx.y, g, 0));
+      if (g.periodic[1]) dy = make_float2(wrap_axis(dy.x, g, 1), wrap_axis(dy.y, g, 1));
+      if (g.periodic[2]) dz = make_float2(wrap_axis(dz.x, g, 2), wrap_axis(dz.y, g, 2));
+    }
+    float2 t = __ffma2_rn(dx, dx, nlo);   // r2 - lo
+    t = __ffma2_rn(dy, dy, t);
+    t = __ffma2_rn(dz, dz, t);
+    const float2 u = __fadd2_rn(t, dlh);   // r2 - hi
+    hA |= (__float_as_uint(t.x) >> 31) << q;
+    hB |= (__float_as_uint(t.y) >> 31) << q;
+    uA |= (__float_as_uint(u.x) >> 31) << q;
+    uB |= (__float_as_uint(u.y) >> 31) << q;
+  }
+  hit = (uint64_t)hA | ((uint64_t)hB << 32);
+  unc = ((uint64_t)uA | ((uint64_t)uB << 32)) & ~hit;
+}
+
+// Launched in both variants; the one whose WRAP does not match the grid (a
+// periodic axis with fewer than 3 cells needs the FP32 wrap) returns at once.
+template <bool WRAP>
+__global__ void __launch_bounds__(kFindThreads) k_find_tile(
+    const Grid* gp, StateView s, const float4* __restrict__ pos32, const uint32_t* occ,
+    const uint32_t* tbl_start, const uint32_t* tbl_count, int32_t* nn, uint16_t* nbr,
+    int max_nb, uint32_t* err, unsigned long long* stats) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  FindWarpSmem& W = reinterpret_cast<FindWarpSmem*>(smem_raw)[warp];
+  Stencil& S = W.S;
   const Grid g = *gp;
-  const int lane = threadIdx.x & 31;
-  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < g.n_occ; k += warps) {
-    const uint32_t code = occ[k];
-    const uint32_t c0 = tbl_start[code], ccount = tbl_count[code];
-    // cell coordinates from the Morton code
-    int ic[3];
-    {
-      uint32_t v[3] = {code, code >> 1, code >> 2};
-      for (int ax = 0; ax < 3; ++ax) {
-        uint32_t t = v[ax] & 0x09249249u;
-        t = (t | (t >> 2)) & 0x030c30c3u;
-        t = (t | (t >> 4)) & 0x0300f00fu;
-        t = (t | (t >> 8)) & 0x030000ffu;
-        t = (t | (t >> 16)) & 0x000003ffu;
-        ic[ax] = (int)t;
-      }
+  if ((g.wrap32 != 0) != WRAP) return;
+  const float esum = g.err32[0] + g.err32[1] + g.err32[2];
+  const float esq = g.err32[0] * g.err32[0] + g.err32[1] * g.err32[1] + g.err32[2] * g.err32[2];
+  unsigned long long tested = 0, exact = 0;
+  const uint32_t gw = blockIdx.x * kFindWarps + warp, nw = gridDim.x * kFindWarps;
+  for (uint32_t cell = gw; cell < g.n_occ; cell += nw) {
+    build_stencil_warp(g, occ[cell], tbl_start, tbl_count, S);
+    const int P = S.off[S.ncell];
+    const int a0 = S.a0, na = S.na;
+    if (P > kMaxSlots || S.maxpop > kMaxCellPop) {
+      for (int t = lane; t < na; t += 32) nn[a0 + t] = 0;
+      if (lane == 0) raise_flag(err, SPH_FLAG_CELL_OVERFLOW);
+      __syncwarp();
+      continue;
     }
-    const AxisCells AX = axis_cells(g, 0, ic[0]);
-    const AxisCells AY = axis_cells(g, 1, ic[1]);
-    const AxisCells AZ = axis_cells(g, 2, ic[2]);
-
-    for (uint32_t t0 = 0; t0 < ccount; t0 += 32) {
-      const bool active = t0 + lane < ccount;
-      const int64_t a = (int64_t)c0 + t0 + (active ? lane : 0);
-      const float4 pa = pos32[a];
-      const double xa = s.x[a], ya = s.y[a], za = s.z[a], ha = s.h[a];
-      const float two_h = 2.0f * pa.w;
-      const float lim = two_h * two_h;
-      const float esum = g.err32[0] + g.err32[1] + g.err32[2];
-      const float esq = g.err32[0] * g.err32[0] + g.err32[1] * g.err32[1] +
-                        g.err32[2] * g.err32[2];
-      const float margin = 2.0f * (2.0f * two_h * esum + esq + 4.76837158203125e-07f * lim);
-      const float lo_lim = lim - margin, hi_lim = lim + margin;
-      int cnt = 0;
-      uint32_t tested = 0, exact = 0;
-      for (int iz = 0; iz < AZ.cnt; ++iz)
-        for (int iy = 0; iy < AY.cnt; ++iy)
-          for (int ix = 0; ix < AX.cnt; ++ix) {
-            const uint32_t cc = morton3(AX.cell[ix], AY.cell[iy], AZ.cell[iz]);
-            const uint32_t b0 = tbl_start[cc], bn = tbl_count[cc];
-            const float sx = AX.shift[ix] * g.cs32[0];
-            const float sy = AY.shift[iy] * g.cs32[1];
-            const float sz = AZ.shift[iz] * g.cs32[2];
-            tested += bn;
-            for (uint32_t j = 0; j < bn; ++j) {
-              const int64_t b = (int64_t)b0 + j;
-              const float4 pb = pos32[b];
-              float dx = wrap32((pb.x + sx) - pa.x, g, 0);
-              float dy = wrap32((pb.y + sy) - pa.y, g, 1);
-              float dz = wrap32((pb.z + sz) - pa.z, g, 2);
-              float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-              bool hit;
-              if (r2 < lo_lim)
-                hit = true;
-              else if (r2 > hi_lim)
-                hit = false;
-              else {
-                hit = exact_neighbor(g, xa, ya, za, ha, s.x[b], s.y[b], s.z[b]);
-                exact += active ? 1u : 0u;
-              }
-              hit = hit && active && (b != a);
-              if (hit) {
-                if (cnt < max_nb) nbr[(int64_t)cnt * stride + a] = (int32_t)b;
-                ++cnt;
-              }
-            }
+    for (int w0 = 0; w0 < P; w0 += kFindWindow) {
+      const int wn = min(kFindWindow, P - w0);
+      const int wpad = (wn + 63) & ~63;
+      // stage slots [w0, w0 + wn) cell by cell (no per-slot search)
+      for (int sc = 0; sc < S.ncell; ++sc) {
+        const int lo = max(S.off[sc], w0), hi = min(S.off[sc + 1], w0 + wn);
+        const float sx = S.shift[sc][0], sy = S.shift[sc][1], sz = S.shift[sc][2];
+        for (int J = lo + lane; J < hi; J += 32) {
+          const float4 p = pos32[S.start[sc] + (J - S.off[sc])];
+          const int q = pair_index(J - w0);
+          W.cx[q] = p.x + sx;
+          W.cy[q] = p.y + sy;
+          W.cz[q] = p.z + sz;
+          W.code[J - w0] = entry_code(sc, J - S.off[sc]);
+        }
+      }
+      for (int i = wn + lane; i < wpad; i += 32) {
+        const int q = pair_index(i);
+        W.cx[q] = kFar;
+        W.cy[q] = kFar;
+        W.cz[q] = kFar;
+      }
+      __syncwarp();
+      for (int t0 = 0; t0 < na; t0 += 32) {
+        const int t = t0 + lane;
+        const bool active = t < na;
+        const int a = a0 + (active ? t : 0);
+        const float4 pa = pos32[a];
+        const float two_h = 2.0f * pa.w;
+        const float lim = two_h * two_h;
+        const float margin = 2.0f * (2.0f * two_h * esum + esq + 4.76837158203125e-07f * lim);
+        const float lo_lim = lim - margin, hi_lim = lim + margin;
+        const float2 npx = make_float2(-pa.x, -pa.x), npy = make_float2(-pa.y, -pa.y),
+                     npz = make_float2(-pa.z, -pa.z);
+        const int self = active ? S.self_slot0 + t - w0 : -1;
+        int k = (w0 == 0 || !active) ? 0 : nn[a];
+        for (int jb = 0; jb < wpad; jb += 64) {
+          uint64_t hit, unc;
+          block_masks<WRAP>(g, W.cx + jb, W.cy + jb, W.cz + jb, npx, npy, npz, lo_lim, hi_lim,
+                            hit, unc);
+          // candidates inside the margin: exact FP64 test
+          while (unc) {
+            const int q = __ffsll((long long)unc) - 1;
+            unc &= unc - 1;
+            const int b = entry_particle(S, W.code[jb + q]);
+            if (exact_neighbor(g, s.x[a], s.y[a], s.z[a], s.h[a], s.x[b], s.y[b], s.z[b]))
+              hit |= 1ull << q;
+            ++exact;
           }
-      if (active) {
-        nn[a] = cnt;
-        if (cnt > max_nb) raise_flag(err, SPH_FLAG_NB_OVERFLOW);
+          if (self >= jb && self < jb + 64) hit &= ~(1ull << (self - jb));
+          if (!active) hit = 0;
+          uint16_t* row = nbr + (int64_t)a * max_nb;
+          while (hit) {
+            const int q = __ffsll((long long)hit) - 1;
+            hit &= hit - 1;
+            if (k < max_nb) row[k] = W.code[jb + q];
+            ++k;
+          }
+        }
+        if (active) {
+          nn[a] = k;
+          if (k > max_nb) raise_flag(err, SPH_FLAG_NB_OVERFLOW);
+          tested += (unsigned long long)wn - (self >= 0 && self < wn ? 1 : 0);
+        }
       }
-      // counters: candidate tests of the active lanes and exact tests
-      unsigned long long t = active ? tested : 0u, e = exact;
-      for (int o = 16; o > 0; o >>= 1) {
-        t += __shfl_xor_sync(0xffffffffu, t, o);
-        e += __shfl_xor_sync(0xffffffffu, e, o);
-      }
-      if (lane == 0) {
-        atomicAdd(stats + 0, t);
-        atomicAdd(stats + 1, e);
-      }
+      __syncwarp();
     }
+  }
+  // counters: one atomic per warp
+  for (int o = 16; o > 0; o >>= 1) {
+    tested += __shfl_xor_sync(0xffffffffu, tested, o);
+    exact += __shfl_xor_sync(0xffffffffu, exact, o);
+  }
+  if (lane == 0) {
+    atomicAdd(stats + 0, tested);
+    atomicAdd(stats + 1, exact);
   }
 }
 
-// Export: ids of the neighbours of each particle, ascending (insertion sort).
-__global__ void k_export(int64_t n, const int32_t* nn, const int32_t* nbr, int64_t stride,
-                         int max_nb, const int64_t* id, int32_t* counts, int64_t* ids) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    int c = nn[p];
-    counts[p] = c;
-    int m = c < max_nb ? c : max_nb;
-    int64_t* row = ids + p * max_nb;
-    for (int k = 0; k < m; ++k) {
-      int64_t v = id[nbr[(int64_t)k * stride + p]];
-      int j = k - 1;
-      while (j >= 0 && row[j] > v) {
-        row[j + 1] = row[j];
-        --j;
+// Export: per cell, map each target's slots to global indices, then to ids
+// sorted ascending (insertion sort).
+__global__ void __launch_bounds__(128) k_export_tile(const Grid* gp, const uint32_t* occ,
+                                                     const uint32_t* tbl_start,
+                                                     const uint32_t* tbl_count, const int32_t* nn,
+                                                     const uint16_t* nbr, int max_nb,
+                                                     const int64_t* id, int32_t* counts,
+                                                     int64_t* ids) {
+  __shared__ Stencil S;
+  const Grid g = *gp;
+  for (uint32_t cell = blockIdx.x; cell < g.n_occ; cell += gridDim.x) {
+    build_stencil(g, occ[cell], tbl_start, tbl_count, S);
+    for (int t = threadIdx.x; t < S.na; t += blockDim.x) {
+      const int64_t a = S.a0 + t;
+      const int c = nn[a];
+      counts[a] = c;
+      const int m = c < max_nb ? c : max_nb;
+      int64_t* row = ids + a * max_nb;
+      for (int k = 0; k < m; ++k) {
+        const int64_t v = id[entry_particle(S, nbr[a * max_nb + k])];
+        int q = k - 1;
+        while (q >= 0 && row[q] > v) {
+          row[q + 1] = row[q];
+          --q;
+        }
+        row[q + 1] = v;
       }
-      row[j + 1] = v;
     }
+    __syncthreads();
   }
 }
+
+int g_find_blocks = 0;
 
 }  // namespace
 
 void launch_find_neighbors(sph_ctx* ctx, const StateView& s, int64_t n, cudaStream_t st) {
   (void)n;
-  int blocks = ctx->sm_count * 16;
-  k_find<<<blocks, 128, 0, st>>>(ctx->grid, s, ctx->pos32, ctx->occ, ctx->tbl_start,
-                                 ctx->tbl_count, ctx->nn, ctx->nbr, ctx->n_max, ctx->prm.max_nb,
-                                 ctx->err, ctx->stats);
-  ctx->launches += 1;
+  const size_t smem = kFindWarps * sizeof(FindWarpSmem);
+  if (!g_find_blocks) {
+    int per_sm = 0;
+    cudaFuncSetAttribute(k_find_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    cudaFuncSetAttribute(k_find_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_find_tile<false>, kFindThreads,
+                                                  smem);
+    g_find_blocks = (per_sm > 0 ? per_sm : 1) * ctx->sm_count;
+  }
+  k_find_tile<false><<<g_find_blocks, kFindThreads, smem, st>>>(
+      ctx->grid, s, ctx->pos32, ctx->occ, ctx->tbl_start, ctx->tbl_count, ctx->nn, ctx->nbr,
+      ctx->prm.max_nb, ctx->err, ctx->stats);
+  k_find_tile<true><<<g_find_blocks, kFindThreads, smem, st>>>(
+      ctx->grid, s, ctx->pos32, ctx->occ, ctx->tbl_start, ctx->tbl_count, ctx->nn, ctx->nbr,
+      ctx->prm.max_nb, ctx->err, ctx->stats);
+  ctx->launches += 2;
 }
 
 void launch_export_neighbors(sph_ctx* ctx, const StateView& s, int64_t n, int32_t* counts,
                              int64_t* ids, cudaStream_t st) {
-  int64_t b = (n + 127) / 128;
-  if (b > ctx->sm_count * 32) b = ctx->sm_count * 32;
-  if (b < 1) b = 1;
-  k_export<<<(int)b, 128, 0, st>>>(n, ctx->nn, ctx->nbr, ctx->n_max, ctx->prm.max_nb, s.id,
-                                   counts, ids);
+  (void)n;
+  k_export_tile<<<ctx->sm_count * 8, 128, 0, st>>>(ctx->grid, ctx->occ, ctx->tbl_start,
+                                                   ctx->tbl_count, ctx->nn, ctx->nbr,
+                                                   ctx->prm.max_nb, s.id, counts, ids);
   ctx->launches += 1;
 }
 

@@ -101,6 +101,9 @@ __global__ void k_grid_reduce(StateView in, int64_t n, sph_params prm, Grid* g, 
     G.periodic[ax] = per;
     maxnc = nc > maxnc ? nc : maxnc;
   }
+  G.wrap32 = 0;
+  for (int ax = 0; ax < 3; ++ax)
+    if (G.periodic[ax] && G.nc[ax] < 3) G.wrap32 = 1;
   int bits = 0;
   while ((1 << bits) < maxnc) ++bits;
   G.bits = bits;
@@ -311,7 +314,7 @@ __device__ __forceinline__ uint32_t compact3(uint32_t v) {
 
 __global__ void k_gather(StateView in, StateView out, int64_t n, const Grid* gp,
                          const int32_t* perm, const uint32_t* code, float4* pos32,
-                         int32_t* cell3, float4* vel32) {
+                         int32_t* cell3, float4* rec_d, float4* rec_m) {
   const Grid g = *gp;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
@@ -339,7 +342,8 @@ __global__ void k_gather(StateView in, StateView out, int64_t n, const Grid* gp,
     float oz = (float)(z - (g.lo[2] + iz * g.cs[2]));
     pos32[p] = make_float4(ox, oy, oz, (float)h);
     cell3[p] = pack_cell(ix, iy, iz);
-    vel32[p] = make_float4((float)vx, (float)vy, (float)vz, (float)m);
+    rec_d[p] = make_float4(ox, oy, oz, (float)m);
+    rec_m[5 * p + 1] = make_float4((float)vx, (float)vy, (float)vz, (float)m);
   }
 }
 
@@ -375,7 +379,7 @@ void launch_sort_gather(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream
                                                   ctx->tbl_count, ctx->perm_tmp, ctx->perm,
                                                   ctx->cell_of);
   k_gather<<<pb, 256, 0, st>>>(in, ctx->s, n, ctx->grid, ctx->perm, ctx->code, ctx->pos32,
-                               ctx->cell3, ctx->vel32);
+                               ctx->cell3, ctx->rec_d, ctx->rec_m);
   ctx->launches += 7;
 }
 
