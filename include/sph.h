@@ -110,7 +110,8 @@ typedef struct {
   double dt_growth;            /* max dt_n / dt_{n-1} [1.1]                     */
   int ng_target;               /* target neighbour count for h adaptation [100];
                                   0 keeps h fixed                               */
-  int max_nb;                  /* neighbour-list capacity per particle [160]    */
+  int max_nb;                  /* neighbour-list capacity per particle, a
+                                  multiple of 4 in [4, 4096] [160]              */
   double sinc_n;               /* exponent n of the sinc kernel, integer 1..12 [6] */
   int precision;               /* SPH_FP64 or SPH_FP32_MIXED [SPH_FP64]         */
   int kernel_mode;             /* SPH_KERNEL_EXACT                              */
@@ -120,7 +121,8 @@ typedef struct {
 /* Fills *p with the defaults above and a periodic unit box. */
 SPH_API void sph_default_params(sph_params* p);
 
-/* Creates a context for states of up to n_max particles on the current
+/* Creates a context for states of up to n_max particles (1 <= n_max <= 2^27)
+ * on the current
  * device, allocating the library-owned scratch (sort buffers, cell tables,
  * neighbour lists of n_max * max_nb int32, per-particle work arrays and
  * reduction buffers).  Computes B_n (the kernel normalisation of Eq. 6) on

@@ -9,6 +9,7 @@
 
 #include "sph_device.cuh"
 #include "sph_internal.cuh"
+#include "sph_tile.cuh"
 
 using sph::OutView;
 using sph::StateView;
@@ -68,8 +69,8 @@ int check_params(sph_ctx* ctx, const sph_params* p) {
   if (!(p->dt_growth >= 1.0))
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "dt_growth must be >= 1");
   if (p->ng_target < 0) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "ng_target < 0");
-  if (p->max_nb < 1 || p->max_nb > 4096)
-    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "max_nb must be in [1, 4096]");
+  if (p->max_nb < 4 || p->max_nb > 4096 || p->max_nb % 4 != 0)
+    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "max_nb must be a multiple of 4 in [4, 4096]");
   if (!(p->sinc_n >= 1.0 && p->sinc_n <= 12.0) || p->sinc_n != floor(p->sinc_n))
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "sinc_n must be an integer in [1, 12]");
   if (p->precision != SPH_FP64 && p->precision != SPH_FP32_MIXED)
@@ -240,7 +241,7 @@ int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {
   sph_ctx* ctx = (sph_ctx*)calloc(1, sizeof(sph_ctx));
   if (!ctx) return SPH_ERR_OOM;
   int rc = check_params(ctx, params);
-  if (rc != SPH_OK || n_max < 1 || n_max > (int64_t)1 << 31) {
+  if (rc != SPH_OK || n_max < 1 || n_max > sph::kMaxParticles) {
     free(ctx);
     return rc != SPH_OK ? rc : SPH_ERR_INVALID_ARG;
   }

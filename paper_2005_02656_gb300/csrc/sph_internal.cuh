@@ -92,9 +92,9 @@ struct sph_ctx {
   float4* pos32;        // offset from the cell origin (x, y, z) and h
   int32_t* cell3;       // packed cell coordinates (10 bits per axis)
 
-  // neighbour lists: nn[n], nbr[p * max_nb + k] = stencil slot (sph_tile.cuh)
+  // neighbour lists: nn[n], nbr[p * max_nb + k] = entry (sph_tile.cuh)
   int32_t* nn;
-  uint16_t* nbr;
+  uint32_t* nbr;
 
   // FP64 per-particle helpers: one block of 5 * n_max doubles
   double* vol;          // m / rho          (vol + 0 n_max)

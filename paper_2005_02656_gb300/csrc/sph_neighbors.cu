@@ -15,8 +15,8 @@
 //      are bit-identical to r^2 < (2h)^2 evaluated in FP64 without FMA;
 //   3. each lane appends its hits of the block, in slot order, from a 64-bit
 //      hit mask.
-// Lists are uint16 entry codes (sph_tile.cuh), row-major per particle:
-// nbr[a * max_nb + k], ascending.
+// Lists are uint32 entries (particle index + cell-shift code, sph_tile.cuh),
+// row-major per particle: nbr[a * max_nb + k], in stencil-slot order.
 #include <cuda_runtime.h>
 
 #include "sph_device.cuh"
@@ -54,7 +54,7 @@ struct FindWarpSmem {
   alignas(16) float cx[kFindWindow];
   alignas(16) float cy[kFindWindow];
   alignas(16) float cz[kFindWindow];
-  uint16_t code[kFindWindow];  // list entry of each staged slot
+  uint32_t entry[kFindWindow];  // list entry of each staged slot (sph_tile.cuh)
 };
 static_assert(sizeof(FindWarpSmem) % 16 == 0, "per-warp window must keep 16-byte alignment");
 
@@ -101,7 +101,7 @@ __device__ __forceinline__ void block_masks(const Grid& g, const float* cx, cons
 template <bool WRAP>
 __global__ void __launch_bounds__(kFindThreads) k_find_tile(
     const Grid* gp, StateView s, const float4* __restrict__ pos32, const uint32_t* occ,
-    const uint32_t* tbl_start, const uint32_t* tbl_count, int32_t* nn, uint16_t* nbr,
+    const uint32_t* tbl_start, const uint32_t* tbl_count, int32_t* nn, uint32_t* nbr,
     int max_nb, uint32_t* err, unsigned long long* stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kFindThreads) k_find_tile(
           W.cx[q] = p.x + sx;
           W.cy[q] = p.y + sy;
           W.cz[q] = p.z + sz;
-          W.code[J - w0] = entry_code(sc, J - S.off[sc]);
+          W.entry[J - w0] = entry_make(S.scode[sc], S.start[sc] + (J - S.off[sc]));
         }
       }
       for (int i = wn + lane; i < wpad; i += 32) {
@@ -167,18 +167,18 @@ __global__ void __launch_bounds__(kFindThreads) k_find_tile(
           while (unc) {
             const int q = __ffsll((long long)unc) - 1;
             unc &= unc - 1;
-            const int b = entry_particle(S, W.code[jb + q]);
+            const int b = entry_index(W.entry[jb + q]);
             if (exact_neighbor(g, s.x[a], s.y[a], s.z[a], s.h[a], s.x[b], s.y[b], s.z[b]))
               hit |= 1ull << q;
             ++exact;
           }
           if (self >= jb && self < jb + 64) hit &= ~(1ull << (self - jb));
           if (!active) hit = 0;
-          uint16_t* row = nbr + (int64_t)a * max_nb;
+          uint32_t* row = nbr + (int64_t)a * max_nb;
           while (hit) {
             const int q = __ffsll((long long)hit) - 1;
             hit &= hit - 1;
-            if (k < max_nb) row[k] = W.code[jb + q];
+            if (k < max_nb) row[k] = W.entry[jb + q];
             ++k;
           }
         }
@@ -202,35 +202,24 @@ __global__ void __launch_bounds__(kFindThreads) k_find_tile(
   }
 }
 
-// Export: per cell, map each target's slots to global indices, then to ids
-// sorted ascending (insertion sort).
-__global__ void __launch_bounds__(128) k_export_tile(const Grid* gp, const uint32_t* occ,
-                                                     const uint32_t* tbl_start,
-                                                     const uint32_t* tbl_count, const int32_t* nn,
-                                                     const uint16_t* nbr, int max_nb,
-                                                     const int64_t* id, int32_t* counts,
-                                                     int64_t* ids) {
-  __shared__ Stencil S;
-  const Grid g = *gp;
-  for (uint32_t cell = blockIdx.x; cell < g.n_occ; cell += gridDim.x) {
-    build_stencil(g, occ[cell], tbl_start, tbl_count, S);
-    for (int t = threadIdx.x; t < S.na; t += blockDim.x) {
-      const int64_t a = S.a0 + t;
-      const int c = nn[a];
-      counts[a] = c;
-      const int m = c < max_nb ? c : max_nb;
-      int64_t* row = ids + a * max_nb;
-      for (int k = 0; k < m; ++k) {
-        const int64_t v = id[entry_particle(S, nbr[a * max_nb + k])];
-        int q = k - 1;
-        while (q >= 0 && row[q] > v) {
-          row[q + 1] = row[q];
-          --q;
-        }
-        row[q + 1] = v;
+// Export: per particle, the neighbours' ids sorted ascending (insertion sort).
+__global__ void k_export(int64_t n, const int32_t* nn, const uint32_t* nbr, int max_nb,
+                         const int64_t* id, int32_t* counts, int64_t* ids) {
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    const int c = nn[a];
+    counts[a] = c;
+    const int m = c < max_nb ? c : max_nb;
+    int64_t* row = ids + a * max_nb;
+    for (int k = 0; k < m; ++k) {
+      const int64_t v = id[entry_index(nbr[a * max_nb + k])];
+      int q = k - 1;
+      while (q >= 0 && row[q] > v) {
+        row[q + 1] = row[q];
+        --q;
       }
+      row[q + 1] = v;
     }
-    __syncthreads();
   }
 }
 
@@ -262,10 +251,10 @@ void launch_find_neighbors(sph_ctx* ctx, const StateView& s, int64_t n, cudaStre
 
 void launch_export_neighbors(sph_ctx* ctx, const StateView& s, int64_t n, int32_t* counts,
                              int64_t* ids, cudaStream_t st) {
-  (void)n;
-  k_export_tile<<<ctx->sm_count * 8, 128, 0, st>>>(ctx->grid, ctx->occ, ctx->tbl_start,
-                                                   ctx->tbl_count, ctx->nn, ctx->nbr,
-                                                   ctx->prm.max_nb, s.id, counts, ids);
+  int64_t b = (n + 127) / 128;
+  if (b > (int64_t)ctx->sm_count * 32) b = ctx->sm_count * 32;
+  if (b < 1) b = 1;
+  k_export<<<(int)b, 128, 0, st>>>(n, ctx->nn, ctx->nbr, ctx->prm.max_nb, s.id, counts, ids);
   ctx->launches += 1;
 }
 

@@ -1,10 +1,13 @@
-// Cell tiles: the neighbour search and every pair kernel process one occupied
-// cell at a time.  The cell's 3x3x3 stencil (distinct cells only) is laid out
-// in a fixed order; slot j is the (j - off[s])-th particle of stencil cell s.
-// A neighbour-list entry is the uint16 code (s << kOffBits) | (j - off[s]),
-// so entries sorted by code are sorted by slot, and a kernel maps an entry to
-// its particle start[s] + offset and to the stencil shift of cell s with one
-// lookup in the cell's stencil.
+// Cell tiles: the neighbour search processes one occupied cell at a time.
+// The cell's 3x3x3 stencil (distinct cells only) is laid out in a fixed
+// order; slot j is the (j - off[s])-th particle of stencil cell s.
+//
+// A neighbour-list entry is a uint32: the neighbour's sorted particle index in
+// the low kIndexBits bits and, above them, the code (sx+1) + 3(sy+1) + 9(sz+1)
+// of the shift (-1, 0, +1 cell sides per axis) of the neighbour's cell
+// relative to the target's cell.  A pair kernel thus gets both the particle
+// and its FP32 position relative to the target's cell from the entry alone:
+// (offset_b + shift * cell side) - offset_a, with no table lookup.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -16,12 +19,27 @@
 namespace sph {
 
 constexpr int kMaxStencil = 27;
-constexpr int kMaxSlots = 65535;       // slots addressable by a window search
-constexpr int kOffBits = 11;           // list entry: stencil cell (5 bits), offset (11 bits)
-constexpr int kMaxCellPop = (1 << kOffBits) - 1;
+constexpr int kMaxSlots = 65535;       // stencil slots of one cell
+constexpr int kIndexBits = 27;         // list entry: particle index (27 bits)
+constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
+constexpr int64_t kMaxParticles = (int64_t)1 << kIndexBits;
+constexpr int kMaxCellPop = kMaxSlots;
 
-__host__ __device__ __forceinline__ uint16_t entry_code(int cell, int off) {
-  return (uint16_t)((cell << kOffBits) | off);
+__host__ __device__ __forceinline__ int shift_code(int sx, int sy, int sz) {
+  return (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1);
+}
+__host__ __device__ __forceinline__ uint32_t entry_make(int code, int particle) {
+  return ((uint32_t)code << kIndexBits) | (uint32_t)particle;
+}
+__device__ __forceinline__ int entry_index(uint32_t e) { return (int)(e & kIndexMask); }
+// FP32 shift of the entry's cell relative to the target's cell.
+__device__ __forceinline__ void entry_shift(uint32_t e, const Grid& g, float& sx, float& sy,
+                                            float& sz) {
+  const int c = (int)(e >> kIndexBits);
+  const int cz = c / 9, cy = (c - 9 * cz) / 3, cx = c - 9 * cz - 3 * cy;
+  sx = (float)(cx - 1) * g.cs32[0];
+  sy = (float)(cy - 1) * g.cs32[1];
+  sz = (float)(cz - 1) * g.cs32[2];
 }
 
 struct alignas(16) Stencil {
@@ -31,6 +49,7 @@ struct alignas(16) Stencil {
   int start[kMaxStencil];         // first sorted index of each stencil cell
   int off[kMaxStencil + 1];       // slot prefix; off[ncell] = total slots
   float shift[kMaxStencil][3];    // stencil-cell origin minus target-cell origin (FP32)
+  int scode[kMaxStencil];         // shift code of each stencil cell (list entries)
   int maxpop;                     // largest stencil-cell population
 };
 
@@ -75,59 +94,8 @@ __device__ __forceinline__ uint32_t compact3_bits(uint32_t v) {
   return v;
 }
 
-// Builds the stencil of occupied cell `code` into shared memory.  Must be
-// called by the whole CTA (contains __syncthreads); warp 0 does the work.
-__device__ __forceinline__ void build_stencil(const Grid& g, uint32_t code,
-                                              const uint32_t* tbl_start,
-                                              const uint32_t* tbl_count, Stencil& S) {
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    const int ic[3] = {(int)compact3_bits(code), (int)compact3_bits(code >> 1),
-                       (int)compact3_bits(code >> 2)};
-    const int nx = axis_count(g, 0, ic[0]);
-    const int ny = axis_count(g, 1, ic[1]);
-    const int nz = axis_count(g, 2, ic[2]);
-    const int ncell = nx * ny * nz;
-    int cnt = 0;
-    bool self = false;
-    if (lane < ncell) {
-      int cx, cy, cz, sx, sy, sz;
-      axis_cell(g, 0, ic[0], lane % nx, cx, sx);
-      axis_cell(g, 1, ic[1], (lane / nx) % ny, cy, sy);
-      axis_cell(g, 2, ic[2], lane / (nx * ny), cz, sz);
-      const uint32_t cc = morton3(cx, cy, cz);
-      S.start[lane] = (int)tbl_start[cc];
-      cnt = (int)tbl_count[cc];
-      S.shift[lane][0] = sx * g.cs32[0];
-      S.shift[lane][1] = sy * g.cs32[1];
-      S.shift[lane][2] = sz * g.cs32[2];
-      self = sx == 0 && sy == 0 && sz == 0;
-    }
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    if (lane < ncell) S.off[lane] = incl - cnt;
-    if (lane == ncell - 1) S.off[ncell] = incl;
-    if (self) {
-      S.self_slot0 = incl - cnt;
-      S.a0 = S.start[lane];
-      S.na = cnt;
-    }
-    int mp = cnt;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mp = max(mp, __shfl_xor_sync(0xffffffffu, mp, o));
-    if (lane == 0) {
-      S.ncell = ncell;
-      S.maxpop = mp;
-    }
-  }
-  __syncthreads();
-}
-
-// Same as build_stencil for one warp that owns its Stencil (no CTA barrier).
+// Builds the stencil of occupied cell `code` into the warp's shared-memory
+// Stencil (warp-synchronous; no CTA barrier).
 __device__ __forceinline__ void build_stencil_warp(const Grid& g, uint32_t code,
                                                    const uint32_t* tbl_start,
                                                    const uint32_t* tbl_count, Stencil& S) {
@@ -151,6 +119,7 @@ __device__ __forceinline__ void build_stencil_warp(const Grid& g, uint32_t code,
     S.shift[lane][0] = sx * g.cs32[0];
     S.shift[lane][1] = sy * g.cs32[1];
     S.shift[lane][2] = sz * g.cs32[2];
+    S.scode[lane] = shift_code(sx, sy, sz);
     self = sx == 0 && sy == 0 && sz == 0;
   }
   int incl = cnt;
@@ -176,35 +145,6 @@ __device__ __forceinline__ void build_stencil_warp(const Grid& g, uint32_t code,
   __syncwarp();
 }
 
-// Particle index of list entry e.
-__device__ __forceinline__ int entry_particle(const Stencil& S, uint32_t e) {
-  return S.start[e >> kOffBits] + (int)(e & kMaxCellPop);
-}
 
-// Stencil cell holding slot j (binary search over off[0..ncell]).
-__device__ __forceinline__ int slot_cell(const Stencil& S, int j) {
-  int lo = 0, hi = S.ncell - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (S.off[mid] <= j)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ int slot_global(const Stencil& S, int j) {
-  const int s = slot_cell(S, j);
-  return S.start[s] + (j - S.off[s]);
-}
-
-// Threads per target for a cell of `na` targets on a CTA of `threads`:
-// the largest power of two <= threads / na, at most kMaxTpp.
-__device__ __forceinline__ int threads_per_target(int na, int threads, int max_tpp) {
-  int t = 1;
-  while (t < max_tpp && (t * 2) * na <= threads) t *= 2;
-  return t;
-}
 
 }  // namespace sph
