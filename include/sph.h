@@ -204,6 +204,25 @@ SPH_API int sph_error_word(sph_ctx* ctx, uint32_t* flags);
 /* Message of the last failing call on this context ("" if none). */
 SPH_API const char* sph_last_error(const sph_ctx* ctx);
 
+/* The conservation sums of sph_diagnostics for callers that cannot allocate
+ * device memory: code that runs while a CUDA graph is being captured (an
+ * allocation there would fail the capture), code inside a host callback, or a
+ * host that owns the whole device memory through its own pool and forbids
+ * other allocations.  No context is needed and nothing is allocated: the
+ * per-block partial sums live in a file-scope static device array of about
+ * 512 KB that every device loading the library holds until the process exits.
+ * The paper has no counterpart; it is an interface convenience.
+ *   state: as for sph_diagnostics; only x y z vx vy vz m u and n are read
+ *          (device arrays); n must be <= 16,777,216, larger states are
+ *          rejected with SPH_ERR_INVALID_ARG.
+ *   out:   HOST array of 8, filled as by sph_diagnostics.
+ * The first call on a device, with that device current, looks up the static
+ * array's device address; make that first call before any stream capture.
+ * All calls share the static array: calls that overlap on the GPU (other
+ * streams or host threads) race.  Synchronises the stream.  Returns SPH_OK,
+ * SPH_ERR_INVALID_ARG or SPH_ERR_CUDA. */
+SPH_API int sph_diagnostics_noalloc(const sph_state* state, double* out, sph_stream_t stream);
+
 /* Stages of sph_step timed by sph_profile. */
 enum {
   SPH_STAGE_SORT = 0,     /* grid, Morton counting sort, gather          */

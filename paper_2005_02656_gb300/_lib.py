@@ -39,7 +39,7 @@ EXPORTS = ("sph_default_params", "sph_init", "sph_destroy", "sph_set_params", "s
            "sph_find_neighbors", "sph_get_neighbors", "sph_density", "sph_iad",
            "sph_momentum_energy", "sph_step", "sph_step_host", "sph_diagnostics",
            "sph_last_diagnostics", "sph_error_word", "sph_last_error", "sph_launch_count",
-           "sph_profile", "sph_stage_times", "sph_stats")
+           "sph_profile", "sph_stage_times", "sph_stats", "sph_diagnostics_noalloc")
 STAGES = ("sort", "find", "density", "iad", "momentum", "dt", "update")
 
 
@@ -109,6 +109,8 @@ def load(path: str = LIB_PATH):
     lib.sph_last_error.restype = C.c_char_p
     lib.sph_launch_count.argtypes = [ctxp]
     lib.sph_launch_count.restype = I64
+    lib.sph_diagnostics_noalloc.argtypes = [sp, P, P]
+    lib.sph_diagnostics_noalloc.restype = I
     lib.sph_stats.argtypes = [ctxp, P]
     lib.sph_stats.restype = I
     lib.sph_profile.argtypes = [ctxp, I]
