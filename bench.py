@@ -44,7 +44,7 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--nx", type=int, default=KH_NX, help="outer lattice of the KH box")
@@ -69,49 +69,60 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling of SM clocks and throttle reasons.  One sampler runs
+    for the whole benchmark (it needs about a second before its first
+    sample); each timed region is summarised from the samples inside it."""
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.p = None
+        self.samples = []
 
     def start(self):
         try:
             self.p = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
 
     def stop(self):
+        import datetime
         if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+            return
         self.p.terminate()
         try:
             out, _ = self.p.communicate(timeout=5)
         except Exception:
             self.p.kill()
             out = ""
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 8:
+            if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[0]))
-                mx = float(f[1])
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                clk, mxc = float(f[1]), float(f[2])
             except ValueError:
                 continue
-            for nm, v in zip(names, f[4:8]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "samples": len(sm), "reasons": sorted(reasons)}
+            reasons = {nm for nm, v in zip(self.NAMES, f[5:9]) if v.lower().startswith("active")}
+            self.samples.append((ts, clk, mxc, reasons))
+
+    def summary(self, t0, t1):
+        """Samples taken between host times t0 and t1 (0.15 s allowance for
+        the sampler's reporting delay)."""
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "samples": 0, "reasons": ["unsampled"]}
+        sel = [s for s in self.samples if t0 - 0.15 <= s[0] <= t1 + 0.15]
+        reasons = sorted(set().union(*[s[3] for s in sel])) if sel else []
+        return {"sm_mhz": statistics.median([s[1] for s in sel]) if sel else None,
+                "sm_max_mhz": sel[-1][2] if sel else None, "samples": len(sel),
+                "reasons": reasons}
 
 
 def source_hash(name):
@@ -133,6 +144,22 @@ def traffic_for(kernel_key):
     return t["bytes_per_launch"]
 
 
+def reduce_max(value, dist, device):
+    """Max of a float over the ranks of the process group (identity alone)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(n_per_rank, world, ms_max):
+    """Particle updates per second of all ranks: every rank advances its own
+    box of n_per_rank particles; the slowest rank sets the time."""
+    return n_per_rank * world / (ms_max * 1e-3)
+
+
 def run_gpu(args, world, rank, local):
     import numpy as np
     import torch
@@ -152,12 +179,11 @@ def run_gpu(args, world, rank, local):
             dist.barrier()
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, dist, dev)
 
+    clocks = Clocks(local)
+    clocks.start()
+    windows = {}
     state = sph_inputs.kelvin_helmholtz(args.nx, seed_index=2)
     n = int(state["x"].shape[0])
 
@@ -171,19 +197,19 @@ def run_gpu(args, world, rank, local):
         sim.stage_times()
         st0 = sim.stats()
         l0 = sim.launch_count()
-        clocks = Clocks(local)
         barrier()
         torch.cuda.synchronize()
-        clocks.start()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        tw0 = time.time()
         e0.record(stream)
         for _ in range(args.steps):
             sim.step()
         e1.record(stream)
         torch.cuda.synchronize()
+        tw1 = time.time()
         barrier()
-        ck = clocks.stop()
+        windows[precision] = (tw0, tw1)
         ms = e0.elapsed_time(e1) / args.steps
         stages, nsteps = sim.stage_times()
         st1 = sim.stats()
@@ -198,7 +224,7 @@ def run_gpu(args, world, rank, local):
         exact = (st1["exact_tests"] - st0["exact_tests"]) / args.steps
         return {"ms": ms, "stages": {k: v / max(nsteps, 1) for k, v in stages.items()},
                 "pairs": pairs, "candidates": cands, "exact_tests": exact, "launches": launches,
-                "flags": flags, "clocks": ck, "dt": float(diag[8])}
+                "flags": flags, "dt": float(diag[8])}
 
     r32 = timed("fp32_mixed")
     r64 = None if args.no_fp64 else timed("fp64")
@@ -220,10 +246,14 @@ def run_gpu(args, world, rank, local):
         h2d, d2h = hs.bytes_per_step()
         hs.close()
         ms_e2e = max_over_ranks((t1 - t0) * 1e3 / args.steps)
-        e2e = {"value": n * world / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
+        e2e = {"value": whole_job_rate(n, world, ms_e2e), "unit": UNIT, "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "path": "sph_step_host (pinned host state, FP32-mixed)"}
 
+    clocks.stop()
+    for key, r in (("fp32_mixed", r32), ("fp64", r64)):
+        if r is not None:
+            r["clocks"] = clocks.summary(*windows[key])
     ms32 = max_over_ranks(r32["ms"])
     res = {"n": n, "r32": r32, "r64": r64, "ms32": ms32, "e2e": e2e}
     if r64 is not None:
@@ -295,7 +325,7 @@ def main():
     n = res["n"]
     r32, r64 = res["r32"], res["r64"]
     ms = res["ms32"]
-    value = n * world / (ms * 1e-3)
+    value = whole_job_rate(n, world, ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -315,7 +345,7 @@ def main():
     }
     if r64 is not None:
         ms64 = res["ms64"]
-        line["fp64"] = {"value": n * world / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+        line["fp64"] = {"value": whole_job_rate(n, world, ms64), "unit": UNIT, "ms_per_step": ms64,
                         "neighbor_pairs_per_s": r64["pairs"] * world / (ms64 * 1e-3),
                         "stages_ms": r64["stages"], "roofline": roofline(r64, n, "fp64"),
                         "gpu_launches": r64["launches"], "error_flags": r64["flags"],
