@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--ensemble-steps", type=int, default=50)
     return ap.parse_args()
 
 
@@ -250,17 +252,63 @@ def run_gpu(args, world, rank, local):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "path": "sph_step_host (pinned host state, FP32-mixed)"}
 
+    ens = None
+    if not args.no_ensemble:
+        ens = run_ensemble(args, dev, windows)
+
     clocks.stop()
+    if ens is not None:
+        ens["clocks"] = clocks.summary(*windows["ensemble"])
     for key, r in (("fp32_mixed", r32), ("fp64", r64)):
         if r is not None:
             r["clocks"] = clocks.summary(*windows[key])
     ms32 = max_over_ranks(r32["ms"])
-    res = {"n": n, "r32": r32, "r64": r64, "ms32": ms32, "e2e": e2e}
+    res = {"n": n, "r32": r32, "r64": r64, "ms32": ms32, "e2e": e2e, "ensemble": ens}
     if r64 is not None:
         res["ms64"] = max_over_ranks(r64["ms"])
     if dist is not None:
         dist.destroy_process_group()
     return res
+
+
+def run_ensemble(args, dev, windows):
+    """Batched ensemble: 256 periodic jittered boxes (sides log-uniform in
+    [8, 48], alpha uniform in [0.5, 1.5]), FP32-mixed, autotuned, the given
+    number of steps captured as one CUDA graph of one persistent launch."""
+    import torch
+
+    import sph_inputs
+    from paper_2005_02656_gb300 import Ensemble
+    boxes = sph_inputs.ensemble(256)
+    ens = Ensemble(boxes, device=dev)
+    tune = ens.autotune(steps=2)
+    ens.step(3)                                   # warm-up steps of the tuned kernel
+    ens.capture(args.ensemble_steps)
+    ens.replay()                                  # warm-up replay
+    ens.synchronize()
+    l0 = ens.info()["launches"]
+    stream = ens._graph_stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    tw0 = time.time()
+    e0.record(stream)
+    ens.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    windows["ensemble"] = (tw0, time.time())
+    ms = e0.elapsed_time(e1)
+    flags = ens.error_word()
+    info = ens.info()
+    n = info["particles"]
+    ens.close()
+    return {"metric": "particle-updates/s, 256-box ensemble, one persistent launch per "
+                      f"{args.ensemble_steps}-step CUDA graph", "value": n * args.ensemble_steps / (ms * 1e-3),
+            "unit": UNIT, "n_particles": n, "n_boxes": 256, "steps": args.ensemble_steps,
+            "ms_per_step": ms / args.ensemble_steps, "gpu_launches": info["launches"] - l0,
+            "persistent_ctas": info["ctas"], "error_flags": flags,
+            "autotune": {"cell_factor": tune["cell_factor"], "blocks_per_sm": tune["blocks_per_sm"],
+                         "tried": [{"s_per_step": t, "cell_factor": c, "blocks_per_sm": b}
+                                   for t, c, b in tune["tried"]]}}
 
 
 def roofline(r, n, precision):
@@ -352,6 +400,8 @@ def main():
                         "clocks": r64["clocks"]}
         line["fp32_mixed_over_fp64"] = ms64 / ms
     line["e2e"] = res["e2e"]
+    if res.get("ensemble") is not None:
+        line["ensemble"] = res["ensemble"]
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

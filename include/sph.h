@@ -223,6 +223,60 @@ SPH_API const char* sph_last_error(const sph_ctx* ctx);
  * SPH_ERR_INVALID_ARG or SPH_ERR_CUDA. */
 SPH_API int sph_diagnostics_noalloc(const sph_state* state, double* out, sph_stream_t stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batched ensemble: independent boxes of uneven sizes, each with its own    */
+/* box, periodicity, viscosity alpha and time step, advanced together by one */
+/* persistent cooperative kernel per call (the single-box pipeline, phase by */
+/* phase over all boxes, FP32-mixed).  The launch can be captured in a CUDA  */
+/* graph and replayed.  Phases are separated by a device-side grid barrier   */
+/* whose wait is bounded (about 2 s): on expiry the kernel sets              */
+/* SPH_FLAG_TIMEOUT and returns; sph_ensemble_error_word reads and clears it */
+/* and re-arms the barrier.                                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct sph_ens sph_ens;
+
+/* Tuning knobs of the ensemble kernel (picked by the Python autotuner). */
+typedef struct {
+  double cell_factor;  /* cells of side >= cell_factor * 2 h_max, in [1, 4] [1]   */
+  int blocks_per_sm;   /* persistent CTAs per SM, 0 = the occupancy maximum [0]   */
+  int test_skip_block; /* test hook: this CTA leaves before the first barrier so
+                          the others' bounded wait expires; -1 disables [-1]     */
+} sph_ens_config;
+
+SPH_API void sph_ens_default_config(sph_ens_config* c);
+
+/* Creates an ensemble of n_boxes boxes.  Box b owns particles
+ * [sum_{c<b} box_n[c], ... + box_n[b]) of the concatenated state; box_lo,
+ * box_hi (3 per box) and box_periodic (3 per box) describe it, box_alpha[b] is
+ * its viscosity coefficient (Eq. 5).  common: gamma, courant, dt_growth,
+ * ng_target, max_nb, sinc_n and precision (must be SPH_FP32_MIXED) shared by
+ * all boxes.  All pointers are HOST arrays.  Allocates the device scratch
+ * (about 1 KB per particle at max_nb = 160). */
+SPH_API int sph_ensemble_init(const sph_params* common, int n_boxes, const int64_t* box_n,
+                              const double* box_lo, const double* box_hi,
+                              const int* box_periodic, const double* box_alpha, sph_ens** out);
+SPH_API void sph_ensemble_destroy(sph_ens* e);
+SPH_API int sph_ensemble_set_config(sph_ens* e, const sph_ens_config* c);
+
+/* Advances every box by `steps` steps in one persistent launch.  state: the
+ * concatenated state (device arrays, n = total particles; each box's range is
+ * reordered in place as by sph_step); dt: DEVICE array of n_boxes doubles,
+ * dt_{n-1} per box on entry (0 before the first step), dt_n on return. */
+SPH_API int sph_ensemble_step(sph_ens* e, sph_state* state, double* dt, int steps,
+                              sph_stream_t stream);
+
+/* Captures the launch of sph_ensemble_step(state, dt, steps) into a CUDA graph
+ * (stream must not be the legacy default stream); sph_ensemble_replay then
+ * launches the graph, advancing the same arrays by `steps` more steps. */
+SPH_API int sph_ensemble_capture(sph_ens* e, sph_state* state, double* dt, int steps,
+                                 sph_stream_t stream);
+SPH_API int sph_ensemble_replay(sph_ens* e, sph_stream_t stream);
+
+SPH_API int sph_ensemble_error_word(sph_ens* e, uint32_t* flags);
+SPH_API const char* sph_ensemble_last_error(const sph_ens* e);
+/* out[0] particles, out[1] boxes, out[2] persistent CTAs, out[3] launches. */
+SPH_API int sph_ensemble_info(const sph_ens* e, int64_t* out);
+
 /* Stages of sph_step timed by sph_profile. */
 enum {
   SPH_STAGE_SORT = 0,     /* grid, Morton counting sort, gather          */

@@ -12,4 +12,7 @@ def __getattr__(name):
     if name in ("SphSim", "Params", "HostStepper"):
         from . import sim
         return getattr(sim, name)
+    if name == "Ensemble":
+        from .ensemble import Ensemble
+        return Ensemble
     raise AttributeError(name)

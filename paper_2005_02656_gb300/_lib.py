@@ -39,7 +39,11 @@ EXPORTS = ("sph_default_params", "sph_init", "sph_destroy", "sph_set_params", "s
            "sph_find_neighbors", "sph_get_neighbors", "sph_density", "sph_iad",
            "sph_momentum_energy", "sph_step", "sph_step_host", "sph_diagnostics",
            "sph_last_diagnostics", "sph_error_word", "sph_last_error", "sph_launch_count",
-           "sph_profile", "sph_stage_times", "sph_stats", "sph_diagnostics_noalloc")
+           "sph_profile", "sph_stage_times", "sph_stats", "sph_diagnostics_noalloc",
+           "sph_ens_default_config", "sph_ensemble_init", "sph_ensemble_destroy",
+           "sph_ensemble_set_config", "sph_ensemble_step", "sph_ensemble_capture",
+           "sph_ensemble_replay", "sph_ensemble_error_word", "sph_ensemble_last_error",
+           "sph_ensemble_info")
 STAGES = ("sort", "find", "density", "iad", "momentum", "dt", "update")
 
 
@@ -55,6 +59,11 @@ class SphParams(C.Structure):
         ("sinc_n", C.c_double), ("precision", C.c_int), ("kernel_mode", C.c_int),
         ("gradh", C.c_int),
     ]
+
+
+class EnsConfig(C.Structure):
+    _fields_ = [("cell_factor", C.c_double), ("blocks_per_sm", C.c_int),
+                ("test_skip_block", C.c_int)]
 
 
 class SphError(RuntimeError):
@@ -109,6 +118,27 @@ def load(path: str = LIB_PATH):
     lib.sph_last_error.restype = C.c_char_p
     lib.sph_launch_count.argtypes = [ctxp]
     lib.sph_launch_count.restype = I64
+    ep = C.POINTER(EnsConfig)
+    lib.sph_ens_default_config.argtypes = [ep]
+    lib.sph_ens_default_config.restype = None
+    lib.sph_ensemble_init.argtypes = [pp, I, P, P, P, P, P, C.POINTER(ctxp)]
+    lib.sph_ensemble_init.restype = I
+    lib.sph_ensemble_destroy.argtypes = [ctxp]
+    lib.sph_ensemble_destroy.restype = None
+    lib.sph_ensemble_set_config.argtypes = [ctxp, ep]
+    lib.sph_ensemble_set_config.restype = I
+    for name in ("sph_ensemble_step", "sph_ensemble_capture"):
+        f = getattr(lib, name)
+        f.argtypes = [ctxp, sp, P, I, P]
+        f.restype = I
+    lib.sph_ensemble_replay.argtypes = [ctxp, P]
+    lib.sph_ensemble_replay.restype = I
+    lib.sph_ensemble_error_word.argtypes = [ctxp, C.POINTER(C.c_uint32)]
+    lib.sph_ensemble_error_word.restype = I
+    lib.sph_ensemble_last_error.argtypes = [ctxp]
+    lib.sph_ensemble_last_error.restype = C.c_char_p
+    lib.sph_ensemble_info.argtypes = [ctxp, P]
+    lib.sph_ensemble_info.restype = I
     lib.sph_diagnostics_noalloc.argtypes = [sp, P, P]
     lib.sph_diagnostics_noalloc.restype = I
     lib.sph_stats.argtypes = [ctxp, P]

@@ -1,0 +1,193 @@
+// The neighbour search of one occupied cell by one warp (findNeighbors,
+// section 4.1: b runs over the particles inside the kernel support
+// |x_a - x_b| < 2 h_a), shared by the single-box kernel (sph_neighbors.cu) and
+// the ensemble's persistent kernel (sph_ensemble.cu).
+//
+// The cell's stencil particles are staged in the warp's shared-memory window
+// as FP32 positions relative to the cell's origin (offset to their own cell +
+// the stencil shift).  Lane t owns target t of the cell (32 at a time) and
+// walks the staged candidates in blocks of 64, all lanes reading the same
+// candidate pair (broadcast loads, paired FP32 arithmetic on candidates j and
+// j + 32 of the block):
+//   1. FP32 prefilter: r2_32 against (2 h_a)^2 within a margin M_a that
+//      bounds the FP32 rounding of the separation (Grid::err32) and of the
+//      squares; outside the margin the FP32 decision is exact;
+//   2. inside the margin, the exact FP64 criterion (exact_neighbor), so lists
+//      are bit-identical to r^2 < (2h)^2 evaluated in FP64 without FMA;
+//   3. each lane appends its hits of the block, in slot order, from a 64-bit
+//      hit mask.
+// Lists are uint32 entries (particle index + cell-shift code, sph_tile.cuh),
+// row-major per particle: nbr[a * max_nb + k], in stencil-slot order.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sph_device.cuh"
+#include "sph_internal.cuh"
+#include "sph_tile.cuh"
+
+namespace sph {
+namespace find {
+
+constexpr int kFindWarps = 4;
+constexpr int kFindThreads = 32 * kFindWarps;
+constexpr int kFindWindow = 768;   // staged candidates per warp and pass (9 KB)
+constexpr float kFar = 1.0e18f;    // position of padding slots (never a neighbour)
+
+__device__ __forceinline__ float wrap_axis(float d, const Grid& g, int ax) {
+  if (d > g.halfL32[ax])
+    d -= g.L32[ax];
+  else if (d < -g.halfL32[ax])
+    d += g.L32[ax];
+  return d;
+}
+
+// Shared-memory layout of a window: per block of 64 slots, the x (y, z)
+// coordinates as 32 float2 pairs (slot q, slot q + 32), so one 8-byte load
+// gives the pair processed by one paired FP32 instruction.
+__device__ __forceinline__ int pair_index(int i) {
+  const int blk = i >> 6, r = i & 63;
+  return (blk << 6) + ((r & 31) << 1) + (r >> 5);
+}
+
+struct FindWarpSmem {
+  Stencil S;
+  // 16-byte aligned: the candidate arrays are read as float2 pairs
+  alignas(16) float cx[kFindWindow];
+  alignas(16) float cy[kFindWindow];
+  alignas(16) float cz[kFindWindow];
+  uint32_t entry[kFindWindow];  // list entry of each staged slot (sph_tile.cuh)
+};
+static_assert(sizeof(FindWarpSmem) % 16 == 0, "per-warp window must keep 16-byte alignment");
+
+// Hit and margin masks of one block of 64 staged candidates for one target.
+// The decisions r2 < lo and r2 < hi are read from the sign bits of r2 - lo and
+// r2 - hi, with the limit folded into the first fused multiply-add (the margin
+// is twice the error bound, so a strict "< hi" is as safe as "<= hi").
+template <bool WRAP>
+__device__ __forceinline__ void block_masks(const Grid& g, const float* cx, const float* cy,
+                                            const float* cz, float2 npx, float2 npy, float2 npz,
+                                            float lo_lim, float hi_lim, uint64_t& hit,
+                                            uint64_t& unc) {
+  const float2* X = reinterpret_cast<const float2*>(cx);
+  const float2* Y = reinterpret_cast<const float2*>(cy);
+  const float2* Z = reinterpret_cast<const float2*>(cz);
+  const float2 nlo = make_float2(-lo_lim, -lo_lim);
+  const float2 dlh = make_float2(lo_lim - hi_lim, lo_lim - hi_lim);
+  uint32_t hA = 0, hB = 0, uA = 0, uB = 0;
+#pragma unroll 8
+  for (int q = 0; q < 32; ++q) {
+    float2 dx = __fadd2_rn(X[q], npx);
+    float2 dy = __fadd2_rn(Y[q], npy);
+    float2 dz = __fadd2_rn(Z[q], npz);
+    if (WRAP) {
+      if (g.periodic[0]) dx = make_float2(wrap_axis(dx.x, g, 0), wrap_axis(dx.y, g, 0));
+      if (g.periodic[1]) dy = make_float2(wrap_axis(dy.x, g, 1), wrap_axis(dy.y, g, 1));
+      if (g.periodic[2]) dz = make_float2(wrap_axis(dz.x, g, 2), wrap_axis(dz.y, g, 2));
+    }
+    float2 t = __ffma2_rn(dx, dx, nlo);   // r2 - lo
+    t = __ffma2_rn(dy, dy, t);
+    t = __ffma2_rn(dz, dz, t);
+    const float2 u = __fadd2_rn(t, dlh);   // r2 - hi
+    hA |= (__float_as_uint(t.x) >> 31) << q;
+    hB |= (__float_as_uint(t.y) >> 31) << q;
+    uA |= (__float_as_uint(u.x) >> 31) << q;
+    uB |= (__float_as_uint(u.y) >> 31) << q;
+  }
+  hit = (uint64_t)hA | ((uint64_t)hB << 32);
+  unc = ((uint64_t)uA | ((uint64_t)uB << 32)) & ~hit;
+}
+
+// Builds the lists of every target of occupied cell `code` (one warp; the
+// warp owns W).  Counts tested candidates and exact FP64 tests.
+template <bool WRAP>
+__device__ __forceinline__ void find_cell(const Grid& g, uint32_t code, const StateView& s,
+                                          const float4* __restrict__ pos32,
+                                          const uint32_t* tbl_start, const uint32_t* tbl_count,
+                                          int32_t* nn, uint32_t* nbr, int max_nb, uint32_t* err,
+                                          FindWarpSmem& W, unsigned long long& tested,
+                                          unsigned long long& exact) {
+  const int lane = threadIdx.x & 31;
+  Stencil& S = W.S;
+  const float esum = g.err32[0] + g.err32[1] + g.err32[2];
+  const float esq = g.err32[0] * g.err32[0] + g.err32[1] * g.err32[1] + g.err32[2] * g.err32[2];
+  build_stencil_warp(g, code, tbl_start, tbl_count, S);
+  const int P = S.off[S.ncell];
+  const int a0 = S.a0, na = S.na;
+  if (P > kMaxSlots || S.maxpop > kMaxCellPop) {
+    for (int t = lane; t < na; t += 32) nn[a0 + t] = 0;
+    if (lane == 0) raise_flag(err, SPH_FLAG_CELL_OVERFLOW);
+    __syncwarp();
+    return;
+  }
+  for (int w0 = 0; w0 < P; w0 += kFindWindow) {
+    const int wn = min(kFindWindow, P - w0);
+    const int wpad = (wn + 63) & ~63;
+    // stage slots [w0, w0 + wn) cell by cell (no per-slot search)
+    for (int sc = 0; sc < S.ncell; ++sc) {
+      const int lo = max(S.off[sc], w0), hi = min(S.off[sc + 1], w0 + wn);
+      const float sx = S.shift[sc][0], sy = S.shift[sc][1], sz = S.shift[sc][2];
+      for (int J = lo + lane; J < hi; J += 32) {
+        const float4 p = pos32[S.start[sc] + (J - S.off[sc])];
+        const int q = pair_index(J - w0);
+        W.cx[q] = p.x + sx;
+        W.cy[q] = p.y + sy;
+        W.cz[q] = p.z + sz;
+        W.entry[J - w0] = entry_make(S.scode[sc], S.start[sc] + (J - S.off[sc]));
+      }
+    }
+    for (int i = wn + lane; i < wpad; i += 32) {
+      const int q = pair_index(i);
+      W.cx[q] = kFar;
+      W.cy[q] = kFar;
+      W.cz[q] = kFar;
+    }
+    __syncwarp();
+    for (int t0 = 0; t0 < na; t0 += 32) {
+      const int t = t0 + lane;
+      const bool active = t < na;
+      const int a = a0 + (active ? t : 0);
+      const float4 pa = pos32[a];
+      const float two_h = 2.0f * pa.w;
+      const float lim = two_h * two_h;
+      const float margin = 2.0f * (2.0f * two_h * esum + esq + 4.76837158203125e-07f * lim);
+      const float lo_lim = lim - margin, hi_lim = lim + margin;
+      const float2 npx = make_float2(-pa.x, -pa.x), npy = make_float2(-pa.y, -pa.y),
+                   npz = make_float2(-pa.z, -pa.z);
+      const int self = active ? S.self_slot0 + t - w0 : -1;
+      int k = (w0 == 0 || !active) ? 0 : nn[a];
+      for (int jb = 0; jb < wpad; jb += 64) {
+        uint64_t hit, unc;
+        block_masks<WRAP>(g, W.cx + jb, W.cy + jb, W.cz + jb, npx, npy, npz, lo_lim, hi_lim,
+                          hit, unc);
+        // candidates inside the margin: exact FP64 test
+        while (unc) {
+          const int q = __ffsll((long long)unc) - 1;
+          unc &= unc - 1;
+          const int b = entry_index(W.entry[jb + q]);
+          if (exact_neighbor(g, s.x[a], s.y[a], s.z[a], s.h[a], s.x[b], s.y[b], s.z[b]))
+            hit |= 1ull << q;
+          ++exact;
+        }
+        if (self >= jb && self < jb + 64) hit &= ~(1ull << (self - jb));
+        if (!active) hit = 0;
+        uint32_t* row = nbr + (int64_t)a * max_nb;
+        while (hit) {
+          const int q = __ffsll((long long)hit) - 1;
+          hit &= hit - 1;
+          if (k < max_nb) row[k] = W.entry[jb + q];
+          ++k;
+        }
+      }
+      if (active) {
+        nn[a] = k;
+        if (k > max_nb) raise_flag(err, SPH_FLAG_NB_OVERFLOW);
+        tested += (unsigned long long)wn - (self >= 0 && self < wn ? 1 : 0);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace find
+}  // namespace sph

@@ -1,0 +1,157 @@
+"""Batched ensemble of independent SPH boxes on one GPU (libsph's
+sph_ensemble_* entry points): one persistent cooperative launch advances all
+boxes by any number of steps; the launch can be captured in a CUDA graph.
+PyTorch provides the device memory and the current stream only.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import time
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import EnsConfig, SphState, check
+from .sim import OUTPUTS, PERSISTENT, Params, _stream_ptr
+
+
+class Ensemble:
+    """boxes: list of (state dict from sph_inputs, alpha).  All boxes share the
+    physical parameters of `params` except their box geometry and alpha."""
+
+    def __init__(self, boxes, params: Params | None = None, device: str = "cuda:0"):
+        self.lib = _lib.load()
+        self.device = torch.device(device)
+        params = params or Params(precision="fp32_mixed")
+        params.precision = "fp32_mixed"
+        self.params = params
+        self.nbox = len(boxes)
+        self.box_n = np.array([b[0]["x"].shape[0] for b in boxes], dtype=np.int64)
+        self.p0 = np.concatenate([[0], np.cumsum(self.box_n)[:-1]]).astype(np.int64)
+        self.n = int(self.box_n.sum())
+        lo = np.array([b[0]["lo"] for b in boxes], dtype=np.float64).ravel()
+        hi = np.array([b[0]["hi"] for b in boxes], dtype=np.float64).ravel()
+        per = np.array([b[0]["periodic"] for b in boxes], dtype=np.int32).ravel()
+        self.alpha = np.array([b[1] for b in boxes], dtype=np.float64)
+        cp = params.c()
+        self.ctx = C.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self.lib, None, self.lib.sph_ensemble_init(
+                C.byref(cp), self.nbox, self.box_n.ctypes.data_as(C.c_void_p),
+                lo.ctypes.data_as(C.c_void_p), hi.ctypes.data_as(C.c_void_p),
+                per.ctypes.data_as(C.c_void_p), self.alpha.ctypes.data_as(C.c_void_p),
+                C.byref(self.ctx)))
+            self.t = {}
+            for k in PERSISTENT:
+                self.t[k] = torch.as_tensor(
+                    np.concatenate([b[0][k] for b in boxes]).astype(np.float64)).to(self.device)
+            self.t["id"] = torch.as_tensor(
+                np.concatenate([b[0]["id"] for b in boxes]).astype(np.int64)).to(self.device)
+            for k in OUTPUTS:
+                self.t[k] = torch.zeros(self.n, dtype=torch.float64, device=self.device)
+            self.t["iad"] = torch.zeros(6 * self.n, dtype=torch.float64, device=self.device)
+            self.dt = torch.zeros(self.nbox, dtype=torch.float64, device=self.device)
+        self.cfg = EnsConfig()
+        self.lib.sph_ens_default_config(C.byref(self.cfg))
+        self._st = SphState()
+        for k in _lib.STATE_FIELDS:
+            setattr(self._st, k, self.t[k].data_ptr())
+        self._st.id = self.t["id"].data_ptr()
+        self._st.n = self.n
+
+    def _err(self, rc):
+        if rc != _lib.SPH_OK:
+            raise _lib.SphError(rc, (self.lib.sph_ensemble_last_error(self.ctx) or b"").decode())
+
+    def set_config(self, cell_factor=None, blocks_per_sm=None, test_skip_block=None):
+        if cell_factor is not None:
+            self.cfg.cell_factor = float(cell_factor)
+        if blocks_per_sm is not None:
+            self.cfg.blocks_per_sm = int(blocks_per_sm)
+        if test_skip_block is not None:
+            self.cfg.test_skip_block = int(test_skip_block)
+        with torch.cuda.device(self.device):
+            self._err(self.lib.sph_ensemble_set_config(self.ctx, C.byref(self.cfg)))
+
+    def step(self, steps: int = 1):
+        with torch.cuda.device(self.device):
+            self._err(self.lib.sph_ensemble_step(self.ctx, C.byref(self._st),
+                                                 C.c_void_p(self.dt.data_ptr()), int(steps),
+                                                 _stream_ptr()))
+
+    def capture(self, steps: int):
+        """Capture `steps` steps of all boxes as a CUDA graph (on a side stream)."""
+        self._graph_stream = torch.cuda.Stream(device=self.device)
+        with torch.cuda.device(self.device):
+            torch.cuda.synchronize(self.device)
+            self._err(self.lib.sph_ensemble_capture(
+                self.ctx, C.byref(self._st), C.c_void_p(self.dt.data_ptr()), int(steps),
+                C.c_void_p(self._graph_stream.cuda_stream)))
+
+    def replay(self):
+        with torch.cuda.device(self.device):
+            self._err(self.lib.sph_ensemble_replay(self.ctx,
+                                                   C.c_void_p(self._graph_stream.cuda_stream)))
+
+    def synchronize(self):
+        torch.cuda.synchronize(self.device)
+
+    def error_word(self) -> int:
+        f = C.c_uint32(0)
+        with torch.cuda.device(self.device):
+            self._err(self.lib.sph_ensemble_error_word(self.ctx, C.byref(f)))
+        return int(f.value)
+
+    def info(self):
+        out = np.zeros(4, dtype=np.int64)
+        self._err(self.lib.sph_ensemble_info(self.ctx, out.ctypes.data_as(C.c_void_p)))
+        return {"particles": int(out[0]), "boxes": int(out[1]), "ctas": int(out[2]),
+                "launches": int(out[3])}
+
+    def box_numpy(self, b: int) -> dict:
+        """State and outputs of box b, ordered by particle id."""
+        torch.cuda.synchronize(self.device)
+        lo, hi = int(self.p0[b]), int(self.p0[b] + self.box_n[b])
+        out = {k: self.t[k][lo:hi].cpu().numpy() for k in PERSISTENT + OUTPUTS + ("id",)}
+        out["iad"] = self.t["iad"][6 * lo:6 * hi].cpu().numpy().reshape(-1, 6)
+        order = np.argsort(out["id"], kind="stable")
+        return {k: v[order] for k, v in out.items()}
+
+    def autotune(self, steps: int = 2, cell_factors=(1.0, 1.15, 1.3), blocks_per_sm=(0,)):
+        """Times `steps` steps of a copy of the current state for each
+        candidate configuration (cell-size factor, persistent CTAs per SM) and
+        keeps the fastest.  The ensemble's own state is not advanced."""
+        saved = {k: v.clone() for k, v in self.t.items()}
+        saved_dt = self.dt.clone()
+        results = []
+        for cf in cell_factors:
+            for bps in blocks_per_sm:
+                self.set_config(cell_factor=cf, blocks_per_sm=bps, test_skip_block=-1)
+                self.step(1)                      # warm-up of this configuration
+                torch.cuda.synchronize(self.device)
+                t0 = time.perf_counter()
+                self.step(steps)
+                torch.cuda.synchronize(self.device)
+                results.append(((time.perf_counter() - t0) / steps, cf, bps))
+                for k in self.t:
+                    self.t[k].copy_(saved[k])
+                self.dt.copy_(saved_dt)
+        best = min(results)
+        self.set_config(cell_factor=best[1], blocks_per_sm=best[2], test_skip_block=-1)
+        self.tuning = results
+        return {"seconds_per_step": best[0], "cell_factor": best[1], "blocks_per_sm": best[2],
+                "tried": results}
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            with torch.cuda.device(self.device):
+                torch.cuda.synchronize(self.device)
+                self.lib.sph_ensemble_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
