@@ -65,7 +65,8 @@ def _load():
         lib.oracle_iad.argtypes = [C.POINTER(_Box), P, P, P, P, P, P, i64, P, P, P, cint, d, d, P, P]
         lib.oracle_momentum_energy.restype = None
         lib.oracle_momentum_energy.argtypes = [C.POINTER(_Box), P, P, P, P, P, P, P, P, P, P, P, P,
-                                               i64, P, P, P, cint, d, d, d, P, P, P, P, P, P]
+                                               i64, P, P, P, cint, d, d, d, P, P, P, P, P, P, P,
+                                               P]
         lib.oracle_timestep.restype = d
         lib.oracle_timestep.argtypes = [i64, P, P, d, d, d]
         lib.oracle_update.restype = None
@@ -177,8 +178,10 @@ def iad(box: Box, s: dict, rho_full, nn, nbr, params: Params, targets=None, Bn=N
 
 
 def momentum_energy(box: Box, s: dict, rho_full, p_full, c_full, iad_full, nn, nbr, params: Params,
-                    targets=None, Bn=None):
-    """Eqs. 2-5.  Returns dict with ax, ay, az, du and the scales sa, sdu."""
+                    targets=None, Bn=None, av_force=None, record_av=False):
+    """Eqs. 2-5.  Returns dict with ax, ay, az, du and the scales sa, sdu.
+    ``av_force`` (int8, shape of ``nbr``) imposes the viscosity switch of Eq. 5
+    per list entry; ``record_av`` returns the switch as decided in ``av``."""
     if Bn is None:
         Bn = kernel_norm(params.sinc_n)
     t = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
@@ -186,12 +189,18 @@ def momentum_energy(box: Box, s: dict, rho_full, p_full, c_full, iad_full, nn, n
     out = {k: np.empty(nt) for k in ("ax", "ay", "az", "du", "sa", "sdu")}
     rho_full, p_full, c_full = map(_f64, (rho_full, p_full, c_full))
     iad_full = np.ascontiguousarray(iad_full, dtype=np.float64).reshape(-1, 6)
+    if av_force is not None:
+        av_force = np.ascontiguousarray(av_force, dtype=np.int8)
+        assert av_force.shape == nbr.shape
+    av = np.zeros(nbr.shape, dtype=np.int8) if record_av else None
     b = box.c()
     _load().oracle_momentum_energy(
         C.byref(b), _p(s["x"]), _p(s["y"]), _p(s["z"]), _p(s["vx"]), _p(s["vy"]), _p(s["vz"]),
         _p(s["h"]), _p(s["m"]), _p(rho_full), _p(p_full), _p(c_full), _p(iad_full), nt, _p(t),
-        _p(nn), _p(nbr), nbr.shape[1], params.sinc_n, Bn, params.alpha,
+        _p(nn), _p(nbr), nbr.shape[1], params.sinc_n, Bn, params.alpha, _p(av_force), _p(av),
         _p(out["ax"]), _p(out["ay"]), _p(out["az"]), _p(out["du"]), _p(out["sa"]), _p(out["sdu"]))
+    if record_av:
+        out["av"] = av
     return out
 
 
@@ -228,7 +237,7 @@ def copy_state(s: dict) -> dict:
     return {k: (np.array(v, copy=True) if isinstance(v, np.ndarray) else v) for k, v in s.items()}
 
 
-def outputs(box: Box, s: dict, params: Params, brute=False):
+def outputs(box: Box, s: dict, params: Params, brute=False, record_av=False):
     """Every per-particle output of one step on the given state (no update):
     neighbour lists, rho, P, c, C (IAD), a, du and the normalisation scales.
     Returns (rc, dict)."""
@@ -239,17 +248,17 @@ def outputs(box: Box, s: dict, params: Params, brute=False):
     Bn = kernel_norm(params.sinc_n)
     rho, p, c = density_eos(box, s, nn, nbr, params, Bn=Bn)
     rc_iad, C6, T6 = iad(box, s, rho, nn, nbr, params, Bn=Bn)
-    me = momentum_energy(box, s, rho, p, c, C6, nn, nbr, params, Bn=Bn)
+    me = momentum_energy(box, s, rho, p, c, C6, nn, nbr, params, Bn=Bn, record_av=record_av)
     out = {"nn": nn, "nbr": nbr, "rho": rho, "p": p, "c": c, "iad": C6, "tau": T6}
     out.update(me)
     return rc_iad, out
 
 
-def step(box: Box, s: dict, params: Params, dt_prev: float, brute=False):
+def step(box: Box, s: dict, params: Params, dt_prev: float, brute=False, record_av=False):
     """One full step in place on ``s`` (find neighbours, density + EOS, IAD,
     momentum/energy, time step, update, smoothing length).  Returns
     (rc, dt, outputs-of-the-step)."""
-    rc, out = outputs(box, s, params, brute=brute)
+    rc, out = outputs(box, s, params, brute=brute, record_av=record_av)
     if rc not in (OK,):
         return rc, float("nan"), out
     dt = timestep(s["h"], out["c"], params, dt_prev)

@@ -411,14 +411,20 @@ static void sym_mul(const double* C6, const double* d, double* out) {
 /* Outputs per target: a (3), du, and the normalisation scales sa and sdu:   */
 /* the pair terms with every factor in magnitude (|X| |A|, |Pi| |Abar|,       */
 /* |v_ab| |A|), the scale of the rounding error of the sums.                  */
+/* The viscosity switch of Eq. 5 (x_ab . v_ab < 0) can be recorded per list   */
+/* entry (av_out[t*max_nb+k] = 1 where it is on) and imposed instead of       */
+/* decided (av_force, same layout): a rollout with its lists frozen is then a */
+/* smooth function of its inputs, which central differences need.  Both NULL */
+/* means the switch is decided from the sign, as printed.                     */
 /* ------------------------------------------------------------------------- */
 void oracle_momentum_energy(const oracle_box* box, const double* x, const double* y,
                             const double* z, const double* vx, const double* vy, const double* vz,
                             const double* h, const double* m, const double* rho, const double* p,
                             const double* c, const double* iad, int64_t nt, const int64_t* targets,
                             const int32_t* nn, const int64_t* nbr, int max_nb, double sinc_n,
-                            double Bn, double alpha, double* ax, double* ay, double* az,
-                            double* du, double* sa, double* sdu) {
+                            double Bn, double alpha, const int8_t* av_force, int8_t* av_out,
+                            double* ax, double* ay, double* az, double* du, double* sa,
+                            double* sdu) {
 #pragma omp parallel for schedule(dynamic, 256)
   for (int64_t t = 0; t < nt; ++t) {
     int64_t a = targets ? targets[t] : t;
@@ -442,7 +448,9 @@ void oracle_momentum_energy(const oracle_box* box, const double* x, const double
       double xv = xab[0] * vab[0] + xab[1] * vab[1] + xab[2] * vab[2];
       double w = r > 0.0 ? xv / r : 0.0;
       double vsig = c[a] + c[b] - 3.0 * w;
-      double Pi = xv < 0.0 ? -0.5 * alpha * vsig * w : 0.0;
+      int on = av_force ? av_force[t * max_nb + k] != 0 : xv < 0.0;
+      if (av_out) av_out[t * max_nb + k] = (int8_t)on;
+      double Pi = on ? -0.5 * alpha * vsig * w : 0.0;
       double Xb = p[b] / (rho[b] * rho[b]);
       double Abar[3];
       for (int i = 0; i < 3; ++i) Abar[i] = Aa[i] / rho[a] + Ab[i] / rho[b];
