@@ -277,6 +277,63 @@ SPH_API const char* sph_ensemble_last_error(const sph_ens* e);
 /* out[0] particles, out[1] boxes, out[2] persistent CTAs, out[3] launches. */
 SPH_API int sph_ensemble_info(const sph_ens* e, int64_t* out);
 
+/* ------------------------------------------------------------------------ */
+/* Differentiable rollout: the gradient of a scalar of the state after K     */
+/* FP64 steps (plus one density pass on the final state) with respect to    */
+/* the initial state and the viscosity alpha of Eq. 5, by hand-written       */
+/* adjoint kernels of the update, momentum/energy (Eqs. 2-5), IAD and        */
+/* density + EOS (Eq. 1).  The neighbour lists, smoothing lengths, time      */
+/* steps and the viscosity switch of Eq. 5 are held at their values on the   */
+/* forward trajectory: the result is the derivative of the rollout with      */
+/* those frozen, which is the rollout's own derivative wherever none of them */
+/* changes under a small perturbation.  The forward pass keeps a state       */
+/* checkpoint every `checkpoint_every` steps; the backward pass re-runs each */
+/* segment from its checkpoint, recording what the reverse kernels need,     */
+/* then runs the segment's reverse steps.  Every reduction is in a fixed     */
+/* order: two backward passes give bit-identical gradients.                  */
+/* All pointers are DEVICE memory of the current device; calls are           */
+/* asynchronous on `stream` except where stated.                             */
+/* ------------------------------------------------------------------------ */
+typedef struct sph_adj sph_adj;
+
+/* Creates a rollout of `steps` >= 1 steps for states of up to n_max
+ * particles; 1 <= checkpoint_every <= steps.  params->precision must be
+ * SPH_FP64 and max_nb <= 4096.  Device memory is allocated here only:
+ * per particle of n_max, (checkpoint_every + 1) * (192 + 4 max_nb) bytes of
+ * tape, 112 bytes per checkpoint (ceil(steps / checkpoint_every) of them),
+ * 104 * max_nb bytes of pair and reverse-list scratch and about 600 bytes
+ * of working arrays, plus one FP64 sph_ctx. */
+SPH_API int sph_adjoint_init(const sph_params* params, int64_t n_max, int steps,
+                             int checkpoint_every, sph_adj** out);
+SPH_API void sph_adjoint_destroy(sph_adj* a);
+
+/* Runs the forward rollout from s0 (its 13 state arrays are read; id and the
+ * output arrays are ignored and may be NULL; s0 is not modified) with the
+ * previous time step dt_prev0 (0 = first step) and viscosity alpha.
+ * final_out (8 n doubles) receives x, y, z, vx, vy, vz, u after the last
+ * step and rho of the final density pass, each n long, particle i at index
+ * i as in s0.  Synchronises the stream and reads the error word: returns
+ * SPH_ERR_NB_OVERFLOW, SPH_ERR_SINGULAR_IAD or SPH_ERR_NONFINITE if a step
+ * raised that flag (and SPH_ERR_INVALID_ARG for SPH_FLAG_BAD_BOX or
+ * SPH_FLAG_CELL_OVERFLOW); the gradient is then not available. */
+SPH_API int sph_adjoint_forward(sph_adj* a, const sph_state* s0, double dt_prev0, double alpha,
+                                double* final_out, sph_stream_t stream);
+
+/* Reverse pass of the last sph_adjoint_forward.  g_final (8 n doubles, the
+ * layout of final_out) holds dL/d(final_out).  g_init (11 n doubles)
+ * receives dL/d of the initial x, y, z, vx, vy, vz, vxh, vyh, vzh, u,
+ * du_prev (in that order, particle order of s0); *g_alpha (one device
+ * double) receives dL/dalpha.  Returns SPH_ERR_ORDER before a forward. */
+SPH_API int sph_adjoint_backward(sph_adj* a, const double* g_final, double* g_init,
+                                 double* g_alpha, sph_stream_t stream);
+
+/* out[0] device bytes held, out[1] kernel launches so far, out[2] steps
+ * re-run from checkpoints so far, out[3] backward passes so far (HOST). */
+SPH_API int sph_adjoint_info(const sph_adj* a, int64_t* out);
+/* The `steps` time steps of the last forward into dt (HOST).  Synchronous. */
+SPH_API int sph_adjoint_time_steps(sph_adj* a, double* dt);
+SPH_API const char* sph_adjoint_last_error(const sph_adj* a);
+
 /* Stages of sph_step timed by sph_profile. */
 enum {
   SPH_STAGE_SORT = 0,     /* grid, Morton counting sort, gather          */

@@ -15,4 +15,7 @@ def __getattr__(name):
     if name == "Ensemble":
         from .ensemble import Ensemble
         return Ensemble
+    if name in ("Rollout", "SphRolloutFn", "rollout"):
+        from . import adjoint
+        return getattr(adjoint, name)
     raise AttributeError(name)

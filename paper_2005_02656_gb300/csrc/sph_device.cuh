@@ -46,6 +46,20 @@ __device__ __forceinline__ double sinc_poly64(double t) {
   return s;
 }
 
+// S(t) and dS/dt of the FP64 series (Horner on both).
+__device__ __forceinline__ void sinc_poly64_d(double t, double& S, double& dS) {
+  constexpr SincCoefs<kSincTerms64> C{};
+  double s = C.c[kSincTerms64 - 1];
+  double d = (kSincTerms64 - 1) * C.c[kSincTerms64 - 1];
+#pragma unroll
+  for (int k = kSincTerms64 - 2; k >= 0; --k) {
+    s = fma(s, t, C.c[k]);
+    if (k >= 1) d = fma(d, t, k * C.c[k]);
+  }
+  S = s;
+  dS = d;
+}
+
 __device__ __forceinline__ float sinc_poly32(float t) {
   constexpr SincCoefs<kSincTerms32> C{};
   float s = (float)C.c[kSincTerms32 - 1];
@@ -63,6 +77,17 @@ __device__ __forceinline__ T ipow(T s, int n) {
   T r = s;
   for (int i = 1; i < n; ++i) r *= s;
   return r;
+}
+
+// W and dW/dt for t = v^2 (FP64); t is clamped at 4, where S = 0.
+__device__ __forceinline__ void kernel_w64_d(double t, double norm, int n, double& W,
+                                             double& dWdt) {
+  t = fmin(t, 4.0);
+  double S, dS;
+  sinc_poly64_d(t, S, dS);
+  const double Sn1 = ipow(S, n - 1);
+  W = norm * Sn1 * S;
+  dWdt = norm * n * Sn1 * dS;
 }
 
 // W for t = v^2 < 4 (caller guarantees the neighbour criterion), norm = B_n/h^3.
