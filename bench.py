@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ensemble-steps", type=int, default=50)
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-side", type=int, default=100)
     return ap.parse_args()
 
 
@@ -256,14 +258,21 @@ def run_gpu(args, world, rank, local):
     if not args.no_ensemble:
         ens = run_ensemble(args, dev, windows)
 
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = run_adjoint(args, dev, windows)
+
     clocks.stop()
     if ens is not None:
         ens["clocks"] = clocks.summary(*windows["ensemble"])
+    if adjoint is not None:
+        adjoint["clocks"] = clocks.summary(*windows["adjoint"])
     for key, r in (("fp32_mixed", r32), ("fp64", r64)):
         if r is not None:
             r["clocks"] = clocks.summary(*windows[key])
     ms32 = max_over_ranks(r32["ms"])
-    res = {"n": n, "r32": r32, "r64": r64, "ms32": ms32, "e2e": e2e, "ensemble": ens}
+    res = {"n": n, "r32": r32, "r64": r64, "ms32": ms32, "e2e": e2e, "ensemble": ens,
+           "adjoint": adjoint}
     if r64 is not None:
         res["ms64"] = max_over_ranks(r64["ms"])
     if dist is not None:
@@ -309,6 +318,59 @@ def run_ensemble(args, dev, windows):
             "autotune": {"cell_factor": tune["cell_factor"], "blocks_per_sm": tune["blocks_per_sm"],
                          "tried": [{"s_per_step": t, "cell_factor": c, "blocks_per_sm": b}
                                    for t, c, b in tune["tried"]]}}
+
+
+def run_adjoint(args, dev, windows, steps=20, every=5):
+    """Gradient of L = sum (rho - 1)^2 + sum m |v|^2 / 2 after 20 FP64 steps
+    of the side^3 periodic jittered box (10^6 particles by default) with
+    respect to the initial x, v, u and alpha: one forward rollout with a
+    checkpoint every 5 steps, one reverse pass (re-running 15 steps from
+    checkpoints).  Timed with CUDA events on the current stream after one
+    untimed forward + reverse."""
+    import torch
+
+    import sph_inputs
+    from paper_2005_02656_gb300 import Params, Rollout
+    s = sph_inputs.jittered_box(args.adjoint_side, seed_index=3, vel_sigma=0.01)
+    n = s["x"].shape[0]
+    ro = Rollout(n, steps, every, Params(box_lo=s["lo"], box_hi=s["hi"], periodic=s["periodic"]),
+                 device=dev)
+    st = {k: torch.as_tensor(s[k], dtype=torch.float64, device=dev)
+          for k in ("x", "y", "z", "vx", "vy", "vz", "vxh", "vyh", "vzh", "h", "m", "u",
+                    "du_prev")}
+
+    def seed(fin):
+        g = torch.zeros_like(fin)
+        g[3:6] = st["m"][None, :] * fin[3:6]
+        g[7] = 2.0 * (fin[7] - 1.0)
+        return g
+
+    fin = ro.forward(st, 1.0)
+    ro.backward(seed(fin))
+    torch.cuda.synchronize()
+    i0 = ro.info()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tw0 = time.time()
+    ev[0].record()
+    fin = ro.forward(st, 1.0)
+    ev[1].record()
+    g = seed(fin)
+    gi, ga = ro.backward(g)
+    ev[2].record()
+    torch.cuda.synchronize()
+    windows["adjoint"] = (tw0, time.time())
+    i1 = ro.info()
+    f_ms, b_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    finite = bool(torch.isfinite(gi).all()) and bool(torch.isfinite(ga))
+    ro.close()
+    return {"metric": "particle-steps/s of a full gradient (forward rollout + reverse pass)",
+            "value": n * steps / ((f_ms + b_ms) * 1e-3), "unit": "particle-steps/s",
+            "workload": f"jittered_box_{n}", "n_particles": n, "steps": steps,
+            "checkpoint_every": every, "forward_ms": f_ms, "reverse_ms": b_ms,
+            "reverse_over_forward": b_ms / f_ms,
+            "recomputed_steps": i1["recomputed_steps"] - i0["recomputed_steps"],
+            "gpu_launches": i1["launches"] - i0["launches"], "device_bytes": i1["bytes"],
+            "gradient_finite": finite, "dtype": "f64"}
 
 
 def roofline(r, n, precision):
@@ -402,6 +464,8 @@ def main():
     line["e2e"] = res["e2e"]
     if res.get("ensemble") is not None:
         line["ensemble"] = res["ensemble"]
+    if res.get("adjoint") is not None:
+        line["adjoint"] = res["adjoint"]
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

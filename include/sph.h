@@ -301,7 +301,7 @@ typedef struct sph_adj sph_adj;
  * SPH_FP64 and max_nb <= 4096.  Device memory is allocated here only:
  * per particle of n_max, (checkpoint_every + 1) * (192 + 4 max_nb) bytes of
  * tape, 112 bytes per checkpoint (ceil(steps / checkpoint_every) of them),
- * 104 * max_nb bytes of pair and reverse-list scratch and about 600 bytes
+ * 120 * max_nb bytes of pair and reverse-list scratch and about 620 bytes
  * of working arrays, plus one FP64 sph_ctx. */
 SPH_API int sph_adjoint_init(const sph_params* params, int64_t n_max, int steps,
                              int checkpoint_every, sph_adj** out);

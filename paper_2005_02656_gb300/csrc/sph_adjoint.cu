@@ -84,9 +84,20 @@ struct Rev {
   uint64_t* list;  // (a << kKBits) | k, rows sorted ascending
 };
 
+// Per list entry (a, k), slot = k * stride + a: the 12 partials of the pair
+// term that belong to the neighbour b (one 96-byte record), and W_a and
+// dW_a/d(r^2) of the entry.
+constexpr int kRec = 12;
 struct PairBuf {
-  double* c[12];  // (k, a) at k * stride + a
+  double* rec;   // kRec doubles per slot
+  double2* wk;   // (W_a, dW_a / d r^2) per slot
   int64_t stride;
+};
+
+// Per-particle factors of one step (sorted order): 1/h^2, B_n/h^3, 1/rho,
+// P/rho^2, m/rho.
+struct Prep {
+  double *hinv2, *norm, *ir, *X, *vol;
 };
 
 struct Consts {
@@ -243,11 +254,26 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_rev_sort(const int64_t* sta
   }
 }
 
+__global__ void k_adj_prep(Slot sl, Prep pr, int64_t n, double Bn) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double h = sl.s.h[i];
+    const double hinv2 = 1.0 / (h * h);
+    const double ir = 1.0 / sl.rho[i];
+    pr.hinv2[i] = hinv2;
+    pr.norm[i] = Bn * hinv2 / h;
+    pr.ir[i] = ir;
+    pr.X[i] = sl.p[i] * ir * ir;
+    pr.vol[i] = sl.s.m[i] * ir;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Reverse of update + momentum/energy, the target's side.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_adj_momentum_a(Slot sl, Bar q, Work w, PairBuf pb,
-                                                             int64_t n, Consts kc, double* apart) {
+__global__ void __launch_bounds__(kThreads) k_adj_momentum_a(Slot sl, Prep pr, Bar q, Work w,
+                                                             PairBuf pb, int64_t n, Consts kc,
+                                                             double* apart) {
   const Grid g = *sl.grid;
   const double dt = sl.dtp[0], dt_prev = sl.dtp[1];
   const double delta = 0.5 * (dt + dt_prev);
@@ -275,11 +301,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_momentum_a(Slot sl, Bar q, Wor
 
     const double xa = s.x[a], ya = s.y[a], za = s.z[a];
     const double vxa = s.vx[a], vya = s.vy[a], vza = s.vz[a];
-    const double ha = s.h[a];
-    const double hinv2a = 1.0 / (ha * ha);
-    const double norma = kc.Bn * hinv2a / ha;
-    const double ira = 1.0 / sl.rho[a];
-    const double Xa = sl.p[a] * ira * ira;
+    const double hinv2a = pr.hinv2[a];
+    const double norma = pr.norm[a];
+    const double ira = pr.ir[a];
+    const double Xa = pr.X[a];
     const double ca = sl.c[a];
     double Ca[6];
 #pragma unroll
@@ -296,11 +321,14 @@ __global__ void __launch_bounds__(kThreads) k_adj_momentum_a(Slot sl, Bar q, Wor
       const double r2 = dx * dx + dy * dy + dz * dz;
       double Wa, dWa;
       sph::kernel_w64_d(r2 * hinv2a, norma, kc.sinc_n, Wa, dWa);
-      const double hb = s.h[b];
-      const double hinv2b = 1.0 / (hb * hb);
+      dWa *= hinv2a;  // dW_a / d r^2
+      const double hinv2b = pr.hinv2[b];
       const double tb = r2 * hinv2b;
       double Wb = 0.0, dWb = 0.0;
-      if (tb < 4.0) sph::kernel_w64_d(tb, kc.Bn * hinv2b / hb, kc.sinc_n, Wb, dWb);
+      if (tb < 4.0) {
+        sph::kernel_w64_d(tb, pr.norm[b], kc.sinc_n, Wb, dWb);
+        dWb *= hinv2b;
+      }
       double Cb[6];
 #pragma unroll
       for (int i = 0; i < 6; ++i) Cb[i] = sl.iad[6 * b + i];
@@ -311,14 +339,14 @@ __global__ void __launch_bounds__(kThreads) k_adj_momentum_a(Slot sl, Bar q, Wor
       const double Abx = Wb * cbx, Aby = Wb * cby, Abz = Wb * cbz;
       const double vabx = vxa - s.vx[b], vaby = vya - s.vy[b], vabz = vza - s.vz[b];
       const double xv = -(dx * vabx + dy * vaby + dz * vabz);
-      const double irb = 1.0 / sl.rho[b];
-      const double Xb = sl.p[b] * irb * irb;
+      const double irb = pr.ir[b];
+      const double Xb = pr.X[b];
       const double cbv = sl.c[b];
       const bool on = xv < 0.0;
-      double r = 0.0, wv = 0.0, vsig = 0.0, Pi = 0.0;
+      double rinv = 0.0, wv = 0.0, vsig = 0.0, Pi = 0.0;
       if (on) {
-        r = sqrt(r2);
-        wv = xv / r;
+        rinv = rsqrt(r2);
+        wv = xv * rinv;
         vsig = ca + cbv - 3.0 * wv;
         Pi = -0.5 * kc.alpha * vsig * wv;
       }
@@ -361,14 +389,14 @@ __global__ void __launch_bounds__(kThreads) k_adj_momentum_a(Slot sl, Bar q, Wor
       double dbx = Wa * t0 + Wb * u0;
       double dby = Wa * t1 + Wb * u1;
       double dbz = Wa * t2 + Wb * u2;
-      double r2b = Wab * dWa * hinv2a + Wbb * dWb * hinv2b;
+      double r2b = Wab * dWa + Wbb * dWb;
       double cpair = 0.0;
       if (on) {
         alpha_bar += Pib * (-0.5 * vsig * wv);
         cpair = Pib * (-0.5 * kc.alpha * wv);
         const double wb = Pib * (-0.5 * kc.alpha * (ca + cbv - 6.0 * wv));
-        const double xvb = wb / r;
-        r2b += -wb * wv / (2.0 * r2);
+        const double xvb = wb * rinv;
+        r2b += -0.5 * wb * wv * rinv * rinv;
         dbx += -xvb * vabx;
         dby += -xvb * vaby;
         dbz += -xvb * vabz;
@@ -387,18 +415,14 @@ __global__ void __launch_bounds__(kThreads) k_adj_momentum_a(Slot sl, Bar q, Wor
       vby += vabby;
       vbz += vabbz;
       const int64_t slot = (int64_t)k * pb.stride + a;
-      pb.c[0][slot] = dbx;
-      pb.c[1][slot] = dby;
-      pb.c[2][slot] = dbz;
-      pb.c[3][slot] = vabbx;
-      pb.c[4][slot] = vabby;
-      pb.c[5][slot] = vabbz;
-      pb.c[6][slot] = Xbb;
-      pb.c[7][slot] = irbb;
-      pb.c[8][slot] = cpair;
-      pb.c[9][slot] = Wb * Abbx;
-      pb.c[10][slot] = Wb * Abby;
-      pb.c[11][slot] = Wb * Abbz;
+      double2* rec = reinterpret_cast<double2*>(pb.rec + kRec * slot);
+      rec[0] = make_double2(dbx, dby);
+      rec[1] = make_double2(dbz, vabbx);
+      rec[2] = make_double2(vabby, vabbz);
+      rec[3] = make_double2(Xbb, irbb);
+      rec[4] = make_double2(cpair, Wb * Abbx);
+      rec[5] = make_double2(Wb * Abby, Wb * Abbz);
+      pb.wk[slot] = make_double2(Wa, dWa);
     }
     w.z.x[a] = q.x[a] + xbx;
     w.z.y[a] = q.y[a] + xby;
@@ -451,16 +475,18 @@ __global__ void __launch_bounds__(kThreads) k_adj_momentum_b(Slot sl, Work w, Pa
       const int64_t a = (int64_t)(ent >> kKBits);
       const int64_t k = (int64_t)(ent & ((1u << kKBits) - 1u));
       const int64_t slot = k * pb.stride + a;
-      dsx += pb.c[0][slot];
-      dsy += pb.c[1][slot];
-      dsz += pb.c[2][slot];
-      vsx += pb.c[3][slot];
-      vsy += pb.c[4][slot];
-      vsz += pb.c[5][slot];
-      Xs += pb.c[6][slot];
-      irs += pb.c[7][slot];
-      cs += pb.c[8][slot];
-      const double Ax = pb.c[9][slot], Ay = pb.c[10][slot], Az = pb.c[11][slot];
+      const double2* rec = reinterpret_cast<const double2*>(pb.rec + kRec * slot);
+      const double2 r0 = rec[0], r1 = rec[1], r2_ = rec[2], r3 = rec[3], r4 = rec[4], r5 = rec[5];
+      dsx += r0.x;
+      dsy += r0.y;
+      dsz += r1.x;
+      vsx += r1.y;
+      vsy += r2_.x;
+      vsz += r2_.y;
+      Xs += r3.x;
+      irs += r3.y;
+      cs += r4.x;
+      const double Ax = r4.y, Ay = r5.x, Az = r5.y;
       double dx, dy, dz;
       sepd(g, s.x[a], s.y[a], s.z[a], xb, yb, zb, dx, dy, dz);
       Cs[0] += Ax * dx;
@@ -518,16 +544,14 @@ __global__ void __launch_bounds__(kThreads) k_adj_momentum_b(Slot sl, Work w, Pa
 // ---------------------------------------------------------------------------
 // Reverse of IAD's tau sums: tau_a = sum_b vol_b W_a d d^T, vol = m / rho.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_adj_iad(Slot sl, Work w, Rev rv, int64_t n,
-                                                      Consts kc) {
+__global__ void __launch_bounds__(kThreads) k_adj_iad(Slot sl, Prep pr, Work w, PairBuf pb, Rev rv,
+                                                      int64_t n, Consts kc) {
   const Grid g = *sl.grid;
   const StateView& s = sl.s;
   const int mb = kc.max_nb;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
-    const double xp = s.x[p], yp = s.y[p], zp = s.z[p], hp = s.h[p];
-    const double hinv2p = 1.0 / (hp * hp);
-    const double normp = kc.Bn * hinv2p / hp;
+    const double xp = s.x[p], yp = s.y[p], zp = s.z[p];
     double Sp[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) Sp[i] = w.Cb[6 * p + i];
@@ -539,49 +563,45 @@ __global__ void __launch_bounds__(kThreads) k_adj_iad(Slot sl, Work w, Rev rv, i
       const int64_t b = sph::entry_index(list[k]);
       double dx, dy, dz;
       sepd(g, xp, yp, zp, s.x[b], s.y[b], s.z[b], dx, dy, dz);
-      const double r2 = dx * dx + dy * dy + dz * dz;
-      double W, dW;
-      sph::kernel_w64_d(r2 * hinv2p, normp, kc.sinc_n, W, dW);
-      const double vol = s.m[b] / sl.rho[b];
+      const double2 wk = pb.wk[(int64_t)k * pb.stride + p];
+      const double vol = pr.vol[b];
       double s0, s1, s2;
       sym_mv(Sp, dx, dy, dz, s0, s1, s2);
       const double wbar = dx * s0 + dy * s1 + dz * s2;
-      const double ww = vol * W;
-      const double f = 2.0 * wbar * vol * dW * hinv2p;
+      const double ww = vol * wk.x;
+      const double f = 2.0 * wbar * vol * wk.y;
       xbx -= 2.0 * ww * s0 + f * dx;
       xby -= 2.0 * ww * s1 + f * dy;
       xbz -= 2.0 * ww * s2 + f * dz;
     }
     // sums of the particles a whose list holds p: pairs (a, p)
-    const double volp = s.m[p] / sl.rho[p];
+    const double volp = pr.vol[p];
     double volbar = 0.0;
     const int64_t e0 = rv.start[p], e1 = rv.start[p + 1];
     for (int64_t e = e0; e < e1; ++e) {
-      const int64_t a = (int64_t)(rv.list[e] >> kKBits);
+      const uint64_t ent = rv.list[e];
+      const int64_t a = (int64_t)(ent >> kKBits);
+      const int64_t k = (int64_t)(ent & ((1u << kKBits) - 1u));
       double dx, dy, dz;
       sepd(g, s.x[a], s.y[a], s.z[a], xp, yp, zp, dx, dy, dz);
-      const double r2 = dx * dx + dy * dy + dz * dz;
-      const double ha = s.h[a];
-      const double hinv2a = 1.0 / (ha * ha);
-      double W, dW;
-      sph::kernel_w64_d(r2 * hinv2a, kc.Bn * hinv2a / ha, kc.sinc_n, W, dW);
+      const double2 wk = pb.wk[k * pb.stride + a];
       double Sa[6];
 #pragma unroll
       for (int i = 0; i < 6; ++i) Sa[i] = w.Cb[6 * a + i];
       double s0, s1, s2;
       sym_mv(Sa, dx, dy, dz, s0, s1, s2);
       const double wbar = dx * s0 + dy * s1 + dz * s2;
-      const double ww = volp * W;
-      const double f = 2.0 * wbar * volp * dW * hinv2a;
+      const double ww = volp * wk.x;
+      const double f = 2.0 * wbar * volp * wk.y;
       xbx += 2.0 * ww * s0 + f * dx;
       xby += 2.0 * ww * s1 + f * dy;
       xbz += 2.0 * ww * s2 + f * dz;
-      volbar += wbar * W;
+      volbar += wbar * wk.x;
     }
     w.z.x[p] += xbx;
     w.z.y[p] += xby;
     w.z.z[p] += xbz;
-    const double ir = 1.0 / sl.rho[p];
+    const double ir = pr.ir[p];
     const double irbar = w.irb[p] + s.m[p] * volbar;
     w.rhob[p] -= irbar * ir * ir;
   }
@@ -589,18 +609,29 @@ __global__ void __launch_bounds__(kThreads) k_adj_iad(Slot sl, Work w, Rev rv, i
 
 // ---------------------------------------------------------------------------
 // Reverse of the density sums (Eq. 1), then the adjoint of the step's input
-// written back through the sort permutation.
+// written back through the sort permutation.  kCached: dW_a/d r^2 of every
+// list entry is in the pair buffer (written by the momentum kernel);
+// otherwise (the final density pass) it is evaluated here.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_adj_density(Slot sl, Work w, Rev rv, Bar out,
-                                                          int64_t n, Consts kc) {
+template <bool kCached>
+__device__ __forceinline__ double dw_dr2(const PairBuf& pb, int64_t k, int64_t a, double r2,
+                                         const Prep& pr, const Consts& kc) {
+  if (kCached) return pb.wk[k * pb.stride + a].y;
+  double W, dW;
+  const double hinv2 = pr.hinv2[a];
+  sph::kernel_w64_d(r2 * hinv2, pr.norm[a], kc.sinc_n, W, dW);
+  return dW * hinv2;
+}
+
+template <bool kCached>
+__global__ void __launch_bounds__(kThreads) k_adj_density(Slot sl, Prep pr, Work w, PairBuf pb,
+                                                          Rev rv, Bar out, int64_t n, Consts kc) {
   const Grid g = *sl.grid;
   const StateView& s = sl.s;
   const int mb = kc.max_nb;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
-    const double xp = s.x[p], yp = s.y[p], zp = s.z[p], hp = s.h[p];
-    const double hinv2p = 1.0 / (hp * hp);
-    const double normp = kc.Bn * hinv2p / hp;
+    const double xp = s.x[p], yp = s.y[p], zp = s.z[p];
     const double rbp = w.rhob[p];
     double xbx = 0, xby = 0, xbz = 0;
     const int cnt = min(sl.nn[p], mb);
@@ -610,9 +641,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_density(Slot sl, Work w, Rev r
       double dx, dy, dz;
       sepd(g, xp, yp, zp, s.x[b], s.y[b], s.z[b], dx, dy, dz);
       const double r2 = dx * dx + dy * dy + dz * dz;
-      double W, dW;
-      sph::kernel_w64_d(r2 * hinv2p, normp, kc.sinc_n, W, dW);
-      const double f = 2.0 * rbp * s.m[b] * dW * hinv2p;
+      const double f = 2.0 * rbp * s.m[b] * dw_dr2<kCached>(pb, k, p, r2, pr, kc);
       xbx -= f * dx;
       xby -= f * dy;
       xbz -= f * dz;
@@ -620,15 +649,13 @@ __global__ void __launch_bounds__(kThreads) k_adj_density(Slot sl, Work w, Rev r
     const double mp = s.m[p];
     const int64_t e0 = rv.start[p], e1 = rv.start[p + 1];
     for (int64_t e = e0; e < e1; ++e) {
-      const int64_t a = (int64_t)(rv.list[e] >> kKBits);
+      const uint64_t ent = rv.list[e];
+      const int64_t a = (int64_t)(ent >> kKBits);
+      const int64_t k = (int64_t)(ent & ((1u << kKBits) - 1u));
       double dx, dy, dz;
       sepd(g, s.x[a], s.y[a], s.z[a], xp, yp, zp, dx, dy, dz);
       const double r2 = dx * dx + dy * dy + dz * dz;
-      const double ha = s.h[a];
-      const double hinv2a = 1.0 / (ha * ha);
-      double W, dW;
-      sph::kernel_w64_d(r2 * hinv2a, kc.Bn * hinv2a / ha, kc.sinc_n, W, dW);
-      const double f = 2.0 * w.rhob[a] * mp * dW * hinv2a;
+      const double f = 2.0 * w.rhob[a] * mp * dw_dr2<kCached>(pb, k, a, r2, pr, kc);
       xbx += f * dx;
       xby += f * dy;
       xbz += f * dz;
@@ -732,7 +759,9 @@ struct sph_adj {
   double* kbuf;
   Work w;
   double* pbuf;
+  double2* wkbuf;
   PairBuf pb;
+  Prep pr;
   int32_t* rcnt;
   int64_t* rstart;
   uint64_t* rlist;
@@ -772,7 +801,7 @@ cudaError_t amalloc(sph_adj* A, T** p, size_t count) {
 
 void free_adj(sph_adj* A) {
   void* ptrs[] = {A->wbuf, A->wid, A->dt_dev, A->cbuf, A->cid, A->cdt, A->tbuf, A->tid,
-                  A->tint, A->tnbr, A->tgrid, A->tdt, A->dts, A->bbuf, A->kbuf, A->pbuf,
+                  A->tint, A->tnbr, A->tgrid, A->tdt, A->dts, A->bbuf, A->kbuf, A->pbuf, A->wkbuf,
                   A->rcnt, A->rstart, A->rlist, A->spart, A->apart, A->alpha_acc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -971,12 +1000,13 @@ int reverse_step(sph_adj* A, int j, cudaStream_t st) {
   const int g = grid_for(n, A->sm_count, kThreads, 8);
   const int ga = g < kAlphaBlocks ? g : kAlphaBlocks;
   A->pb.stride = n;
-  k_adj_momentum_a<<<ga, kThreads, 0, st>>>(sl, A->q, A->w, A->pb, n, kc, A->apart);
+  k_adj_prep<<<g, kThreads, 0, st>>>(sl, A->pr, n, kc.Bn);
+  k_adj_momentum_a<<<ga, kThreads, 0, st>>>(sl, A->pr, A->q, A->w, A->pb, n, kc, A->apart);
   k_alpha_sum<<<1, 32, 0, st>>>(A->apart, ga, A->alpha_acc);
   k_adj_momentum_b<<<g, kThreads, 0, st>>>(sl, A->w, A->pb, rev_of(A), n, kc);
-  k_adj_iad<<<g, kThreads, 0, st>>>(sl, A->w, rev_of(A), n, kc);
-  k_adj_density<<<g, kThreads, 0, st>>>(sl, A->w, rev_of(A), A->pnext, n, kc);
-  A->launches += 5;
+  k_adj_iad<<<g, kThreads, 0, st>>>(sl, A->pr, A->w, A->pb, rev_of(A), n, kc);
+  k_adj_density<true><<<g, kThreads, 0, st>>>(sl, A->pr, A->w, A->pb, rev_of(A), A->pnext, n, kc);
+  A->launches += 6;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return acuda(A, e, "reverse-step launch");
   const Bar t = A->q;
@@ -1030,8 +1060,9 @@ int sph_adjoint_init(const sph_params* params, int64_t n_max, int steps, int che
   AM(A->tdt, 2 * nslot);
   AM(A->dts, steps);
   AM(A->bbuf, 22 * N);
-  AM(A->kbuf, 24 * N);  // Work.z 11 + X, ir, c + C 6 + rho = 21
-  AM(A->pbuf, 12 * N * mb);
+  AM(A->kbuf, 26 * N);  // Work: z 11 + X, ir, c + C 6 + rho = 21; Prep 5
+  AM(A->pbuf, kRec * N * mb);
+  AM(A->wkbuf, N * mb);
   AM(A->rcnt, N);
   AM(A->rstart, N + 1);
   AM(A->rlist, N * mb);
@@ -1079,8 +1110,14 @@ int sph_adjoint_init(const sph_params* params, int64_t n_max, int steps, int che
   A->w.cb = A->kbuf + 13 * N;
   A->w.Cb = A->kbuf + 14 * N;
   A->w.rhob = A->kbuf + 20 * N;
-  for (int c = 0; c < 12; ++c) A->pb.c[c] = A->pbuf + (size_t)c * N * mb;
+  A->pb.rec = A->pbuf;
+  A->pb.wk = A->wkbuf;
   A->pb.stride = (int64_t)N;
+  A->pr.hinv2 = A->kbuf + 21 * N;
+  A->pr.norm = A->kbuf + 22 * N;
+  A->pr.ir = A->kbuf + 23 * N;
+  A->pr.X = A->kbuf + 24 * N;
+  A->pr.vol = A->kbuf + 25 * N;
   *out = A;
   return SPH_OK;
 }
@@ -1205,9 +1242,11 @@ int sph_adjoint_backward(sph_adj* A, const double* g_final, double* g_init, doub
   const Slot& sf = A->slot[A->every];
   int rc = build_rev(A, sf, st);
   if (rc != SPH_OK) return rc;
+  A->pb.stride = n;
   k_seed<<<g, kThreads, 0, st>>>(g_final, sf.s.id, n, A->w);
-  k_adj_density<<<g, kThreads, 0, st>>>(sf, A->w, rev_of(A), A->q, n, kc);
-  A->launches += 2;
+  k_adj_prep<<<g, kThreads, 0, st>>>(sf, A->pr, n, kc.Bn);
+  k_adj_density<false><<<g, kThreads, 0, st>>>(sf, A->pr, A->w, A->pb, rev_of(A), A->q, n, kc);
+  A->launches += 3;
   for (int seg = A->nseg - 1; seg >= 0; --seg) {
     if (A->tape_seg != seg) {
       rc = record_segment(A, seg, st);
