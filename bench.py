@@ -129,9 +129,11 @@ class Clocks:
                 "reasons": reasons}
 
 
-def source_hash(name):
+def source_hash(names):
+    """Hash of the kernel's source files (a name or a list of names in csrc/)."""
     h = hashlib.sha256()
-    h.update(open(os.path.join(ROOT, "paper_2005_02656_gb300", "csrc", name), "rb").read())
+    for name in ([names] if isinstance(names, str) else names):
+        h.update(open(os.path.join(ROOT, "paper_2005_02656_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
 
