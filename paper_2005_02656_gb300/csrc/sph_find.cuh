@@ -63,7 +63,9 @@ static_assert(sizeof(FindWarpSmem) % 16 == 0, "per-warp window must keep 16-byte
 // Hit and margin masks of one block of 64 staged candidates for one target.
 // The decisions r2 < lo and r2 < hi are read from the sign bits of r2 - lo and
 // r2 - hi, with the limit folded into the first fused multiply-add (the margin
-// is twice the error bound, so a strict "< hi" is as safe as "<= hi").
+// is twice the error bound, so a strict "< hi" is as safe as "<= hi").  Each
+// sign bit is shifted into its mask by one funnel shift, so slot s of the
+// block ends at bit 63 - s (kTop >> s).
 template <bool WRAP>
 __device__ __forceinline__ void block_masks(const Grid& g, const float* cx, const float* cy,
                                             const float* cz, float2 npx, float2 npy, float2 npz,
@@ -76,7 +78,7 @@ __device__ __forceinline__ void block_masks(const Grid& g, const float* cx, cons
   const float2 dlh = make_float2(lo_lim - hi_lim, lo_lim - hi_lim);
   uint32_t hA = 0, hB = 0, uA = 0, uB = 0;
 #pragma unroll 8
-  for (int q = 0; q < 32; ++q) {
+  for (int q = 0; q < 32; ++q) {  // slots q (.x) and q + 32 (.y)
     float2 dx = __fadd2_rn(X[q], npx);
     float2 dy = __fadd2_rn(Y[q], npy);
     float2 dz = __fadd2_rn(Z[q], npz);
@@ -89,14 +91,16 @@ __device__ __forceinline__ void block_masks(const Grid& g, const float* cx, cons
     t = __ffma2_rn(dy, dy, t);
     t = __ffma2_rn(dz, dz, t);
     const float2 u = __fadd2_rn(t, dlh);   // r2 - hi
-    hA |= (__float_as_uint(t.x) >> 31) << q;
-    hB |= (__float_as_uint(t.y) >> 31) << q;
-    uA |= (__float_as_uint(u.x) >> 31) << q;
-    uB |= (__float_as_uint(u.y) >> 31) << q;
+    hA = __funnelshift_l(__float_as_uint(t.x), hA, 1);
+    hB = __funnelshift_l(__float_as_uint(t.y), hB, 1);
+    uA = __funnelshift_l(__float_as_uint(u.x), uA, 1);
+    uB = __funnelshift_l(__float_as_uint(u.y), uB, 1);
   }
-  hit = (uint64_t)hA | ((uint64_t)hB << 32);
-  unc = ((uint64_t)uA | ((uint64_t)uB << 32)) & ~hit;
+  hit = ((uint64_t)hA << 32) | hB;
+  unc = (((uint64_t)uA << 32) | uB) & ~hit;
 }
+
+constexpr uint64_t kTop = 1ull << 63;
 
 // Builds the lists of every target of occupied cell `code` (one warp; the
 // warp owns W).  Counts tested candidates and exact FP64 tests.
@@ -162,19 +166,19 @@ __device__ __forceinline__ void find_cell(const Grid& g, uint32_t code, const St
                           hit, unc);
         // candidates inside the margin: exact FP64 test
         while (unc) {
-          const int q = __ffsll((long long)unc) - 1;
-          unc &= unc - 1;
+          const int q = __clzll((long long)unc);
+          unc ^= kTop >> q;
           const int b = entry_index(W.entry[jb + q]);
           if (exact_neighbor(g, s.x[a], s.y[a], s.z[a], s.h[a], s.x[b], s.y[b], s.z[b]))
-            hit |= 1ull << q;
+            hit |= kTop >> q;
           ++exact;
         }
-        if (self >= jb && self < jb + 64) hit &= ~(1ull << (self - jb));
+        if (self >= jb && self < jb + 64) hit &= ~(kTop >> (self - jb));
         if (!active) hit = 0;
         uint32_t* row = nbr + (int64_t)a * max_nb;
-        while (hit) {
-          const int q = __ffsll((long long)hit) - 1;
-          hit &= hit - 1;
+        while (hit) {  // slot order
+          const int q = __clzll((long long)hit);
+          hit ^= kTop >> q;
           if (k < max_nb) row[k] = W.entry[jb + q];
           ++k;
         }

@@ -58,13 +58,25 @@ __global__ void k_grid_reduce(StateView in, int64_t n, sph_params prm, Grid* g, 
     last = (done == gridDim.x - 1);
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
+  // last block: every thread folds a strided subset of the block partials
+  // (read from L2), then warp and block trees (min/max: order-free)
   __threadfence();
   double r[7] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0};
-  for (unsigned int b = 0; b < gridDim.x; ++b) {
-    const volatile double* pb = part + b * 8;
-    for (int k = 0; k < 3; ++k) r[k] = fmin(r[k], pb[k]);
-    for (int k = 3; k < 7; ++k) r[k] = fmax(r[k], pb[k]);
+  for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    const double* pb = part + b * 8;
+    for (int k = 0; k < 3; ++k) r[k] = fmin(r[k], __ldcg(pb + k));
+    for (int k = 3; k < 7; ++k) r[k] = fmax(r[k], __ldcg(pb + k));
+  }
+  for (int k = 0; k < 3; ++k) r[k] = warp_min(r[k]);
+  for (int k = 3; k < 7; ++k) r[k] = warp_max(r[k]);
+  if (l == 0)
+    for (int k = 0; k < 7; ++k) sh[w][k] = r[k];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) {
+    for (int k = 0; k < 3; ++k) r[k] = fmin(r[k], sh[ww][k]);
+    for (int k = 3; k < 7; ++k) r[k] = fmax(r[k], sh[ww][k]);
   }
   *counter = 0;
   Grid G;

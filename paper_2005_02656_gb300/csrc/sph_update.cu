@@ -11,8 +11,8 @@
 //             neighbour-count statistics of the new state (section 4.2: the
 //             optional conservation reduction)
 // k_diag      the same sums for any state
-// Cross-block totals are summed in block order with compensation, so every
-// reduction here is deterministic.
+// Cross-block totals are combined by the last block in a fixed-shape tree, so
+// every reduction here is deterministic.
 #include <cuda_runtime.h>
 
 #include "sph_device.cuh"
@@ -53,18 +53,44 @@ __device__ __forceinline__ void block_sums(double (&v)[NV], double* part) {
   }
 }
 
-__device__ void finalize_sums(const double* part, int nblocks, int nv, double* out) {
-  // thread k < nv: compensated sum over blocks in block order
-  int k = threadIdx.x;
-  if (k >= nv) return;
-  double s = 0.0, comp = 0.0;
-  for (int b = 0; b < nblocks; ++b) {
-    double y = ((const volatile double*)part)[b * kParts + k] - comp;
-    double t = s + y;
-    comp = (t - s) - y;
-    s = t;
+// The last block's reduction of the per-block partials part[b * kParts + k]:
+// every thread takes the blocks b = tid, tid + blockDim, ... in order, then a
+// fixed-shape warp and block tree combines them, so the result does not
+// depend on timing.  Reads go to L2 (the partials were written by other
+// blocks before their fence and counter increment).  Called by all threads of
+// the block; out (shared) receives the NV results.
+enum class Op { kSum, kMin, kMax };
+
+__device__ __forceinline__ double op_apply(Op op, double a, double b) {
+  return op == Op::kSum ? a + b : (op == Op::kMin ? fmin(a, b) : fmax(a, b));
+}
+
+template <int NV>
+__device__ void finalize_block(const double* part, int nblocks, const Op (&op)[NV],
+                               double* out) {
+  __shared__ double sh[kThreads / 32][NV];
+  double v[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+    v[k] = op[k] == Op::kSum ? 0.0 : (op[k] == Op::kMin ? INFINITY : -INFINITY);
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = op_apply(op[k], v[k], __ldcg(part + b * kParts + k));
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+    for (int o = 16; o > 0; o >>= 1) v[k] = op_apply(op[k], v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[w][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    const int k = threadIdx.x;
+    double r = sh[0][k];
+    for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) r = op_apply(op[k], r, sh[ww][k]);
+    out[k] = r;
   }
-  out[k] = s;
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kThreads) k_timestep(const double* h, const double* c, int64_t n,
@@ -84,10 +110,12 @@ __global__ void __launch_bounds__(kThreads) k_timestep(const double* h, const do
     part[blockIdx.x * kParts] = mn;
   }
   if (!block_last(counter)) return;
+  __threadfence();
+  __shared__ double res[1];
+  const Op ops[1] = {Op::kMin};
+  finalize_block<1>(part, gridDim.x, ops, res);
   if (threadIdx.x == 0) {
-    double m = INFINITY;
-    for (unsigned int b = 0; b < gridDim.x; ++b)
-      m = fmin(m, ((const volatile double*)part)[b * kParts]);
+    const double m = res[0];
     const double prev = *dt_io;
     double dt = courant * m;
     if (prev > 0.0) dt = fmin(dt, growth * prev);
@@ -186,27 +214,19 @@ __global__ void __launch_bounds__(kThreads) k_update(StateView s, OutView o, Sta
   }
   if (!block_last(counter)) return;
   __threadfence();
-  double tmp[11];
   __shared__ double res[11];
-  if (threadIdx.x < 11) {
-    finalize_sums(part, gridDim.x, 11, res);
-  }
-  __syncthreads();
+  const Op ops[11] = {Op::kSum, Op::kSum, Op::kSum, Op::kSum, Op::kSum, Op::kSum,
+                      Op::kSum, Op::kSum, Op::kMin, Op::kMax, Op::kSum};
+  finalize_block<11>(part, gridDim.x, ops, res);
   if (threadIdx.x == 0) {
     for (int k = 0; k < 8; ++k) diag[k] = res[k];
-    double mn = INFINITY, mx = -INFINITY;
-    for (unsigned int b = 0; b < gridDim.x; ++b) {
-      mn = fmin(mn, ((const volatile double*)part)[b * kParts + 8]);
-      mx = fmax(mx, ((const volatile double*)part)[b * kParts + 9]);
-    }
-    diag[9] = mn;
-    diag[10] = mx;
+    diag[9] = res[8];
+    diag[10] = res[9];
     diag[11] = res[10];
     stats[2] += (unsigned long long)res[10];
     stats[3] += (unsigned long long)n;
     *counter = 0;
   }
-  (void)tmp;
 }
 
 __global__ void __launch_bounds__(kThreads) k_diag(StateView s, int64_t n, double* diag,
@@ -229,8 +249,9 @@ __global__ void __launch_bounds__(kThreads) k_diag(StateView s, int64_t n, doubl
   if (!block_last(counter)) return;
   __threadfence();
   __shared__ double res[8];
-  if (threadIdx.x < 8) finalize_sums(part, gridDim.x, 8, res);
-  __syncthreads();
+  const Op ops[8] = {Op::kSum, Op::kSum, Op::kSum, Op::kSum,
+                     Op::kSum, Op::kSum, Op::kSum, Op::kSum};
+  finalize_block<8>(part, gridDim.x, ops, res);
   if (threadIdx.x < 8) diag[threadIdx.x] = res[threadIdx.x];
   if (threadIdx.x == 0) *counter = 0;
 }
