@@ -152,7 +152,7 @@ int dalloc(sph_ctx* ctx, T** p, size_t count, size_t* total) {
 }
 
 void free_all(sph_ctx* ctx) {
-  void* ptrs[] = {ctx->grid, ctx->err, ctx->dt_dev, ctx->diag, ctx->code, ctx->slot,
+  void* ptrs[] = {ctx->grid, ctx->err, ctx->dt_dev, ctx->diag, ctx->hfac, ctx->code, ctx->slot,
                   ctx->perm_tmp, ctx->perm, ctx->tbl_count, ctx->tbl_start, ctx->occ,
                   ctx->scan_part, ctx->cell_of, ctx->s.x, ctx->s_id_buf, ctx->pos32,
                   ctx->cell3, ctx->nn, ctx->nbr, ctx->vol, ctx->rec_d, ctx->rec_i, ctx->rec_m, ctx->red.part, ctx->red.counter, ctx->stats, ctx->hm_buf, ctx->hm_id};
@@ -247,6 +247,7 @@ int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {
   }
   ctx->prm = *params;
   ctx->n_max = n_max;
+  ctx->hfac_ng = -1;
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -265,6 +266,7 @@ int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {
   ALLOC(ctx->err, 1);
   ALLOC(ctx->dt_dev, 1);
   ALLOC(ctx->diag, 32);
+  ALLOC(ctx->hfac, sph::kHTab);
   ALLOC(ctx->code, n);
   ALLOC(ctx->slot, n);
   ALLOC(ctx->perm_tmp, n);

@@ -14,6 +14,7 @@ constexpr uint32_t kMaxTable = 1u << (3 * kMaxCellBits);
 constexpr int kReduceBlocks = 1024;             // partial slots of grid reductions
 constexpr int kScanItems = 4096;                // cell-table entries per scan block
 constexpr int kProfRing = 64;                   // step event sets kept before folding
+constexpr int kHTab = 4097;                     // h factors tabulated for counts 0..4096
 
 // Cell grid of the current step, computed on the device from the particles'
 // extent and h_max, read by every later kernel of the step.
@@ -72,6 +73,8 @@ struct sph_ctx {
   double* dt_dev;       // scratch dt (host-step path)
   double* diag;         // 16 doubles: [0..7] sums of the new state, [8] dt,
                         // [9] min nn, [10] max nn, [11] sum nn, [12] dt_prev
+  double* hfac;         // kHTab: 0.5 (1 + cbrt(ng_target / max(k, 1))) for count k
+  int hfac_ng;          // ng_target the table was built for (-1: none)
 
   // sort
   uint32_t* code;       // Morton cell code per particle (input order)
@@ -163,6 +166,9 @@ void launch_momentum_f32(sph_ctx* ctx, const StateView& s, const OutView& o, int
 // --- sph_update.cu ---
 void launch_timestep(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n, double* dt_io,
                      cudaStream_t st);
+// Table of the smoothing-length factor per neighbour count (rebuilt when
+// ng_target changes).
+void launch_hfac_table(sph_ctx* ctx, cudaStream_t st);
 // Update from the sorted scratch `s` into the caller's state `dst`.
 void launch_update(sph_ctx* ctx, const StateView& s, const OutView& o, const StateView& dst,
                    int64_t n, const double* dt_io, cudaStream_t st);

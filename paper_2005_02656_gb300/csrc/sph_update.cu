@@ -127,9 +127,23 @@ __global__ void __launch_bounds__(kThreads) k_timestep(const double* h, const do
   }
 }
 
+// h factor of the rule h <- h (1 + (n_t / max(nn, 1))^(1/3)) / 2: the product
+// h * [0.5 (1 + c)] equals (h * 0.5) * (1 + c) bit for bit (scaling by 0.5 is
+// exact), so the table changes no result.
+__device__ __forceinline__ double hfac_of(int ng, int cnt) {
+  const int kk = cnt > 1 ? cnt : 1;
+  return 0.5 * (1.0 + cbrt((double)ng / (double)kk));
+}
+
+__global__ void k_hfac_table(double* tab, int ng) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kHTab; k += gridDim.x * blockDim.x)
+    tab[k] = hfac_of(ng, k);
+}
+
 __global__ void __launch_bounds__(kThreads) k_update(StateView s, OutView o, StateView d,
                                                      const int32_t* nn, int64_t n,
-                                                     sph_params prm, double* diag, double* part,
+                                                     sph_params prm, const double* hfac,
+                                                     double* diag, double* part,
                                                      unsigned int* counter,
                                                      unsigned long long* stats) {
   const double dt = diag[8], dt_prev = diag[12];
@@ -162,10 +176,8 @@ __global__ void __launch_bounds__(kThreads) k_update(StateView s, OutView o, Sta
     const double un = dt_prev > 0.0 ? u + dt * ((1.0 + q) * du - q * s.du_prev[p]) : u + dt * du;
     const int cnt = nn[p];
     double h = s.h[p];
-    if (prm.ng_target > 0) {
-      const int kk = cnt > 1 ? cnt : 1;
-      h = h * 0.5 * (1.0 + cbrt((double)prm.ng_target / (double)kk));
-    }
+    if (prm.ng_target > 0)
+      h = h * (cnt >= 0 && cnt < kHTab ? __ldg(hfac + cnt) : hfac_of(prm.ng_target, cnt));
     const double m = s.m[p];
     d.x[p] = xn[0];
     d.y[p] = xn[1];
@@ -275,12 +287,19 @@ void launch_timestep(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t
   ctx->launches += 1;
 }
 
+void launch_hfac_table(sph_ctx* ctx, cudaStream_t st) {
+  k_hfac_table<<<(kHTab + 255) / 256, 256, 0, st>>>(ctx->hfac, ctx->prm.ng_target);
+  ctx->hfac_ng = ctx->prm.ng_target;
+  ctx->launches += 1;
+}
+
 void launch_update(sph_ctx* ctx, const StateView& s, const OutView& o, const StateView& dst,
                    int64_t n, const double* dt_io, cudaStream_t st) {
   (void)dt_io;
+  if (ctx->hfac_ng != ctx->prm.ng_target) launch_hfac_table(ctx, st);
   k_update<<<red_blocks(n, ctx->sm_count), kThreads, 0, st>>>(
-      s, o, dst, ctx->nn, n, ctx->prm, ctx->diag, ctx->red.part, ctx->red.counter + 2,
-      ctx->stats);
+      s, o, dst, ctx->nn, n, ctx->prm, ctx->hfac, ctx->diag, ctx->red.part,
+      ctx->red.counter + 2, ctx->stats);
   ctx->launches += 1;
 }
 
