@@ -31,7 +31,7 @@ namespace find {
 
 constexpr int kFindWarps = 4;
 constexpr int kFindThreads = 32 * kFindWarps;
-constexpr int kFindWindow = 768;   // staged candidates per warp and pass (9 KB)
+constexpr int kFindWindow = 512;   // staged candidates per warp and pass (6 KB)
 constexpr float kFar = 1.0e18f;    // position of padding slots (never a neighbour)
 
 __device__ __forceinline__ float wrap_axis(float d, const Grid& g, int ax) {
