@@ -298,6 +298,7 @@ def run_ensemble(args, dev, windows):
     ens.replay()                                  # warm-up replay
     ens.synchronize()
     l0 = ens.info()["launches"]
+    ens.phase_times()                             # clears the device phase timer
     stream = ens._graph_stream
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -308,6 +309,7 @@ def run_ensemble(args, dev, windows):
     torch.cuda.synchronize()
     windows["ensemble"] = (tw0, time.time())
     ms = e0.elapsed_time(e1)
+    phase_ms, phase_steps = ens.phase_times()
     flags = ens.error_word()
     info = ens.info()
     n = info["particles"]
@@ -317,9 +319,10 @@ def run_ensemble(args, dev, windows):
             "unit": UNIT, "n_particles": n, "n_boxes": 256, "steps": args.ensemble_steps,
             "ms_per_step": ms / args.ensemble_steps, "gpu_launches": info["launches"] - l0,
             "persistent_ctas": info["ctas"], "error_flags": flags,
-            "autotune": {"cell_factor": tune["cell_factor"], "blocks_per_sm": tune["blocks_per_sm"],
-                         "tried": [{"s_per_step": t, "cell_factor": c, "blocks_per_sm": b}
-                                   for t, c, b in tune["tried"]]}}
+            "phase_ms_per_step": {k: round(v, 4) for k, v in phase_ms.items()},
+            "phase_steps": phase_steps,
+            "autotune": {k: tune[k] for k in ("cell_factor", "find_window", "threads_per_particle",
+                                              "blocks_per_sm", "seconds_per_step", "tried")}}
 
 
 def run_adjoint(args, dev, windows, steps=20, every=5):

@@ -241,6 +241,12 @@ typedef struct {
   int blocks_per_sm;   /* persistent CTAs per SM, 0 = the occupancy maximum [0]   */
   int test_skip_block; /* test hook: this CTA leaves before the first barrier so
                           the others' bounded wait expires; -1 disables [-1]     */
+  int find_window;     /* tile shape of the neighbour search: candidate slots
+                          staged per warp, 128, 256 or 512 [512]; smaller
+                          windows leave more of the SM's L1 to the pair phases */
+  int threads_per_particle; /* lanes sharing one particle's neighbour list in
+                          the density, IAD and momentum phases: 1, 2 or 4 [1];
+                          with 1 a box's results equal a single-box sph_step */
 } sph_ens_config;
 
 SPH_API void sph_ens_default_config(sph_ens_config* c);
@@ -276,6 +282,15 @@ SPH_API int sph_ensemble_error_word(sph_ens* e, uint32_t* flags);
 SPH_API const char* sph_ensemble_last_error(const sph_ens* e);
 /* out[0] particles, out[1] boxes, out[2] persistent CTAs, out[3] launches. */
 SPH_API int sph_ensemble_info(const sph_ens* e, int64_t* out);
+/* Phases of one ensemble step, in launch order (SPH_ENS_NPHASE of them). */
+#define SPH_ENS_NPHASE 15
+/* Milliseconds per phase (ms[SPH_ENS_NPHASE], HOST) accumulated over *steps
+ * steps since the last call, measured on the device by block 0 between grid
+ * barriers (the slowest block's time for each phase; with SPH_FLAG_TIMEOUT the
+ * sums are partial).  Phases: reset, extent, grid, count, scan, cell items,
+ * scatter, in-cell order, gather, find, density, IAD, momentum, dt, update.
+ * Synchronises the device and clears the sums. */
+SPH_API int sph_ensemble_phase_times(sph_ens* e, double* ms, int64_t* steps);
 
 /* ------------------------------------------------------------------------ */
 /* Differentiable rollout: the gradient of a scalar of the state after K     */

@@ -43,10 +43,12 @@ EXPORTS = ("sph_default_params", "sph_init", "sph_destroy", "sph_set_params", "s
            "sph_ens_default_config", "sph_ensemble_init", "sph_ensemble_destroy",
            "sph_ensemble_set_config", "sph_ensemble_step", "sph_ensemble_capture",
            "sph_ensemble_replay", "sph_ensemble_error_word", "sph_ensemble_last_error",
-           "sph_ensemble_info", "sph_adjoint_init", "sph_adjoint_destroy", "sph_adjoint_forward",
+           "sph_ensemble_info", "sph_ensemble_phase_times", "sph_adjoint_init", "sph_adjoint_destroy", "sph_adjoint_forward",
            "sph_adjoint_backward", "sph_adjoint_info", "sph_adjoint_time_steps",
            "sph_adjoint_last_error")
 STAGES = ("sort", "find", "density", "iad", "momentum", "dt", "update")
+ENS_PHASES = ("reset", "extent", "grid", "count", "scan", "items", "scatter", "order", "gather",
+              "find", "density", "iad", "momentum", "dt", "update")
 
 
 class SphState(C.Structure):
@@ -65,7 +67,8 @@ class SphParams(C.Structure):
 
 class EnsConfig(C.Structure):
     _fields_ = [("cell_factor", C.c_double), ("blocks_per_sm", C.c_int),
-                ("test_skip_block", C.c_int)]
+                ("test_skip_block", C.c_int), ("find_window", C.c_int),
+                ("threads_per_particle", C.c_int)]
 
 
 class SphError(RuntimeError):
@@ -141,6 +144,8 @@ def load(path: str = LIB_PATH):
     lib.sph_ensemble_last_error.restype = C.c_char_p
     lib.sph_ensemble_info.argtypes = [ctxp, P]
     lib.sph_ensemble_info.restype = I
+    lib.sph_ensemble_phase_times.argtypes = [ctxp, P, P]
+    lib.sph_ensemble_phase_times.restype = I
     lib.sph_adjoint_init.argtypes = [pp, I64, I, I, C.POINTER(ctxp)]
     lib.sph_adjoint_init.restype = I
     lib.sph_adjoint_destroy.argtypes = [ctxp]

@@ -20,6 +20,7 @@
 //   4.2) -> IAD -> momentum/energy (Eqs. 2-5) -> dt -> update (4.1).
 #include <cuda_runtime.h>
 #include <stdarg.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -51,11 +52,24 @@ struct Box {
   int has_nonfinite;
 };
 
+constexpr int kPhases = 15;
+
 struct Sync {
   unsigned int count;
   unsigned int gen;
   unsigned int abort;
+  unsigned int pad;
+  // phase timer: nanoseconds between the barrier completions seen by block 0
+  // (the slowest block's time for each phase), and the number of steps
+  unsigned long long ptime[kPhases];
+  unsigned long long psteps;
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 struct Args {
   Box* boxes;
@@ -86,6 +100,7 @@ struct Args {
   float Bn;
   double cell_factor;    // cells of side >= cell_factor * 2 h_max
   int skip_block;        // test hook (sph_ens_config::test_skip_block)
+  int tpp;               // threads per particle of the pair phases (1, 2, 4)
 };
 
 // --- ordered-integer encodings of doubles for atomic min/max ---
@@ -409,7 +424,8 @@ __device__ void ph_gather(const Args& A) {
   }
 }
 
-__device__ void ph_find(const Args& A, find::FindWarpSmem& W) {
+template <int WIN>
+__device__ void ph_find(const Args& A, find::FindWarpSmemT<WIN>& W) {
   const int64_t nitems = A.item_off[A.nbox];
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long tested = 0, exact = 0;
@@ -421,11 +437,11 @@ __device__ void ph_find(const Args& A, find::FindWarpSmem& W) {
     const uint32_t* ts = A.tbl_start + B.tbl_off;
     const uint32_t* tc = A.tbl_count + B.tbl_off;
     if (B.g.wrap32)
-      find::find_cell<true>(B.g, code, A.s, A.pos32, ts, tc, A.nn, A.nbr, A.prm.max_nb, A.err, W,
-                            tested, exact);
+      find::find_cell<true, WIN>(B.g, code, A.s, A.pos32, ts, tc, A.nn, A.nbr, A.prm.max_nb,
+                                 A.err, W, tested, exact);
     else
-      find::find_cell<false>(B.g, code, A.s, A.pos32, ts, tc, A.nn, A.nbr, A.prm.max_nb, A.err,
-                             W, tested, exact);
+      find::find_cell<false, WIN>(B.g, code, A.s, A.pos32, ts, tc, A.nn, A.nbr, A.prm.max_nb,
+                                  A.err, W, tested, exact);
   }
 }
 
@@ -445,48 +461,96 @@ __device__ __forceinline__ pairs32::Lists lists_of(const Args& A) {
   return l;
 }
 
+// The pair phases run NSUB threads per particle (sph_ens_config::
+// threads_per_particle): thread t of the grid-stride sweep works on particle
+// t / NSUB as sub-lane t % NSUB, and every warp runs the loop uniformly (the
+// group sums are warp shuffles).  The box's Grid is copied into registers,
+// since the pair loop reads it for every pair.
+
 // density + EOS, and the per-box minimum of h / c for the time step
-__device__ void ph_density(const Args& A) {
+template <int NSUB>
+__device__ void ph_density_t(const Args& A) {
   const pairs32::F32 f = f32_of(A);
   const pairs32::Lists L = lists_of(A);
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < A.n; base += stride) {
-    const int64_t p = base + threadIdx.x;
-    const bool on = p < A.n;
+  const int lane = threadIdx.x & 31, sub = threadIdx.x % NSUB;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, total = A.n * NSUB;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += stride) {
+    const int64_t t = base + threadIdx.x;
+    const bool on = t < total;
+    const int64_t p = on ? t / NSUB : 0;
     const int b = on ? A.box_of[p] : -1;
-    double q = INFINITY;
-    if (on) {
-      pairs32::density_one(p, A.boxes[b].g, f, A.out, A.s.u, L, A.Bn, (int)A.prm.sinc_n,
-                           A.prm.gamma, A.err);
-      q = A.s.h[p] / A.out.c[p];
-    }
+    const Grid g = A.boxes[on ? b : 0].g;
+    pairs32::density_one<NSUB>(p, g, f, A.out, A.s.u, L, A.Bn, (int)A.prm.sinc_n, A.prm.gamma,
+                               A.err, on, sub);
+    const bool own = on && sub == 0;
+    const double q = own ? A.s.h[p] / A.out.c[p] : INFINITY;
+    const int bq = own ? b : -1;
     const int b0 = __shfl_sync(0xffffffffu, b, 0);
     if (__all_sync(0xffffffffu, b == b0 || b < 0) && b0 >= 0) {
-      for (int o = 16; o > 0; o >>= 1) q = fmin(q, __shfl_xor_sync(0xffffffffu, q, o));
-      if (lane == 0) atomicMin(&A.boxes[b0].qmin_o, ord(q));
-    } else if (on) {
-      atomicMin(&A.boxes[b].qmin_o, ord(q));
+      double m = q;
+      for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) atomicMin(&A.boxes[b0].qmin_o, ord(m));
+    } else if (bq >= 0) {
+      atomicMin(&A.boxes[bq].qmin_o, ord(q));
     }
   }
 }
 
-__device__ void ph_iad(const Args& A) {
+template <int NSUB>
+__device__ void ph_iad_t(const Args& A) {
   const pairs32::F32 f = f32_of(A);
   const pairs32::Lists L = lists_of(A);
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < A.n;
-       p += (int64_t)gridDim.x * blockDim.x)
-    pairs32::iad_one(p, A.boxes[A.box_of[p]].g, f, A.out, L, (int)A.prm.sinc_n, A.err);
+  const int sub = threadIdx.x % NSUB;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, total = A.n * NSUB;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += stride) {
+    const int64_t t = base + threadIdx.x;
+    const bool on = t < total;
+    const int64_t p = on ? t / NSUB : 0;
+    const Grid g = A.boxes[on ? A.box_of[p] : 0].g;
+    pairs32::iad_one<NSUB>(p, g, f, A.out, L, (int)A.prm.sinc_n, A.err, on, sub);
+  }
 }
 
-__device__ void ph_momentum(const Args& A) {
+template <int NSUB>
+__device__ void ph_momentum_t(const Args& A) {
   const pairs32::F32 f = f32_of(A);
   const pairs32::Lists L = lists_of(A);
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < A.n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const Box& B = A.boxes[A.box_of[p]];
-    pairs32::momentum_one(p, B.g, f, A.out, L, (int)A.prm.sinc_n, (float)B.alpha, A.err);
+  const int sub = threadIdx.x % NSUB;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, total = A.n * NSUB;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += stride) {
+    const int64_t t = base + threadIdx.x;
+    const bool on = t < total;
+    const int64_t p = on ? t / NSUB : 0;
+    const Box& B = A.boxes[on ? A.box_of[p] : 0];
+    const Grid g = B.g;
+    pairs32::momentum_one<NSUB>(p, g, f, A.out, L, (int)A.prm.sinc_n, (float)B.alpha, A.err, on,
+                                sub);
   }
+}
+
+__device__ void ph_density(const Args& A) {
+  if (A.tpp == 4)
+    ph_density_t<4>(A);
+  else if (A.tpp == 2)
+    ph_density_t<2>(A);
+  else
+    ph_density_t<1>(A);
+}
+__device__ void ph_iad(const Args& A) {
+  if (A.tpp == 4)
+    ph_iad_t<4>(A);
+  else if (A.tpp == 2)
+    ph_iad_t<2>(A);
+  else
+    ph_iad_t<1>(A);
+}
+__device__ void ph_momentum(const Args& A) {
+  if (A.tpp == 4)
+    ph_momentum_t<4>(A);
+  else if (A.tpp == 2)
+    ph_momentum_t<2>(A);
+  else
+    ph_momentum_t<1>(A);
 }
 
 // dt_n = min(courant * min h/c, dt_growth * dt_{n-1}) per box (section 4.2)
@@ -555,42 +619,42 @@ __device__ void ph_update(const Args& A) {
   }
 }
 
+template <int WIN>
 __global__ void __launch_bounds__(kThreads) k_ensemble(Args A, int steps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  find::FindWarpSmem& W = reinterpret_cast<find::FindWarpSmem*>(smem_raw)[threadIdx.x >> 5];
+  find::FindWarpSmemT<WIN>& W =
+      reinterpret_cast<find::FindWarpSmemT<WIN>*>(smem_raw)[threadIdx.x >> 5];
   if ((int)blockIdx.x == A.skip_block) return;  // test hook: the others' wait expires
-  for (int step = 0; step < steps; ++step) {
-    ph_reset(A);
-    if (!grid_sync(A.sync, A.err)) return;
-    ph_extent(A);
-    if (!grid_sync(A.sync, A.err)) return;
-    ph_grid(A);
-    if (!grid_sync(A.sync, A.err)) return;
-    ph_count(A);
-    if (!grid_sync(A.sync, A.err)) return;
-    ph_scan(A);
-    if (!grid_sync(A.sync, A.err)) return;
-    ph_items(A);
-    if (!grid_sync(A.sync, A.err)) return;
-    ph_scatter(A);
-    if (!grid_sync(A.sync, A.err)) return;
-    ph_order(A);
-    if (!grid_sync(A.sync, A.err)) return;
-    ph_gather(A);
-    if (!grid_sync(A.sync, A.err)) return;
-    ph_find(A, W);
-    if (!grid_sync(A.sync, A.err)) return;
-    ph_density(A);
-    if (!grid_sync(A.sync, A.err)) return;
-    ph_iad(A);
-    if (!grid_sync(A.sync, A.err)) return;
-    ph_momentum(A);
-    if (!grid_sync(A.sync, A.err)) return;
-    ph_dt(A);
-    if (!grid_sync(A.sync, A.err)) return;
-    ph_update(A);
-    if (!grid_sync(A.sync, A.err)) return;
+  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+  unsigned long long t_last = timer ? global_ns() : 0ull;
+  // runs one phase, the grid barrier after it, and the phase timer
+#define SPH_PHASE(k, call)                                   \
+  call;                                                      \
+  if (!grid_sync(A.sync, A.err)) return;                     \
+  if (timer) {                                               \
+    const unsigned long long t = global_ns();                \
+    A.sync->ptime[k] += t - t_last;                          \
+    t_last = t;                                              \
   }
+  for (int step = 0; step < steps; ++step) {
+    SPH_PHASE(0, ph_reset(A))
+    SPH_PHASE(1, ph_extent(A))
+    SPH_PHASE(2, ph_grid(A))
+    SPH_PHASE(3, ph_count(A))
+    SPH_PHASE(4, ph_scan(A))
+    SPH_PHASE(5, ph_items(A))
+    SPH_PHASE(6, ph_scatter(A))
+    SPH_PHASE(7, ph_order(A))
+    SPH_PHASE(8, ph_gather(A))
+    SPH_PHASE(9, ph_find<WIN>(A, W))
+    SPH_PHASE(10, ph_density(A))
+    SPH_PHASE(11, ph_iad(A))
+    SPH_PHASE(12, ph_momentum(A))
+    SPH_PHASE(13, ph_dt(A))
+    SPH_PHASE(14, ph_update(A))
+    if (timer) A.sync->psteps += 1;
+  }
+#undef SPH_PHASE
 }
 
 }  // namespace ens
@@ -735,6 +799,7 @@ Args args_of(sph_ens* e, const sph_state* st, double* dt_dev) {
   A.Bn = (float)e->Bn;
   A.cell_factor = e->cfg.cell_factor;
   A.skip_block = e->cfg.test_skip_block;
+  A.tpp = e->cfg.threads_per_particle;
   return A;
 }
 
@@ -750,32 +815,59 @@ int check_ens_state(sph_ens* e, const sph_state* s, const double* dt) {
   return SPH_OK;
 }
 
+// The kernel instance and its shared memory for a find window (tile shape).
+template <int WIN>
+size_t window_smem() {
+  return sph::find::kFindWarps * sizeof(sph::find::FindWarpSmemT<WIN>);
+}
+
 int launch(sph_ens* e, const Args& A, int steps, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(e->blocks);
   cfg.blockDim = dim3(sph::ens::kThreads);
-  cfg.dynamicSmemBytes = sph::find::kFindWarps * sizeof(sph::find::FindWarpSmem);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t err = cudaLaunchKernelEx(&cfg, sph::ens::k_ensemble, A, steps);
+  cudaError_t err;
+  switch (e->cfg.find_window) {
+    case 128:
+      cfg.dynamicSmemBytes = window_smem<128>();
+      err = cudaLaunchKernelEx(&cfg, sph::ens::k_ensemble<128>, A, steps);
+      break;
+    case 256:
+      cfg.dynamicSmemBytes = window_smem<256>();
+      err = cudaLaunchKernelEx(&cfg, sph::ens::k_ensemble<256>, A, steps);
+      break;
+    default:
+      cfg.dynamicSmemBytes = window_smem<512>();
+      err = cudaLaunchKernelEx(&cfg, sph::ens::k_ensemble<512>, A, steps);
+      break;
+  }
   if (err != cudaSuccess)
     return ens_fail(e, SPH_ERR_CUDA, "ensemble launch: %s", cudaGetErrorString(err));
   e->launches += 1;
   return SPH_OK;
 }
 
-int configure(sph_ens* e) {
-  const size_t smem = sph::find::kFindWarps * sizeof(sph::find::FindWarpSmem);
-  cudaError_t err = cudaFuncSetAttribute(sph::ens::k_ensemble,
+template <int WIN>
+cudaError_t occupancy(int* per_sm) {
+  const size_t smem = window_smem<WIN>();
+  cudaError_t err = cudaFuncSetAttribute(sph::ens::k_ensemble<WIN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0;
   if (err == cudaSuccess)
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sph::ens::k_ensemble,
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, sph::ens::k_ensemble<WIN>,
                                                         sph::ens::kThreads, smem);
+  return err;
+}
+
+int configure(sph_ens* e) {
+  int per_sm = 0;
+  cudaError_t err = e->cfg.find_window == 128   ? occupancy<128>(&per_sm)
+                    : e->cfg.find_window == 256 ? occupancy<256>(&per_sm)
+                                                : occupancy<512>(&per_sm);
   if (err != cudaSuccess || per_sm < 1)
     return ens_fail(e, SPH_ERR_CUDA, "ensemble occupancy: %s", cudaGetErrorString(err));
   int want = e->cfg.blocks_per_sm > 0 ? e->cfg.blocks_per_sm : per_sm;
@@ -793,6 +885,8 @@ void sph_ens_default_config(sph_ens_config* c) {
   c->cell_factor = 1.0;
   c->blocks_per_sm = 0;
   c->test_skip_block = -1;
+  c->find_window = 512;
+  c->threads_per_particle = 1;
 }
 
 int sph_ensemble_init(const sph_params* common, int n_boxes, const int64_t* box_n,
@@ -905,6 +999,11 @@ int sph_ensemble_set_config(sph_ens* e, const sph_ens_config* c) {
   if (!e || !c) return SPH_ERR_INVALID_ARG;
   if (!(c->cell_factor >= 1.0 && c->cell_factor <= 4.0) || c->blocks_per_sm < 0)
     return ens_fail(e, SPH_ERR_INVALID_ARG, "cell_factor must be in [1, 4]");
+  if (c->find_window != 128 && c->find_window != 256 && c->find_window != 512)
+    return ens_fail(e, SPH_ERR_INVALID_ARG, "find_window must be 128, 256 or 512");
+  if (c->threads_per_particle != 1 && c->threads_per_particle != 2 &&
+      c->threads_per_particle != 4)
+    return ens_fail(e, SPH_ERR_INVALID_ARG, "threads_per_particle must be 1, 2 or 4");
   e->cfg = *c;
   if (e->graph) {
     cudaGraphExecDestroy(e->graph);
@@ -968,6 +1067,22 @@ int sph_ensemble_error_word(sph_ens* e, uint32_t* flags) {
 }
 
 const char* sph_ensemble_last_error(const sph_ens* e) { return e ? e->last_error : "no context"; }
+
+int sph_ensemble_phase_times(sph_ens* e, double* ms, int64_t* steps) {
+  if (!e || !ms || !steps) return SPH_ERR_INVALID_ARG;
+  sph::ens::Sync h;
+  cudaError_t err = cudaDeviceSynchronize();
+  if (err == cudaSuccess) err = cudaMemcpy(&h, e->sync, sizeof(h), cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess) {
+    const size_t off = offsetof(sph::ens::Sync, ptime);
+    err = cudaMemset((char*)e->sync + off, 0, sizeof(h) - off);
+  }
+  if (err != cudaSuccess) return ens_fail(e, SPH_ERR_CUDA, "sph_ensemble_phase_times: %s",
+                                         cudaGetErrorString(err));
+  for (int k = 0; k < sph::ens::kPhases; ++k) ms[k] = 1e-6 * (double)h.ptime[k];
+  *steps = (int64_t)h.psteps;
+  return SPH_OK;
+}
 
 int sph_ensemble_info(const sph_ens* e, int64_t* out) {
   if (!e || !out) return SPH_ERR_INVALID_ARG;

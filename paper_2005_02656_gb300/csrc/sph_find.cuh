@@ -31,7 +31,8 @@ namespace find {
 
 constexpr int kFindWarps = 4;
 constexpr int kFindThreads = 32 * kFindWarps;
-constexpr int kFindWindow = 512;   // staged candidates per warp and pass (6 KB)
+constexpr int kFindWindow = 512;   // staged candidates per warp and pass (8 KB; the
+                                   // ensemble also instantiates smaller windows)
 constexpr float kFar = 1.0e18f;    // position of padding slots (never a neighbour)
 
 __device__ __forceinline__ float wrap_axis(float d, const Grid& g, int ax) {
@@ -50,15 +51,19 @@ __device__ __forceinline__ int pair_index(int i) {
   return (blk << 6) + ((r & 31) << 1) + (r >> 5);
 }
 
-struct FindWarpSmem {
+template <int WIN>
+struct FindWarpSmemT {
+  static_assert(WIN % 64 == 0, "the window holds whole blocks of 64 slots");
   Stencil S;
   // 16-byte aligned: the candidate arrays are read as float2 pairs
-  alignas(16) float cx[kFindWindow];
-  alignas(16) float cy[kFindWindow];
-  alignas(16) float cz[kFindWindow];
-  uint32_t entry[kFindWindow];  // list entry of each staged slot (sph_tile.cuh)
+  alignas(16) float cx[WIN];
+  alignas(16) float cy[WIN];
+  alignas(16) float cz[WIN];
+  uint32_t entry[WIN];  // list entry of each staged slot (sph_tile.cuh)
 };
-static_assert(sizeof(FindWarpSmem) % 16 == 0, "per-warp window must keep 16-byte alignment");
+using FindWarpSmem = FindWarpSmemT<kFindWindow>;
+static_assert(sizeof(FindWarpSmemT<128>) % 16 == 0 && sizeof(FindWarpSmem) % 16 == 0,
+              "per-warp window must keep 16-byte alignment");
 
 // Hit and margin masks of one block of 64 staged candidates for one target.
 // The decisions r2 < lo and r2 < hi are read from the sign bits of r2 - lo and
@@ -103,13 +108,14 @@ __device__ __forceinline__ void block_masks(const Grid& g, const float* cx, cons
 constexpr uint64_t kTop = 1ull << 63;
 
 // Builds the lists of every target of occupied cell `code` (one warp; the
-// warp owns W).  Counts tested candidates and exact FP64 tests.
-template <bool WRAP>
+// warp owns W, a window of WIN staged slots).  Counts tested candidates and
+// exact FP64 tests.
+template <bool WRAP, int WIN = kFindWindow>
 __device__ __forceinline__ void find_cell(const Grid& g, uint32_t code, const StateView& s,
                                           const float4* __restrict__ pos32,
                                           const uint32_t* tbl_start, const uint32_t* tbl_count,
                                           int32_t* nn, uint32_t* nbr, int max_nb, uint32_t* err,
-                                          FindWarpSmem& W, unsigned long long& tested,
+                                          FindWarpSmemT<WIN>& W, unsigned long long& tested,
                                           unsigned long long& exact) {
   const int lane = threadIdx.x & 31;
   Stencil& S = W.S;
@@ -124,8 +130,8 @@ __device__ __forceinline__ void find_cell(const Grid& g, uint32_t code, const St
     __syncwarp();
     return;
   }
-  for (int w0 = 0; w0 < P; w0 += kFindWindow) {
-    const int wn = min(kFindWindow, P - w0);
+  for (int w0 = 0; w0 < P; w0 += WIN) {
+    const int wn = min(WIN, P - w0);
     const int wpad = (wn + 63) & ~63;
     // stage slots [w0, w0 + wn) cell by cell (no per-slot search)
     for (int sc = 0; sc < S.ncell; ++sc) {

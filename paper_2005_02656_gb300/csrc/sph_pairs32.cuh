@@ -79,25 +79,67 @@ __device__ __forceinline__ void for_entries(const uint32_t* row, int cnt, Body b
   }
 }
 
+// The entries of a row owned by sub-lane `sub` of a group of NSUB lanes that
+// share one target: 16-byte chunks c = sub, sub + NSUB, ...  NSUB = 1 is
+// for_entries (every entry, in order).
+template <int NSUB, typename Body>
+__device__ __forceinline__ void for_entries_part(const uint32_t* row, int cnt, int sub,
+                                                 Body body) {
+  if (NSUB == 1) {
+    for_entries(row, cnt, body);
+    return;
+  }
+  const uint4* r4 = reinterpret_cast<const uint4*>(row);
+  for (int c = sub; 4 * c < cnt; c += NSUB) {
+    const uint4 e = r4[c];
+    const int k = 4 * c;
+    body(e.x);
+    if (k + 1 < cnt) body(e.y);
+    if (k + 2 < cnt) body(e.z);
+    if (k + 3 < cnt) body(e.w);
+  }
+}
+
+// Sum over the NSUB lanes of a group (fixed butterfly; all 32 lanes of the
+// warp must call it).
+template <int NSUB>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = NSUB / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// The functions below compute target a with NSUB lanes (NSUB = 1, 2 or 4;
+// `sub` is the lane's index in its group, `on` false for lanes past the last
+// target).  With NSUB > 1 every lane of the warp must call them; lane sub = 0
+// writes the results.
+
 // ---------------------------------------------------------------- density --
 // Eq. 1 (self term included) and the ideal-gas EOS for particle a; writes the
 // FP64 outputs and the IAD / momentum records of a.
+template <int NSUB = 1>
 __device__ __forceinline__ void density_one(int64_t a, const Grid& g, const F32& f,
                                             const OutView& o, const double* u, const Lists& L,
-                                            float Bn, int sinc_n, double gamma, uint32_t* err) {
+                                            float Bn, int sinc_n, double gamma, uint32_t* err,
+                                            bool on = true, int sub = 0) {
   const bool wrap = g.wrap32 != 0;
-  const float4 pa = f.pos[a];
-  const float hinv2 = 1.0f / (pa.w * pa.w);
-  const float norm = Bn * hinv2 / pa.w;
-  const int cnt = min(L.nn[a], L.max_nb);
-  float acc = 0.0f;
-  for_entries(L.nbr + a * L.max_nb, cnt, [&](uint32_t e) {
-    const float4 rb = f.rec_d[entry_index(e)];
-    float dx, dy, dz;
-    rel(g, wrap, e, rb, pa, dx, dy, dz);
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    acc = fmaf(rb.w, kernel_w32(r2 * hinv2, norm, sinc_n), acc);
-  });
+  float4 pa = make_float4(0.f, 0.f, 0.f, 1.f);
+  float hinv2 = 0.f, norm = 0.f, acc = 0.0f;
+  if (on) {
+    pa = f.pos[a];
+    hinv2 = 1.0f / (pa.w * pa.w);
+    norm = Bn * hinv2 / pa.w;
+    const int cnt = min(L.nn[a], L.max_nb);
+    for_entries_part<NSUB>(L.nbr + a * L.max_nb, cnt, sub, [&](uint32_t e) {
+      const float4 rb = f.rec_d[entry_index(e)];
+      float dx, dy, dz;
+      rel(g, wrap, e, rb, pa, dx, dy, dz);
+      const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      acc = fmaf(rb.w, kernel_w32(r2 * hinv2, norm, sinc_n), acc);
+    });
+  }
+  acc = group_sum<NSUB>(acc);
+  if (!on || sub != 0) return;
   const float ma = f.rec_d[a].w;
   const float rho = fmaf(ma, norm, acc);  // self term: W(0, h_a) = B_n / h_a^3
   const double rho64 = (double)rho;
@@ -117,33 +159,45 @@ __device__ __forceinline__ void density_one(int64_t a, const Grid& g, const F32&
 // -------------------------------------------------------------------- IAD --
 // tau_a and C_a = tau_a^{-1} for particle a (separations scaled by 1/h_a so
 // that tau is of order one in FP32).
+template <int NSUB = 1>
 __device__ __forceinline__ void iad_one(int64_t a, const Grid& g, const F32& f, const OutView& o,
-                                        const Lists& L, int sinc_n, uint32_t* err) {
+                                        const Lists& L, int sinc_n, uint32_t* err,
+                                        bool on = true, int sub = 0) {
   const bool wrap = g.wrap32 != 0;
-  const float4 pa = f.pos[a];
-  const float hinv2 = f.rec_m[5 * a].w;
-  const float norm = f.rec_m[5 * a + 2].x;
-  const float inv_h = 1.0f / pa.w;
-  const int cnt = min(L.nn[a], L.max_nb);
   float t00 = 0, t01 = 0, t02 = 0, t11 = 0, t12 = 0, t22 = 0;
-  for_entries(L.nbr + a * L.max_nb, cnt, [&](uint32_t e) {
-    const float4 rb = f.rec_i[entry_index(e)];
-    float dx, dy, dz;
-    rel(g, wrap, e, rb, pa, dx, dy, dz);
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    // separation scaled by 1/h_a keeps tau of order one in FP32
-    dx *= inv_h;
-    dy *= inv_h;
-    dz *= inv_h;
-    const float w = rb.w * kernel_w32(r2 * hinv2, norm, sinc_n);
-    const float wx = w * dx, wy = w * dy, wz = w * dz;
-    t00 = fmaf(wx, dx, t00);
-    t01 = fmaf(wx, dy, t01);
-    t02 = fmaf(wx, dz, t02);
-    t11 = fmaf(wy, dy, t11);
-    t12 = fmaf(wy, dz, t12);
-    t22 = fmaf(wz, dz, t22);
-  });
+  float hinv2 = 0.f;
+  if (on) {
+    const float4 pa = f.pos[a];
+    hinv2 = f.rec_m[5 * a].w;
+    const float norm = f.rec_m[5 * a + 2].x;
+    const float inv_h = 1.0f / pa.w;
+    const int cnt = min(L.nn[a], L.max_nb);
+    for_entries_part<NSUB>(L.nbr + a * L.max_nb, cnt, sub, [&](uint32_t e) {
+      const float4 rb = f.rec_i[entry_index(e)];
+      float dx, dy, dz;
+      rel(g, wrap, e, rb, pa, dx, dy, dz);
+      const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      // separation scaled by 1/h_a keeps tau of order one in FP32
+      dx *= inv_h;
+      dy *= inv_h;
+      dz *= inv_h;
+      const float w = rb.w * kernel_w32(r2 * hinv2, norm, sinc_n);
+      const float wx = w * dx, wy = w * dy, wz = w * dz;
+      t00 = fmaf(wx, dx, t00);
+      t01 = fmaf(wx, dy, t01);
+      t02 = fmaf(wx, dz, t02);
+      t11 = fmaf(wy, dy, t11);
+      t12 = fmaf(wy, dz, t12);
+      t22 = fmaf(wz, dz, t22);
+    });
+  }
+  t00 = group_sum<NSUB>(t00);
+  t01 = group_sum<NSUB>(t01);
+  t02 = group_sum<NSUB>(t02);
+  t11 = group_sum<NSUB>(t11);
+  t12 = group_sum<NSUB>(t12);
+  t22 = group_sum<NSUB>(t22);
+  if (!on || sub != 0) return;
   const float c00 = t11 * t22 - t12 * t12;
   const float c01 = t02 * t12 - t01 * t22;
   const float c02 = t01 * t12 - t02 * t11;
@@ -175,54 +229,63 @@ __device__ __forceinline__ void iad_one(int64_t a, const Grid& g, const F32& f, 
 
 // ------------------------------------------------------- momentum/energy --
 // Eqs. 2-5 for particle a with viscosity coefficient alpha.
+template <int NSUB = 1>
 __device__ __forceinline__ void momentum_one(int64_t a, const Grid& g, const F32& f,
                                              const OutView& o, const Lists& L, int sinc_n,
-                                             float alpha, uint32_t* err) {
+                                             float alpha, uint32_t* err, bool on = true,
+                                             int sub = 0) {
   const bool wrap = g.wrap32 != 0;
-  const float4* ra = f.rec_m + 5 * a;
-  const float4 pa = ra[0];       // offset, 1/h_a^2
-  const float4 va = ra[1];       // v, m
-  const float4 qa = ra[2];       // B_n/h^3, P/rho^2, c, 1/rho
-  const float4 Aa = ra[3], Ba = ra[4];
-  const float a00 = Aa.x, a01 = Aa.y, a02 = Aa.z, a11 = Aa.w, a12 = Ba.x, a22 = Ba.y;
-  const float Xa = qa.y, csa = qa.z, ira = qa.w;
-  const int cnt = min(L.nn[a], L.max_nb);
   float accx = 0, accy = 0, accz = 0, du = 0;
-  for_entries(L.nbr + a * L.max_nb, cnt, [&](uint32_t e) {
-    // one pair of Eqs. 2-5 (x_ab = -d, d = x_b - x_a)
-    const float4* rb = f.rec_m + 5 * (int64_t)entry_index(e);
-    const float4 b0 = rb[0];
-    float dx, dy, dz;
-    rel(g, wrap, e, b0, pa, dx, dy, dz);
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    const float4 b2 = rb[2];
-    const float Wa = kernel_w32(r2 * pa.w, qa.x, sinc_n);
-    const float Wb = kernel_w32(r2 * b0.w, b2.x, sinc_n);  // clamped at t = 4 (S = 0)
-    const float Cadx = fmaf(a02, dz, fmaf(a01, dy, a00 * dx));
-    const float Cady = fmaf(a12, dz, fmaf(a11, dy, a01 * dx));
-    const float Cadz = fmaf(a22, dz, fmaf(a12, dy, a02 * dx));
-    const float4 b3 = rb[3], b4 = rb[4];
-    const float Cbdx = fmaf(b3.z, dz, fmaf(b3.y, dy, b3.x * dx));
-    const float Cbdy = fmaf(b4.x, dz, fmaf(b3.w, dy, b3.y * dx));
-    const float Cbdz = fmaf(b4.y, dz, fmaf(b4.x, dy, b3.z * dx));
-    const float4 vb = rb[1];
-    const float vabx = va.x - vb.x, vaby = va.y - vb.y, vabz = va.z - vb.z;
-    const float xv = -fmaf(dz, vabz, fmaf(dy, vaby, dx * vabx));
-    // Eq. 5 without a branch: w_ab = x_ab.v_ab / r, Pi = 0 unless approaching
-    const float w = xv * rsqrtf(r2);
-    const float vsig = csa + b2.z - 3.0f * w;
-    const float Pi = xv < 0.0f ? -0.5f * alpha * vsig * w : 0.0f;
-    const float irb = b2.w;
-    const float mb = vb.w;
-    const float fa = mb * Wa * fmaf(0.5f * Pi, ira, Xa);
-    const float fb = mb * Wb * fmaf(0.5f * Pi, irb, b2.y);
-    accx -= fmaf(fa, Cadx, fb * Cbdx);
-    accy -= fmaf(fa, Cady, fb * Cbdy);
-    accz -= fmaf(fa, Cadz, fb * Cbdz);
-    const float vCa = fmaf(vabz, Cadz, fmaf(vaby, Cady, vabx * Cadx));
-    const float vCb = fmaf(vabz, Cbdz, fmaf(vaby, Cbdy, vabx * Cbdx));
-    du = fmaf(mb, fmaf(Wa * fmaf(0.25f * Pi, ira, Xa), vCa, 0.25f * Pi * irb * Wb * vCb), du);
-  });
+  if (on) {
+    const float4* ra = f.rec_m + 5 * a;
+    const float4 pa = ra[0];       // offset, 1/h_a^2
+    const float4 va = ra[1];       // v, m
+    const float4 qa = ra[2];       // B_n/h^3, P/rho^2, c, 1/rho
+    const float4 Aa = ra[3], Ba = ra[4];
+    const float a00 = Aa.x, a01 = Aa.y, a02 = Aa.z, a11 = Aa.w, a12 = Ba.x, a22 = Ba.y;
+    const float Xa = qa.y, csa = qa.z, ira = qa.w;
+    const int cnt = min(L.nn[a], L.max_nb);
+    for_entries_part<NSUB>(L.nbr + a * L.max_nb, cnt, sub, [&](uint32_t e) {
+      // one pair of Eqs. 2-5 (x_ab = -d, d = x_b - x_a)
+      const float4* rb = f.rec_m + 5 * (int64_t)entry_index(e);
+      const float4 b0 = rb[0];
+      float dx, dy, dz;
+      rel(g, wrap, e, b0, pa, dx, dy, dz);
+      const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      const float4 b2 = rb[2];
+      const float Wa = kernel_w32(r2 * pa.w, qa.x, sinc_n);
+      const float Wb = kernel_w32(r2 * b0.w, b2.x, sinc_n);  // clamped at t = 4 (S = 0)
+      const float Cadx = fmaf(a02, dz, fmaf(a01, dy, a00 * dx));
+      const float Cady = fmaf(a12, dz, fmaf(a11, dy, a01 * dx));
+      const float Cadz = fmaf(a22, dz, fmaf(a12, dy, a02 * dx));
+      const float4 b3 = rb[3], b4 = rb[4];
+      const float Cbdx = fmaf(b3.z, dz, fmaf(b3.y, dy, b3.x * dx));
+      const float Cbdy = fmaf(b4.x, dz, fmaf(b3.w, dy, b3.y * dx));
+      const float Cbdz = fmaf(b4.y, dz, fmaf(b4.x, dy, b3.z * dx));
+      const float4 vb = rb[1];
+      const float vabx = va.x - vb.x, vaby = va.y - vb.y, vabz = va.z - vb.z;
+      const float xv = -fmaf(dz, vabz, fmaf(dy, vaby, dx * vabx));
+      // Eq. 5 without a branch: w_ab = x_ab.v_ab / r, Pi = 0 unless approaching
+      const float w = xv * rsqrtf(r2);
+      const float vsig = csa + b2.z - 3.0f * w;
+      const float Pi = xv < 0.0f ? -0.5f * alpha * vsig * w : 0.0f;
+      const float irb = b2.w;
+      const float mb = vb.w;
+      const float fa = mb * Wa * fmaf(0.5f * Pi, ira, Xa);
+      const float fb = mb * Wb * fmaf(0.5f * Pi, irb, b2.y);
+      accx -= fmaf(fa, Cadx, fb * Cbdx);
+      accy -= fmaf(fa, Cady, fb * Cbdy);
+      accz -= fmaf(fa, Cadz, fb * Cbdz);
+      const float vCa = fmaf(vabz, Cadz, fmaf(vaby, Cady, vabx * Cadx));
+      const float vCb = fmaf(vabz, Cbdz, fmaf(vaby, Cbdy, vabx * Cbdx));
+      du = fmaf(mb, fmaf(Wa * fmaf(0.25f * Pi, ira, Xa), vCa, 0.25f * Pi * irb * Wb * vCb), du);
+    });
+  }
+  accx = group_sum<NSUB>(accx);
+  accy = group_sum<NSUB>(accy);
+  accz = group_sum<NSUB>(accz);
+  du = group_sum<NSUB>(du);
+  if (!on || sub != 0) return;
   o.ax[a] = accx;
   o.ay[a] = accy;
   o.az[a] = accz;

@@ -64,13 +64,18 @@ class Ensemble:
         if rc != _lib.SPH_OK:
             raise _lib.SphError(rc, (self.lib.sph_ensemble_last_error(self.ctx) or b"").decode())
 
-    def set_config(self, cell_factor=None, blocks_per_sm=None, test_skip_block=None):
+    def set_config(self, cell_factor=None, blocks_per_sm=None, test_skip_block=None,
+                   find_window=None, threads_per_particle=None):
         if cell_factor is not None:
             self.cfg.cell_factor = float(cell_factor)
         if blocks_per_sm is not None:
             self.cfg.blocks_per_sm = int(blocks_per_sm)
         if test_skip_block is not None:
             self.cfg.test_skip_block = int(test_skip_block)
+        if find_window is not None:
+            self.cfg.find_window = int(find_window)
+        if threads_per_particle is not None:
+            self.cfg.threads_per_particle = int(threads_per_particle)
         with torch.cuda.device(self.device):
             self._err(self.lib.sph_ensemble_set_config(self.ctx, C.byref(self.cfg)))
 
@@ -109,6 +114,17 @@ class Ensemble:
         return {"particles": int(out[0]), "boxes": int(out[1]), "ctas": int(out[2]),
                 "launches": int(out[3])}
 
+    def phase_times(self):
+        """Milliseconds per step of each phase since the last call (device
+        timer of block 0 between grid barriers), and the step count."""
+        ms = np.zeros(len(_lib.ENS_PHASES))
+        steps = C.c_int64(0)
+        with torch.cuda.device(self.device):
+            self._err(self.lib.sph_ensemble_phase_times(self.ctx, ms.ctypes.data_as(C.c_void_p),
+                                                         C.byref(steps)))
+        k = max(int(steps.value), 1)
+        return {name: float(v) / k for name, v in zip(_lib.ENS_PHASES, ms)}, int(steps.value)
+
     def box_numpy(self, b: int) -> dict:
         """State and outputs of box b, ordered by particle id."""
         torch.cuda.synchronize(self.device)
@@ -118,30 +134,58 @@ class Ensemble:
         order = np.argsort(out["id"], kind="stable")
         return {k: v[order] for k, v in out.items()}
 
-    def autotune(self, steps: int = 2, cell_factors=(1.0, 1.15, 1.3), blocks_per_sm=(0,)):
-        """Times `steps` steps of a copy of the current state for each
-        candidate configuration (cell-size factor, persistent CTAs per SM) and
-        keeps the fastest.  The ensemble's own state is not advanced."""
+    KNOBS = ("cell_factor", "find_window", "threads_per_particle", "blocks_per_sm")
+
+    def _time(self, steps, knobs):
+        """Seconds per step of `steps` steps of a copy of the current state
+        under the configuration `knobs` (the state is restored afterwards)."""
         saved = {k: v.clone() for k, v in self.t.items()}
         saved_dt = self.dt.clone()
+        self.set_config(test_skip_block=-1, **knobs)
+        self.step(1)                              # warm-up of this configuration
+        torch.cuda.synchronize(self.device)
+        t0 = time.perf_counter()
+        self.step(steps)
+        torch.cuda.synchronize(self.device)
+        sec = (time.perf_counter() - t0) / steps
+        for k in self.t:
+            self.t[k].copy_(saved[k])
+        self.dt.copy_(saved_dt)
+        return sec
+
+    def autotune(self, steps: int = 2, cell_factors=(1.0, 1.15, 1.3), find_windows=(128, 256, 512),
+                 threads_per_particle=(1, 2, 4), blocks_per_sm=(0,)):
+        """Picks the ensemble kernel's configuration by timing `steps` steps
+        of a copy of the current state per candidate: the tile shape of the
+        neighbour search (find_window) and the threads per particle of the
+        pair phases over their full grid at the first cell factor, then the
+        cell-size factor and the persistent CTAs per SM one at a time around
+        the best.  The ensemble's own state is not advanced."""
         results = []
-        for cf in cell_factors:
-            for bps in blocks_per_sm:
-                self.set_config(cell_factor=cf, blocks_per_sm=bps, test_skip_block=-1)
-                self.step(1)                      # warm-up of this configuration
-                torch.cuda.synchronize(self.device)
-                t0 = time.perf_counter()
-                self.step(steps)
-                torch.cuda.synchronize(self.device)
-                results.append(((time.perf_counter() - t0) / steps, cf, bps))
-                for k in self.t:
-                    self.t[k].copy_(saved[k])
-                self.dt.copy_(saved_dt)
-        best = min(results)
-        self.set_config(cell_factor=best[1], blocks_per_sm=best[2], test_skip_block=-1)
+
+        def trial(**knobs):
+            sec = self._time(steps, knobs)
+            results.append((sec, dict(knobs)))
+            return sec
+
+        best = None
+        for w in find_windows:
+            for tp in threads_per_particle:
+                k = {"cell_factor": cell_factors[0], "find_window": w,
+                     "threads_per_particle": tp, "blocks_per_sm": blocks_per_sm[0]}
+                sec = trial(**k)
+                if best is None or sec < best[0]:
+                    best = (sec, k)
+        for name, values in (("cell_factor", cell_factors[1:]), ("blocks_per_sm", blocks_per_sm[1:])):
+            for v in values:
+                k = dict(best[1], **{name: v})
+                sec = trial(**k)
+                if sec < best[0]:
+                    best = (sec, k)
+        self.set_config(test_skip_block=-1, **best[1])
         self.tuning = results
-        return {"seconds_per_step": best[0], "cell_factor": best[1], "blocks_per_sm": best[2],
-                "tried": results}
+        return dict(best[1], seconds_per_step=best[0],
+                    tried=[dict(k, seconds_per_step=s) for s, k in results])
 
     def close(self):
         if getattr(self, "ctx", None):

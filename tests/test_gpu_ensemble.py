@@ -95,12 +95,52 @@ def test_barrier_timeout_is_reported_and_context_recovers():
     ens.close()
 
 
+@pytest.mark.parametrize("find_window,tpp", [(128, 1), (256, 2), (512, 4)])
+def test_tile_shape_and_threads_per_particle_against_oracle(find_window, tpp):
+    """Every tile shape and thread count gives the same neighbour sets and
+    sums within the FP32-mixed tolerances (the split changes only the
+    summation order)."""
+    from paper_2005_02656_gb300 import Ensemble
+    boxes = _boxes()
+    ens = Ensemble(boxes)
+    ens.set_config(find_window=find_window, threads_per_particle=tpp)
+    ens.step(1)
+    assert ens.error_word() == 0
+    for b in (0, 5):
+        s, alpha = boxes[b]
+        order = np.argsort(s["id"])
+        ref_s = {k: (v[order] if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+        rc, out = oracle.outputs(oracle.Box(s["lo"], s["hi"], s["periodic"]), ref_s,
+                                 oracle.Params(alpha=alpha))
+        assert rc == 0
+        got = ens.box_numpy(b)
+        assert np.max(np.abs(got["rho"] - out["rho"]) / out["rho"]) < 1e-5
+        a_g = np.stack([got["ax"], got["ay"], got["az"]], 1)
+        a_r = np.stack([out["ax"], out["ay"], out["az"]], 1)
+        assert np.max(np.abs(a_g - a_r).max(1) / out["sa"]) < 1e-4
+        assert np.max(np.abs(got["du"] - out["du"]) / out["sdu"]) < 1e-4
+    ens.close()
+
+
+def test_bad_config_is_rejected():
+    from paper_2005_02656_gb300 import Ensemble, _lib
+    ens = Ensemble(_boxes()[:2])
+    with pytest.raises(_lib.SphError):
+        ens.set_config(find_window=200)
+    with pytest.raises(_lib.SphError):
+        ens.set_config(find_window=512, threads_per_particle=3)
+    ens.close()
+
+
 def test_autotune_picks_a_configuration():
     from paper_2005_02656_gb300 import Ensemble
     ens = Ensemble(_boxes())
     before = ens.box_numpy(3)
-    res = ens.autotune(steps=1, cell_factors=(1.0, 1.3))
+    res = ens.autotune(steps=1, cell_factors=(1.0, 1.3), find_windows=(128, 512),
+                       threads_per_particle=(1, 2))
     assert res["cell_factor"] in (1.0, 1.3) and res["seconds_per_step"] > 0
+    assert res["find_window"] in (128, 512) and res["threads_per_particle"] in (1, 2)
+    assert len(res["tried"]) == 5
     after = ens.box_numpy(3)
     np.testing.assert_array_equal(before["x"], after["x"])   # tuning leaves the state alone
     ens.step(1)
