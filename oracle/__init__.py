@@ -56,17 +56,21 @@ def _load():
         lib.oracle_kernel_norm.argtypes = [d]
         lib.oracle_kernel_W.restype = d
         lib.oracle_kernel_W.argtypes = [d, d, d, d]
+        lib.oracle_kernel_dWdv.restype = d
+        lib.oracle_kernel_dWdv.argtypes = [d, d, d, d]
+        lib.oracle_kernel_dWdh.restype = d
+        lib.oracle_kernel_dWdh.argtypes = [d, d, d, d]
         lib.oracle_find_neighbors.restype = cint
         lib.oracle_find_neighbors.argtypes = [C.POINTER(_Box), i64, P, P, P, P, i64, P, cint, cint, P, P]
         lib.oracle_density_eos.restype = None
         lib.oracle_density_eos.argtypes = [C.POINTER(_Box), P, P, P, P, P, P, i64, P, P, P, cint,
-                                           d, d, d, P, P, P]
+                                           d, d, d, P, P, P, P]
         lib.oracle_iad.restype = cint
         lib.oracle_iad.argtypes = [C.POINTER(_Box), P, P, P, P, P, P, i64, P, P, P, cint, d, d, P, P]
         lib.oracle_momentum_energy.restype = None
         lib.oracle_momentum_energy.argtypes = [C.POINTER(_Box), P, P, P, P, P, P, P, P, P, P, P, P,
-                                               i64, P, P, P, cint, d, d, d, P, P, P, P, P, P, P,
-                                               P]
+                                               P, i64, P, P, P, cint, d, d, d, P, P, P, P, P, P,
+                                               P, P]
         lib.oracle_timestep.restype = d
         lib.oracle_timestep.argtypes = [i64, P, P, d, d, d]
         lib.oracle_update.restype = None
@@ -114,6 +118,7 @@ class Params:
     sinc_n: float = 6.0
     ng_target: int = 100
     max_nb: int = 160
+    gradh: int = 0          # 1: grad-h terms Omega in Eqs. 2-3
 
 
 def num_threads() -> int:
@@ -133,6 +138,20 @@ def kernel_W(v: float, h: float, sinc_n: float = 6.0, Bn: float | None = None) -
     return _load().oracle_kernel_W(float(v), float(h), float(sinc_n), float(Bn))
 
 
+def kernel_dWdv(v: float, h: float, sinc_n: float = 6.0, Bn: float | None = None) -> float:
+    """dW/dv of Eq. 6 at fixed h."""
+    if Bn is None:
+        Bn = kernel_norm(sinc_n)
+    return _load().oracle_kernel_dWdv(float(v), float(h), float(sinc_n), float(Bn))
+
+
+def kernel_dWdh(v: float, h: float, sinc_n: float = 6.0, Bn: float | None = None) -> float:
+    """dW/dh of Eq. 6 at fixed separation (v = r / h)."""
+    if Bn is None:
+        Bn = kernel_norm(sinc_n)
+    return _load().oracle_kernel_dWdh(float(v), float(h), float(sinc_n), float(Bn))
+
+
 def find_neighbors(box: Box, x, y, z, h, targets=None, brute=False, max_nb=160):
     """Neighbour lists (b != a, r_ab^2 < (2 h_a)^2).  Returns (rc, nn, nbr)."""
     x, y, z, h = map(_f64, (x, y, z, h))
@@ -147,18 +166,21 @@ def find_neighbors(box: Box, x, y, z, h, targets=None, brute=False, max_nb=160):
     return rc, nn, nbr
 
 
-def density_eos(box: Box, s: dict, nn, nbr, params: Params, targets=None, Bn=None):
-    """Eq. 1 density (self term included) and the ideal-gas EOS.  Returns (rho, p, c)."""
+def density_eos(box: Box, s: dict, nn, nbr, params: Params, targets=None, Bn=None,
+                with_omega=False):
+    """Eq. 1 density (self term included) and the ideal-gas EOS.  Returns
+    (rho, p, c), plus the grad-h terms Omega when with_omega."""
     if Bn is None:
         Bn = kernel_norm(params.sinc_n)
     t = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
     nt = s["x"].shape[0] if t is None else t.shape[0]
     rho, p, c = (np.empty(nt) for _ in range(3))
+    omega = np.empty(nt) if with_omega else None
     b = box.c()
     _load().oracle_density_eos(C.byref(b), _p(s["x"]), _p(s["y"]), _p(s["z"]), _p(s["h"]),
                                _p(s["m"]), _p(s["u"]), nt, _p(t), _p(nn), _p(nbr), nbr.shape[1],
-                               params.sinc_n, Bn, params.gamma, _p(rho), _p(p), _p(c))
-    return rho, p, c
+                               params.sinc_n, Bn, params.gamma, _p(rho), _p(p), _p(c), _p(omega))
+    return (rho, p, c, omega) if with_omega else (rho, p, c)
 
 
 def iad(box: Box, s: dict, rho_full, nn, nbr, params: Params, targets=None, Bn=None):
@@ -178,10 +200,11 @@ def iad(box: Box, s: dict, rho_full, nn, nbr, params: Params, targets=None, Bn=N
 
 
 def momentum_energy(box: Box, s: dict, rho_full, p_full, c_full, iad_full, nn, nbr, params: Params,
-                    targets=None, Bn=None, av_force=None, record_av=False):
+                    targets=None, Bn=None, av_force=None, record_av=False, omega_full=None):
     """Eqs. 2-5.  Returns dict with ax, ay, az, du and the scales sa, sdu.
     ``av_force`` (int8, shape of ``nbr``) imposes the viscosity switch of Eq. 5
-    per list entry; ``record_av`` returns the switch as decided in ``av``."""
+    per list entry; ``record_av`` returns the switch as decided in ``av``;
+    ``omega_full`` holds the grad-h terms (None: Omega = 1)."""
     if Bn is None:
         Bn = kernel_norm(params.sinc_n)
     t = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
@@ -189,6 +212,7 @@ def momentum_energy(box: Box, s: dict, rho_full, p_full, c_full, iad_full, nn, n
     out = {k: np.empty(nt) for k in ("ax", "ay", "az", "du", "sa", "sdu")}
     rho_full, p_full, c_full = map(_f64, (rho_full, p_full, c_full))
     iad_full = np.ascontiguousarray(iad_full, dtype=np.float64).reshape(-1, 6)
+    omega_full = None if omega_full is None else _f64(omega_full)
     if av_force is not None:
         av_force = np.ascontiguousarray(av_force, dtype=np.int8)
         assert av_force.shape == nbr.shape
@@ -196,7 +220,8 @@ def momentum_energy(box: Box, s: dict, rho_full, p_full, c_full, iad_full, nn, n
     b = box.c()
     _load().oracle_momentum_energy(
         C.byref(b), _p(s["x"]), _p(s["y"]), _p(s["z"]), _p(s["vx"]), _p(s["vy"]), _p(s["vz"]),
-        _p(s["h"]), _p(s["m"]), _p(rho_full), _p(p_full), _p(c_full), _p(iad_full), nt, _p(t),
+        _p(s["h"]), _p(s["m"]), _p(rho_full), _p(p_full), _p(c_full), _p(iad_full),
+        _p(omega_full), nt, _p(t),
         _p(nn), _p(nbr), nbr.shape[1], params.sinc_n, Bn, params.alpha, _p(av_force), _p(av),
         _p(out["ax"]), _p(out["ay"]), _p(out["az"]), _p(out["du"]), _p(out["sa"]), _p(out["sdu"]))
     if record_av:
@@ -246,10 +271,17 @@ def outputs(box: Box, s: dict, params: Params, brute=False, record_av=False):
     if rc != OK:
         return rc, {"nn": nn, "nbr": nbr}
     Bn = kernel_norm(params.sinc_n)
-    rho, p, c = density_eos(box, s, nn, nbr, params, Bn=Bn)
+    omega = None
+    if params.gradh:
+        rho, p, c, omega = density_eos(box, s, nn, nbr, params, Bn=Bn, with_omega=True)
+    else:
+        rho, p, c = density_eos(box, s, nn, nbr, params, Bn=Bn)
     rc_iad, C6, T6 = iad(box, s, rho, nn, nbr, params, Bn=Bn)
-    me = momentum_energy(box, s, rho, p, c, C6, nn, nbr, params, Bn=Bn, record_av=record_av)
+    me = momentum_energy(box, s, rho, p, c, C6, nn, nbr, params, Bn=Bn, record_av=record_av,
+                         omega_full=omega)
     out = {"nn": nn, "nbr": nbr, "rho": rho, "p": p, "c": c, "iad": C6, "tau": T6}
+    if omega is not None:
+        out["omega"] = omega
     out.update(me)
     return rc_iad, out
 
@@ -291,13 +323,19 @@ def sampled_outputs(box: Box, s: dict, params: Params, sample):
     rho = np.full(n, np.nan)
     pp = np.full(n, np.nan)
     cc = np.full(n, np.nan)
-    r2, p2, c2 = density_eos(box, s, nn2, nbr2, params, targets=ring2, Bn=Bn)
-    rho[ring2], pp[ring2], cc[ring2] = r2, p2, c2
+    om = np.full(n, np.nan) if params.gradh else None
+    dens = density_eos(box, s, nn2, nbr2, params, targets=ring2, Bn=Bn, with_omega=bool(params.gradh))
+    rho[ring2], pp[ring2], cc[ring2] = dens[:3]
+    if params.gradh:
+        om[ring2] = dens[3]
     iadf = np.full((n, 6), np.nan)
     rc_iad, C1, _ = iad(box, s, rho, nn1, nbr1, params, targets=ring1, Bn=Bn)
     iadf[ring1] = C1
-    me = momentum_energy(box, s, rho, pp, cc, iadf, nn0, nbr0, params, targets=sample, Bn=Bn)
+    me = momentum_energy(box, s, rho, pp, cc, iadf, nn0, nbr0, params, targets=sample, Bn=Bn,
+                         omega_full=om)
     out = {"nn": nn0, "nbr": nbr0, "rho": rho[sample], "p": pp[sample], "c": cc[sample],
            "iad": iadf[sample]}
+    if params.gradh:
+        out["omega"] = om[sample]
     out.update(me)
     return rc_iad, out

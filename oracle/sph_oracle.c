@@ -114,6 +114,23 @@ double oracle_kernel_W(double v, double h, double sinc_n, double Bn) {
   return Bn / (h * h * h) * pow(sinc_half_pi(v), sinc_n);
 }
 
+/* dW/dv of Eq. 6 at fixed h: B_n/h^3 n S^(n-1) dS/dv with S = sin(x)/x,
+ * x = pi v / 2, dS/dv = (pi/2) (x cos x - sin x) / x^2 (0 at v = 0). */
+double oracle_kernel_dWdv(double v, double h, double sinc_n, double Bn) {
+  if (v <= 0.0 || v > 2.0) return 0.0;
+  double x = 0.5 * M_PI * v;
+  double S = sin(x) / x;
+  double dS = 0.5 * M_PI * (x * cos(x) - sin(x)) / (x * x);
+  return Bn / (h * h * h) * sinc_n * pow(S, sinc_n - 1.0) * dS;
+}
+
+/* dW/dh at fixed separation r, v = r / h: W = B_n h^-3 f(v) gives
+ * dW/dh = -(3 W + v dW/dv) / h. */
+double oracle_kernel_dWdh(double v, double h, double sinc_n, double Bn) {
+  if (v < 0.0 || v > 2.0) return 0.0;
+  return -(3.0 * oracle_kernel_W(v, h, sinc_n, Bn) + v * oracle_kernel_dWdv(v, h, sinc_n, Bn)) / h;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Pair separation and the neighbour criterion (section 4.1: b runs over the  */
 /* neighbours of a; the kernel's support is v <= 2 with v = r / h_a).         */
@@ -289,24 +306,35 @@ int oracle_find_neighbors(const oracle_box* box, int64_t n, const double* x, con
 /* a uniform lattice would come out about a quarter of its true density.      */
 /* Equation of state (not printed in the paper): ideal gas,                   */
 /*   P = (gamma - 1) rho u,   c = sqrt(gamma P / rho).                        */
+/* Grad-h terms (section 4.1 names Omega_a, "the grad-h terms that take into  */
+/* account the changes in the local smoothing length", without a formula).   */
+/* Reading, the standard definition for h tied to the density (h ~ rho^-1/3, */
+/* so dh/drho = -h / (3 rho)) and the same sum as Eq. 1, self term included: */
+/*   Omega_a = 1 - (dh_a/drho_a) sum_b m_b dW_ab(h_a)/dh_a                    */
+/*           = 1 + h_a / (3 rho_a) sum_b m_b dW_ab(h_a)/dh_a.                 */
+/* omega == NULL skips it (Omega = 1 everywhere).                            */
 /* ------------------------------------------------------------------------- */
 void oracle_density_eos(const oracle_box* box, const double* x, const double* y, const double* z,
                         const double* h, const double* m, const double* u, int64_t nt,
                         const int64_t* targets, const int32_t* nn, const int64_t* nbr, int max_nb,
-                        double sinc_n, double Bn, double gamma, double* rho, double* p, double* c) {
+                        double sinc_n, double Bn, double gamma, double* rho, double* p, double* c,
+                        double* omega) {
 #pragma omp parallel for schedule(dynamic, 256)
   for (int64_t t = 0; t < nt; ++t) {
     int64_t a = targets ? targets[t] : t;
     double sum = m[a] * oracle_kernel_W(0.0, h[a], sinc_n, Bn);
+    double dsum = m[a] * oracle_kernel_dWdh(0.0, h[a], sinc_n, Bn);
     for (int k = 0; k < nn[t]; ++k) {
       int64_t b = nbr[t * max_nb + k];
       double dx = sep(box, 0, x[a], x[b]), dy = sep(box, 1, y[a], y[b]), dz = sep(box, 2, z[a], z[b]);
       double r = sqrt((dx * dx + dy * dy) + dz * dz);
       sum += m[b] * oracle_kernel_W(r / h[a], h[a], sinc_n, Bn);
+      dsum += m[b] * oracle_kernel_dWdh(r / h[a], h[a], sinc_n, Bn);
     }
     rho[t] = sum;
     p[t] = (gamma - 1.0) * sum * u[a];
     c[t] = sqrt(gamma * p[t] / sum);
+    if (omega) omega[t] = 1.0 + h[a] / (3.0 * sum) * dsum;
   }
 }
 
@@ -401,6 +429,8 @@ static void sym_mul(const double* C6, const double* d, double* out) {
 /*   Abar = A_a / rho_a + A_b / rho_b                                          */
 /*   dv_a/dt = -sum_b m_b (X_a A_a + X_b A_b) - 1/2 sum_b m_b Pi_ab Abar       */
 /*   du_a/dt =  X_a sum_b m_b v_ab . A_a + 1/4 sum_b m_b Pi_ab v_ab . Abar     */
+/* With the grad-h terms (omega != NULL) X_a = P_a / (Omega_a rho_a^2), as    */
+/* printed in Eqs. 2-3; the viscous terms carry no Omega (Eq. 4).             */
 /* Readings of two garbled points: the energy prefactor of Eq. 3 is taken as  */
 /* P_a/(Omega_a rho_a^2) (the dimensionally consistent form, and the one that */
 /* makes the pair exchange conserve energy), and the viscous acceleration of  */
@@ -420,7 +450,8 @@ static void sym_mul(const double* C6, const double* d, double* out) {
 void oracle_momentum_energy(const oracle_box* box, const double* x, const double* y,
                             const double* z, const double* vx, const double* vy, const double* vz,
                             const double* h, const double* m, const double* rho, const double* p,
-                            const double* c, const double* iad, int64_t nt, const int64_t* targets,
+                            const double* c, const double* iad, const double* omega, int64_t nt,
+                            const int64_t* targets,
                             const int32_t* nn, const int64_t* nbr, int max_nb, double sinc_n,
                             double Bn, double alpha, const int8_t* av_force, int8_t* av_out,
                             double* ax, double* ay, double* az, double* du, double* sa,
@@ -429,7 +460,7 @@ void oracle_momentum_energy(const oracle_box* box, const double* x, const double
   for (int64_t t = 0; t < nt; ++t) {
     int64_t a = targets ? targets[t] : t;
     double acc[3] = {0, 0, 0}, energy = 0.0, sacc = 0.0, sen = 0.0;
-    double Xa = p[a] / (rho[a] * rho[a]);
+    double Xa = p[a] / ((omega ? omega[a] : 1.0) * rho[a] * rho[a]);
     for (int k = 0; k < nn[t]; ++k) {
       int64_t b = nbr[t * max_nb + k];
       double d[3] = {sep(box, 0, x[a], x[b]), sep(box, 1, y[a], y[b]), sep(box, 2, z[a], z[b])};
@@ -451,7 +482,7 @@ void oracle_momentum_energy(const oracle_box* box, const double* x, const double
       int on = av_force ? av_force[t * max_nb + k] != 0 : xv < 0.0;
       if (av_out) av_out[t * max_nb + k] = (int8_t)on;
       double Pi = on ? -0.5 * alpha * vsig * w : 0.0;
-      double Xb = p[b] / (rho[b] * rho[b]);
+      double Xb = p[b] / ((omega ? omega[b] : 1.0) * rho[b] * rho[b]);
       double Abar[3];
       for (int i = 0; i < 3; ++i) Abar[i] = Aa[i] / rho[a] + Ab[i] / rho[b];
       double term[3];

@@ -456,3 +456,58 @@ def test_energy_error_second_order(oracle_mod):
         assert np.abs(d1[:3] - d0[:3]).max() < 1e-13
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 3.6 < r1 < 4.8 and 3.6 < r2 < 4.6, (errs, r1, r2)
+
+
+# -------------------------------------------------- grad-h terms (Omega) --
+def test_kernel_derivatives_vs_central_differences(oracle_mod):
+    """dW/dv and dW/dh of the oracle against central differences of its own W."""
+    Bn = oracle_mod.kernel_norm(6.0)
+    h = 0.37
+    for v in (0.05, 0.4, 0.9, 1.3, 1.7, 1.95):
+        e = 1e-6
+        fd_v = (oracle_mod.kernel_W(v + e, h, 6.0, Bn) - oracle_mod.kernel_W(v - e, h, 6.0, Bn)) / (2 * e)
+        assert oracle_mod.kernel_dWdv(v, h, 6.0, Bn) == pytest.approx(fd_v, rel=1e-7, abs=1e-12)
+        r = v * h
+        eh = 1e-7 * h
+        fd_h = (oracle_mod.kernel_W(r / (h + eh), h + eh, 6.0, Bn)
+                - oracle_mod.kernel_W(r / (h - eh), h - eh, 6.0, Bn)) / (2 * eh)
+        assert oracle_mod.kernel_dWdh(v, h, 6.0, Bn) == pytest.approx(fd_h, rel=1e-6, abs=1e-10)
+    # at v = 0 only the h^-3 factor varies: dW/dh = -3 W(0) / h
+    assert oracle_mod.kernel_dWdh(0.0, h, 6.0, Bn) == pytest.approx(-3 * Bn / h ** 4, rel=1e-15)
+
+
+def test_omega_equals_density_derivative_in_h(oracle_mod):
+    """Omega_a = 1 + h_a / (3 rho_a) d rho_a / d h_a (the definition behind the
+    grad-h terms), with d rho / d h by central differences of the oracle's
+    density at fixed neighbour lists."""
+    s = _conservation_case(seed=34, side=8, vel=0.1)
+    s["h"] *= np.random.default_rng(5).uniform(0.9, 1.1, s["h"].shape[0])
+    box = box_of(s)
+    prm = Params(ng_target=0, gradh=1)
+    rc, nn, nbr = oracle_mod.find_neighbors(box, s["x"], s["y"], s["z"], 1.02 * s["h"])
+    assert rc == 0
+    rho, _, _, omega = oracle_mod.density_eos(box, s, nn, nbr, prm, with_omega=True)
+    eps = 1e-6
+    hp = dict(s, h=s["h"] * (1 + eps))
+    hm = dict(s, h=s["h"] * (1 - eps))
+    rp = oracle_mod.density_eos(box, hp, nn, nbr, prm)[0]
+    rm = oracle_mod.density_eos(box, hm, nn, nbr, prm)[0]
+    drho_dh = (rp - rm) / (2 * eps * s["h"])
+    np.testing.assert_allclose(omega, 1 + s["h"] / (3 * rho) * drho_dh, rtol=1e-7)
+    assert (omega > 0).all() and np.abs(omega - 1).max() > 1e-3   # the terms are not trivial
+
+
+def test_gradh_momentum_energy_conservation_and_effect(oracle_mod):
+    """With the grad-h terms the pair exchange still conserves momentum and
+    energy (Omega only rescales X = P/(Omega rho^2)), and the forces change."""
+    s = _conservation_case(seed=35)
+    o0 = all_outputs(oracle_mod, s)
+    o1 = all_outputs(oracle_mod, s, Params(ng_target=0, gradh=1))
+    m = s["m"]
+    a = np.stack([o1["ax"], o1["ay"], o1["az"]], 1)
+    assert np.abs((m[:, None] * a).sum(0)).max() < 1e-13 * (m * o1["sa"]).sum()
+    v = np.stack([s["vx"], s["vy"], s["vz"]], 1)
+    power = (m * ((v * a).sum(1) + o1["du"])).sum()
+    assert abs(power) < 1e-13 * (m * (np.linalg.norm(v, axis=1) * o1["sa"] + o1["sdu"])).sum()
+    np.testing.assert_array_equal(o1["rho"], o0["rho"])
+    assert np.abs(o1["ax"] - o0["ax"]).max() > 1e-6 * o0["sa"].max()
