@@ -88,13 +88,14 @@ enum { SPH_KERNEL_EXACT = 0 };
  *  outputs of a step (valid for the state as it was before the update):
  *    rho, p, c (density, pressure, sound speed), iad (6 per particle: the
  *    symmetric IAD matrix C = tau^{-1} as xx xy xz yy yz zz, particle-major),
- *    ax ay az (acceleration), du (du/dt).
+ *    ax ay az (acceleration), du (du/dt); omega (the grad-h terms Omega of
+ *    Eqs. 2-3, written when params.gradh = 1; may be NULL).
  * The library reorders every array of the state in place (particles are kept
  * sorted by cell in Morton order), so callers identify particles by id. */
 typedef struct {
   double *x, *y, *z, *vx, *vy, *vz, *h, *m, *u;
   double *vxh, *vyh, *vzh, *du_prev;
-  double *rho, *p, *c, *iad, *ax, *ay, *az, *du;
+  double *rho, *p, *c, *iad, *ax, *ay, *az, *du, *omega;
   int64_t* id;
   int64_t n;
 } sph_state;
@@ -115,7 +116,11 @@ typedef struct {
   double sinc_n;               /* exponent n of the sinc kernel, integer 1..12 [6] */
   int precision;               /* SPH_FP64 or SPH_FP32_MIXED [SPH_FP64]         */
   int kernel_mode;             /* SPH_KERNEL_EXACT                              */
-  int gradh;                   /* 0: Omega = 1 (the only supported value)       */
+  int gradh;                   /* grad-h terms of Eqs. 2-3 (section 4.1): 0 sets
+                                  Omega = 1; 1 computes Omega_a = 1 + h_a/(3 rho_a)
+                                  sum_b m_b dW_ab(h_a)/dh_a in the density pass
+                                  (self term included) and uses P/(Omega rho^2)
+                                  in momentum and energy [0]                    */
 } sph_params;
 
 /* Fills *p with the defaults above and a periodic unit box. */

@@ -32,7 +32,7 @@ SPH_FP64 = 0
 SPH_FP32_MIXED = 1
 
 STATE_FIELDS = ("x", "y", "z", "vx", "vy", "vz", "h", "m", "u", "vxh", "vyh", "vzh", "du_prev",
-                "rho", "p", "c", "iad", "ax", "ay", "az", "du")
+                "rho", "p", "c", "iad", "ax", "ay", "az", "du", "omega")
 
 # Every exported symbol of include/sph.h (checked by the ABI test).
 EXPORTS = ("sph_default_params", "sph_init", "sph_destroy", "sph_set_params", "sph_kernel_norm",

@@ -77,7 +77,8 @@ int check_params(sph_ctx* ctx, const sph_params* p) {
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "unknown precision %d", p->precision);
   if (p->kernel_mode != SPH_KERNEL_EXACT)
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "unknown kernel_mode %d", p->kernel_mode);
-  if (p->gradh != 0) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "gradh must be 0");
+  if (p->gradh != 0 && p->gradh != 1)
+    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "gradh must be 0 or 1");
   return SPH_OK;
 }
 
@@ -129,6 +130,7 @@ OutView outs_of(const sph_state* s) {
   o.ay = s->ay;
   o.az = s->az;
   o.du = s->du;
+  o.omega = s->omega;
   return o;
 }
 
@@ -458,6 +460,7 @@ int sph_step_host(sph_ctx* ctx, sph_state* hs, double* dt_inout, sph_stream_t st
     if (e != cudaSuccess) return sph::cuda_fail(ctx, e, "sph_step_host mirrors");
   }
   sph_state ds;
+  memset(&ds, 0, sizeof(ds));  // omega stays NULL: not mirrored
   double* base = ctx->hm_buf;
   double** dfields[21] = {&ds.x, &ds.y, &ds.z, &ds.vx, &ds.vy, &ds.vz, &ds.h, &ds.m, &ds.u,
                           &ds.vxh, &ds.vyh, &ds.vzh, &ds.du_prev, &ds.rho, &ds.p, &ds.c,

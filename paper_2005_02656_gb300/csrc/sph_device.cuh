@@ -74,9 +74,24 @@ __device__ __forceinline__ T ipow(T s, int n) {
     T s2 = s * s;
     return s2 * s2 * s2;
   }
+  if (n <= 0) return T(1);
   T r = s;
   for (int i = 1; i < n; ++i) r *= s;
   return r;
+}
+
+// S(t) and dS/dt of the FP32 series.
+__device__ __forceinline__ void sinc_poly32_d(float t, float& S, float& dS) {
+  constexpr SincCoefs<kSincTerms32> C{};
+  float s = (float)C.c[kSincTerms32 - 1];
+  float d = (float)((kSincTerms32 - 1) * C.c[kSincTerms32 - 1]);
+#pragma unroll
+  for (int k = kSincTerms32 - 2; k >= 0; --k) {
+    s = fmaf(s, t, (float)C.c[k]);
+    if (k >= 1) d = fmaf(d, t, (float)(k * C.c[k]));
+  }
+  S = s;
+  dS = d;
 }
 
 // W and dW/dt for t = v^2 (FP64); t is clamped at 4, where S = 0.
@@ -93,6 +108,13 @@ __device__ __forceinline__ void kernel_w64_d(double t, double norm, int n, doubl
 // W for t = v^2 < 4 (caller guarantees the neighbour criterion), norm = B_n/h^3.
 __device__ __forceinline__ double kernel_w64(double t, double norm, int n) {
   return norm * ipow(sinc_poly64(t), n);
+}
+// t dW/dt (FP32), for the grad-h sum: v dW/dv = 2 t dW/dt.
+__device__ __forceinline__ float kernel_tdw32(float t, float norm, int n) {
+  t = fminf(t, 4.0f);
+  float S, dS;
+  sinc_poly32_d(t, S, dS);
+  return norm * (float)n * ipow(S, n - 1) * dS * t;
 }
 __device__ __forceinline__ float kernel_w32(float t, float norm, int n) {
   // t can exceed 4 by rounding for pairs on the support edge; clamp so that the

@@ -481,7 +481,7 @@ __device__ void ph_density_t(const Args& A) {
     const int b = on ? A.box_of[p] : -1;
     const Grid g = A.boxes[on ? b : 0].g;
     pairs32::density_one<NSUB>(p, g, f, A.out, A.s.u, L, A.Bn, (int)A.prm.sinc_n, A.prm.gamma,
-                               A.err, on, sub);
+                               A.err, on, sub, A.prm.gradh != 0);
     const bool own = on && sub == 0;
     const double q = own ? A.s.h[p] / A.out.c[p] : INFINITY;
     const int bq = own ? b : -1;
@@ -762,6 +762,7 @@ Args args_of(sph_ens* e, const sph_state* st, double* dt_dev) {
   A.out.ay = st->ay;
   A.out.az = st->az;
   A.out.du = st->du;
+  A.out.omega = st->omega;
   double* f[13] = {};
   for (int k = 0; k < 13; ++k) f[k] = e->sbuf + (size_t)k * e->n;
   A.s.x = f[0];

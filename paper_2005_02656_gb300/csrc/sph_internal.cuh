@@ -45,6 +45,7 @@ struct StateView {
 
 struct OutView {
   double *rho, *p, *c, *iad, *ax, *ay, *az, *du;
+  double* omega;  // grad-h terms (NULL: not written)
 };
 
 // Block-reduction partials (per block) and finalisation counters.

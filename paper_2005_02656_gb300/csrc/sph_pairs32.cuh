@@ -116,15 +116,18 @@ __device__ __forceinline__ float group_sum(float v) {
 
 // ---------------------------------------------------------------- density --
 // Eq. 1 (self term included) and the ideal-gas EOS for particle a; writes the
-// FP64 outputs and the IAD / momentum records of a.
+// FP64 outputs and the IAD / momentum records of a.  With gradh, also the
+// grad-h terms Omega_a = -(2 / (3 rho_a)) sum_{b != a} m_b t dW/dt (the form
+// of 1 + h/(3 rho) sum m dW/dh for this kernel, t = v^2), folded into the
+// record's X = P / (Omega rho^2).
 template <int NSUB = 1>
 __device__ __forceinline__ void density_one(int64_t a, const Grid& g, const F32& f,
                                             const OutView& o, const double* u, const Lists& L,
                                             float Bn, int sinc_n, double gamma, uint32_t* err,
-                                            bool on = true, int sub = 0) {
+                                            bool on = true, int sub = 0, bool gradh = false) {
   const bool wrap = g.wrap32 != 0;
   float4 pa = make_float4(0.f, 0.f, 0.f, 1.f);
-  float hinv2 = 0.f, norm = 0.f, acc = 0.0f;
+  float hinv2 = 0.f, norm = 0.f, acc = 0.0f, gsum = 0.0f;
   if (on) {
     pa = f.pos[a];
     hinv2 = 1.0f / (pa.w * pa.w);
@@ -136,9 +139,11 @@ __device__ __forceinline__ void density_one(int64_t a, const Grid& g, const F32&
       rel(g, wrap, e, rb, pa, dx, dy, dz);
       const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
       acc = fmaf(rb.w, kernel_w32(r2 * hinv2, norm, sinc_n), acc);
+      if (gradh) gsum = fmaf(rb.w, kernel_tdw32(r2 * hinv2, norm, sinc_n), gsum);
     });
   }
   acc = group_sum<NSUB>(acc);
+  if (gradh) gsum = group_sum<NSUB>(gsum);
   if (!on || sub != 0) return;
   const float ma = f.rec_d[a].w;
   const float rho = fmaf(ma, norm, acc);  // self term: W(0, h_a) = B_n / h_a^3
@@ -152,7 +157,13 @@ __device__ __forceinline__ void density_one(int64_t a, const Grid& g, const F32&
   f.rec_i[a] = make_float4(pa.x, pa.y, pa.z, ma * inv_rho);
   float4* m = f.rec_m + 5 * a;
   m[0] = make_float4(pa.x, pa.y, pa.z, hinv2);
-  m[2] = make_float4(norm, (float)(p / (rho64 * rho64)), (float)c, inv_rho);
+  double X = p / (rho64 * rho64);
+  if (gradh) {
+    const double omega = -2.0 * (double)gsum / (3.0 * rho64);
+    X /= omega;
+    if (o.omega) o.omega[a] = omega;
+  }
+  m[2] = make_float4(norm, (float)X, (float)c, inv_rho);
   if (!isfinite(rho64) || !isfinite(c)) raise_flag(err, SPH_FLAG_NONFINITE);
 }
 

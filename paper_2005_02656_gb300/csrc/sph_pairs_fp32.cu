@@ -19,11 +19,11 @@ constexpr int kThreads = 128;
 __global__ void __launch_bounds__(kThreads) k_density_p(const Grid* gp, F32 f, OutView o,
                                                         const double* u, Lists L, int64_t n,
                                                         float Bn, int sinc_n, double gamma,
-                                                        uint32_t* err) {
+                                                        bool gradh, uint32_t* err) {
   const Grid g = *gp;
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
        a += (int64_t)gridDim.x * blockDim.x)
-    pairs32::density_one(a, g, f, o, u, L, Bn, sinc_n, gamma, err);
+    pairs32::density_one(a, g, f, o, u, L, Bn, sinc_n, gamma, err, true, 0, gradh);
 }
 
 __global__ void __launch_bounds__(kThreads) k_iad_p(const Grid* gp, F32 f, OutView o, Lists L,
@@ -74,7 +74,7 @@ void launch_density_f32(sph_ctx* ctx, const StateView& s, const OutView& o, int6
                         cudaStream_t st) {
   k_density_p<<<blocks_for(n, ctx->sm_count), kThreads, 0, st>>>(
       ctx->grid, f32_of(ctx), o, s.u, lists_of(ctx), n, (float)ctx->Bn, (int)ctx->prm.sinc_n,
-      ctx->prm.gamma, ctx->err);
+      ctx->prm.gamma, ctx->prm.gradh != 0, ctx->err);
   ctx->launches += 1;
 }
 

@@ -39,6 +39,12 @@ __device__ __forceinline__ void sep64(const Grid& g, double xa, double ya, doubl
   dz = min_image(zb - za, g.Lbox[2], g.halfL[2], g.periodic[2]);
 }
 
+// GRADH: also the grad-h terms, Omega_a = 1 + h_a/(3 rho_a) sum_b m_b dW/dh_a.
+// With dW/dh = -(3 W + v dW/dv) / h and sum_b m_b W = rho_a (self term
+// included) this is Omega_a = -(2 / (3 rho_a)) sum_{b != a} m_b t dW/dt,
+// t = v^2 (the self term has t = 0); X = P / (Omega rho^2) then carries it
+// into Eqs. 2-3.
+template <bool GRADH>
 __global__ void __launch_bounds__(kThreads64) k_density64(const Grid* gp, StateView s, OutView o,
                                                           Aux64 aux, Lists64 L, int64_t n,
                                                           double Bn, int sinc_n, double gamma,
@@ -51,13 +57,21 @@ __global__ void __launch_bounds__(kThreads64) k_density64(const Grid* gp, StateV
     const double norm = Bn * hinv2 / ha;
     const int cnt = min(L.nn[a], L.max_nb);
     const uint32_t* list = L.nbr + a * L.max_nb;
-    double acc = 0.0;
+    double acc = 0.0, gsum = 0.0;
     for (int k = 0; k < cnt; ++k) {
       const int64_t b = entry_index(list[k]);
       double dx, dy, dz;
       sep64(g, xa, ya, za, s.x[b], s.y[b], s.z[b], dx, dy, dz);
       const double r2 = dx * dx + dy * dy + dz * dz;
-      acc += s.m[b] * kernel_w64(fmin(r2 * hinv2, 4.0), norm, sinc_n);
+      const double t = fmin(r2 * hinv2, 4.0);
+      if (GRADH) {
+        double W, dW;
+        kernel_w64_d(t, norm, sinc_n, W, dW);
+        acc += s.m[b] * W;
+        gsum += s.m[b] * t * dW;
+      } else {
+        acc += s.m[b] * kernel_w64(t, norm, sinc_n);
+      }
     }
     const double rho = s.m[a] * norm + acc;  // self term: W(0, h_a) = B_n / h_a^3
     const double p = (gamma - 1.0) * rho * s.u[a];
@@ -68,7 +82,13 @@ __global__ void __launch_bounds__(kThreads64) k_density64(const Grid* gp, StateV
     const double inv_rho = 1.0 / rho;
     aux.inv_rho[a] = inv_rho;
     aux.vol[a] = s.m[a] * inv_rho;
-    aux.X[a] = p * inv_rho * inv_rho;
+    if (GRADH) {
+      const double omega = -2.0 * gsum * inv_rho / 3.0;
+      aux.X[a] = p * inv_rho * inv_rho / omega;
+      if (o.omega) o.omega[a] = omega;
+    } else {
+      aux.X[a] = p * inv_rho * inv_rho;
+    }
     aux.hinv2[a] = hinv2;
     aux.wnorm[a] = norm;
     if (!isfinite(rho) || !isfinite(c)) raise_flag(err, SPH_FLAG_NONFINITE);
@@ -217,7 +237,8 @@ inline int blocks64(int64_t n, int sm) {
 
 void launch_density_f64(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
                         cudaStream_t st) {
-  k_density64<<<blocks64(n, ctx->sm_count), kThreads64, 0, st>>>(
+  auto kern = ctx->prm.gradh ? k_density64<true> : k_density64<false>;
+  kern<<<blocks64(n, ctx->sm_count), kThreads64, 0, st>>>(
       ctx->grid, s, o, aux_of(ctx), lists64_of(ctx), n, ctx->Bn, (int)ctx->prm.sinc_n,
       ctx->prm.gamma, ctx->err);
   ctx->launches += 1;

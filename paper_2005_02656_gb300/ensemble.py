@@ -51,6 +51,7 @@ class Ensemble:
             for k in OUTPUTS:
                 self.t[k] = torch.zeros(self.n, dtype=torch.float64, device=self.device)
             self.t["iad"] = torch.zeros(6 * self.n, dtype=torch.float64, device=self.device)
+            self.t["omega"] = torch.ones(self.n, dtype=torch.float64, device=self.device)
             self.dt = torch.zeros(self.nbox, dtype=torch.float64, device=self.device)
         self.cfg = EnsConfig()
         self.lib.sph_ens_default_config(C.byref(self.cfg))

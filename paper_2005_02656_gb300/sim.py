@@ -30,6 +30,7 @@ class Params:
     max_nb: int = 160
     sinc_n: float = 6.0
     precision: str = "fp64"   # "fp64" | "fp32_mixed"
+    gradh: int = 0            # 1: grad-h terms Omega in Eqs. 2-3
 
     def c(self) -> SphParams:
         p = SphParams()
@@ -41,7 +42,7 @@ class Params:
         p.ng_target, p.max_nb, p.sinc_n = int(self.ng_target), int(self.max_nb), float(self.sinc_n)
         p.precision = {"fp64": _lib.SPH_FP64, "fp32_mixed": _lib.SPH_FP32_MIXED}[self.precision]
         p.kernel_mode = 0
-        p.gradh = 0
+        p.gradh = int(self.gradh)
         return p
 
 
@@ -80,6 +81,7 @@ class SphSim:
             for k in OUTPUTS:
                 self.t[k] = torch.zeros(n, dtype=torch.float64, device=dev)
             self.t["iad"] = torch.zeros(6 * n, dtype=torch.float64, device=dev)
+            self.t["omega"] = torch.ones(n, dtype=torch.float64, device=dev)  # grad-h terms
             self.dt = torch.zeros(1, dtype=torch.float64, device=dev)
         self._st = SphState()
         self._bind()
@@ -185,7 +187,7 @@ class SphSim:
     def to_numpy(self, by_id: bool = True) -> dict:
         """State and outputs as numpy arrays, ordered by particle id if by_id."""
         torch.cuda.synchronize(self.device)
-        out = {k: self.t[k].cpu().numpy() for k in PERSISTENT + OUTPUTS + ("id",)}
+        out = {k: self.t[k].cpu().numpy() for k in PERSISTENT + OUTPUTS + ("id", "omega")}
         out["iad"] = self.t["iad"].cpu().numpy().reshape(-1, 6)
         if by_id:
             order = np.argsort(out["id"], kind="stable")

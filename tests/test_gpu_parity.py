@@ -96,6 +96,28 @@ def test_fp32_mixed_fields(name):
         assert e[k] <= tol, (k, e)
 
 
+@pytest.mark.parametrize("name", ["box20", "box16_varh", "kh32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+def test_gradh_fields(name, precision):
+    """Grad-h terms (params.gradh = 1): Omega and the fields that depend on
+    it, against the oracle with the same reading of Omega."""
+    s = CASES[name]
+    rc, ref_s, ref = oracle_outputs(s, ng_target=0, max_nb=MAX_NB, gradh=1)
+    assert rc == 0
+    got, _, _, flags = _gpu(s, precision=precision, gradh=1)
+    assert flags == 0
+    e = field_errors(got, ref)
+    om = float(np.max(np.abs(got["omega"] - ref["omega"]) / ref["omega"]))
+    if precision == "fp64":
+        assert om <= FP64_TOL
+        for k in ("rho", "p", "c", "iad", "a", "du"):
+            assert e[k] <= FP64_TOL, (k, e)
+    else:
+        assert om <= FP32_TOL["rho"] * 10, om       # a sum of FP32 kernel derivatives
+        for k, tol in FP32_TOL.items():
+            assert e[k] <= tol, (k, e)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
 def test_full_step_matches_oracle(precision):
     """One sph_step (sort, search, sums, dt, update, h) against the oracle step."""
