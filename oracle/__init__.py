@@ -60,6 +60,10 @@ def _load():
         lib.oracle_kernel_dWdv.argtypes = [d, d, d, d]
         lib.oracle_kernel_dWdh.restype = d
         lib.oracle_kernel_dWdh.argtypes = [d, d, d, d]
+        lib.oracle_set_kernel_mode.restype = None
+        lib.oracle_set_kernel_mode.argtypes = [cint, d]
+        lib.oracle_kernel_W_table.restype = d
+        lib.oracle_kernel_W_table.argtypes = [d, d, d, d]
         lib.oracle_find_neighbors.restype = cint
         lib.oracle_find_neighbors.argtypes = [C.POINTER(_Box), i64, P, P, P, P, i64, P, cint, cint, P, P]
         lib.oracle_density_eos.restype = None
@@ -119,6 +123,7 @@ class Params:
     ng_target: int = 100
     max_nb: int = 160
     gradh: int = 0          # 1: grad-h terms Omega in Eqs. 2-3
+    kernel_mode: int = 0    # 0: exact sinc kernel; 1: 20,000-entry table (section 4.5)
 
 
 def num_threads() -> int:
@@ -136,6 +141,18 @@ def kernel_W(v: float, h: float, sinc_n: float = 6.0, Bn: float | None = None) -
     if Bn is None:
         Bn = kernel_norm(sinc_n)
     return _load().oracle_kernel_W(float(v), float(h), float(sinc_n), float(Bn))
+
+
+def kernel_W_table(v: float, h: float, sinc_n: float = 6.0, Bn: float | None = None) -> float:
+    """W(v, h) from the 20,000-entry table with linear interpolation."""
+    if Bn is None:
+        Bn = kernel_norm(sinc_n)
+    return _load().oracle_kernel_W_table(float(v), float(h), float(sinc_n), float(Bn))
+
+
+def _mode(params):
+    """Select the oracle's kernel evaluation for the next call."""
+    _load().oracle_set_kernel_mode(int(getattr(params, "kernel_mode", 0)), float(params.sinc_n))
 
 
 def kernel_dWdv(v: float, h: float, sinc_n: float = 6.0, Bn: float | None = None) -> float:
@@ -177,6 +194,7 @@ def density_eos(box: Box, s: dict, nn, nbr, params: Params, targets=None, Bn=Non
     rho, p, c = (np.empty(nt) for _ in range(3))
     omega = np.empty(nt) if with_omega else None
     b = box.c()
+    _mode(params)
     _load().oracle_density_eos(C.byref(b), _p(s["x"]), _p(s["y"]), _p(s["z"]), _p(s["h"]),
                                _p(s["m"]), _p(s["u"]), nt, _p(t), _p(nn), _p(nbr), nbr.shape[1],
                                params.sinc_n, Bn, params.gamma, _p(rho), _p(p), _p(c), _p(omega))
@@ -193,6 +211,7 @@ def iad(box: Box, s: dict, rho_full, nn, nbr, params: Params, targets=None, Bn=N
     T6 = np.empty((nt, 6))
     rho_full = _f64(rho_full)
     b = box.c()
+    _mode(params)
     rc = _load().oracle_iad(C.byref(b), _p(s["x"]), _p(s["y"]), _p(s["z"]), _p(s["h"]), _p(s["m"]),
                             _p(rho_full), nt, _p(t), _p(nn), _p(nbr), nbr.shape[1], params.sinc_n, Bn,
                             _p(C6), _p(T6))
@@ -218,6 +237,7 @@ def momentum_energy(box: Box, s: dict, rho_full, p_full, c_full, iad_full, nn, n
         assert av_force.shape == nbr.shape
     av = np.zeros(nbr.shape, dtype=np.int8) if record_av else None
     b = box.c()
+    _mode(params)
     _load().oracle_momentum_energy(
         C.byref(b), _p(s["x"]), _p(s["y"]), _p(s["z"]), _p(s["vx"]), _p(s["vy"]), _p(s["vz"]),
         _p(s["h"]), _p(s["m"]), _p(rho_full), _p(p_full), _p(c_full), _p(iad_full),

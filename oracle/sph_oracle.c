@@ -114,6 +114,52 @@ double oracle_kernel_W(double v, double h, double sinc_n, double Bn) {
   return Bn / (h * h * h) * pow(sinc_half_pi(v), sinc_n);
 }
 
+/* ------------------------------------------------------------------------- */
+/* Lookup-table kernel (section 4.5: 20,000 precomputed kernel values and a   */
+/* linear interpolation in the relative distance v instead of sin and pow).   */
+/* Reading: nodes v_i = 2 i / (N - 1), i = 0..N-1, values T_i = S(v_i)^n;     */
+/* for 0 <= v <= 2, with q = v (N - 1) / 2, i = min(floor(q), N - 2) and      */
+/* f = q - i:  W = B_n / h^3 (T_i + (T_{i+1} - T_i) f).                       */
+/* The mode is process-wide: oracle_set_kernel_mode(1) builds the table for  */
+/* the given n and makes every kernel evaluation below use it; mode 0 (the   */
+/* default) is the exact kernel.  The Python wrapper sets it before each     */
+/* call from its parameters.                                                 */
+/* ------------------------------------------------------------------------- */
+#define ORACLE_TABLE_N 20000
+static int g_kernel_mode = 0;
+static double g_table_n = -1.0;
+static double g_table[ORACLE_TABLE_N];
+
+void oracle_set_kernel_mode(int mode, double sinc_n) {
+  g_kernel_mode = mode;
+  if (mode == 1 && g_table_n != sinc_n) {
+    for (int i = 0; i < ORACLE_TABLE_N; ++i)
+      g_table[i] = pow(sinc_half_pi(2.0 * i / (ORACLE_TABLE_N - 1)), sinc_n);
+    g_table_n = sinc_n;
+  }
+}
+
+int oracle_kernel_mode(void) { return g_kernel_mode; }
+
+/* The kernel used by the sums: W of Eq. 6, or its tabulated form. */
+static double kernel_value(double v, double h, double sinc_n, double Bn) {
+  if (g_kernel_mode != 1) return oracle_kernel_W(v, h, sinc_n, Bn);
+  if (v < 0.0 || v > 2.0) return 0.0;
+  double q = v * (0.5 * (ORACLE_TABLE_N - 1));
+  int i = (int)floor(q);
+  if (i > ORACLE_TABLE_N - 2) i = ORACLE_TABLE_N - 2;
+  double f = q - i;
+  return Bn / (h * h * h) * (g_table[i] + (g_table[i + 1] - g_table[i]) * f);
+}
+
+double oracle_kernel_W_table(double v, double h, double sinc_n, double Bn) {
+  int saved = g_kernel_mode;
+  oracle_set_kernel_mode(1, sinc_n);
+  double w = kernel_value(v, h, sinc_n, Bn);
+  g_kernel_mode = saved;
+  return w;
+}
+
 /* dW/dv of Eq. 6 at fixed h: B_n/h^3 n S^(n-1) dS/dv with S = sin(x)/x,
  * x = pi v / 2, dS/dv = (pi/2) (x cos x - sin x) / x^2 (0 at v = 0). */
 double oracle_kernel_dWdv(double v, double h, double sinc_n, double Bn) {
@@ -322,13 +368,13 @@ void oracle_density_eos(const oracle_box* box, const double* x, const double* y,
 #pragma omp parallel for schedule(dynamic, 256)
   for (int64_t t = 0; t < nt; ++t) {
     int64_t a = targets ? targets[t] : t;
-    double sum = m[a] * oracle_kernel_W(0.0, h[a], sinc_n, Bn);
+    double sum = m[a] * kernel_value(0.0, h[a], sinc_n, Bn);
     double dsum = m[a] * oracle_kernel_dWdh(0.0, h[a], sinc_n, Bn);
     for (int k = 0; k < nn[t]; ++k) {
       int64_t b = nbr[t * max_nb + k];
       double dx = sep(box, 0, x[a], x[b]), dy = sep(box, 1, y[a], y[b]), dz = sep(box, 2, z[a], z[b]);
       double r = sqrt((dx * dx + dy * dy) + dz * dz);
-      sum += m[b] * oracle_kernel_W(r / h[a], h[a], sinc_n, Bn);
+      sum += m[b] * kernel_value(r / h[a], h[a], sinc_n, Bn);
       dsum += m[b] * oracle_kernel_dWdh(r / h[a], h[a], sinc_n, Bn);
     }
     rho[t] = sum;
@@ -364,7 +410,7 @@ int oracle_iad(const oracle_box* box, const double* x, const double* y, const do
       int64_t b = nbr[t * max_nb + k];
       double d[3] = {sep(box, 0, x[a], x[b]), sep(box, 1, y[a], y[b]), sep(box, 2, z[a], z[b])};
       double r = sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
-      double w = m[b] / rho[b] * oracle_kernel_W(r / h[a], h[a], sinc_n, Bn);
+      double w = m[b] / rho[b] * kernel_value(r / h[a], h[a], sinc_n, Bn);
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) T[i][j] += w * d[i] * d[j];
     }
@@ -465,8 +511,8 @@ void oracle_momentum_energy(const oracle_box* box, const double* x, const double
       int64_t b = nbr[t * max_nb + k];
       double d[3] = {sep(box, 0, x[a], x[b]), sep(box, 1, y[a], y[b]), sep(box, 2, z[a], z[b])};
       double r = sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
-      double Wa = oracle_kernel_W(r / h[a], h[a], sinc_n, Bn);
-      double Wb = oracle_kernel_W(r / h[b], h[b], sinc_n, Bn);
+      double Wa = kernel_value(r / h[a], h[a], sinc_n, Bn);
+      double Wb = kernel_value(r / h[b], h[b], sinc_n, Bn);
       double Ca_d[3], Cb_d[3], Aa[3], Ab[3];
       sym_mul(iad + 6 * a, d, Ca_d);
       sym_mul(iad + 6 * b, d, Cb_d);

@@ -511,3 +511,46 @@ def test_gradh_momentum_energy_conservation_and_effect(oracle_mod):
     assert abs(power) < 1e-13 * (m * (np.linalg.norm(v, axis=1) * o1["sa"] + o1["sdu"])).sum()
     np.testing.assert_array_equal(o1["rho"], o0["rho"])
     assert np.abs(o1["ax"] - o0["ax"]).max() > 1e-6 * o0["sa"].max()
+
+
+# ------------------------------------------- lookup-table kernel (section 4.5) --
+def test_kernel_table_nodes_and_interpolation_bound(oracle_mod):
+    """The 20,000-entry table reproduces W at its nodes, and between them the
+    linear interpolation error is within its textbook bound
+    (delta^2 / 8) max |T''| B_n / h^3, with T = S(v)^n and T'' by central
+    differences of the exact kernel."""
+    Bn = oracle_mod.kernel_norm(6.0)
+    h = 1.0
+    N = 20000
+    delta = 2.0 / (N - 1)
+    for i in (0, 1, 137, 5000, 9999, 15000, N - 2, N - 1):
+        v = 2.0 * i / (N - 1)
+        assert oracle_mod.kernel_W_table(v, h, 6.0, Bn) == pytest.approx(
+            oracle_mod.kernel_W(v, h, 6.0, Bn), rel=1e-13, abs=1e-15 * Bn)
+    vs = np.linspace(0.0, 2.0, 7919)
+    w_ex = np.array([oracle_mod.kernel_W(v, h, 6.0, Bn) for v in vs])
+    w_tb = np.array([oracle_mod.kernel_W_table(v, h, 6.0, Bn) for v in vs])
+    e = 1e-4
+    d2 = np.array([(oracle_mod.kernel_W(min(v + e, 2), h, 6.0, Bn) - 2 * oracle_mod.kernel_W(v, h, 6.0, Bn)
+                    + oracle_mod.kernel_W(max(v - e, 0), h, 6.0, Bn)) / e ** 2 for v in vs[1:-1]])
+    bound = delta ** 2 / 8 * np.abs(d2).max()
+    err = np.abs(w_tb - w_ex).max()
+    assert err <= 1.05 * bound, (err, bound)
+    assert err > 0.05 * bound          # the table is really in use
+    assert oracle_mod.kernel_W_table(2.0000001, h, 6.0, Bn) == 0.0
+
+
+def test_table_mode_outputs_close_to_exact(oracle_mod):
+    """Density, forces and du in table mode differ from the exact kernel by
+    the interpolation error only (relative ~1e-8)."""
+    s = _conservation_case(seed=36, side=9)
+    o0 = all_outputs(oracle_mod, s)
+    o1 = all_outputs(oracle_mod, s, Params(ng_target=0, kernel_mode=1))
+    assert 0 < np.abs(o1["rho"] / o0["rho"] - 1).max() < 1e-7
+    a0 = np.stack([o0["ax"], o0["ay"], o0["az"]], 1)
+    a1 = np.stack([o1["ax"], o1["ay"], o1["az"]], 1)
+    assert np.abs(a1 - a0).max(1).max() < 1e-6 * o0["sa"].max()
+    assert np.abs(o1["du"] - o0["du"]).max() < 1e-6 * o0["sdu"].max()
+    # the process-wide mode is back to exact after the call with default params
+    o2 = all_outputs(oracle_mod, s)
+    np.testing.assert_array_equal(o2["rho"], o0["rho"])
