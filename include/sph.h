@@ -77,7 +77,14 @@ enum {
 
 /* Kernel evaluation (section 4.5 of the paper mentions a 20,000-entry lookup
  * table; SPH_KERNEL_EXACT evaluates sinc by a polynomial).                     */
-enum { SPH_KERNEL_EXACT = 0 };
+enum { SPH_KERNEL_EXACT = 0, SPH_KERNEL_TABLE = 1 };
+/* SPH_KERNEL_TABLE (section 4.5): the paper's lookup table of 20,000 kernel
+ * values S(v_i)^n at v_i = 2 i / 19999, built on the host with libm sin and
+ * pow, interpolated linearly in v = r / h (q = v * 19999 / 2, i = floor(q)
+ * capped at 19998, W = B_n / h^3 (T_i + (T_{i+1} - T_i) (q - i))).  It
+ * differs from the exact kernel by the interpolation error, relative
+ * ~1e-8; gradh, the ensemble and the differentiable rollout require
+ * SPH_KERNEL_EXACT. */
 
 /* Particle state: structure of arrays of caller-owned device memory.
  *  inputs (persistent state): x y z (positions), vx vy vz (velocity at integer
@@ -115,7 +122,7 @@ typedef struct {
                                   multiple of 4 in [4, 4096] [160]              */
   double sinc_n;               /* exponent n of the sinc kernel, integer 1..12 [6] */
   int precision;               /* SPH_FP64 or SPH_FP32_MIXED [SPH_FP64]         */
-  int kernel_mode;             /* SPH_KERNEL_EXACT                              */
+  int kernel_mode;             /* SPH_KERNEL_EXACT or SPH_KERNEL_TABLE [EXACT]  */
   int gradh;                   /* grad-h terms of Eqs. 2-3 (section 4.1): 0 sets
                                   Omega = 1; 1 computes Omega_a = 1 + h_a/(3 rho_a)
                                   sum_b m_b dW_ab(h_a)/dh_a in the density pass

@@ -30,6 +30,8 @@ FLAG_TIMEOUT = 0x20
 
 SPH_FP64 = 0
 SPH_FP32_MIXED = 1
+SPH_KERNEL_EXACT = 0
+SPH_KERNEL_TABLE = 1
 
 STATE_FIELDS = ("x", "y", "z", "vx", "vy", "vz", "h", "m", "u", "vxh", "vyh", "vzh", "du_prev",
                 "rho", "p", "c", "iad", "ax", "ay", "az", "du", "omega")

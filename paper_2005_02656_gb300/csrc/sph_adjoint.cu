@@ -1027,7 +1027,8 @@ int sph_adjoint_init(const sph_params* params, int64_t n_max, int steps, int che
       checkpoint_every > steps || n_max < 1 || n_max > sph::kMaxParticles)
     return SPH_ERR_INVALID_ARG;
   if (params->max_nb > (1 << kKBits)) return SPH_ERR_INVALID_ARG;
-  if (params->gradh != 0) return SPH_ERR_INVALID_ARG;  // the reverse kernels assume Omega = 1
+  // the reverse kernels assume Omega = 1 and the exact kernel
+  if (params->gradh != 0 || params->kernel_mode != SPH_KERNEL_EXACT) return SPH_ERR_INVALID_ARG;
   sph_adj* A = (sph_adj*)calloc(1, sizeof(sph_adj));
   if (!A) return SPH_ERR_OOM;
   int rc = sph_init(params, n_max, &A->ctx);

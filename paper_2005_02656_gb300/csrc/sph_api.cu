@@ -75,10 +75,55 @@ int check_params(sph_ctx* ctx, const sph_params* p) {
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "sinc_n must be an integer in [1, 12]");
   if (p->precision != SPH_FP64 && p->precision != SPH_FP32_MIXED)
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "unknown precision %d", p->precision);
-  if (p->kernel_mode != SPH_KERNEL_EXACT)
+  if (p->kernel_mode != SPH_KERNEL_EXACT && p->kernel_mode != SPH_KERNEL_TABLE)
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "unknown kernel_mode %d", p->kernel_mode);
   if (p->gradh != 0 && p->gradh != 1)
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "gradh must be 0 or 1");
+  if (p->gradh && p->kernel_mode != SPH_KERNEL_EXACT)
+    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "gradh needs SPH_KERNEL_EXACT");
+  return SPH_OK;
+}
+
+// SPH_KERNEL_TABLE: T_i = S(v_i)^n at v_i = 2 i / (N - 1) with libm sin and
+// pow on the host (section 4.5), stored as (T_i, T_{i+1} - T_i) in FP64 and
+// FP32; rebuilt when sinc_n changes.
+int build_kernel_table(sph_ctx* ctx) {
+  if (ctx->prm.kernel_mode != SPH_KERNEL_TABLE || ctx->ktab_n == ctx->prm.sinc_n) return SPH_OK;
+  const int N = sph::kKernelTableN;
+  cudaError_t e = cudaSuccess;
+  if (!ctx->ktab64) e = cudaMalloc((void**)&ctx->ktab64, sizeof(double2) * N);
+  if (e == cudaSuccess && !ctx->ktab32) e = cudaMalloc((void**)&ctx->ktab32, sizeof(float2) * N);
+  if (e != cudaSuccess) return sph::cuda_fail(ctx, e, "kernel table");
+  double* T = (double*)malloc(sizeof(double) * N);
+  double2* t64 = (double2*)malloc(sizeof(double2) * N);
+  float2* t32 = (float2*)malloc(sizeof(float2) * N);
+  if (!T || !t64 || !t32) {
+    free(T);
+    free(t64);
+    free(t32);
+    return sph::set_error(ctx, SPH_ERR_OOM, "kernel table");
+  }
+  for (int i = 0; i < N; ++i) {
+    const double v = 2.0 * i / (N - 1);
+    double S = 1.0;
+    if (v != 0.0) {
+      const double x = 0.5 * 3.14159265358979323846 * v;
+      S = sin(x) / x;
+    }
+    T[i] = pow(S, ctx->prm.sinc_n);
+  }
+  for (int i = 0; i < N; ++i) {
+    const double d = i + 1 < N ? T[i + 1] - T[i] : 0.0;
+    t64[i] = make_double2(T[i], d);
+    t32[i] = make_float2((float)T[i], (float)d);
+  }
+  e = cudaMemcpy(ctx->ktab64, t64, sizeof(double2) * N, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->ktab32, t32, sizeof(float2) * N, cudaMemcpyHostToDevice);
+  free(T);
+  free(t64);
+  free(t32);
+  if (e != cudaSuccess) return sph::cuda_fail(ctx, e, "kernel table");
+  ctx->ktab_n = ctx->prm.sinc_n;
   return SPH_OK;
 }
 
@@ -154,7 +199,8 @@ int dalloc(sph_ctx* ctx, T** p, size_t count, size_t* total) {
 }
 
 void free_all(sph_ctx* ctx) {
-  void* ptrs[] = {ctx->grid, ctx->err, ctx->dt_dev, ctx->diag, ctx->hfac, ctx->code, ctx->slot,
+  void* ptrs[] = {ctx->grid, ctx->err, ctx->dt_dev, ctx->diag, ctx->hfac, ctx->ktab64,
+                  ctx->ktab32, ctx->code, ctx->slot,
                   ctx->perm_tmp, ctx->perm, ctx->tbl_count, ctx->tbl_start, ctx->occ,
                   ctx->scan_part, ctx->cell_of, ctx->s.x, ctx->s_id_buf, ctx->pos32,
                   ctx->cell3, ctx->nn, ctx->nbr, ctx->vol, ctx->rec_d, ctx->rec_i, ctx->rec_m, ctx->red.part, ctx->red.counter, ctx->stats, ctx->hm_buf, ctx->hm_id};
@@ -250,6 +296,7 @@ int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {
   ctx->prm = *params;
   ctx->n_max = n_max;
   ctx->hfac_ng = -1;
+  ctx->ktab_n = -1.0;
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -313,6 +360,7 @@ int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) rc = sph::cuda_fail(ctx, e, "init");
   }
+  if (rc == SPH_OK) rc = build_kernel_table(ctx);
   if (rc != SPH_OK) {
     free_all(ctx);
     free(ctx);
@@ -342,7 +390,7 @@ int sph_set_params(sph_ctx* ctx, const sph_params* params) {
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "max_nb and sinc_n are fixed at sph_init");
   ctx->prm = *params;
   ctx->have_density = ctx->have_iad = 0;
-  return SPH_OK;
+  return build_kernel_table(ctx);
 }
 
 double sph_kernel_norm(const sph_ctx* ctx) { return ctx ? ctx->Bn : 0.0; }

@@ -105,6 +105,23 @@ __device__ __forceinline__ void kernel_w64_d(double t, double norm, int n, doubl
   dWdt = norm * n * Sn1 * dS;
 }
 
+// Tabulated kernel (SPH_KERNEL_TABLE): entry i holds (T_i, T_{i+1} - T_i),
+// T_i = S(v_i)^n at v_i = 2 i / (N - 1); linear interpolation in v = sqrt(t).
+__device__ __forceinline__ double kernel_w64_tab(double t, double norm, const double2* tab) {
+  const double q = sqrt(fmin(t, 4.0)) * (0.5 * (kKernelTableN - 1));
+  int i = (int)q;
+  if (i > kKernelTableN - 2) i = kKernelTableN - 2;
+  const double2 e = tab[i];
+  return norm * (e.x + e.y * (q - (double)i));
+}
+__device__ __forceinline__ float kernel_w32_tab(float t, float norm, const float2* tab) {
+  const float q = sqrtf(fminf(t, 4.0f)) * (0.5f * (kKernelTableN - 1));
+  int i = (int)q;
+  if (i > kKernelTableN - 2) i = kKernelTableN - 2;
+  const float2 e = tab[i];
+  return norm * fmaf(e.y, q - (float)i, e.x);
+}
+
 // W for t = v^2 < 4 (caller guarantees the neighbour criterion), norm = B_n/h^3.
 __device__ __forceinline__ double kernel_w64(double t, double norm, int n) {
   return norm * ipow(sinc_poly64(t), n);
@@ -121,6 +138,14 @@ __device__ __forceinline__ float kernel_w32(float t, float norm, int n) {
   // truncated series does not grow there (S(2) = 0).
   t = fminf(t, 4.0f);
   return norm * ipow(sinc_poly32(t), n);
+}
+
+// The kernel of the context's mode: the series, or the table when tab != NULL.
+__device__ __forceinline__ double kw64(double t, double norm, int n, const double2* tab) {
+  return tab ? kernel_w64_tab(t, norm, tab) : kernel_w64(t, norm, n);
+}
+__device__ __forceinline__ float kw32(float t, float norm, int n, const float2* tab) {
+  return tab ? kernel_w32_tab(t, norm, tab) : kernel_w32(t, norm, n);
 }
 
 // ---------------------------------------------------------------------------

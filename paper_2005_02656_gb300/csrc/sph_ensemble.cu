@@ -451,6 +451,7 @@ __device__ __forceinline__ pairs32::F32 f32_of(const Args& A) {
   f.rec_d = A.rec_d;
   f.rec_i = A.rec_i;
   f.rec_m = A.rec_m;
+  f.ktab = nullptr;  // the ensemble runs the exact kernel
   return f;
 }
 __device__ __forceinline__ pairs32::Lists lists_of(const Args& A) {
@@ -898,7 +899,8 @@ int sph_ensemble_init(const sph_params* common, int n_boxes, const int64_t* box_
     return SPH_ERR_INVALID_ARG;
   *out = nullptr;
   if (common->precision != SPH_FP32_MIXED || common->max_nb % 4 != 0 || common->max_nb < 4 ||
-      !(common->sinc_n >= 1.0 && common->sinc_n <= 12.0))
+      !(common->sinc_n >= 1.0 && common->sinc_n <= 12.0) ||
+      common->kernel_mode != SPH_KERNEL_EXACT)
     return SPH_ERR_INVALID_ARG;
   sph_ens* e = (sph_ens*)calloc(1, sizeof(sph_ens));
   if (!e) return SPH_ERR_OOM;

@@ -15,6 +15,7 @@ constexpr int kReduceBlocks = 1024;             // partial slots of grid reducti
 constexpr int kScanItems = 4096;                // cell-table entries per scan block
 constexpr int kProfRing = 64;                   // step event sets kept before folding
 constexpr int kHTab = 4097;                     // h factors tabulated for counts 0..4096
+constexpr int kKernelTableN = 20000;            // kernel values of SPH_KERNEL_TABLE
 
 // Cell grid of the current step, computed on the device from the particles'
 // extent and h_max, read by every later kernel of the step.
@@ -75,6 +76,9 @@ struct sph_ctx {
   double* diag;         // 16 doubles: [0..7] sums of the new state, [8] dt,
                         // [9] min nn, [10] max nn, [11] sum nn, [12] dt_prev
   double* hfac;         // kHTab: 0.5 (1 + cbrt(ng_target / max(k, 1))) for count k
+  double2* ktab64;      // SPH_KERNEL_TABLE: (T_i, T_{i+1} - T_i), kKernelTableN entries
+  float2* ktab32;       //   the same in FP32 (NULL when the mode is exact)
+  double ktab_n;        // sinc_n the tables were built for (-1: none)
   int hfac_ng;          // ng_target the table was built for (-1: none)
 
   // sort

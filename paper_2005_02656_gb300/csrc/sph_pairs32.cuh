@@ -28,6 +28,7 @@ struct F32 {
   const float4* rec_d;  // offset x, y, z, m
   float4* rec_i;        // offset x, y, z, m/rho
   float4* rec_m;        // 5 float4 per particle
+  const float2* ktab;   // SPH_KERNEL_TABLE values, NULL for the exact kernel
 };
 
 struct Lists {
@@ -138,7 +139,7 @@ __device__ __forceinline__ void density_one(int64_t a, const Grid& g, const F32&
       float dx, dy, dz;
       rel(g, wrap, e, rb, pa, dx, dy, dz);
       const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-      acc = fmaf(rb.w, kernel_w32(r2 * hinv2, norm, sinc_n), acc);
+      acc = fmaf(rb.w, kw32(r2 * hinv2, norm, sinc_n, f.ktab), acc);
       if (gradh) gsum = fmaf(rb.w, kernel_tdw32(r2 * hinv2, norm, sinc_n), gsum);
     });
   }
@@ -192,7 +193,7 @@ __device__ __forceinline__ void iad_one(int64_t a, const Grid& g, const F32& f, 
       dx *= inv_h;
       dy *= inv_h;
       dz *= inv_h;
-      const float w = rb.w * kernel_w32(r2 * hinv2, norm, sinc_n);
+      const float w = rb.w * kw32(r2 * hinv2, norm, sinc_n, f.ktab);
       const float wx = w * dx, wy = w * dy, wz = w * dz;
       t00 = fmaf(wx, dx, t00);
       t01 = fmaf(wx, dy, t01);
@@ -264,8 +265,8 @@ __device__ __forceinline__ void momentum_one(int64_t a, const Grid& g, const F32
       rel(g, wrap, e, b0, pa, dx, dy, dz);
       const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
       const float4 b2 = rb[2];
-      const float Wa = kernel_w32(r2 * pa.w, qa.x, sinc_n);
-      const float Wb = kernel_w32(r2 * b0.w, b2.x, sinc_n);  // clamped at t = 4 (S = 0)
+      const float Wa = kw32(r2 * pa.w, qa.x, sinc_n, f.ktab);
+      const float Wb = kw32(r2 * b0.w, b2.x, sinc_n, f.ktab);  // clamped at t = 4 (S = 0)
       const float Cadx = fmaf(a02, dz, fmaf(a01, dy, a00 * dx));
       const float Cady = fmaf(a12, dz, fmaf(a11, dy, a01 * dx));
       const float Cadz = fmaf(a22, dz, fmaf(a12, dy, a02 * dx));

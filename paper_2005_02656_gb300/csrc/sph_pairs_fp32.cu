@@ -49,6 +49,7 @@ inline F32 f32_of(sph_ctx* ctx) {
   f.rec_d = ctx->rec_d;
   f.rec_i = ctx->rec_i;
   f.rec_m = ctx->rec_m;
+  f.ktab = ctx->prm.kernel_mode == SPH_KERNEL_TABLE ? ctx->ktab32 : nullptr;
   return f;
 }
 

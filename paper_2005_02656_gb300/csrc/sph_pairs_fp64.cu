@@ -24,6 +24,7 @@ struct Aux64 {
   double* inv_rho;
   double* hinv2;   // 1 / h^2
   double* wnorm;   // B_n / h^3
+  const double2* ktab;  // SPH_KERNEL_TABLE values, NULL for the exact kernel
 };
 
 struct Lists64 {
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(kThreads64) k_density64(const Grid* gp, StateV
         acc += s.m[b] * W;
         gsum += s.m[b] * t * dW;
       } else {
-        acc += s.m[b] * kernel_w64(t, norm, sinc_n);
+        acc += s.m[b] * kw64(t, norm, sinc_n, aux.ktab);
       }
     }
     const double rho = s.m[a] * norm + acc;  // self term: W(0, h_a) = B_n / h_a^3
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(kThreads64) k_iad64(const Grid* gp, StateView 
       double dx, dy, dz;
       sep64(g, xa, ya, za, s.x[b], s.y[b], s.z[b], dx, dy, dz);
       const double r2 = dx * dx + dy * dy + dz * dz;
-      const double w = aux.vol[b] * kernel_w64(fmin(r2 * hinv2, 4.0), norm, sinc_n);
+      const double w = aux.vol[b] * kw64(fmin(r2 * hinv2, 4.0), norm, sinc_n, aux.ktab);
       const double wx = w * dx, wy = w * dy, wz = w * dz;
       t00 += wx * dx;
       t01 += wx * dy;
@@ -167,9 +168,9 @@ __global__ void __launch_bounds__(kThreads64) k_momentum64(const Grid* gp, State
       double dx, dy, dz;
       sep64(g, xa, ya, za, s.x[b], s.y[b], s.z[b], dx, dy, dz);
       const double r2 = dx * dx + dy * dy + dz * dz;
-      const double Wa = kernel_w64(fmin(r2 * hinv2a, 4.0), norma, sinc_n);
+      const double Wa = kw64(fmin(r2 * hinv2a, 4.0), norma, sinc_n, aux.ktab);
       const double tb = r2 * aux.hinv2[b];
-      const double Wb = tb < 4.0 ? kernel_w64(tb, aux.wnorm[b], sinc_n) : 0.0;
+      const double Wb = tb < 4.0 ? kw64(tb, aux.wnorm[b], sinc_n, aux.ktab) : 0.0;
       // C_a d and C_b d, d = x_b - x_a
       const double Cadx = a00 * dx + a01 * dy + a02 * dz;
       const double Cady = a01 * dx + a11 * dy + a12 * dz;
@@ -214,6 +215,7 @@ inline Aux64 aux_of(sph_ctx* ctx) {
   a.inv_rho = ctx->inv_rho;
   a.hinv2 = ctx->vol + 3 * ctx->n_max;
   a.wnorm = ctx->vol + 4 * ctx->n_max;
+  a.ktab = ctx->prm.kernel_mode == SPH_KERNEL_TABLE ? ctx->ktab64 : nullptr;
   return a;
 }
 

@@ -31,6 +31,7 @@ class Params:
     sinc_n: float = 6.0
     precision: str = "fp64"   # "fp64" | "fp32_mixed"
     gradh: int = 0            # 1: grad-h terms Omega in Eqs. 2-3
+    kernel_mode: str = "exact"  # "exact" | "table" (section 4.5: 20,000-entry table)
 
     def c(self) -> SphParams:
         p = SphParams()
@@ -41,7 +42,7 @@ class Params:
         p.gamma, p.alpha, p.courant, p.dt_growth = self.gamma, self.alpha, self.courant, self.dt_growth
         p.ng_target, p.max_nb, p.sinc_n = int(self.ng_target), int(self.max_nb), float(self.sinc_n)
         p.precision = {"fp64": _lib.SPH_FP64, "fp32_mixed": _lib.SPH_FP32_MIXED}[self.precision]
-        p.kernel_mode = 0
+        p.kernel_mode = {"exact": _lib.SPH_KERNEL_EXACT, "table": _lib.SPH_KERNEL_TABLE}[self.kernel_mode]
         p.gradh = int(self.gradh)
         return p
 

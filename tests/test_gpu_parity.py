@@ -118,6 +118,32 @@ def test_gradh_fields(name, precision):
             assert e[k] <= tol, (k, e)
 
 
+@pytest.mark.parametrize("name", ["box20", "box16_varh", "kh32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+def test_table_kernel_fields(name, precision):
+    """Lookup-table kernel (kernel_mode "table", section 4.5) against the
+    oracle's table mode; lists do not depend on the kernel."""
+    s = CASES[name]
+    rc, ref_s, ref = oracle_outputs(s, ng_target=0, max_nb=MAX_NB, kernel_mode=1)
+    assert rc == 0
+    got, counts, _, flags = _gpu(s, precision=precision, kernel_mode="table")
+    assert flags == 0
+    np.testing.assert_array_equal(counts, ref["nn"])
+    e = field_errors(got, ref)
+    if precision == "fp64":
+        for k in ("rho", "p", "c", "iad", "a", "du"):
+            assert e[k] <= FP64_TOL, (k, e)
+    else:
+        for k, tol in FP32_TOL.items():
+            assert e[k] <= tol, (k, e)
+
+
+def test_table_kernel_rejected_with_gradh():
+    from paper_2005_02656_gb300 import SphSim, _lib
+    with pytest.raises(_lib.SphError):
+        SphSim(CASES["box20"], gradh=1, kernel_mode="table")
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
 def test_full_step_matches_oracle(precision):
     """One sph_step (sort, search, sums, dt, update, h) against the oracle step."""
