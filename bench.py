@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ensemble-steps", type=int, default=50)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-table", action="store_true", help="skip the lookup-table kernel leg")
     ap.add_argument("--adjoint-side", type=int, default=100)
     return ap.parse_args()
 
@@ -193,8 +194,10 @@ def run_gpu(args, world, rank, local):
     state = sph_inputs.kelvin_helmholtz(args.nx, seed_index=2)
     n = int(state["x"].shape[0])
 
-    def timed(precision):
-        sim = SphSim(state, precision=precision, device=dev)
+    def timed(precision, kernel_mode="exact", steps=None, key=None):
+        steps = steps or args.steps
+        key = key or precision
+        sim = SphSim(state, precision=precision, device=dev, kernel_mode=kernel_mode)
         stream = torch.cuda.current_stream()
         for _ in range(args.warmup):
             sim.step()
@@ -209,14 +212,14 @@ def run_gpu(args, world, rank, local):
         e1 = torch.cuda.Event(enable_timing=True)
         tw0 = time.time()
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             sim.step()
         e1.record(stream)
         torch.cuda.synchronize()
         tw1 = time.time()
         barrier()
-        windows[precision] = (tw0, tw1)
-        ms = e0.elapsed_time(e1) / args.steps
+        windows[key] = (tw0, tw1)
+        ms = e0.elapsed_time(e1) / steps
         stages, nsteps = sim.stage_times()
         st1 = sim.stats()
         launches = sim.launch_count() - l0
@@ -225,15 +228,21 @@ def run_gpu(args, world, rank, local):
         sim.close()
         del sim
         torch.cuda.empty_cache()
-        pairs = (st1["pairs"] - st0["pairs"]) / args.steps
-        cands = (st1["candidates"] - st0["candidates"]) / args.steps
-        exact = (st1["exact_tests"] - st0["exact_tests"]) / args.steps
+        pairs = (st1["pairs"] - st0["pairs"]) / steps
+        cands = (st1["candidates"] - st0["candidates"]) / steps
+        exact = (st1["exact_tests"] - st0["exact_tests"]) / steps
         return {"ms": ms, "stages": {k: v / max(nsteps, 1) for k, v in stages.items()},
                 "pairs": pairs, "candidates": cands, "exact_tests": exact, "launches": launches,
                 "flags": flags, "dt": float(diag[8])}
 
     r32 = timed("fp32_mixed")
     r64 = None if args.no_fp64 else timed("fp64")
+    # the paper's lookup-table kernel (section 4.5) on the same workload
+    tab = None
+    if not args.no_table:
+        tab = {"fp32_mixed": timed("fp32_mixed", "table", steps=5, key="table_fp32_mixed")}
+        if not args.no_fp64:
+            tab["fp64"] = timed("fp64", "table", steps=3, key="table_fp64")
 
     e2e = None
     if not args.no_e2e:
@@ -274,7 +283,7 @@ def run_gpu(args, world, rank, local):
             r["clocks"] = clocks.summary(*windows[key])
     ms32 = max_over_ranks(r32["ms"])
     res = {"n": n, "r32": r32, "r64": r64, "ms32": ms32, "e2e": e2e, "ensemble": ens,
-           "adjoint": adjoint}
+           "adjoint": adjoint, "table": tab}
     if r64 is not None:
         res["ms64"] = max_over_ranks(r64["ms"])
     if dist is not None:
@@ -471,6 +480,12 @@ def main():
         line["ensemble"] = res["ensemble"]
     if res.get("adjoint") is not None:
         line["adjoint"] = res["adjoint"]
+    if res.get("table") is not None:
+        exact_ms = {"fp32_mixed": ms, "fp64": res.get("ms64")}
+        line["kernel_table"] = {
+            prec: {"ms_per_step": r["ms"], "stages_ms": r["stages"], "error_flags": r["flags"],
+                   "time_vs_exact": (r["ms"] / exact_ms[prec]) if exact_ms.get(prec) else None}
+            for prec, r in res["table"].items()}
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

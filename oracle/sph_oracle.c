@@ -369,13 +369,13 @@ void oracle_density_eos(const oracle_box* box, const double* x, const double* y,
   for (int64_t t = 0; t < nt; ++t) {
     int64_t a = targets ? targets[t] : t;
     double sum = m[a] * kernel_value(0.0, h[a], sinc_n, Bn);
-    double dsum = m[a] * oracle_kernel_dWdh(0.0, h[a], sinc_n, Bn);
+    double dsum = omega ? m[a] * oracle_kernel_dWdh(0.0, h[a], sinc_n, Bn) : 0.0;
     for (int k = 0; k < nn[t]; ++k) {
       int64_t b = nbr[t * max_nb + k];
       double dx = sep(box, 0, x[a], x[b]), dy = sep(box, 1, y[a], y[b]), dz = sep(box, 2, z[a], z[b]);
       double r = sqrt((dx * dx + dy * dy) + dz * dz);
       sum += m[b] * kernel_value(r / h[a], h[a], sinc_n, Bn);
-      dsum += m[b] * oracle_kernel_dWdh(r / h[a], h[a], sinc_n, Bn);
+      if (omega) dsum += m[b] * oracle_kernel_dWdh(r / h[a], h[a], sinc_n, Bn);
     }
     rho[t] = sum;
     p[t] = (gamma - 1.0) * sum * u[a];

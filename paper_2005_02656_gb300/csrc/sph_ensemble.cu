@@ -202,7 +202,8 @@ __device__ void ph_extent(const Args& A) {
       if (lane == 0) {
         Box& B = A.boxes[b0];
         atomicMax(&B.hmax_o, ord(h));
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < 3; ++k) {  // the extent is needed on open axes only
+          if (B.periodic[k]) continue;
           atomicMin(&B.xmin_o[k], ord(v[k]));
           atomicMax(&B.xmax_o[k], ord(v[3 + k]));
         }
@@ -211,6 +212,7 @@ __device__ void ph_extent(const Args& A) {
       Box& B = A.boxes[b];
       atomicMax(&B.hmax_o, ord(h));
       for (int k = 0; k < 3; ++k) {
+        if (B.periodic[k]) continue;
         atomicMin(&B.xmin_o[k], ord(v[k]));
         atomicMax(&B.xmax_o[k], ord(v[3 + k]));
       }
