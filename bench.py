@@ -31,9 +31,12 @@ KH_NX = 224            # 224x112x112 + 282x141x141 = 8,416,298 particles
 SAMPLE_NX = 112        # the same recipe at 1/8 scale for the CPU oracle (1,067,054 particles)
 
 # Flop model per directed neighbour pair (add/sub/mul = 1, FMA = 2,
-# rsqrt/div = 1), counted on the operations of each pair loop; the neighbour
-# search counts per (target, candidate) test.  See the design doc.
+# rsqrt/div = 1), counted on the operations of each pair loop as written; the
+# neighbour search counts per (target, candidate) test.  The FP64 kernels
+# evaluate a 15-term series for W (32 flops, 9 terms in FP32) and IAD and
+# momentum read W_ab(h_a) cached by the density pass.
 FLOPS = {"find": 14, "density": 37, "iad": 57, "momentum": 140}
+FLOPS64 = {"find": 14, "density": 43, "iad": 19, "momentum": 131}
 # Derived non-tensor peaks: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz, and
 # the FP64 pipe at 1/64 of that rate.
 SM, LANES, MHZ = 152, 128, 2070.0
@@ -393,7 +396,7 @@ def roofline(r, n, precision):
     units = {"find": r["candidates"], "density": r["pairs"], "iad": r["pairs"],
              "momentum": r["pairs"]}
     kern = max(("find", "density", "iad", "momentum"), key=lambda k: st[k])
-    flops = FLOPS[kern] * units[kern]
+    flops = (FLOPS64 if precision == "fp64" else FLOPS)[kern] * units[kern]
     ms = st[kern]
     achieved = flops / (ms * 1e-3) / 1e12
     if precision == "fp64" and kern != "find":

@@ -203,7 +203,7 @@ void free_all(sph_ctx* ctx) {
                   ctx->ktab32, ctx->code, ctx->slot,
                   ctx->perm_tmp, ctx->perm, ctx->tbl_count, ctx->tbl_start, ctx->occ,
                   ctx->scan_part, ctx->cell_of, ctx->s.x, ctx->s_id_buf, ctx->pos32,
-                  ctx->cell3, ctx->nn, ctx->nbr, ctx->vol, ctx->rec_d, ctx->rec_i, ctx->rec_m, ctx->red.part, ctx->red.counter, ctx->stats, ctx->hm_buf, ctx->hm_id};
+                  ctx->cell3, ctx->nn, ctx->nbr, ctx->wcache, ctx->vol, ctx->rec_d, ctx->rec_i, ctx->rec_m, ctx->red.part, ctx->red.counter, ctx->stats, ctx->hm_buf, ctx->hm_id};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -332,6 +332,7 @@ int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {
   ALLOC(ctx->cell3, n);
   ALLOC(ctx->nn, n);
   ALLOC(ctx->nbr, (size_t)mb * n);
+  if (params->precision == SPH_FP64) ALLOC(ctx->wcache, (size_t)mb * n);
   ALLOC(ctx->vol, 5 * n);
   ALLOC(ctx->rec_d, n);
   ALLOC(ctx->rec_i, n);
@@ -388,6 +389,15 @@ int sph_set_params(sph_ctx* ctx, const sph_params* params) {
   if (rc != SPH_OK) return rc;
   if (params->max_nb != ctx->prm.max_nb || params->sinc_n != ctx->prm.sinc_n)
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "max_nb and sinc_n are fixed at sph_init");
+  if (params->precision == SPH_FP64 && !ctx->wcache) {
+    // a context created for FP32-mixed gets the FP64 kernel-value cache now
+    cudaError_t e = cudaMalloc((void**)&ctx->wcache,
+                               sizeof(double) * (size_t)ctx->prm.max_nb * (size_t)ctx->n_max);
+    if (e != cudaSuccess) {
+      ctx->wcache = nullptr;
+      return sph::cuda_fail(ctx, e, "sph_set_params: FP64 kernel-value cache");
+    }
+  }
   ctx->prm = *params;
   ctx->have_density = ctx->have_iad = 0;
   return build_kernel_table(ctx);

@@ -104,6 +104,10 @@ struct sph_ctx {
   int32_t* nn;
   uint32_t* nbr;
 
+  // FP64 path: W_ab(h_a) of every list entry, written by the density pass and
+  // read by IAD and momentum (nbr layout; allocated for SPH_FP64 contexts)
+  double* wcache;
+
   // FP64 per-particle helpers: one block of 5 * n_max doubles
   double* vol;          // m / rho          (vol + 0 n_max)
   double* X;            // P / rho^2        (vol + 1 n_max)

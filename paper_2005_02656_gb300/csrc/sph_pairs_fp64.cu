@@ -5,7 +5,9 @@
 // (particles are in Morton cell order, so a warp's neighbours share lines).
 // Separations are FP64 minimum-image differences of the positions.  On this
 // part the FP64 pipe bounds these kernels, so per-pair divisions are hoisted
-// into per-particle arrays (m/rho, P/rho^2, 1/rho, 1/h^2, B_n/h^3).
+// into per-particle arrays (m/rho, P/rho^2, 1/rho, 1/h^2, B_n/h^3), and the
+// kernel value W_ab(h_a) of each list entry is evaluated once, by the density
+// pass, and read back by IAD and momentum (Lists64::w).
 #include <cuda_runtime.h>
 
 #include "sph_device.cuh"
@@ -30,6 +32,7 @@ struct Aux64 {
 struct Lists64 {
   const int32_t* nn;
   const uint32_t* nbr;
+  double* w;  // W_ab(h_a) per entry, same layout as nbr
   int max_nb;
 };
 
@@ -58,6 +61,7 @@ __global__ void __launch_bounds__(kThreads64) k_density64(const Grid* gp, StateV
     const double norm = Bn * hinv2 / ha;
     const int cnt = min(L.nn[a], L.max_nb);
     const uint32_t* list = L.nbr + a * L.max_nb;
+    double* wrow = L.w + a * L.max_nb;
     double acc = 0.0, gsum = 0.0;
     for (int k = 0; k < cnt; ++k) {
       const int64_t b = entry_index(list[k]);
@@ -70,8 +74,11 @@ __global__ void __launch_bounds__(kThreads64) k_density64(const Grid* gp, StateV
         kernel_w64_d(t, norm, sinc_n, W, dW);
         acc += s.m[b] * W;
         gsum += s.m[b] * t * dW;
+        wrow[k] = W;
       } else {
-        acc += s.m[b] * kw64(t, norm, sinc_n, aux.ktab);
+        const double W = kw64(t, norm, sinc_n, aux.ktab);
+        acc += s.m[b] * W;
+        wrow[k] = W;
       }
     }
     const double rho = s.m[a] * norm + acc;  // self term: W(0, h_a) = B_n / h_a^3
@@ -103,16 +110,15 @@ __global__ void __launch_bounds__(kThreads64) k_iad64(const Grid* gp, StateView 
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
        a += (int64_t)gridDim.x * blockDim.x) {
     const double xa = s.x[a], ya = s.y[a], za = s.z[a];
-    const double hinv2 = aux.hinv2[a], norm = aux.wnorm[a];
     const int cnt = min(L.nn[a], L.max_nb);
     const uint32_t* list = L.nbr + a * L.max_nb;
+    const double* wrow = L.w + a * L.max_nb;
     double t00 = 0, t01 = 0, t02 = 0, t11 = 0, t12 = 0, t22 = 0;
     for (int k = 0; k < cnt; ++k) {
       const int64_t b = entry_index(list[k]);
       double dx, dy, dz;
       sep64(g, xa, ya, za, s.x[b], s.y[b], s.z[b], dx, dy, dz);
-      const double r2 = dx * dx + dy * dy + dz * dz;
-      const double w = aux.vol[b] * kw64(fmin(r2 * hinv2, 4.0), norm, sinc_n, aux.ktab);
+      const double w = aux.vol[b] * wrow[k];
       const double wx = w * dx, wy = w * dy, wz = w * dz;
       t00 += wx * dx;
       t01 += wx * dy;
@@ -156,19 +162,19 @@ __global__ void __launch_bounds__(kThreads64) k_momentum64(const Grid* gp, State
        a += (int64_t)gridDim.x * blockDim.x) {
     const double xa = s.x[a], ya = s.y[a], za = s.z[a];
     const double vxa = s.vx[a], vya = s.vy[a], vza = s.vz[a];
-    const double hinv2a = aux.hinv2[a], norma = aux.wnorm[a];
     const double Xa = aux.X[a], ira = aux.inv_rho[a], ca = o.c[a];
     const double* Ca = o.iad + 6 * a;
     const double a00 = Ca[0], a01 = Ca[1], a02 = Ca[2], a11 = Ca[3], a12 = Ca[4], a22 = Ca[5];
     const int cnt = min(L.nn[a], L.max_nb);
     const uint32_t* list = L.nbr + a * L.max_nb;
+    const double* wrow = L.w + a * L.max_nb;
     double accx = 0, accy = 0, accz = 0, du = 0;
     for (int k = 0; k < cnt; ++k) {
       const int64_t b = entry_index(list[k]);
       double dx, dy, dz;
       sep64(g, xa, ya, za, s.x[b], s.y[b], s.z[b], dx, dy, dz);
       const double r2 = dx * dx + dy * dy + dz * dz;
-      const double Wa = kw64(fmin(r2 * hinv2a, 4.0), norma, sinc_n, aux.ktab);
+      const double Wa = wrow[k];
       const double tb = r2 * aux.hinv2[b];
       const double Wb = tb < 4.0 ? kw64(tb, aux.wnorm[b], sinc_n, aux.ktab) : 0.0;
       // C_a d and C_b d, d = x_b - x_a
@@ -223,6 +229,7 @@ inline Lists64 lists64_of(sph_ctx* ctx) {
   Lists64 t;
   t.nn = ctx->nn;
   t.nbr = ctx->nbr;
+  t.w = ctx->wcache;
   t.max_nb = ctx->prm.max_nb;
   return t;
 }

@@ -160,3 +160,25 @@ def test_profile_and_counters():
     assert st["pairs"] > 0 and st["candidates"] > st["pairs"] and st["particle_updates"] == 2 * sim.n
     assert sim.launch_count() > 0
     sim.close()
+
+
+def test_precision_switch_to_fp64_allocates_its_cache():
+    """A context created FP32-mixed and switched to FP64 by set_params gets
+    the FP64 path's per-entry kernel cache and then matches the oracle to the
+    FP64 tolerance."""
+    from helpers import field_errors, oracle_outputs
+    s = sph_inputs.jittered_box(12, seed_index=49, vel_sigma=0.2)
+    sim = _sim(s, precision="fp32_mixed", ng_target=0)
+    sim.set_params(precision="fp64")
+    sim.find_neighbors()
+    sim.density()
+    sim.iad()
+    sim.momentum_energy()
+    got = sim.to_numpy()
+    assert sim.error_word() == 0
+    sim.close()
+    rc, _, ref = oracle_outputs(s, ng_target=0)
+    assert rc == 0
+    e = field_errors(got, ref)
+    for k in ("rho", "iad", "a", "du"):
+        assert e[k] <= 1e-12, (k, e)
