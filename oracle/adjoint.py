@@ -103,9 +103,14 @@ def frozen_loss(box: Box, s0: dict, params: Params, tape: Tape, alpha: float | N
     s = copy_state(s0)
     for k in range(len(tape.dt)):
         nn, nbr = tape.nn[k], tape.nbr[k]
-        rho, p, c = density_eos(box, s, nn, nbr, prm, Bn=Bn)
+        omega = None
+        if prm.gradh:
+            rho, p, c, omega = density_eos(box, s, nn, nbr, prm, Bn=Bn, with_omega=True)
+        else:
+            rho, p, c = density_eos(box, s, nn, nbr, prm, Bn=Bn)
         _, C6, _ = iad(box, s, rho, nn, nbr, prm, Bn=Bn)
-        me = momentum_energy(box, s, rho, p, c, C6, nn, nbr, prm, Bn=Bn, av_force=tape.av[k])
+        me = momentum_energy(box, s, rho, p, c, C6, nn, nbr, prm, Bn=Bn, av_force=tape.av[k],
+                             omega_full=omega)
         update(box, s, me["ax"], me["ay"], me["az"], me["du"], nn, tape.dt[k], tape.dt_prev[k],
                prm.ng_target)
     rho, _, _ = density_eos(box, s, tape.nn_final, tape.nbr_final, prm, Bn=Bn)
@@ -146,20 +151,42 @@ def _W(v, h, Bn: float, sinc_n: float):
     return Bn / h ** 3 * (torch.sin(xq) / xq) ** sinc_n
 
 
-def _density(box, x, h, m, u, a, b, Bn, prm):
+def _dWdh(v, h, Bn: float, sinc_n: float):
+    """dW/dh at fixed separation: -(3 W + v dW/dv) / h, with
+    dW/dv = B_n / h^3 n S^(n-1) (pi/2) (x cos x - sin x) / x^2, x = pi v / 2."""
+    xq = 0.5 * math.pi * v
+    S = torch.sin(xq) / xq
+    dS = 0.5 * math.pi * (xq * torch.cos(xq) - torch.sin(xq)) / (xq * xq)
+    W = Bn / h ** 3 * S ** sinc_n
+    dWdv = Bn / h ** 3 * sinc_n * S ** (sinc_n - 1.0) * dS
+    return -(3.0 * W + v * dWdv) / h
+
+
+def _density(box, x, h, m, u, a, b, Bn, prm, with_omega=False):
+    """Eq. 1 with the self term and the EOS; with_omega also returns the
+    grad-h terms Omega = 1 + h / (3 rho) sum_b m_b dW/dh (self term included)."""
     d = _sep(box, x, a, b)
     r = torch.sqrt((d * d).sum(1))
     rho = m * Bn / h ** 3                    # self term, W(0, h) = B_n / h^3
     rho = rho.index_add(0, a, m[b] * _W(r / h[a], h[a], Bn, prm.sinc_n))
     p = (prm.gamma - 1.0) * rho * u
     c = torch.sqrt(prm.gamma * p / rho)
-    return rho, p, c, d, r
+    if not with_omega:
+        return rho, p, c, d, r
+    dsum = m * (-3.0 * Bn / h ** 4)          # self term: dW(0, h)/dh = -3 B_n / h^4
+    dsum = dsum.index_add(0, a, m[b] * _dWdh(r / h[a], h[a], Bn, prm.sinc_n))
+    omega = 1.0 + h / (3.0 * rho) * dsum
+    return rho, p, c, d, r, omega
 
 
 def _step(box, st, h, m, nn, nbr, av, dt, dt_prev, alpha, Bn, prm):
     x, v, vh, u, du_prev = st
     a, b, on = _pairs(nbr, av)
-    rho, p, c, d, r = _density(box, x, h, m, u, a, b, Bn, prm)
+    if prm.gradh:
+        rho, p, c, d, r, omega = _density(box, x, h, m, u, a, b, Bn, prm, with_omega=True)
+    else:
+        rho, p, c, d, r = _density(box, x, h, m, u, a, b, Bn, prm)
+        omega = torch.ones_like(rho)
     # IAD: tau_a = sum_b (m_b / rho_b) W_ab(h_a) d d^T, C_a = tau_a^{-1}
     Wa = _W(r / h[a], h[a], Bn, prm.sinc_n)
     w = (m[b] / rho[b] * Wa)[:, None, None] * d[:, :, None] * d[:, None, :]
@@ -171,7 +198,8 @@ def _step(box, st, h, m, nn, nbr, av, dt, dt_prev, alpha, Bn, prm):
                      torch.zeros_like(va))
     Aa = torch.einsum("pij,pj->pi", C[a], d) * Wa[:, None]
     Ab = torch.einsum("pij,pj->pi", C[b], d) * Wb[:, None]
-    Xa, Xb = (p / rho ** 2)[a], (p / rho ** 2)[b]
+    X = p / (omega * rho ** 2)              # P / (Omega rho^2), Eqs. 2-3
+    Xa, Xb = X[a], X[b]
     vab = v[a] - v[b]
     xv = (-d * vab).sum(1)
     wv = xv / r

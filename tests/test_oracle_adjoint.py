@@ -136,3 +136,37 @@ def test_symmetry_closed_forms(case):
     # Galilean shift: sum_a dL/dv_a = sum_a m_a v_a(K)
     pK = np.array([(m * fin["vx"]).sum(), (m * fin["vy"]).sum(), (m * fin["vz"]).sum()])
     np.testing.assert_allclose(g["v"].sum(0), pK, rtol=1e-10, atol=1e-13 * np.abs(g["v"]).sum())
+
+
+@pytest.fixture(scope="module")
+def case_gradh():
+    s = sph_inputs.jittered_box(10, seed_index=72, vel_sigma=0.05)
+    box = oracle.Box(s["lo"], s["hi"], s["periodic"])
+    prm = oracle.Params(gradh=1)
+    tape = adj.record(box, s, prm, 3)
+    g = adj.reference_gradients(box, s, prm, tape)
+    return s, box, prm, tape, g
+
+
+def test_gradh_torch_forward_equals_c_oracle(case_gradh):
+    s, box, prm, tape, _ = case_gradh
+    L, fin, rho = adj.frozen_loss(box, s, prm, tape)
+    x0, v0, u0, al = adj._inputs(s, prm.alpha)
+    x, v, u, r = adj.torch_rollout(box, s, prm, tape, x0, v0, al, u0=u0)
+    vr = np.stack([fin["vx"], fin["vy"], fin["vz"]], 1)
+    assert np.abs(v.numpy() - vr).max() <= 1e-12 * np.abs(vr).max()
+    np.testing.assert_allclose(r.numpy(), rho, rtol=1e-13)
+
+
+@pytest.mark.parametrize("kind", ["x", "v", "mixed"])
+def test_gradh_reference_gradient_matches_central_differences(case_gradh, kind):
+    """With the grad-h terms the gradient also carries d Omega / dx (second
+    derivatives of W), checked against central differences of the C oracle."""
+    s, box, prm, tape, g = case_gradh
+    rng = np.random.default_rng(hash(kind) % 1000 + 7)
+    dx, dv, du, da = _directions(s["x"].shape[0], rng, kind)
+    fd = _fd(box, s, prm, tape, dx, dv, du, da, 1e-6)
+    ad = (g["x"] * dx).sum() + (g["v"] * dv).sum() + (g["u"] * du).sum() + g["alpha"] * da
+    scale = (np.abs(g["x"] * dx).sum() + np.abs(g["v"] * dv).sum() + np.abs(g["u"] * du).sum()
+             + abs(g["alpha"] * da))
+    assert abs(fd - ad) <= 1e-6 * scale, (fd, ad, scale)
