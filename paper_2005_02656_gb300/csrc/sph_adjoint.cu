@@ -23,8 +23,12 @@
 //   IAD         C = tau^{-1}: tau_bar = -C sym(C_bar) C, then
 //               tau_a = sum_b (m_b/rho_b) W_a d d^T, gathered over the list
 //               (for a) and over the reverse list (for b);
-//   EOS         P = (gamma-1) rho u, c = sqrt(gamma P / rho);
-//   density     Eq. 1, gathered over list and reverse list as for IAD.
+//   EOS         P = (gamma-1) rho u, c = sqrt(gamma P / rho), and with the
+//               grad-h terms X = P / (Omega rho^2), Omega = -(2/(3 rho)) G,
+//               G = sum_b m_b t dW/dt (t = r^2 / h_a^2);
+//   density     Eq. 1 (and G's pair terms, whose r^2-derivative is
+//               m_b (W' + t W'') / h_a^2), gathered over list and reverse
+//               list as for IAD.
 // Reverse lists are built per step from the tape's lists (count, scan,
 // scatter, then each row sorted), so every sum runs in a fixed order and the
 // gradient is bit-reproducible.  The viscosity switch x_ab . v_ab < 0 is
@@ -65,6 +69,7 @@ struct Work {
   double* cb;    // dL/dc
   double* Cb;    // 6 per particle: sym(dL/dC), then S = -C sym(dL/dC) C
   double* rhob;  // dL/drho
+  double* Gb;    // dL/dG of the grad-h sum (0 without grad-h terms)
 };
 
 // One recorded step, sorted order.
@@ -74,6 +79,7 @@ struct Slot {
   int32_t* nn;
   uint32_t* nbr;
   double *rho, *p, *c, *iad;
+  double* omega;  // grad-h terms of the step (read when gradh)
   Grid* grid;
   double* dtp;  // device [dt, dt_prev]
 };
@@ -103,6 +109,7 @@ struct Prep {
 struct Consts {
   double gamma, alpha, Bn;
   int sinc_n, max_nb;
+  int gradh;
 };
 
 __device__ __forceinline__ void sepd(const Grid& g, double xa, double ya, double za, double xb,
@@ -254,7 +261,7 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_rev_sort(const int64_t* sta
   }
 }
 
-__global__ void k_adj_prep(Slot sl, Prep pr, int64_t n, double Bn) {
+__global__ void k_adj_prep(Slot sl, Prep pr, int64_t n, double Bn, int gradh) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double h = sl.s.h[i];
@@ -263,7 +270,7 @@ __global__ void k_adj_prep(Slot sl, Prep pr, int64_t n, double Bn) {
     pr.hinv2[i] = hinv2;
     pr.norm[i] = Bn * hinv2 / h;
     pr.ir[i] = ir;
-    pr.X[i] = sl.p[i] * ir * ir;
+    pr.X[i] = gradh ? sl.p[i] * ir * ir / sl.omega[i] : sl.p[i] * ir * ir;
     pr.vol[i] = sl.s.m[i] * ir;
   }
 }
@@ -530,11 +537,21 @@ __global__ void __launch_bounds__(kThreads) k_adj_momentum_b(Slot sl, Work w, Pa
     w.Cb[6 * b + 3] = S[1][1];
     w.Cb[6 * b + 4] = 0.5 * (S[1][2] + S[2][1]);
     w.Cb[6 * b + 5] = S[2][2];
-    // EOS and X = P / rho^2, 1/rho
+    // EOS and X = P / (Omega rho^2), 1/rho
     const double rho = sl.rho[b], p = sl.p[b], c = sl.c[b];
     const double ir = 1.0 / rho;
-    const double pbar = Xbar * ir * ir + cbar * kc.gamma / (2.0 * c * rho);
-    irbar += 2.0 * Xbar * p * ir;
+    const double om = kc.gradh ? sl.omega[b] : 1.0;
+    const double pbar = Xbar * ir * ir / om + cbar * kc.gamma / (2.0 * c * rho);
+    irbar += 2.0 * Xbar * p * ir / om;
+    if (kc.gradh) {
+      // Omega = -(2/3) (1/rho) G with G = -(3/2) Omega rho
+      const double X = p * ir * ir / om;
+      const double ombar = -Xbar * X / om;
+      w.Gb[b] = -2.0 / 3.0 * ir * ombar;
+      irbar += -2.0 / 3.0 * (-1.5 * om * rho) * ombar;
+    } else {
+      w.Gb[b] = 0.0;
+    }
     w.rhob[b] = pbar * (kc.gamma - 1.0) * s.u[b] - cbar * c / (2.0 * rho);
     w.irb[b] = irbar;
     w.z.u[b] += pbar * (kc.gamma - 1.0) * rho;
@@ -623,7 +640,14 @@ __device__ __forceinline__ double dw_dr2(const PairBuf& pb, int64_t k, int64_t a
   return dW * hinv2;
 }
 
-template <bool kCached>
+// r^2-derivative of the grad-h pair term m_b t dW/dt of target a (t = r^2/h_a^2),
+// without m_b.
+__device__ __forceinline__ double dg_dr2(int64_t a, double r2, const Prep& pr, const Consts& kc) {
+  const double hinv2 = pr.hinv2[a];
+  return sph::kernel_tdw_dt64(r2 * hinv2, pr.norm[a], kc.sinc_n) * hinv2;
+}
+
+template <bool kCached, bool GRADH>
 __global__ void __launch_bounds__(kThreads) k_adj_density(Slot sl, Prep pr, Work w, PairBuf pb,
                                                           Rev rv, Bar out, int64_t n, Consts kc) {
   const Grid g = *sl.grid;
@@ -633,6 +657,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_density(Slot sl, Prep pr, Work
        p += (int64_t)gridDim.x * blockDim.x) {
     const double xp = s.x[p], yp = s.y[p], zp = s.z[p];
     const double rbp = w.rhob[p];
+    const double gbp = GRADH ? w.Gb[p] : 0.0;
     double xbx = 0, xby = 0, xbz = 0;
     const int cnt = min(sl.nn[p], mb);
     const uint32_t* list = sl.nbr + p * mb;
@@ -641,7 +666,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_density(Slot sl, Prep pr, Work
       double dx, dy, dz;
       sepd(g, xp, yp, zp, s.x[b], s.y[b], s.z[b], dx, dy, dz);
       const double r2 = dx * dx + dy * dy + dz * dz;
-      const double f = 2.0 * rbp * s.m[b] * dw_dr2<kCached>(pb, k, p, r2, pr, kc);
+      double f = 2.0 * rbp * s.m[b] * dw_dr2<kCached>(pb, k, p, r2, pr, kc);
+      if (GRADH) f += 2.0 * gbp * s.m[b] * dg_dr2(p, r2, pr, kc);
       xbx -= f * dx;
       xby -= f * dy;
       xbz -= f * dz;
@@ -655,7 +681,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_density(Slot sl, Prep pr, Work
       double dx, dy, dz;
       sepd(g, s.x[a], s.y[a], s.z[a], xp, yp, zp, dx, dy, dz);
       const double r2 = dx * dx + dy * dy + dz * dz;
-      const double f = 2.0 * w.rhob[a] * mp * dw_dr2<kCached>(pb, k, a, r2, pr, kc);
+      double f = 2.0 * w.rhob[a] * mp * dw_dr2<kCached>(pb, k, a, r2, pr, kc);
+      if (GRADH) f += 2.0 * w.Gb[a] * mp * dg_dr2(a, r2, pr, kc);
       xbx += f * dx;
       xby += f * dy;
       xbz += f * dz;
@@ -906,6 +933,7 @@ int run_step(sph_adj* A, int k, int j, cudaStream_t st) {
     s.p = sl.p;
     s.c = sl.c;
     s.iad = sl.iad;
+    s.omega = sl.omega;  // written by the density pass when params.gradh = 1
     Redirect r(A->ctx, sl);
     rc = sph_step(A->ctx, &s, A->dt_dev, st);
     if (rc != SPH_OK) return aerr(A, rc, "step %d: %s", k, sph_last_error(A->ctx));
@@ -979,6 +1007,7 @@ Consts consts_of(const sph_adj* A) {
   k.Bn = sph_kernel_norm(A->ctx);
   k.sinc_n = (int)A->prm.sinc_n;
   k.max_nb = A->prm.max_nb;
+  k.gradh = A->prm.gradh;
   return k;
 }
 
@@ -1000,12 +1029,17 @@ int reverse_step(sph_adj* A, int j, cudaStream_t st) {
   const int g = grid_for(n, A->sm_count, kThreads, 8);
   const int ga = g < kAlphaBlocks ? g : kAlphaBlocks;
   A->pb.stride = n;
-  k_adj_prep<<<g, kThreads, 0, st>>>(sl, A->pr, n, kc.Bn);
+  k_adj_prep<<<g, kThreads, 0, st>>>(sl, A->pr, n, kc.Bn, kc.gradh);
   k_adj_momentum_a<<<ga, kThreads, 0, st>>>(sl, A->pr, A->q, A->w, A->pb, n, kc, A->apart);
   k_alpha_sum<<<1, 32, 0, st>>>(A->apart, ga, A->alpha_acc);
   k_adj_momentum_b<<<g, kThreads, 0, st>>>(sl, A->w, A->pb, rev_of(A), n, kc);
   k_adj_iad<<<g, kThreads, 0, st>>>(sl, A->pr, A->w, A->pb, rev_of(A), n, kc);
-  k_adj_density<true><<<g, kThreads, 0, st>>>(sl, A->pr, A->w, A->pb, rev_of(A), A->pnext, n, kc);
+  if (kc.gradh)
+    k_adj_density<true, true><<<g, kThreads, 0, st>>>(sl, A->pr, A->w, A->pb, rev_of(A), A->pnext,
+                                                      n, kc);
+  else
+    k_adj_density<true, false><<<g, kThreads, 0, st>>>(sl, A->pr, A->w, A->pb, rev_of(A),
+                                                       A->pnext, n, kc);
   A->launches += 6;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return acuda(A, e, "reverse-step launch");
@@ -1027,8 +1061,8 @@ int sph_adjoint_init(const sph_params* params, int64_t n_max, int steps, int che
       checkpoint_every > steps || n_max < 1 || n_max > sph::kMaxParticles)
     return SPH_ERR_INVALID_ARG;
   if (params->max_nb > (1 << kKBits)) return SPH_ERR_INVALID_ARG;
-  // the reverse kernels assume Omega = 1 and the exact kernel
-  if (params->gradh != 0 || params->kernel_mode != SPH_KERNEL_EXACT) return SPH_ERR_INVALID_ARG;
+  // the reverse kernels differentiate the exact kernel (the table's is not built)
+  if (params->kernel_mode != SPH_KERNEL_EXACT) return SPH_ERR_INVALID_ARG;
   sph_adj* A = (sph_adj*)calloc(1, sizeof(sph_adj));
   if (!A) return SPH_ERR_OOM;
   int rc = sph_init(params, n_max, &A->ctx);
@@ -1054,7 +1088,7 @@ int sph_adjoint_init(const sph_params* params, int64_t n_max, int steps, int che
   AM(A->cbuf, (size_t)A->nseg * 13 * N);
   AM(A->cid, (size_t)A->nseg * N);
   AM(A->cdt, A->nseg);
-  AM(A->tbuf, (size_t)nslot * 22 * N);  // 13 sorted state + rho p c + iad 6
+  AM(A->tbuf, (size_t)nslot * 23 * N);  // 13 sorted state + rho p c + iad 6 + omega
   AM(A->tid, (size_t)nslot * N);
   AM(A->tint, (size_t)nslot * 2 * N);
   AM(A->tnbr, (size_t)nslot * N * mb);
@@ -1062,7 +1096,7 @@ int sph_adjoint_init(const sph_params* params, int64_t n_max, int steps, int che
   AM(A->tdt, 2 * nslot);
   AM(A->dts, steps);
   AM(A->bbuf, 22 * N);
-  AM(A->kbuf, 26 * N);  // Work: z 11 + X, ir, c + C 6 + rho = 21; Prep 5
+  AM(A->kbuf, 27 * N);  // Work: z 11 + X, ir, c + C 6 + rho = 21; Prep 5; G 1
   AM(A->pbuf, kRec * N * mb);
   AM(A->wkbuf, N * mb);
   AM(A->rcnt, N);
@@ -1092,12 +1126,13 @@ int sph_adjoint_init(const sph_params* params, int64_t n_max, int steps, int che
   A->W.du = A->wbuf + 25 * N;
   for (int j = 0; j < nslot; ++j) {
     Slot& sl = A->slot[j];
-    double* base = A->tbuf + (size_t)j * 22 * N;
+    double* base = A->tbuf + (size_t)j * 23 * N;
     sl.s = view13(base, N, A->tid + (size_t)j * N);
     sl.rho = base + 13 * N;
     sl.p = base + 14 * N;
     sl.c = base + 15 * N;
     sl.iad = base + 16 * N;
+    sl.omega = base + 22 * N;
     sl.perm = A->tint + (size_t)j * 2 * N;
     sl.nn = A->tint + (size_t)j * 2 * N + N;
     sl.nbr = A->tnbr + (size_t)j * N * mb;
@@ -1120,6 +1155,7 @@ int sph_adjoint_init(const sph_params* params, int64_t n_max, int steps, int che
   A->pr.ir = A->kbuf + 23 * N;
   A->pr.X = A->kbuf + 24 * N;
   A->pr.vol = A->kbuf + 25 * N;
+  A->w.Gb = A->kbuf + 26 * N;
   *out = A;
   return SPH_OK;
 }
@@ -1246,8 +1282,9 @@ int sph_adjoint_backward(sph_adj* A, const double* g_final, double* g_init, doub
   if (rc != SPH_OK) return rc;
   A->pb.stride = n;
   k_seed<<<g, kThreads, 0, st>>>(g_final, sf.s.id, n, A->w);
-  k_adj_prep<<<g, kThreads, 0, st>>>(sf, A->pr, n, kc.Bn);
-  k_adj_density<false><<<g, kThreads, 0, st>>>(sf, A->pr, A->w, A->pb, rev_of(A), A->q, n, kc);
+  k_adj_prep<<<g, kThreads, 0, st>>>(sf, A->pr, n, kc.Bn, 0);
+  k_adj_density<false, false><<<g, kThreads, 0, st>>>(sf, A->pr, A->w, A->pb, rev_of(A), A->q, n,
+                                                      kc);
   A->launches += 3;
   for (int seg = A->nseg - 1; seg >= 0; --seg) {
     if (A->tape_seg != seg) {

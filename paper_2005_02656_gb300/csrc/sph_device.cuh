@@ -80,6 +80,23 @@ __device__ __forceinline__ T ipow(T s, int n) {
   return r;
 }
 
+// S(t), dS/dt and d2S/dt2 of the FP64 series.
+__device__ __forceinline__ void sinc_poly64_d2(double t, double& S, double& dS, double& d2S) {
+  constexpr SincCoefs<kSincTerms64> C{};
+  double s = C.c[kSincTerms64 - 1];
+  double d = (kSincTerms64 - 1) * C.c[kSincTerms64 - 1];
+  double e = (kSincTerms64 - 1) * (kSincTerms64 - 2) * C.c[kSincTerms64 - 1];
+#pragma unroll
+  for (int k = kSincTerms64 - 2; k >= 0; --k) {
+    s = fma(s, t, C.c[k]);
+    if (k >= 1) d = fma(d, t, k * C.c[k]);
+    if (k >= 2) e = fma(e, t, k * (k - 1) * C.c[k]);
+  }
+  S = s;
+  dS = d;
+  d2S = e;
+}
+
 // S(t) and dS/dt of the FP32 series.
 __device__ __forceinline__ void sinc_poly32_d(float t, float& S, float& dS) {
   constexpr SincCoefs<kSincTerms32> C{};
@@ -120,6 +137,19 @@ __device__ __forceinline__ float kernel_w32_tab(float t, float norm, const float
   if (i > kKernelTableN - 2) i = kKernelTableN - 2;
   const float2 e = tab[i];
   return norm * fmaf(e.y, q - (float)i, e.x);
+}
+
+// dW/dt + t d2W/dt2 (FP64): the t-derivative of t dW/dt, the pair term of the
+// grad-h sum's derivative; t is clamped at 4.
+__device__ __forceinline__ double kernel_tdw_dt64(double t, double norm, int n) {
+  t = fmin(t, 4.0);
+  double S, dS, d2S;
+  sinc_poly64_d2(t, S, dS, d2S);
+  const double Sn1 = ipow(S, n - 1);
+  const double Sn2 = n >= 2 ? ipow(S, n - 2) : 0.0;  // multiplied by n - 1 = 0 when n = 1
+  const double dW = norm * n * Sn1 * dS;
+  const double d2W = norm * n * ((n - 1) * Sn2 * dS * dS + Sn1 * d2S);
+  return dW + t * d2W;
 }
 
 // W for t = v^2 < 4 (caller guarantees the neighbour criterion), norm = B_n/h^3.

@@ -215,3 +215,42 @@ def test_full_size_symmetry_closed_forms():
     pK = (s["m"][None, :] * f[3:6]).sum(1)
     assert np.abs(g["v"].sum(0) - pK).max() <= 1e-10 * (np.abs(g["v"]).sum() + np.abs(pK).sum())
     assert g["info"]["recomputed_steps"] == K - EVERY
+
+
+def test_gradh_adjoint_matches_reference_and_central_differences():
+    """With the grad-h terms (gradh = 1) the reverse pass also carries
+    dOmega/dx (second derivatives of W): against the reference adjoint with
+    the same Omega and against central differences of the C oracle."""
+    from paper_2005_02656_gb300 import Params, Rollout
+    s, box = _case(side=10, seed=73)
+    prm = oracle.Params(gradh=1)
+    steps = 6
+    tape = adj.record(box, s, prm, steps)
+    ref = adj.reference_gradients(box, s, prm, tape)
+    n = s["x"].shape[0]
+    ro = Rollout(n, steps, 3, Params(box_lo=s["lo"], box_hi=s["hi"], periodic=s["periodic"],
+                                     gradh=1))
+    gpu = _gpu_grad(s, steps=steps, every=3, ro=ro)
+    ro.close()
+    np.testing.assert_allclose(gpu["dt"], np.array(tape.dt), rtol=1e-12)
+    for field in ("x", "v", "u"):
+        err = np.abs(gpu[field] - ref[field]).max()
+        assert err <= TOL * np.abs(ref[field]).max(), (field, err)
+    assert gpu["alpha"] == pytest.approx(ref["alpha"], rel=TOL)
+    rng = np.random.default_rng(17)
+    sx, sv = 1e-3, 0.05
+    for _ in range(4):
+        dx = rng.standard_normal((n, 3)) * sx
+        dv = rng.standard_normal((n, 3)) * sv
+
+        def at(sign):
+            q = oracle.copy_state(s)
+            for c, k in enumerate("xyz"):
+                q[k] = q[k] + sign * 1e-6 * dx[:, c]
+                q["v" + k] = q["v" + k] + sign * 1e-6 * dv[:, c]
+                q["v" + k + "h"] = q["v" + k + "h"] + sign * 1e-6 * dv[:, c]
+            return adj.frozen_loss(box, q, prm, tape)[0]
+        fd = (at(1.0) - at(-1.0)) / 2e-6
+        ad = (gpu["x"] * dx).sum() + (gpu["v"] * dv).sum()
+        scale = np.abs(gpu["x"] * dx).sum() + np.abs(gpu["v"] * dv).sum()
+        assert abs(fd - ad) <= TOL * scale, (fd, ad)
