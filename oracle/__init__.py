@@ -82,6 +82,10 @@ def _load():
         lib.oracle_diagnostics.restype = None
         lib.oracle_diagnostics.argtypes = [i64] + [P] * 9
         lib.oracle_any_nonfinite.restype = cint
+        lib.oracle_gravity_direct.restype = None
+        lib.oracle_gravity_direct.argtypes = [i64, P, P, P, P, d, d, i64, P, P, P, P]
+        lib.oracle_gravity_tree.restype = cint
+        lib.oracle_gravity_tree.argtypes = [i64, P, P, P, P, P, d, d, d, i64, P, P, P, P, P]
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = cint
         lib.oracle_any_nonfinite.argtypes = [i64, P]
@@ -359,3 +363,29 @@ def sampled_outputs(box: Box, s: dict, params: Params, sample):
         out["omega"] = om[sample]
     out.update(me)
     return rc_iad, out
+
+
+def gravity_direct(s: dict, G: float = 1.0, eps: float = 0.0, targets=None):
+    """Softened Newtonian self-gravity by direct summation (the definition).
+    Returns g (nt, 3)."""
+    x, y, z, m = (_f64(s[k]) for k in ("x", "y", "z", "m"))
+    t = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = x.shape[0] if t is None else t.shape[0]
+    g = np.empty((3, nt))
+    _load().oracle_gravity_direct(x.shape[0], _p(x), _p(y), _p(z), _p(m), float(G), float(eps),
+                                  nt, _p(t), _p(g[0]), _p(g[1]), _p(g[2]))
+    return g.T.copy()
+
+
+def gravity_tree(s: dict, G: float = 1.0, eps: float = 0.0, theta: float = 0.5, targets=None):
+    """Self-gravity by the multipole tree on the neighbour grid's cells.
+    Returns (rc, g (nt, 3), [node interactions, particle interactions])."""
+    x, y, z, h, m = (_f64(s[k]) for k in ("x", "y", "z", "h", "m"))
+    t = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = x.shape[0] if t is None else t.shape[0]
+    g = np.empty((3, nt))
+    stats = np.zeros(2, dtype=np.int64)
+    rc = _load().oracle_gravity_tree(x.shape[0], _p(x), _p(y), _p(z), _p(h), _p(m), float(G),
+                                     float(eps), float(theta), nt, _p(t), _p(g[0]), _p(g[1]),
+                                     _p(g[2]), _p(stats))
+    return rc, g.T.copy(), stats

@@ -674,3 +674,272 @@ int oracle_any_nonfinite(int64_t n, const double* v) {
     if (!isfinite(v[i])) return 1;
   return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Self-gravity (section 4.1: a multipolar expansion evaluated on the tree    */
+/* used to find neighbours; no formula is printed).  Reading:                 */
+/*   g_a = -G sum_{b != a} m_b (x_a - x_b) / (|x_a - x_b|^2 + eps^2)^(3/2)    */
+/* (Newtonian gravity with Plummer softening eps, open boundaries), which    */
+/* oracle_gravity_direct evaluates exactly, and its tree approximation       */
+/* oracle_gravity_tree:                                                      */
+/*  - leaves: the cells of the neighbour grid on open axes (per axis lo =    */
+/*    min x, L = extent, nc = min(floor(L / (2 h_max (1 + 1e-9))), 256) and  */
+/*    at least 1, cs = L / nc, cell = floor((x - lo) * (1 / cs)) clamped),   */
+/*    keyed by the Morton code of the cell (bit i of the x cell at 3i, y at  */
+/*    3i+1, z at 3i+2; bits = ceil(log2(max nc)) per axis);                  */
+/*  - node at level l (0 = root, bits = leaves): the cells sharing the top   */
+/*    3 l bits of the code; its box is those cells' union, its size s the   */
+/*    box's longest side; its moments (about its centre of mass c) are the   */
+/*    mass M and the traceless quadrupole Q_ij = sum m (3 d_i d_j - |d|^2   */
+/*    delta_ij), d = x - c;                                                  */
+/*  - for target a, depth-first from the root with children in Morton order: */
+/*    a node whose box does not contain x_a and with s / |x_a - c| < theta   */
+/*    adds, with r = x_a - c, R = |r|:                                       */
+/*      -G M r / (R^2 + eps^2)^(3/2) + G Q r / R^5 - (5/2) G (r.Q.r) r / R^7  */
+/*    (the gradient of -G (M/R + r.Q.r / (2 R^5)), the monopole softened);    */
+/*    an opened leaf adds its particles by the direct formula; other nodes   */
+/*    open their children.                                                   */
+/* ------------------------------------------------------------------------- */
+void oracle_gravity_direct(int64_t n, const double* x, const double* y, const double* z,
+                           const double* m, double G, double eps, int64_t nt,
+                           const int64_t* targets, double* gx, double* gy, double* gz) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t t = 0; t < nt; ++t) {
+    int64_t a = targets ? targets[t] : t;
+    double s[3] = {0, 0, 0};
+    for (int64_t b = 0; b < n; ++b) {
+      if (b == a) continue;
+      double d[3] = {x[a] - x[b], y[a] - y[b], z[a] - z[b]};
+      double r2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2] + eps * eps;
+      double f = m[b] / (r2 * sqrt(r2));
+      for (int k = 0; k < 3; ++k) s[k] -= G * f * d[k];
+    }
+    gx[t] = s[0];
+    gy[t] = s[1];
+    gz[t] = s[2];
+  }
+}
+
+typedef struct {
+  uint32_t code;     /* Morton prefix */
+  int level;
+  int64_t first;     /* first child (index into the node array), or -1 for a leaf */
+  int nchild;
+  int64_t p0, np;    /* particles of the node: order[p0 .. p0 + np) */
+  double box_lo[3], box_hi[3], size;
+  double M, c[3], Q[6];   /* xx xy xz yy yz zz */
+} oracle_node;
+
+static uint32_t spread_bits(uint32_t v) {
+  uint32_t r = 0;
+  for (int i = 0; i < 10; ++i) r |= ((v >> i) & 1u) << (3 * i);
+  return r;
+}
+
+typedef struct {
+  uint32_t code;
+  int64_t index;
+} code_index;
+
+static int cmp_code_index(const void* p, const void* q) {
+  const code_index* a = (const code_index*)p;
+  const code_index* b = (const code_index*)q;
+  if (a->code != b->code) return a->code < b->code ? -1 : 1;
+  return (a->index > b->index) - (a->index < b->index);
+}
+
+static void node_moments(oracle_node* nd, const int64_t* order, const double* x, const double* y,
+                         const double* z, const double* m) {
+  double M = 0, s[3] = {0, 0, 0};
+  for (int64_t i = nd->p0; i < nd->p0 + nd->np; ++i) {
+    int64_t b = order[i];
+    M += m[b];
+    s[0] += m[b] * x[b];
+    s[1] += m[b] * y[b];
+    s[2] += m[b] * z[b];
+  }
+  nd->M = M;
+  for (int k = 0; k < 3; ++k) nd->c[k] = s[k] / M;
+  double Q[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t i = nd->p0; i < nd->p0 + nd->np; ++i) {
+    int64_t b = order[i];
+    double d[3] = {x[b] - nd->c[0], y[b] - nd->c[1], z[b] - nd->c[2]};
+    double d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+    Q[0] += m[b] * (3 * d[0] * d[0] - d2);
+    Q[1] += m[b] * (3 * d[0] * d[1]);
+    Q[2] += m[b] * (3 * d[0] * d[2]);
+    Q[3] += m[b] * (3 * d[1] * d[1] - d2);
+    Q[4] += m[b] * (3 * d[1] * d[2]);
+    Q[5] += m[b] * (3 * d[2] * d[2] - d2);
+  }
+  memcpy(nd->Q, Q, sizeof(Q));
+}
+
+static void tree_walk(const oracle_node* nodes, int64_t k, const int64_t* order, const double* x,
+                      const double* y, const double* z, const double* m, int64_t a, double G,
+                      double eps, double theta, double* acc, int64_t* counts) {
+  const oracle_node* nd = &nodes[k];
+  double p[3] = {x[a], y[a], z[a]};
+  int inside = 1;
+  for (int ax = 0; ax < 3; ++ax)
+    if (p[ax] < nd->box_lo[ax] || p[ax] > nd->box_hi[ax]) inside = 0;
+  double r[3] = {p[0] - nd->c[0], p[1] - nd->c[1], p[2] - nd->c[2]};
+  double R2 = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
+  double R = sqrt(R2);
+  if (!inside && nd->size < theta * R) {
+    double s2 = R2 + eps * eps;
+    double mono = G * nd->M / (s2 * sqrt(s2));
+    const double* Q = nd->Q;
+    double Qr[3] = {Q[0] * r[0] + Q[1] * r[1] + Q[2] * r[2],
+                    Q[1] * r[0] + Q[3] * r[1] + Q[4] * r[2],
+                    Q[2] * r[0] + Q[4] * r[1] + Q[5] * r[2]};
+    double rQr = r[0] * Qr[0] + r[1] * Qr[1] + r[2] * Qr[2];
+    double R5 = R2 * R2 * R;
+    double R7 = R5 * R2;
+    for (int i = 0; i < 3; ++i)
+      acc[i] += -mono * r[i] + G * Qr[i] / R5 - 2.5 * G * rQr * r[i] / R7;
+    counts[0] += 1;
+    return;
+  }
+  if (nd->first < 0) {
+    for (int64_t i = nd->p0; i < nd->p0 + nd->np; ++i) {
+      int64_t b = order[i];
+      if (b == a) continue;
+      double d[3] = {p[0] - x[b], p[1] - y[b], p[2] - z[b]};
+      double r2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2] + eps * eps;
+      double f = m[b] / (r2 * sqrt(r2));
+      for (int q = 0; q < 3; ++q) acc[q] -= G * f * d[q];
+      counts[1] += 1;
+    }
+    return;
+  }
+  for (int j = 0; j < nd->nchild; ++j)
+    tree_walk(nodes, nd->first + j, order, x, y, z, m, a, G, eps, theta, acc, counts);
+}
+
+/* Returns ORACLE_OK, or ORACLE_INVALID_ARG (n < 1, or no positive h).
+ * stats (optional, 2 values): node and particle interactions summed over the
+ * targets. */
+int oracle_gravity_tree(int64_t n, const double* x, const double* y, const double* z,
+                        const double* h, const double* m, double G, double eps, double theta,
+                        int64_t nt, const int64_t* targets, double* gx, double* gy, double* gz,
+                        int64_t* stats) {
+  if (n < 1) return ORACLE_INVALID_ARG;
+  const double* pos[3] = {x, y, z};
+  double lo[3], L[3], cs[3], inv[3], hmax = 0.0;
+  int nc[3], maxnc = 1;
+  for (int64_t i = 0; i < n; ++i) hmax = h[i] > hmax ? h[i] : hmax;
+  if (!(hmax > 0.0)) return ORACLE_INVALID_ARG;
+  for (int ax = 0; ax < 3; ++ax) {
+    double mn = pos[ax][0], mx = pos[ax][0];
+    for (int64_t i = 1; i < n; ++i) {
+      mn = pos[ax][i] < mn ? pos[ax][i] : mn;
+      mx = pos[ax][i] > mx ? pos[ax][i] : mx;
+    }
+    lo[ax] = mn;
+    L[ax] = mx - mn;
+    int c = 1;
+    if (L[ax] > 0.0) {
+      double q = floor(L[ax] / (2.0 * hmax * (1.0 + 1e-9)));
+      c = q < 1.0 ? 1 : (q > 256.0 ? 256 : (int)q);
+    }
+    nc[ax] = c;
+    cs[ax] = L[ax] > 0.0 ? L[ax] / c : 0.0;
+    inv[ax] = cs[ax] > 0.0 ? 1.0 / cs[ax] : 0.0;
+    maxnc = c > maxnc ? c : maxnc;
+  }
+  int bits = 0;
+  while ((1 << bits) < maxnc) ++bits;
+  code_index* ci = (code_index*)malloc(sizeof(code_index) * (size_t)n);
+  int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    uint32_t cell[3];
+    for (int ax = 0; ax < 3; ++ax) {
+      double q = floor((pos[ax][i] - lo[ax]) * inv[ax]);
+      int v = q < 0.0 ? 0 : (q >= (double)nc[ax] ? nc[ax] - 1 : (int)q);
+      cell[ax] = (uint32_t)v;
+    }
+    ci[i].code = spread_bits(cell[0]) | (spread_bits(cell[1]) << 1) | (spread_bits(cell[2]) << 2);
+    ci[i].index = i;
+  }
+  qsort(ci, (size_t)n, sizeof(code_index), cmp_code_index);
+  for (int64_t i = 0; i < n; ++i) order[i] = ci[i].index;
+  /* nodes level by level from the leaves up: a node = a run of equal prefixes */
+  int64_t cap = (int64_t)(bits + 1) * n + 1, nn = 0;
+  oracle_node* nodes = (oracle_node*)calloc((size_t)cap, sizeof(oracle_node));
+  int64_t* level_start = (int64_t*)malloc(sizeof(int64_t) * (bits + 2));
+  /* leaves */
+  level_start[bits] = 0;
+  for (int64_t i = 0; i < n;) {
+    int64_t j = i;
+    while (j < n && ci[j].code == ci[i].code) ++j;
+    oracle_node* nd = &nodes[nn++];
+    nd->code = ci[i].code;
+    nd->level = bits;
+    nd->first = -1;
+    nd->p0 = i;
+    nd->np = j - i;
+    i = j;
+  }
+  int64_t prev0 = 0, prev1 = nn;
+  for (int l = bits - 1; l >= 0; --l) {
+    level_start[l] = nn;
+    for (int64_t i = prev0; i < prev1;) {
+      uint32_t pc = nodes[i].code >> 3;
+      int64_t j = i;
+      while (j < prev1 && (nodes[j].code >> 3) == pc) ++j;
+      oracle_node* nd = &nodes[nn++];
+      nd->code = pc;
+      nd->level = l;
+      nd->first = i;
+      nd->nchild = (int)(j - i);
+      nd->p0 = nodes[i].p0;
+      nd->np = nodes[j - 1].p0 + nodes[j - 1].np - nodes[i].p0;
+      i = j;
+    }
+    prev0 = level_start[l];
+    prev1 = nn;
+  }
+  /* boxes and moments (each node from its own particles) */
+  for (int64_t k = 0; k < nn; ++k) {
+    oracle_node* nd = &nodes[k];
+    int span = 1 << (bits - nd->level);
+    uint32_t c3[3] = {0, 0, 0};
+    for (int i = 0; i < 10; ++i)
+      for (int ax = 0; ax < 3; ++ax) c3[ax] |= ((nd->code >> (3 * i + ax)) & 1u) << i;
+    double size = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+      int c0 = (int)c3[ax] * span, c1 = c0 + span - 1;
+      if (c1 > nc[ax] - 1) c1 = nc[ax] - 1;
+      nd->box_lo[ax] = lo[ax] + c0 * cs[ax];
+      nd->box_hi[ax] = lo[ax] + (c1 + 1) * cs[ax];
+      double ext = nd->box_hi[ax] - nd->box_lo[ax];
+      size = ext > size ? ext : size;
+    }
+    nd->size = size;
+    node_moments(nd, order, x, y, z, m);
+  }
+  int64_t root = nn - 1;
+  int64_t tot[2] = {0, 0};
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : tot[:2])
+  for (int64_t t = 0; t < nt; ++t) {
+    int64_t a = targets ? targets[t] : t;
+    double acc[3] = {0, 0, 0};
+    int64_t counts[2] = {0, 0};
+    tree_walk(nodes, root, order, x, y, z, m, a, G, eps, theta, acc, counts);
+    gx[t] = acc[0];
+    gy[t] = acc[1];
+    gz[t] = acc[2];
+    tot[0] += counts[0];
+    tot[1] += counts[1];
+  }
+  if (stats) {
+    stats[0] = tot[0];
+    stats[1] = tot[1];
+  }
+  free(level_start);
+  free(nodes);
+  free(order);
+  free(ci);
+  return ORACLE_OK;
+}

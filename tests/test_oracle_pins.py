@@ -554,3 +554,62 @@ def test_table_mode_outputs_close_to_exact(oracle_mod):
     # the process-wide mode is back to exact after the call with default params
     o2 = all_outputs(oracle_mod, s)
     np.testing.assert_array_equal(o2["rho"], o0["rho"])
+
+
+# -------------------------------------------------- self-gravity (section 4.1) --
+def _sphere(side=24, seed=3, eps_jitter=0.1):
+    rng = np.random.default_rng(seed)
+    g1 = (np.arange(side) + 0.5) / side * 2 - 1
+    X, Y, Z = np.meshgrid(g1, g1, g1, indexing="ij")
+    P = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    P += rng.uniform(-eps_jitter, eps_jitter, P.shape) * (2 / side)
+    P = P[(P ** 2).sum(1) < 1]
+    n = P.shape[0]
+    return {"x": P[:, 0].copy(), "y": P[:, 1].copy(), "z": P[:, 2].copy(),
+            "m": np.full(n, 1.0 / n), "h": np.full(n, 1.44 * 2 / side)}
+
+
+def test_gravity_direct_two_body_and_third_law(oracle_mod):
+    s = {"x": np.array([0.0, 0.3]), "y": np.array([0.0, 0.4]), "z": np.zeros(2),
+         "m": np.array([2.0, 0.5])}
+    g = oracle_mod.gravity_direct(s, G=1.5, eps=0.1)
+    d = np.array([0.3, 0.4, 0.0])
+    f = 1.5 / (0.25 + 0.01) ** 1.5
+    np.testing.assert_allclose(g[0], f * 0.5 * d, rtol=1e-14)
+    np.testing.assert_allclose(g[1], -f * 2.0 * d, rtol=1e-14)
+    s = _sphere(14)
+    g = oracle_mod.gravity_direct(s, eps=1e-3)
+    mg = s["m"][:, None] * g
+    assert np.abs(mg.sum(0)).max() < 1e-13 * np.abs(mg).sum()
+
+
+def test_gravity_uniform_sphere_interior_field(oracle_mod):
+    """Shell theorem: inside a uniform sphere g = -G M r / R^3 (lattice noise
+    aside)."""
+    s = _sphere(24)
+    g = oracle_mod.gravity_direct(s, eps=1e-3)
+    r = np.stack([s["x"], s["y"], s["z"]], 1)
+    rad = np.linalg.norm(r, axis=1)
+    sel = (rad > 0.2) & (rad < 0.6)
+    expect = -r[sel]          # G = M = R = 1
+    err = np.linalg.norm(g[sel] - expect, axis=1) / np.linalg.norm(expect, axis=1)
+    assert np.median(err) < 0.03
+
+
+def test_gravity_tree_reduces_to_direct_and_converges(oracle_mod):
+    """theta = 0 accepts no node: the tree sum is the direct sum.  With the
+    quadrupole the error falls faster than (theta)^2 per halving (a monopole-
+    only expansion gives about 4x; a wrong quadrupole term does no better)."""
+    s = _sphere(24)
+    gd = oracle_mod.gravity_direct(s, eps=1e-3)
+    rc, g0, st = oracle_mod.gravity_tree(s, eps=1e-3, theta=0.0)
+    assert rc == 0 and st[0] == 0
+    np.testing.assert_allclose(g0, gd, rtol=1e-12, atol=1e-14 * np.abs(gd).max())
+    rms = []
+    for th in (0.2, 0.4, 0.8):
+        rc, gt, st = oracle_mod.gravity_tree(s, eps=1e-3, theta=th)
+        assert rc == 0 and st[0] > 0
+        e = np.linalg.norm(gt - gd, axis=1) / np.linalg.norm(gd, axis=1)
+        rms.append(np.sqrt((e ** 2).mean()))
+    assert rms[1] < 1e-3
+    assert rms[1] / rms[0] > 6 and rms[2] / rms[1] > 6, rms
