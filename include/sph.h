@@ -235,6 +235,25 @@ SPH_API const char* sph_last_error(const sph_ctx* ctx);
  * SPH_ERR_INVALID_ARG or SPH_ERR_CUDA. */
 SPH_API int sph_diagnostics_noalloc(const sph_state* state, double* out, sph_stream_t stream);
 
+/* Self-gravity (section 4.1: a multipolar expansion evaluated on the tree
+ * used for the neighbour search), as an acceleration added by the caller:
+ *   g_a = -G sum_{b != a} m_b (x_a - x_b) / (|x_a - x_b|^2 + eps^2)^(3/2),
+ * approximated on a tree whose leaves are the occupied cells of the
+ * neighbour grid (side >= 2 h_max) and whose level-l nodes are the cells
+ * sharing the top 3 l Morton bits.  Each node carries its mass, centre of
+ * mass c and traceless quadrupole Q; a node whose box does not contain x_a
+ * and whose longest side s satisfies s < theta |x_a - c| contributes
+ * -G M r / (|r|^2 + eps^2)^(3/2) + G Q r / |r|^5 - (5/2) G (r.Q.r) r / |r|^7
+ * (r = x_a - c); leaves that are opened contribute their particles directly.
+ * theta = 0 gives the direct sum.  All axes must be open (params.periodic all
+ * 0).  Sorts the state in place like sph_find_neighbors (and invalidates the
+ * lists); gx gy gz (DEVICE, n each) receive g in the new order.
+ * interactions (HOST, optional, 2 values): node and particle interactions.
+ * FP64 whatever params.precision.  Synchronises the stream. */
+SPH_API int sph_gravity(sph_ctx* ctx, sph_state* state, double G, double eps, double theta,
+                        double* gx, double* gy, double* gz, int64_t* interactions,
+                        sph_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Batched ensemble: independent boxes of uneven sizes, each with its own    */
 /* box, periodicity, viscosity alpha and time step, advanced together by one */

@@ -45,7 +45,7 @@ EXPORTS = ("sph_default_params", "sph_init", "sph_destroy", "sph_set_params", "s
            "sph_ens_default_config", "sph_ensemble_init", "sph_ensemble_destroy",
            "sph_ensemble_set_config", "sph_ensemble_step", "sph_ensemble_capture",
            "sph_ensemble_replay", "sph_ensemble_error_word", "sph_ensemble_last_error",
-           "sph_ensemble_info", "sph_ensemble_phase_times", "sph_adjoint_init", "sph_adjoint_destroy", "sph_adjoint_forward",
+           "sph_ensemble_info", "sph_ensemble_phase_times", "sph_gravity", "sph_adjoint_init", "sph_adjoint_destroy", "sph_adjoint_forward",
            "sph_adjoint_backward", "sph_adjoint_info", "sph_adjoint_time_steps",
            "sph_adjoint_last_error")
 STAGES = ("sort", "find", "density", "iad", "momentum", "dt", "update")
@@ -162,6 +162,8 @@ def load(path: str = LIB_PATH):
     lib.sph_adjoint_time_steps.restype = I
     lib.sph_adjoint_last_error.argtypes = [ctxp]
     lib.sph_adjoint_last_error.restype = C.c_char_p
+    lib.sph_gravity.argtypes = [ctxp, sp, D, D, D, P, P, P, P, P]
+    lib.sph_gravity.restype = I
     lib.sph_diagnostics_noalloc.argtypes = [sp, P, P]
     lib.sph_diagnostics_noalloc.restype = I
     lib.sph_stats.argtypes = [ctxp, P]

@@ -42,9 +42,11 @@
 
 #include "sph_device.cuh"
 #include "sph_internal.cuh"
+#include "sph_scan.cuh"
 #include "sph_tile.cuh"
 
 using sph::Grid;
+using sph::scan::kScanItems;
 using sph::StateView;
 
 namespace {
@@ -53,7 +55,6 @@ constexpr int kThreads = 128;
 constexpr int kRowSmem = 512;     // reverse-list rows sorted in shared memory up to this length
 constexpr int kSortWarps = 4;
 constexpr int kKBits = 12;        // reverse entry: (a << 12) | k with k < 4096 = max max_nb
-constexpr int kScanItems = 4096;  // per scan block (1024 threads x 4)
 constexpr int kAlphaBlocks = 1024;
 
 // Adjoint of the 11 differentiated state fields, one array each.
@@ -138,75 +139,6 @@ __global__ void k_rev_count(const int32_t* nn, const uint32_t* nbr, int mb, int6
     const uint32_t* row = nbr + a * mb;
     for (int k = 0; k < c; ++k) atomicAdd(&cnt[sph::entry_index(row[k])], 1);
   }
-}
-
-// Exclusive scan of cnt[0..n) into start[0..n], three passes.
-__device__ __forceinline__ int64_t block_exclusive(int64_t v, int64_t* total) {
-  __shared__ int64_t wsum[32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int64_t x = v;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    int64_t s = lane < nw ? wsum[lane] : 0;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
-    }
-    if (lane < nw) wsum[lane] = s;
-  }
-  __syncthreads();
-  const int64_t before = (w > 0 ? wsum[w - 1] : 0) + x - v;
-  *total = wsum[(blockDim.x >> 5) - 1];
-  __syncthreads();
-  return before;
-}
-
-__global__ void __launch_bounds__(1024) k_scan_sum(const int32_t* cnt, int64_t n, int64_t* part) {
-  const int64_t base = blockIdx.x * (int64_t)kScanItems + threadIdx.x * 4;
-  int64_t s = 0;
-  for (int i = 0; i < 4; ++i)
-    if (base + i < n) s += cnt[base + i];
-  int64_t tot;
-  block_exclusive(s, &tot);
-  if (threadIdx.x == 0) part[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(1024) k_scan_parts(int64_t* part, int nparts) {
-  // one block: exclusive scan of the block sums, in chunks of 1024
-  int64_t carry = 0;
-  for (int b0 = 0; b0 < nparts; b0 += 1024) {
-    const int i = b0 + threadIdx.x;
-    const int64_t v = i < nparts ? part[i] : 0;
-    int64_t tot;
-    const int64_t ex = block_exclusive(v, &tot);
-    if (i < nparts) part[i] = carry + ex;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) part[nparts] = carry;
-}
-
-__global__ void __launch_bounds__(1024) k_scan_apply(const int32_t* cnt, int64_t n,
-                                                     const int64_t* part, int nparts,
-                                                     int64_t* start) {
-  const int64_t base = blockIdx.x * (int64_t)kScanItems + threadIdx.x * 4;
-  int64_t v[4], s = 0;
-  for (int i = 0; i < 4; ++i) {
-    v[i] = base + i < n ? cnt[base + i] : 0;
-    s += v[i];
-  }
-  int64_t tot;
-  int64_t ex = block_exclusive(s, &tot) + part[blockIdx.x];
-  for (int i = 0; i < 4; ++i) {
-    if (base + i < n) start[base + i] = ex;
-    ex += v[i];
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) start[n] = part[nparts];
 }
 
 __global__ void k_rev_fill(const int32_t* nn, const uint32_t* nbr, int mb, int64_t n,
@@ -985,10 +917,7 @@ int build_rev(sph_adj* A, const Slot& sl, cudaStream_t st) {
   if (e != cudaSuccess) return acuda(A, e, "reverse lists");
   const int g = grid_for(n, A->sm_count, 256, 16);
   k_rev_count<<<g, 256, 0, st>>>(sl.nn, sl.nbr, mb, n, A->rcnt);
-  const int nparts = (int)((n + kScanItems - 1) / kScanItems);
-  k_scan_sum<<<nparts, 1024, 0, st>>>(A->rcnt, n, A->spart);
-  k_scan_parts<<<1, 1024, 0, st>>>(A->spart, nparts);
-  k_scan_apply<<<nparts, 1024, 0, st>>>(A->rcnt, n, A->spart, nparts, A->rstart);
+  sph::scan::exclusive_scan(A->rcnt, n, A->spart, A->rstart, st);
   e = cudaMemsetAsync(A->rcnt, 0, sizeof(int32_t) * (size_t)n, st);
   if (e != cudaSuccess) return acuda(A, e, "reverse lists");
   k_rev_fill<<<g, 256, 0, st>>>(sl.nn, sl.nbr, mb, n, A->rstart, A->rcnt, A->rlist);

@@ -203,7 +203,8 @@ void free_all(sph_ctx* ctx) {
                   ctx->ktab32, ctx->code, ctx->slot,
                   ctx->perm_tmp, ctx->perm, ctx->tbl_count, ctx->tbl_start, ctx->occ,
                   ctx->scan_part, ctx->cell_of, ctx->s.x, ctx->s_id_buf, ctx->pos32,
-                  ctx->cell3, ctx->nn, ctx->nbr, ctx->wcache, ctx->vol, ctx->rec_d, ctx->rec_i, ctx->rec_m, ctx->red.part, ctx->red.counter, ctx->stats, ctx->hm_buf, ctx->hm_id};
+                  ctx->cell3, ctx->nn, ctx->nbr, ctx->wcache, ctx->vol, ctx->rec_d, ctx->rec_i, ctx->rec_m, ctx->red.part, ctx->red.counter, ctx->stats, ctx->hm_buf, ctx->hm_id,
+                  ctx->grav_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }

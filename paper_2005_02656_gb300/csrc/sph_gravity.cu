@@ -1,0 +1,379 @@
+// Self-gravity (sph_gravity in include/sph.h): section 4.1 evaluates it by a
+// multipolar expansion on the tree used to find neighbours.  Here the tree's
+// leaves are the occupied cells of the neighbour grid (side >= 2 h_max, in
+// Morton order after the library's sort) and a node of level l groups the
+// cells that share the top 3 l bits of their Morton code.
+//
+//   build     leaves from the occupied-cell list; each upper level by a flag
+//             per run of equal parent codes (code >> 3) and an exclusive scan
+//   moments   leaves from their particles (mass, centre of mass c, traceless
+//             quadrupole Q_ij = sum m (3 d_i d_j - |d|^2 delta_ij), d = x - c,
+//             two passes); parents from their children by the parallel-axis
+//             rule Q = sum (Q_k + M_k (3 e e^T - |e|^2 I)), e = c_k - c
+//   walk      one thread per particle, depth first from the root with the
+//             children in Morton order (an explicit stack): a node whose box
+//             does not contain the particle and whose longest side s satisfies
+//             s < theta |x - c| adds the softened monopole and the quadrupole
+//             term; an opened leaf adds its particles by the direct softened
+//             formula; other nodes push their children.
+// Everything is FP64, and the walk visits nodes in the same order as the
+// oracle's recursion.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "sph_device.cuh"
+#include "sph_internal.cuh"
+#include "sph_scan.cuh"
+
+namespace sph {
+namespace grav {
+
+struct Node {
+  double box_lo[3], box_hi[3];
+  double size, M;
+  double c[3];
+  double Q[6];      // xx xy xz yy yz zz
+  int32_t first;    // first child (node index), -1 for a leaf
+  int32_t nchild;
+  int32_t p0, np;   // particles [p0, p0 + np) of the sorted order
+};
+
+constexpr int kStack = 80;  // >= 7 * 8 + 8 pending nodes for up to 8 Morton bits
+
+__device__ __forceinline__ uint32_t compact3(uint32_t v) {
+  uint32_t r = 0;
+  for (int i = 0; i < 10; ++i) r |= ((v >> (3 * i)) & 1u) << i;
+  return r;
+}
+
+// Box and longest side of the node with Morton prefix `code` at level `l`.
+__device__ __forceinline__ void node_box(const Grid& g, uint32_t code, int l, Node& nd) {
+  const int span = 1 << (g.bits - l);
+  const uint32_t c3[3] = {compact3(code), compact3(code >> 1), compact3(code >> 2)};
+  double size = 0.0;
+  for (int ax = 0; ax < 3; ++ax) {
+    const int c0 = (int)c3[ax] * span;
+    int c1 = c0 + span - 1;
+    if (c1 > g.nc[ax] - 1) c1 = g.nc[ax] - 1;
+    nd.box_lo[ax] = g.lo[ax] + c0 * g.cs[ax];
+    nd.box_hi[ax] = g.lo[ax] + (c1 + 1) * g.cs[ax];
+    const double ext = nd.box_hi[ax] - nd.box_lo[ax];
+    size = ext > size ? ext : size;
+  }
+  nd.size = size;
+}
+
+__global__ void k_leaves(const Grid* gp, const uint32_t* occ, const uint32_t* tbl_start,
+                         const uint32_t* tbl_count, int64_t n_occ, uint32_t* code, Node* nodes,
+                         StateView s) {
+  const Grid g = *gp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_occ;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t cc = occ[i];
+    code[i] = cc;
+    Node nd;
+    nd.first = -1;
+    nd.nchild = 0;
+    nd.p0 = (int32_t)tbl_start[cc];
+    nd.np = (int32_t)tbl_count[cc];
+    node_box(g, cc, g.bits, nd);
+    double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int32_t b = nd.p0; b < nd.p0 + nd.np; ++b) {
+      M += s.m[b];
+      sx += s.m[b] * s.x[b];
+      sy += s.m[b] * s.y[b];
+      sz += s.m[b] * s.z[b];
+    }
+    nd.M = M;
+    nd.c[0] = sx / M;
+    nd.c[1] = sy / M;
+    nd.c[2] = sz / M;
+    double Q[6] = {0, 0, 0, 0, 0, 0};
+    for (int32_t b = nd.p0; b < nd.p0 + nd.np; ++b) {
+      const double dx = s.x[b] - nd.c[0], dy = s.y[b] - nd.c[1], dz = s.z[b] - nd.c[2];
+      const double d2 = (dx * dx + dy * dy) + dz * dz;
+      const double mb = s.m[b];
+      Q[0] += mb * (3 * dx * dx - d2);
+      Q[1] += mb * (3 * dx * dy);
+      Q[2] += mb * (3 * dx * dz);
+      Q[3] += mb * (3 * dy * dy - d2);
+      Q[4] += mb * (3 * dy * dz);
+      Q[5] += mb * (3 * dz * dz - d2);
+    }
+    for (int q = 0; q < 6; ++q) nd.Q[q] = Q[q];
+    nodes[i] = nd;
+  }
+}
+
+__global__ void k_run_flags(const uint32_t* code, int64_t m, int32_t* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = (i == 0 || (code[i] >> 3) != (code[i - 1] >> 3)) ? 1 : 0;
+}
+
+// Parents of the m children at nodes[coff ..): code, first child, first particle.
+__global__ void k_parents(const uint32_t* code, const int32_t* flag, const int64_t* idx, int64_t m,
+                          int64_t coff, int64_t poff, uint32_t* pcode, Node* nodes) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (!flag[i]) continue;
+    const int64_t j = idx[i];
+    pcode[j] = code[i] >> 3;
+    nodes[poff + j].first = (int32_t)(coff + i);
+    nodes[poff + j].p0 = nodes[coff + i].p0;
+  }
+}
+
+// Child counts, particle counts, boxes and moments (parallel-axis rule).
+__global__ void k_parent_moments(const Grid* gp, const uint32_t* pcode, int64_t npar, int64_t m,
+                                 int64_t coff, int64_t poff, int level, Node* nodes) {
+  const Grid g = *gp;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < npar;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    Node nd = nodes[poff + j];
+    const int64_t f = nd.first - coff;
+    const int64_t next = j + 1 < npar ? nodes[poff + j + 1].first - coff : m;
+    nd.nchild = (int32_t)(next - f);
+    const Node& last = nodes[coff + next - 1];
+    nd.np = last.p0 + last.np - nd.p0;
+    node_box(g, pcode[j], level, nd);
+    double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int64_t k = coff + f; k < coff + next; ++k) {
+      const Node& ch = nodes[k];
+      M += ch.M;
+      sx += ch.M * ch.c[0];
+      sy += ch.M * ch.c[1];
+      sz += ch.M * ch.c[2];
+    }
+    nd.M = M;
+    nd.c[0] = sx / M;
+    nd.c[1] = sy / M;
+    nd.c[2] = sz / M;
+    double Q[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t k = coff + f; k < coff + next; ++k) {
+      const Node& ch = nodes[k];
+      const double ex = ch.c[0] - nd.c[0], ey = ch.c[1] - nd.c[1], ez = ch.c[2] - nd.c[2];
+      const double e2 = (ex * ex + ey * ey) + ez * ez;
+      Q[0] += ch.Q[0] + ch.M * (3 * ex * ex - e2);
+      Q[1] += ch.Q[1] + ch.M * (3 * ex * ey);
+      Q[2] += ch.Q[2] + ch.M * (3 * ex * ez);
+      Q[3] += ch.Q[3] + ch.M * (3 * ey * ey - e2);
+      Q[4] += ch.Q[4] + ch.M * (3 * ey * ez);
+      Q[5] += ch.Q[5] + ch.M * (3 * ez * ez - e2);
+    }
+    for (int q = 0; q < 6; ++q) nd.Q[q] = Q[q];
+    nodes[poff + j] = nd;
+  }
+}
+
+__global__ void k_walk(const Node* nodes, int32_t root, StateView s, int64_t n, double G,
+                       double eps, double theta, double* gx, double* gy, double* gz,
+                       unsigned long long* stats, uint32_t* err) {
+  unsigned long long nodes_used = 0, pairs = 0;
+  const double eps2 = eps * eps;
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    const double p[3] = {s.x[a], s.y[a], s.z[a]};
+    double acc[3] = {0.0, 0.0, 0.0};
+    int32_t stack[kStack];
+    int sp = 0;
+    stack[sp++] = root;
+    while (sp > 0) {
+      const Node& nd = nodes[stack[--sp]];
+      bool inside = true;
+      for (int ax = 0; ax < 3; ++ax)
+        if (p[ax] < nd.box_lo[ax] || p[ax] > nd.box_hi[ax]) inside = false;
+      const double r[3] = {p[0] - nd.c[0], p[1] - nd.c[1], p[2] - nd.c[2]};
+      const double R2 = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
+      const double R = sqrt(R2);
+      if (!inside && nd.size < theta * R) {
+        const double s2 = R2 + eps2;
+        const double mono = G * nd.M / (s2 * sqrt(s2));
+        const double* Q = nd.Q;
+        const double Qr[3] = {Q[0] * r[0] + Q[1] * r[1] + Q[2] * r[2],
+                              Q[1] * r[0] + Q[3] * r[1] + Q[4] * r[2],
+                              Q[2] * r[0] + Q[4] * r[1] + Q[5] * r[2]};
+        const double rQr = r[0] * Qr[0] + r[1] * Qr[1] + r[2] * Qr[2];
+        const double R5 = R2 * R2 * R;
+        const double R7 = R5 * R2;
+        for (int i = 0; i < 3; ++i)
+          acc[i] += -mono * r[i] + G * Qr[i] / R5 - 2.5 * G * rQr * r[i] / R7;
+        ++nodes_used;
+      } else if (nd.first < 0) {
+        for (int32_t b = nd.p0; b < nd.p0 + nd.np; ++b) {
+          if (b == a) continue;
+          const double d[3] = {p[0] - s.x[b], p[1] - s.y[b], p[2] - s.z[b]};
+          const double r2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2] + eps2;
+          const double f = s.m[b] / (r2 * sqrt(r2));
+          for (int q = 0; q < 3; ++q) acc[q] -= G * f * d[q];
+          ++pairs;
+        }
+      } else {
+        if (sp + nd.nchild > kStack) {  // cannot happen for <= 8 Morton bits; kept as a guard
+          raise_flag(err, SPH_FLAG_CELL_OVERFLOW);
+          break;
+        }
+        for (int j = nd.nchild - 1; j >= 0; --j) stack[sp++] = nd.first + j;
+      }
+    }
+    gx[a] = acc[0];
+    gy[a] = acc[1];
+    gz[a] = acc[2];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    nodes_used += __shfl_xor_sync(0xffffffffu, nodes_used, o);
+    pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(stats, nodes_used);
+    atomicAdd(stats + 1, pairs);
+  }
+}
+
+inline int blocks_for(int64_t n, int sm, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  const int64_t cap = (int64_t)sm * 32;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace grav
+}  // namespace sph
+
+namespace {
+
+int gfail(sph_ctx* ctx, cudaError_t e, const char* what) { return sph::cuda_fail(ctx, e, what); }
+
+// Grow-only scratch of the gravity call.
+int grav_scratch(sph_ctx* ctx, size_t bytes) {
+  if (ctx->grav_bytes >= bytes) return SPH_OK;
+  if (ctx->grav_buf) cudaFree(ctx->grav_buf);
+  ctx->grav_buf = nullptr;
+  ctx->grav_bytes = 0;
+  cudaError_t e = cudaMalloc(&ctx->grav_buf, bytes);
+  if (e != cudaSuccess) return gfail(ctx, e, "sph_gravity scratch");
+  ctx->grav_bytes = bytes;
+  return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" int sph_gravity(sph_ctx* ctx, sph_state* state, double G, double eps, double theta,
+                           double* gx, double* gy, double* gz, int64_t* interactions,
+                           sph_stream_t stream) {
+  using sph::grav::Node;
+  if (!ctx) return SPH_ERR_INVALID_ARG;
+  if (!state || !gx || !gy || !gz)
+    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "NULL state or output");
+  const int64_t n = state->n;
+  if (n < 0 || n > ctx->n_max)
+    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "n = %lld outside [0, n_max]", (long long)n);
+  if (!(theta >= 0.0) || !(eps >= 0.0) || !(G == G))
+    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "theta and eps must be >= 0");
+  for (int k = 0; k < 3; ++k)
+    if (ctx->prm.periodic[k])
+      return sph::set_error(ctx, SPH_ERR_INVALID_ARG,
+                            "self-gravity needs open boundaries on every axis");
+  if (n == 0) {
+    if (interactions) interactions[0] = interactions[1] = 0;
+    return SPH_OK;
+  }
+  const double* req[] = {state->x, state->y, state->z, state->vx, state->vy, state->vz,
+                         state->vxh, state->vyh, state->vzh, state->h, state->m, state->u,
+                         state->du_prev};
+  for (const double* q : req)
+    if (!q) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "a state array is NULL");
+  if (!state->id) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "id is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  sph::StateView in;
+  in.x = state->x;
+  in.y = state->y;
+  in.z = state->z;
+  in.vx = state->vx;
+  in.vy = state->vy;
+  in.vz = state->vz;
+  in.vxh = state->vxh;
+  in.vyh = state->vyh;
+  in.vzh = state->vzh;
+  in.h = state->h;
+  in.m = state->m;
+  in.u = state->u;
+  in.du_prev = state->du_prev;
+  in.id = state->id;
+  // the library's grid and Morton sort (the state is reordered in place)
+  sph::launch_grid(ctx, in, n, st);
+  sph::launch_sort_gather(ctx, in, n, st);
+  sph::launch_copy_state(in, ctx->s, n, st, ctx);
+  ctx->have_lists = 0;
+  ctx->have_density = ctx->have_iad = 0;
+  sph::Grid g;
+  cudaError_t e = cudaMemcpyAsync(&g, ctx->grid, sizeof(g), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return gfail(ctx, e, "sph_gravity grid");
+  const int64_t n_occ = g.n_occ;
+  const int bits = g.bits;
+  // scratch: nodes (worst case n_occ per level), two code arrays, flags, scan
+  const int64_t cap = n_occ * (bits + 1) + 1;
+  const int64_t nparts = (n_occ + sph::scan::kScanItems - 1) / sph::scan::kScanItems + 1;
+  const size_t off_code0 = sizeof(Node) * (size_t)cap;
+  const size_t off_code1 = off_code0 + sizeof(uint32_t) * (size_t)n_occ;
+  const size_t off_flag = off_code1 + sizeof(uint32_t) * (size_t)n_occ;
+  const size_t off_idx = (off_flag + sizeof(int32_t) * (size_t)n_occ + 15) & ~(size_t)15;
+  const size_t off_part = off_idx + sizeof(int64_t) * (size_t)(n_occ + 1);
+  const size_t off_stats = off_part + sizeof(int64_t) * (size_t)nparts;
+  const size_t bytes = off_stats + 2 * sizeof(unsigned long long);
+  int rc = grav_scratch(ctx, bytes);
+  if (rc != SPH_OK) return rc;
+  char* base = (char*)ctx->grav_buf;
+  Node* nodes = (Node*)base;
+  uint32_t* code_a = (uint32_t*)(base + off_code0);
+  uint32_t* code_b = (uint32_t*)(base + off_code1);
+  int32_t* flag = (int32_t*)(base + off_flag);
+  int64_t* idx = (int64_t*)(base + off_idx);
+  int64_t* part = (int64_t*)(base + off_part);
+  unsigned long long* stats = (unsigned long long*)(base + off_stats);
+  e = cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return gfail(ctx, e, "sph_gravity");
+  const int sm = ctx->sm_count;
+  sph::grav::k_leaves<<<sph::grav::blocks_for(n_occ, sm, 128), 128, 0, st>>>(
+      ctx->grid, ctx->occ, ctx->tbl_start, ctx->tbl_count, n_occ, code_a, nodes, in);
+  ctx->launches += 1;
+  int64_t coff = 0, m = n_occ, noff = n_occ;
+  for (int l = bits - 1; l >= 0; --l) {
+    sph::grav::k_run_flags<<<sph::grav::blocks_for(m, sm, 256), 256, 0, st>>>(code_a, m, flag);
+    sph::scan::exclusive_scan(flag, m, part, idx, st);
+    int64_t npar = 0;
+    e = cudaMemcpyAsync(&npar, idx + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return gfail(ctx, e, "sph_gravity tree level");
+    sph::grav::k_parents<<<sph::grav::blocks_for(m, sm, 256), 256, 0, st>>>(
+        code_a, flag, idx, m, coff, noff, code_b, nodes);
+    sph::grav::k_parent_moments<<<sph::grav::blocks_for(npar, sm, 128), 128, 0, st>>>(
+        ctx->grid, code_b, npar, m, coff, noff, l, nodes);
+    ctx->launches += 6;
+    uint32_t* t = code_a;
+    code_a = code_b;
+    code_b = t;
+    coff = noff;
+    noff += npar;
+    m = npar;
+  }
+  const int32_t root = (int32_t)(noff - 1);
+  sph::grav::k_walk<<<sph::grav::blocks_for(n, sm, 128), 128, 0, st>>>(
+      nodes, root, in, n, G, eps, theta, gx, gy, gz, stats, ctx->err);
+  ctx->launches += 1;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return gfail(ctx, e, "sph_gravity launch");
+  if (interactions) {
+    unsigned long long h[2];
+    e = cudaMemcpyAsync(h, stats, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return gfail(ctx, e, "sph_gravity stats");
+    interactions[0] = (int64_t)h[0];
+    interactions[1] = (int64_t)h[1];
+  }
+  return SPH_OK;
+}

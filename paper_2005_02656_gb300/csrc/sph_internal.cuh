@@ -131,6 +131,10 @@ struct sph_ctx {
   double prof_ms[SPH_NSTAGE];
   int64_t prof_steps;
 
+  // self-gravity tree scratch (sph_gravity.cu), grown on demand
+  void* grav_buf;
+  size_t grav_bytes;
+
   // host-step mirrors
   double* hm_buf;       // device mirror storage for sph_step_host
   int64_t* hm_id;

@@ -136,6 +136,17 @@ class SphSim:
             self._call(self.lib.sph_step, C.byref(self._st), C.c_void_p(self.dt.data_ptr()),
                        _stream_ptr())
 
+    def gravity(self, G: float = 1.0, eps: float = 0.0, theta: float = 0.5):
+        """Self-gravity by the multipole tree (sph_gravity); sorts the state.
+        Returns (g (n, 3) device tensor in the current order, [node, particle]
+        interactions)."""
+        g = torch.empty(3, self.n, dtype=torch.float64, device=self.device)
+        cnt = np.zeros(2, dtype=np.int64)
+        self._call(self.lib.sph_gravity, C.byref(self._st), float(G), float(eps), float(theta),
+                   C.c_void_p(g[0].data_ptr()), C.c_void_p(g[1].data_ptr()),
+                   C.c_void_p(g[2].data_ptr()), cnt.ctypes.data_as(C.c_void_p), _stream_ptr())
+        return g.t(), cnt
+
     def get_neighbors(self):
         """(counts[n] int32, ids[n, max_nb] int64) in id space, rows by current position."""
         mb = self.params.max_nb

@@ -25,6 +25,10 @@ Workloads (the paper's setups, section 4.6 and the configurations measured):
                        gamma = 5/3 (u = 3.75 / rho).
   * ``ensemble``       boxes of the jittered-box recipe, side counts drawn
                        log-uniformly from [8, 48], alpha uniform in [0.5, 1.5].
+  * ``uniform_sphere`` the self-gravity workload: the lattice points of
+                       [-1, 1]^3 inside the unit sphere, jittered by U(-0.1,
+                       0.1) spacing, total mass 1, at rest, u = 1, open
+                       boundaries.
 """
 from __future__ import annotations
 
@@ -170,3 +174,23 @@ def ensemble(n_boxes: int = 256, lo: int = 8, hi: int = 48, seed_index: int = 4)
 
 def to_numpy_state(s: dict) -> dict:
     return {k: (np.array(v, copy=True) if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+
+
+def uniform_sphere(side: int = 124, seed_index: int = 5, jitter: float = 0.1, ng: int = NG_TARGET,
+                   shuffle=True):
+    """Uniform sphere of radius 1 and mass 1 from a jittered cubic lattice of
+    spacing 2/side (side = 124 gives about 10^6 particles), at rest, u = 1,
+    all axes open."""
+    rng = np.random.default_rng(SEED_BASE + seed_index)
+    dx = 2.0 / side
+    X, Y, Z = _lattice(side, side, side, (-1.0, -1.0, -1.0), dx)
+    X = X + rng.uniform(-jitter, jitter, X.shape) * dx
+    Y = Y + rng.uniform(-jitter, jitter, Y.shape) * dx
+    Z = Z + rng.uniform(-jitter, jitter, Z.shape) * dx
+    inside = X * X + Y * Y + Z * Z < 1.0
+    X, Y, Z = X[inside], Y[inside], Z[inside]
+    n = X.shape[0]
+    zeros = np.zeros(n)
+    return _finish(X, Y, Z, zeros, zeros.copy(), zeros.copy(), np.full(n, h_for_neighbors(dx, ng)),
+                   np.full(n, 1.0 / n), np.ones(n), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), (0, 0, 0),
+                   rng=rng, shuffle=shuffle)

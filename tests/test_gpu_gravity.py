@@ -1,0 +1,84 @@
+"""Self-gravity on the GPU (sph_gravity): the multipole tree on the
+neighbour grid's cells against the oracle's tree (same reading, same
+acceptance decisions, so the sums agree to FP64 rounding and the interaction
+counts exactly) and against the exact direct sum (the approximation error of
+the quadrupole expansion at theta = 0.5)."""
+import numpy as np
+import pytest
+
+import oracle
+import sph_inputs
+
+pytestmark = pytest.mark.gpu
+
+EPS = 1e-3
+
+
+def _gpu(s, theta, G=1.0, eps=EPS):
+    from paper_2005_02656_gb300 import Params, SphSim
+    sim = SphSim(s, Params(box_lo=s["lo"], box_hi=s["hi"], periodic=s["periodic"]))
+    g, counts = sim.gravity(G, eps, theta)
+    g = g.cpu().numpy()
+    ids = sim.t["id"].cpu().numpy()
+    assert sim.error_word() == 0
+    sim.close()
+    out = np.empty_like(g)
+    out[ids] = g                  # back to id order
+    return out, counts
+
+
+def _by_id(s):
+    order = np.argsort(s["id"])
+    return {k: (v[order] if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.5, 0.8])
+def test_tree_matches_oracle_tree(theta):
+    s = sph_inputs.uniform_sphere(22, seed_index=81)
+    g, counts = _gpu(s, theta)
+    # the oracle sees the arrays in the order the GPU received them
+    rc, ref, st = oracle.gravity_tree(s, eps=EPS, theta=theta)
+    assert rc == 0
+    ref_by_id = np.empty_like(ref)
+    ref_by_id[s["id"]] = ref
+    scale = np.abs(ref_by_id).max()
+    assert np.abs(g - ref_by_id).max() <= 1e-12 * scale
+    np.testing.assert_array_equal(counts, st)
+
+
+def test_tree_error_against_direct_sum():
+    s = sph_inputs.uniform_sphere(22, seed_index=82)
+    g, _ = _gpu(s, 0.5)
+    d = oracle.gravity_direct(_by_id(s), eps=EPS)
+    e = np.linalg.norm(g - d, axis=1) / np.linalg.norm(d, axis=1)
+    assert np.sqrt((e ** 2).mean()) < 1e-3 and e.max() < 1e-2
+
+
+def test_full_size_sampled():
+    """About 10^6 particles: sampled targets against the oracle's tree (exact
+    agreement) and the direct sum (approximation error)."""
+    s = sph_inputs.uniform_sphere(124, seed_index=83)
+    n = s["x"].shape[0]
+    assert n > 990_000
+    g, counts = _gpu(s, 0.5)
+    rng = np.random.default_rng(4)
+    sample_ids = rng.choice(n, 300, replace=False)
+    pos = np.empty(n, dtype=np.int64)
+    pos[s["id"]] = np.arange(n)             # array position of each id
+    rc, ref, st = oracle.gravity_tree(s, eps=EPS, theta=0.5, targets=pos[sample_ids])
+    assert rc == 0
+    assert np.abs(g[sample_ids] - ref).max() <= 1e-12 * np.abs(ref).max()
+    d = oracle.gravity_direct(s, eps=EPS, targets=pos[sample_ids])
+    e = np.linalg.norm(g[sample_ids] - d, axis=1) / np.linalg.norm(d, axis=1)
+    assert np.sqrt((e ** 2).mean()) < 1e-3
+    assert counts[0] > 0 and counts[1] > 0
+
+
+def test_periodic_box_is_rejected():
+    from paper_2005_02656_gb300 import SphSim, _lib
+    s = sph_inputs.jittered_box(8, seed_index=84)
+    sim = SphSim(s)
+    with pytest.raises(_lib.SphError) as e:
+        sim.gravity()
+    assert e.value.code == _lib.SPH_ERR_INVALID_ARG
+    sim.close()
