@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--ensemble-steps", type=int, default=50)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-table", action="store_true", help="skip the lookup-table kernel leg")
+    ap.add_argument("--no-gravity", action="store_true", help="skip the self-gravity leg")
     ap.add_argument("--adjoint-side", type=int, default=100)
     return ap.parse_args()
 
@@ -276,17 +277,23 @@ def run_gpu(args, world, rank, local):
     if not args.no_adjoint:
         adjoint = run_adjoint(args, dev, windows)
 
+    gravity = None
+    if not args.no_gravity:
+        gravity = run_gravity(args, dev, windows)
+
     clocks.stop()
     if ens is not None:
         ens["clocks"] = clocks.summary(*windows["ensemble"])
     if adjoint is not None:
         adjoint["clocks"] = clocks.summary(*windows["adjoint"])
+    if gravity is not None:
+        gravity["clocks"] = clocks.summary(*windows["gravity"])
     for key, r in (("fp32_mixed", r32), ("fp64", r64)):
         if r is not None:
             r["clocks"] = clocks.summary(*windows[key])
     ms32 = max_over_ranks(r32["ms"])
     res = {"n": n, "r32": r32, "r64": r64, "ms32": ms32, "e2e": e2e, "ensemble": ens,
-           "adjoint": adjoint, "table": tab}
+           "adjoint": adjoint, "table": tab, "gravity": gravity}
     if r64 is not None:
         res["ms64"] = max_over_ranks(r64["ms"])
     if dist is not None:
@@ -390,6 +397,54 @@ def run_adjoint(args, dev, windows, steps=20, every=5):
             "gradient_finite": finite, "dtype": "f64"}
 
 
+# FP64 operations per interaction of the gravity formulas (add, sub, mul,
+# division and square root count 1 each): an accepted node (softened monopole
+# + quadrupole) and a particle of an opened leaf.
+GRAV_FLOPS = {"node": 65, "particle": 21}
+
+
+def run_gravity(args, dev, windows, calls=3, theta=0.5):
+    """Self-gravity of the about-10^6-particle uniform sphere (open
+    boundaries) by the multipole tree: sort, tree build, moments and walk per
+    call, FP64, timed with CUDA events after one untimed call."""
+    import numpy as np
+    import torch
+
+    import sph_inputs
+    from paper_2005_02656_gb300 import Params, SphSim
+    s = sph_inputs.uniform_sphere(124, seed_index=83)
+    n = s["x"].shape[0]
+    sim = SphSim(s, Params(box_lo=s["lo"], box_hi=s["hi"], periodic=s["periodic"]), device=dev)
+    sim.gravity(1.0, 1e-3, theta)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    tw0 = time.time()
+    ev[0].record()
+    counts = np.zeros(2)
+    for _ in range(calls):
+        _, c = sim.gravity(1.0, 1e-3, theta)
+        counts += c
+    ev[1].record()
+    torch.cuda.synchronize()
+    windows["gravity"] = (tw0, time.time())
+    ms = ev[0].elapsed_time(ev[1]) / calls
+    flags = sim.error_word()
+    sim.close()
+    node, part = counts / calls
+    flops = GRAV_FLOPS["node"] * node + GRAV_FLOPS["particle"] * part
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"metric": "particles/s of one self-gravity evaluation (tree build + walk)",
+            "value": n / (ms * 1e-3), "unit": "particles/s", "workload": f"uniform_sphere_{n}",
+            "n_particles": n, "theta": theta, "eps": 1e-3, "ms_per_call": ms,
+            "node_interactions": node, "particle_interactions": part,
+            "interactions_per_s": (node + part) / (ms * 1e-3), "error_flags": flags,
+            "dtype": "f64",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "peak_source": "fp64 pipe, derived: 1/64 of 152 SMs x 128 lanes x 2 x 2070 MHz",
+                         "flops_per_call": flops}}
+
+
 def roofline(r, n, precision):
     """Dominant kernel's achieved vs peak under the flop model above."""
     st = r["stages"]
@@ -483,6 +538,8 @@ def main():
         line["ensemble"] = res["ensemble"]
     if res.get("adjoint") is not None:
         line["adjoint"] = res["adjoint"]
+    if res.get("gravity") is not None:
+        line["gravity"] = res["gravity"]
     if res.get("table") is not None:
         exact_ms = {"fp32_mixed": ms, "fp64": res.get("ms64")}
         line["kernel_table"] = {

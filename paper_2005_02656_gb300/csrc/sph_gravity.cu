@@ -10,12 +10,13 @@
 //             quadrupole Q_ij = sum m (3 d_i d_j - |d|^2 delta_ij), d = x - c,
 //             two passes); parents from their children by the parallel-axis
 //             rule Q = sum (Q_k + M_k (3 e e^T - |e|^2 I)), e = c_k - c
-//   walk      one thread per particle, depth first from the root with the
-//             children in Morton order (an explicit stack): a node whose box
-//             does not contain the particle and whose longest side s satisfies
-//             s < theta |x - c| adds the softened monopole and the quadrupole
-//             term; an opened leaf adds its particles by the direct softened
-//             formula; other nodes push their children.
+//   walk      per particle, depth first from the root with the children in
+//             Morton order: a node whose box does not contain the particle and
+//             whose longest side s satisfies s < theta |x - c| adds the
+//             softened monopole and the quadrupole term; an opened leaf adds
+//             its particles by the direct softened formula; other nodes are
+//             opened.  A warp walks its 32 particles together on one stack of
+//             (node, lane mask) entries (k_walk).
 // Everything is FP64, and the walk visits nodes in the same order as the
 // oracle's recursion.
 #include <cuda_runtime.h>
@@ -168,65 +169,116 @@ __global__ void k_parent_moments(const Grid* gp, const uint32_t* pcode, int64_t 
   }
 }
 
-__global__ void k_walk(const Node* nodes, int32_t root, StateView s, int64_t n, double G,
-                       double eps, double theta, double* gx, double* gy, double* gz,
-                       unsigned long long* stats, uint32_t* err) {
+// The walk of a warp: 32 consecutive sorted particles (one lane each) share
+// one depth-first stack whose entries carry the mask of lanes that reached
+// the node through nodes they opened.  Every lane still takes its own
+// decisions and sees its nodes in its own depth-first order (so the result
+// equals a walk per particle), but node and particle loads are common to the
+// warp and an opened leaf is summed by all its lanes in lockstep.
+constexpr int kWalkWarps = 4;
+
+__global__ void __launch_bounds__(32 * kWalkWarps) k_walk(const Node* nodes, int32_t root,
+                                                          StateView s, int64_t n, double G,
+                                                          double eps, double theta, double* gx,
+                                                          double* gy, double* gz,
+                                                          unsigned long long* stats,
+                                                          uint32_t* err) {
+  __shared__ int32_t st_node[kWalkWarps][kStack];
+  __shared__ uint32_t st_mask[kWalkWarps][kStack];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned long long nodes_used = 0, pairs = 0;
   const double eps2 = eps * eps;
-  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
-       a += (int64_t)gridDim.x * blockDim.x) {
-    const double p[3] = {s.x[a], s.y[a], s.z[a]};
+  const int64_t tiles = (n + 31) / 32;
+  for (int64_t tile = blockIdx.x * (int64_t)kWalkWarps + w; tile < tiles;
+       tile += (int64_t)gridDim.x * kWalkWarps) {
+    const int64_t a = tile * 32 + lane;
+    const bool valid = a < n;
+    const double p[3] = {valid ? s.x[a] : 0.0, valid ? s.y[a] : 0.0, valid ? s.z[a] : 0.0};
     double acc[3] = {0.0, 0.0, 0.0};
-    int32_t stack[kStack];
     int sp = 0;
-    stack[sp++] = root;
+    const uint32_t all = __ballot_sync(0xffffffffu, valid);
+    if (lane == 0) {
+      st_node[w][0] = root;
+      st_mask[w][0] = all;
+    }
+    sp = 1;
+    __syncwarp();
+    bool overflow = false;
     while (sp > 0) {
-      const Node& nd = nodes[stack[--sp]];
-      bool inside = true;
-      for (int ax = 0; ax < 3; ++ax)
-        if (p[ax] < nd.box_lo[ax] || p[ax] > nd.box_hi[ax]) inside = false;
-      const double r[3] = {p[0] - nd.c[0], p[1] - nd.c[1], p[2] - nd.c[2]};
-      const double R2 = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
-      const double R = sqrt(R2);
-      if (!inside && nd.size < theta * R) {
-        const double s2 = R2 + eps2;
-        const double mono = G * nd.M / (s2 * sqrt(s2));
-        const double* Q = nd.Q;
-        const double Qr[3] = {Q[0] * r[0] + Q[1] * r[1] + Q[2] * r[2],
-                              Q[1] * r[0] + Q[3] * r[1] + Q[4] * r[2],
-                              Q[2] * r[0] + Q[4] * r[1] + Q[5] * r[2]};
-        const double rQr = r[0] * Qr[0] + r[1] * Qr[1] + r[2] * Qr[2];
-        const double R5 = R2 * R2 * R;
-        const double R7 = R5 * R2;
-        for (int i = 0; i < 3; ++i)
-          acc[i] += -mono * r[i] + G * Qr[i] / R5 - 2.5 * G * rQr * r[i] / R7;
-        ++nodes_used;
-      } else if (nd.first < 0) {
+      --sp;
+      const int32_t k = st_node[w][sp];
+      const uint32_t mask = st_mask[w][sp];
+      __syncwarp();
+      const Node& nd = nodes[k];
+      const bool live = (mask >> lane) & 1u;
+      bool open = false;
+      if (live) {
+        bool inside = true;
+        for (int ax = 0; ax < 3; ++ax)
+          if (p[ax] < nd.box_lo[ax] || p[ax] > nd.box_hi[ax]) inside = false;
+        const double r[3] = {p[0] - nd.c[0], p[1] - nd.c[1], p[2] - nd.c[2]};
+        const double R2 = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
+        const double R = sqrt(R2);
+        if (!inside && nd.size < theta * R) {
+          // one reciprocal and one reciprocal square root per node: the FP64
+          // pipe runs divisions and square roots as multi-instruction sequences
+          const double inv_s = rsqrt(R2 + eps2);
+          const double mono = G * nd.M * (inv_s * inv_s * inv_s);
+          const double inv_R = 1.0 / R;
+          const double inv_R2 = inv_R * inv_R;
+          const double g5 = G * (inv_R2 * inv_R2 * inv_R);
+          const double* Q = nd.Q;
+          const double Qr[3] = {Q[0] * r[0] + Q[1] * r[1] + Q[2] * r[2],
+                                Q[1] * r[0] + Q[3] * r[1] + Q[4] * r[2],
+                                Q[2] * r[0] + Q[4] * r[1] + Q[5] * r[2]};
+          const double rQr = r[0] * Qr[0] + r[1] * Qr[1] + r[2] * Qr[2];
+          const double g7 = 2.5 * g5 * rQr * inv_R2;
+          for (int i = 0; i < 3; ++i) acc[i] += -mono * r[i] + g5 * Qr[i] - g7 * r[i];
+          ++nodes_used;
+        } else {
+          open = true;
+        }
+      }
+      const uint32_t omask = __ballot_sync(0xffffffffu, open);
+      if (omask == 0) continue;
+      if (nd.first < 0) {
+        // an opened leaf: its particles, in order, for the lanes that opened it
         for (int32_t b = nd.p0; b < nd.p0 + nd.np; ++b) {
-          if (b == a) continue;
-          const double d[3] = {p[0] - s.x[b], p[1] - s.y[b], p[2] - s.z[b]};
-          const double r2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2] + eps2;
-          const double f = s.m[b] / (r2 * sqrt(r2));
-          for (int q = 0; q < 3; ++q) acc[q] -= G * f * d[q];
-          ++pairs;
+          const double xb = s.x[b], yb = s.y[b], zb = s.z[b], mb = s.m[b];
+          if (open && b != a) {
+            const double d[3] = {p[0] - xb, p[1] - yb, p[2] - zb};
+            const double inv = rsqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2] + eps2);
+            const double f = G * mb * (inv * inv * inv);
+            for (int q = 0; q < 3; ++q) acc[q] -= f * d[q];
+            ++pairs;
+          }
         }
       } else {
         if (sp + nd.nchild > kStack) {  // cannot happen for <= 8 Morton bits; kept as a guard
-          raise_flag(err, SPH_FLAG_CELL_OVERFLOW);
+          overflow = true;
           break;
         }
-        for (int j = nd.nchild - 1; j >= 0; --j) stack[sp++] = nd.first + j;
+        if (lane == 0)
+          for (int j = nd.nchild - 1, q = sp; j >= 0; --j, ++q) {
+            st_node[w][q] = nd.first + j;
+            st_mask[w][q] = omask;
+          }
+        sp += nd.nchild;
+        __syncwarp();
       }
     }
-    gx[a] = acc[0];
-    gy[a] = acc[1];
-    gz[a] = acc[2];
+    if (overflow && lane == 0) raise_flag(err, SPH_FLAG_CELL_OVERFLOW);
+    if (valid) {
+      gx[a] = acc[0];
+      gy[a] = acc[1];
+      gz[a] = acc[2];
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     nodes_used += __shfl_xor_sync(0xffffffffu, nodes_used, o);
     pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
   }
-  if ((threadIdx.x & 31) == 0) {
+  if (lane == 0) {
     atomicAdd(stats, nodes_used);
     atomicAdd(stats + 1, pairs);
   }
@@ -362,8 +414,11 @@ extern "C" int sph_gravity(sph_ctx* ctx, sph_state* state, double G, double eps,
     m = npar;
   }
   const int32_t root = (int32_t)(noff - 1);
-  sph::grav::k_walk<<<sph::grav::blocks_for(n, sm, 128), 128, 0, st>>>(
-      nodes, root, in, n, G, eps, theta, gx, gy, gz, stats, ctx->err);
+  const int64_t tiles = (n + 31) / 32;
+  int wb = (int)((tiles + sph::grav::kWalkWarps - 1) / sph::grav::kWalkWarps);
+  if (wb > sm * 256) wb = sm * 256;
+  sph::grav::k_walk<<<wb, 32 * sph::grav::kWalkWarps, 0, st>>>(nodes, root, in, n, G, eps, theta,
+                                                               gx, gy, gz, stats, ctx->err);
   ctx->launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return gfail(ctx, e, "sph_gravity launch");
