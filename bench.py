@@ -287,7 +287,8 @@ def run_gpu(args, world, rank, local):
     if adjoint is not None:
         adjoint["clocks"] = clocks.summary(*windows["adjoint"])
     if gravity is not None:
-        gravity["clocks"] = clocks.summary(*windows["gravity"])
+        for key, r in gravity.items():
+            r["clocks"] = clocks.summary(*windows["gravity_" + key])
     for key, r in (("fp32_mixed", r32), ("fp64", r64)):
         if r is not None:
             r["clocks"] = clocks.summary(*windows[key])
@@ -397,7 +398,7 @@ def run_adjoint(args, dev, windows, steps=20, every=5):
             "gradient_finite": finite, "dtype": "f64"}
 
 
-# FP64 operations per interaction of the gravity formulas (add, sub, mul,
+# Operations per interaction of the gravity formulas (add, sub, mul,
 # division and square root count 1 each): an accepted node (softened monopole
 # + quadrupole) and a particle of an opened leaf.
 GRAV_FLOPS = {"node": 65, "particle": 21}
@@ -405,8 +406,16 @@ GRAV_FLOPS = {"node": 65, "particle": 21}
 
 def run_gravity(args, dev, windows, calls=3, theta=0.5):
     """Self-gravity of the about-10^6-particle uniform sphere (open
-    boundaries) by the multipole tree: sort, tree build, moments and walk per
-    call, FP64, timed with CUDA events after one untimed call."""
+    boundaries) by the multipole tree, in FP64 and in FP32-mixed: sort, tree
+    build, moments and walk per call, timed with CUDA events after one untimed
+    call."""
+    out = {}
+    for precision in ("fp64", "fp32_mixed"):
+        out[precision] = _gravity_one(dev, windows, calls, theta, precision)
+    return out
+
+
+def _gravity_one(dev, windows, calls, theta, precision):
     import numpy as np
     import torch
 
@@ -414,7 +423,8 @@ def run_gravity(args, dev, windows, calls=3, theta=0.5):
     from paper_2005_02656_gb300 import Params, SphSim
     s = sph_inputs.uniform_sphere(124, seed_index=83)
     n = s["x"].shape[0]
-    sim = SphSim(s, Params(box_lo=s["lo"], box_hi=s["hi"], periodic=s["periodic"]), device=dev)
+    sim = SphSim(s, Params(box_lo=s["lo"], box_hi=s["hi"], periodic=s["periodic"],
+                           precision=precision), device=dev)
     sim.gravity(1.0, 1e-3, theta)
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -426,22 +436,26 @@ def run_gravity(args, dev, windows, calls=3, theta=0.5):
         counts += c
     ev[1].record()
     torch.cuda.synchronize()
-    windows["gravity"] = (tw0, time.time())
+    windows["gravity_" + precision] = (tw0, time.time())
     ms = ev[0].elapsed_time(ev[1]) / calls
     flags = sim.error_word()
     sim.close()
     node, part = counts / calls
     flops = GRAV_FLOPS["node"] * node + GRAV_FLOPS["particle"] * part
     achieved = flops / (ms * 1e-3) / 1e12
+    if precision == "fp64":
+        peak, pk = FP64_PEAK_TFLOPS, "fp64 pipe, derived: 1/64 of 152 SMs x 128 lanes x 2 x 2070 MHz"
+    else:
+        peak, pk = FP32_PEAK_TFLOPS, "fp32 pipe, derived: 152 SMs x 128 lanes x 2 x 2070 MHz"
     return {"metric": "particles/s of one self-gravity evaluation (tree build + walk)",
+            "precision": precision,
             "value": n / (ms * 1e-3), "unit": "particles/s", "workload": f"uniform_sphere_{n}",
             "n_particles": n, "theta": theta, "eps": 1e-3, "ms_per_call": ms,
             "node_interactions": node, "particle_interactions": part,
             "interactions_per_s": (node + part) / (ms * 1e-3), "error_flags": flags,
-            "dtype": "f64",
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "peak_source": "fp64 pipe, derived: 1/64 of 152 SMs x 128 lanes x 2 x 2070 MHz",
+            "dtype": "f64" if precision == "fp64" else "f32+f64",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": pk,
                          "flops_per_call": flops}}
 
 

@@ -249,7 +249,15 @@ SPH_API int sph_diagnostics_noalloc(const sph_state* state, double* out, sph_str
  * 0).  Sorts the state in place like sph_find_neighbors (and invalidates the
  * lists); gx gy gz (DEVICE, n each) receive g in the new order.
  * interactions (HOST, optional, 2 values): node and particle interactions.
- * FP64 whatever params.precision.  Synchronises the stream. */
+ * Precision follows params.precision.  SPH_FP64: everything in FP64.
+ * SPH_FP32_MIXED: the node and particle terms are evaluated and summed in
+ * FP32 (node coordinates relative to the grid origin, particles relative to
+ * their leaf's centre of mass, the target's offset from a leaf formed in
+ * FP64); the opening decisions are exact (an FP32 test with a margin that
+ * covers its rounding, the FP64 test inside the margin), so both precisions
+ * make the same interactions.  Scratch: about 150 B per occupied cell and
+ * level, plus 16 B per particle in SPH_FP32_MIXED (grow-only, kept by ctx).
+ * Synchronises the stream. */
 SPH_API int sph_gravity(sph_ctx* ctx, sph_state* state, double G, double eps, double theta,
                         double* gx, double* gy, double* gz, int64_t* interactions,
                         sph_stream_t stream);

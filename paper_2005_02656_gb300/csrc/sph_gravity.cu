@@ -169,6 +169,19 @@ __global__ void k_parent_moments(const Grid* gp, const uint32_t* pcode, int64_t 
   }
 }
 
+// The opening decision: accept a node whose box does not contain p and whose
+// longest side is below theta |p - c| (r = p - c, R2, R returned).
+__device__ __forceinline__ bool accept64(const Node& nd, const double p[3], double theta,
+                                         double r[3], double& R2, double& R) {
+  bool inside = true;
+  for (int ax = 0; ax < 3; ++ax)
+    if (p[ax] < nd.box_lo[ax] || p[ax] > nd.box_hi[ax]) inside = false;
+  for (int ax = 0; ax < 3; ++ax) r[ax] = p[ax] - nd.c[ax];
+  R2 = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
+  R = sqrt(R2);
+  return !inside && nd.size < theta * R;
+}
+
 // The walk of a warp: 32 consecutive sorted particles (one lane each) share
 // one depth-first stack whose entries carry the mask of lanes that reached
 // the node through nodes they opened.  Every lane still takes its own
@@ -213,13 +226,8 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_walk(const Node* nodes, int
       const bool live = (mask >> lane) & 1u;
       bool open = false;
       if (live) {
-        bool inside = true;
-        for (int ax = 0; ax < 3; ++ax)
-          if (p[ax] < nd.box_lo[ax] || p[ax] > nd.box_hi[ax]) inside = false;
-        const double r[3] = {p[0] - nd.c[0], p[1] - nd.c[1], p[2] - nd.c[2]};
-        const double R2 = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
-        const double R = sqrt(R2);
-        if (!inside && nd.size < theta * R) {
+        double r[3], R2, R;
+        if (accept64(nd, p, theta, r, R2, R)) {
           // one reciprocal and one reciprocal square root per node: the FP64
           // pipe runs divisions and square roots as multi-instruction sequences
           const double inv_s = rsqrt(R2 + eps2);
@@ -264,6 +272,188 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_walk(const Node* nodes, int
             st_mask[w][q] = omask;
           }
         sp += nd.nchild;
+        __syncwarp();
+      }
+    }
+    if (overflow && lane == 0) raise_flag(err, SPH_FLAG_CELL_OVERFLOW);
+    if (valid) {
+      gx[a] = acc[0];
+      gy[a] = acc[1];
+      gz[a] = acc[2];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    nodes_used += __shfl_xor_sync(0xffffffffu, nodes_used, o);
+    pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+  }
+  if (lane == 0) {
+    atomicAdd(stats, nodes_used);
+    atomicAdd(stats + 1, pairs);
+  }
+}
+
+// ---- FP32-mixed walk ------------------------------------------------------
+// The node and particle terms in FP32, the opening decisions exact.  Node
+// coordinates are stored relative to the grid origin lo (so |value| <= L, the
+// grid's largest extent) and each particle relative to its leaf's centre of
+// mass; a lane forms p - c_leaf in FP64 once per opened leaf.
+
+struct NodeF {     // 96 B, read with uniform (broadcast) loads
+  float4 cm;       // c - lo, M
+  float4 q0;       // Q xx xy xz yy
+  float4 q1;       // Q yz zz, size, 0
+  float4 lo;       // box_lo - lo, 0
+  float4 hi;       // box_hi - lo, 0
+  int4 t;          // first, nchild, p0, np
+};
+
+__global__ void k_nodes32(const Node* nodes, int64_t nn, double lx, double ly, double lz,
+                          NodeF* out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nn;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const Node& nd = nodes[k];
+    NodeF f;
+    f.cm = make_float4((float)(nd.c[0] - lx), (float)(nd.c[1] - ly), (float)(nd.c[2] - lz),
+                       (float)nd.M);
+    f.q0 = make_float4((float)nd.Q[0], (float)nd.Q[1], (float)nd.Q[2], (float)nd.Q[3]);
+    f.q1 = make_float4((float)nd.Q[4], (float)nd.Q[5], (float)nd.size, 0.f);
+    f.lo = make_float4((float)(nd.box_lo[0] - lx), (float)(nd.box_lo[1] - ly),
+                       (float)(nd.box_lo[2] - lz), 0.f);
+    f.hi = make_float4((float)(nd.box_hi[0] - lx), (float)(nd.box_hi[1] - ly),
+                       (float)(nd.box_hi[2] - lz), 0.f);
+    f.t = make_int4(nd.first, nd.nchild, nd.p0, nd.np);
+    out[k] = f;
+  }
+}
+
+// Particle b of leaf k: (x_b - c_k, m_b) in FP32.
+__global__ void k_leaf_offsets(const Node* nodes, int64_t n_leaves, StateView s, float4* po) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_leaves;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const Node& nd = nodes[k];
+    for (int32_t b = nd.p0; b < nd.p0 + nd.np; ++b)
+      po[b] = make_float4((float)(s.x[b] - nd.c[0]), (float)(s.y[b] - nd.c[1]),
+                          (float)(s.z[b] - nd.c[2]), (float)s.m[b]);
+  }
+}
+
+// Same warp walk as k_walk.  The FP32 decision uses margins that cover the
+// rounding of the stored coordinates (each <= L 2^-24 absolute) and of the
+// FP32 distance (relative 2^-22 with rsqrtf): mb on a box face, aL + 2e-6 R
+// on the distance.  A lane inside a margin takes the FP64 decision of k_walk
+// (accept64 on the FP64 node), so every lane accepts and opens exactly the
+// nodes that the FP64 walk does.
+__global__ void __launch_bounds__(32 * kWalkWarps) k_walk32(const Node* nodes,
+                                                            const NodeF* nf, const float4* po,
+                                                            int32_t root, StateView s,
+                                                            int64_t n, double lx, double ly,
+                                                            double lz, double L, double G,
+                                                            double eps, double theta,
+                                                            double* gx, double* gy, double* gz,
+                                                            unsigned long long* stats,
+                                                            uint32_t* err) {
+  __shared__ int32_t st_node[kWalkWarps][kStack];
+  __shared__ uint32_t st_mask[kWalkWarps][kStack];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long nodes_used = 0, pairs = 0;
+  const float eps2 = (float)(eps * eps), Gf = (float)G, th = (float)theta;
+  const float mb = (float)(4.0 * L * 5.9604644775390625e-8);   // 4 L 2^-24
+  const float aL = (float)(8.0 * L * 5.9604644775390625e-8);   // 8 L 2^-24
+  const int64_t tiles = (n + 31) / 32;
+  for (int64_t tile = blockIdx.x * (int64_t)kWalkWarps + w; tile < tiles;
+       tile += (int64_t)gridDim.x * kWalkWarps) {
+    const int64_t a = tile * 32 + lane;
+    const bool valid = a < n;
+    const double p[3] = {valid ? s.x[a] : 0.0, valid ? s.y[a] : 0.0, valid ? s.z[a] : 0.0};
+    const float pf[3] = {(float)(p[0] - lx), (float)(p[1] - ly), (float)(p[2] - lz)};
+    float acc[3] = {0.f, 0.f, 0.f};
+    const uint32_t all = __ballot_sync(0xffffffffu, valid);
+    if (lane == 0) {
+      st_node[w][0] = root;
+      st_mask[w][0] = all;
+    }
+    int sp = 1;
+    __syncwarp();
+    bool overflow = false;
+    while (sp > 0) {
+      --sp;
+      const int32_t k = st_node[w][sp];
+      const uint32_t mask = st_mask[w][sp];
+      __syncwarp();
+      const NodeF* f = nf + k;
+      const float4 cm = __ldg(&f->cm);
+      const float4 q1 = __ldg(&f->q1);
+      const int4 t = __ldg(&f->t);
+      const bool live = (mask >> lane) & 1u;
+      bool open = false;
+      if (live) {
+        const float4 blo = __ldg(&f->lo), bhi = __ldg(&f->hi);
+        const float r[3] = {pf[0] - cm.x, pf[1] - cm.y, pf[2] - cm.z};
+        const float R2 = fmaf(r[2], r[2], fmaf(r[1], r[1], r[0] * r[0]));
+        const float inv_R = rsqrtf(R2);
+        const float Rf = R2 * inv_R;
+        const float size = q1.z;
+        // the box: certainly outside, certainly inside, or within mb of a face
+        const bool out_c = pf[0] < blo.x - mb || pf[0] > bhi.x + mb || pf[1] < blo.y - mb ||
+                           pf[1] > bhi.y + mb || pf[2] < blo.z - mb || pf[2] > bhi.z + mb;
+        const bool in_c = pf[0] >= blo.x + mb && pf[0] <= bhi.x - mb && pf[1] >= blo.y + mb &&
+                          pf[1] <= bhi.y - mb && pf[2] >= blo.z + mb && pf[2] <= bhi.z - mb;
+        const bool acc_c = size * (1.f + 1e-6f) < th * (Rf * (1.f - 2e-6f) - aL);
+        const bool rej_c = size * (1.f - 1e-6f) > th * (Rf * (1.f + 2e-6f) + aL);
+        bool accept;
+        if (in_c || rej_c) {
+          accept = false;
+        } else if (out_c && acc_c) {
+          accept = true;
+        } else {
+          double r64[3], R2_64, R64;
+          accept = accept64(nodes[k], p, theta, r64, R2_64, R64);
+        }
+        if (accept) {
+          const float4 q0 = __ldg(&f->q0);
+          const float inv_s = eps2 > 0.f ? rsqrtf(R2 + eps2) : inv_R;
+          const float mono = Gf * cm.w * (inv_s * inv_s * inv_s);
+          const float inv_R2 = inv_R * inv_R;
+          const float g5 = Gf * (inv_R2 * inv_R2 * inv_R);
+          const float Qr[3] = {q0.x * r[0] + q0.y * r[1] + q0.z * r[2],
+                               q0.y * r[0] + q0.w * r[1] + q1.x * r[2],
+                               q0.z * r[0] + q1.x * r[1] + q1.y * r[2]};
+          const float rQr = r[0] * Qr[0] + r[1] * Qr[1] + r[2] * Qr[2];
+          const float g7 = 2.5f * g5 * rQr * inv_R2;
+          for (int i = 0; i < 3; ++i) acc[i] += -mono * r[i] + g5 * Qr[i] - g7 * r[i];
+          ++nodes_used;
+        } else {
+          open = true;
+        }
+      }
+      const uint32_t omask = __ballot_sync(0xffffffffu, open);
+      if (omask == 0) continue;
+      if (t.x < 0) {
+        // an opened leaf: p - c_leaf once in FP64, then its particles in FP32
+        const Node& nd = nodes[k];
+        const float q[3] = {(float)(p[0] - nd.c[0]), (float)(p[1] - nd.c[1]),
+                            (float)(p[2] - nd.c[2])};
+        for (int32_t b = t.z; b < t.z + t.w; ++b) {
+          const float4 o = __ldg(po + b);
+          if (open && b != a) {
+            const float d[3] = {q[0] - o.x, q[1] - o.y, q[2] - o.z};
+            const float inv = rsqrtf(fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0])) + eps2);
+            const float fb = Gf * o.w * (inv * inv * inv);
+            for (int c = 0; c < 3; ++c) acc[c] -= fb * d[c];
+            ++pairs;
+          }
+        }
+      } else {
+        if (sp + t.y > kStack) {  // cannot happen for <= 8 Morton bits; kept as a guard
+          overflow = true;
+          break;
+        }
+        if (lane == 0)
+          for (int j = t.y - 1, q = sp; j >= 0; --j, ++q) {
+            st_node[w][q] = t.x + j;
+            st_mask[w][q] = omask;
+          }
+        sp += t.y;
         __syncwarp();
       }
     }
@@ -376,7 +566,10 @@ extern "C" int sph_gravity(sph_ctx* ctx, sph_state* state, double G, double eps,
   const size_t off_idx = (off_flag + sizeof(int32_t) * (size_t)n_occ + 15) & ~(size_t)15;
   const size_t off_part = off_idx + sizeof(int64_t) * (size_t)(n_occ + 1);
   const size_t off_stats = off_part + sizeof(int64_t) * (size_t)nparts;
-  const size_t bytes = off_stats + 2 * sizeof(unsigned long long);
+  const bool fp32 = ctx->prm.precision == SPH_FP32_MIXED;
+  const size_t off_nf = (off_stats + 2 * sizeof(unsigned long long) + 127) & ~(size_t)127;
+  const size_t off_po = off_nf + (fp32 ? sizeof(sph::grav::NodeF) * (size_t)cap : 0);
+  const size_t bytes = off_po + (fp32 ? sizeof(float4) * (size_t)n : 0);
   int rc = grav_scratch(ctx, bytes);
   if (rc != SPH_OK) return rc;
   char* base = (char*)ctx->grav_buf;
@@ -417,9 +610,25 @@ extern "C" int sph_gravity(sph_ctx* ctx, sph_state* state, double G, double eps,
   const int64_t tiles = (n + 31) / 32;
   int wb = (int)((tiles + sph::grav::kWalkWarps - 1) / sph::grav::kWalkWarps);
   if (wb > sm * 256) wb = sm * 256;
-  sph::grav::k_walk<<<wb, 32 * sph::grav::kWalkWarps, 0, st>>>(nodes, root, in, n, G, eps, theta,
-                                                               gx, gy, gz, stats, ctx->err);
-  ctx->launches += 1;
+  if (fp32) {
+    sph::grav::NodeF* nf = (sph::grav::NodeF*)(base + off_nf);
+    float4* po = (float4*)(base + off_po);
+    double L = 0.0;
+    for (int ax = 0; ax < 3; ++ax) L = fmax(L, 1.001 * g.nc[ax] * g.cs[ax]);
+    sph::grav::k_nodes32<<<sph::grav::blocks_for(noff, sm, 128), 128, 0, st>>>(
+        nodes, noff, g.lo[0], g.lo[1], g.lo[2], nf);
+    sph::grav::k_leaf_offsets<<<sph::grav::blocks_for(n_occ, sm, 128), 128, 0, st>>>(
+        nodes, n_occ, in, po);
+    sph::grav::k_walk32<<<wb, 32 * sph::grav::kWalkWarps, 0, st>>>(
+        nodes, nf, po, root, in, n, g.lo[0], g.lo[1], g.lo[2], L, G, eps, theta, gx, gy, gz,
+        stats, ctx->err);
+    ctx->launches += 3;
+  } else {
+    sph::grav::k_walk<<<wb, 32 * sph::grav::kWalkWarps, 0, st>>>(nodes, root, in, n, G, eps,
+                                                                 theta, gx, gy, gz, stats,
+                                                                 ctx->err);
+    ctx->launches += 1;
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return gfail(ctx, e, "sph_gravity launch");
   if (interactions) {

@@ -137,9 +137,9 @@ class SphSim:
                        _stream_ptr())
 
     def gravity(self, G: float = 1.0, eps: float = 0.0, theta: float = 0.5):
-        """Self-gravity by the multipole tree (sph_gravity); sorts the state.
-        Returns (g (n, 3) device tensor in the current order, [node, particle]
-        interactions)."""
+        """Self-gravity by the multipole tree (sph_gravity), in the sim's
+        precision; sorts the state.  Returns (g (n, 3) FP64 device tensor in
+        the current order, [node, particle] interactions)."""
         g = torch.empty(3, self.n, dtype=torch.float64, device=self.device)
         cnt = np.zeros(2, dtype=np.int64)
         self._call(self.lib.sph_gravity, C.byref(self._st), float(G), float(eps), float(theta),

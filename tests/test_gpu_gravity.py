@@ -2,7 +2,9 @@
 neighbour grid's cells against the oracle's tree (same reading, same
 acceptance decisions, so the sums agree to FP64 rounding and the interaction
 counts exactly) and against the exact direct sum (the approximation error of
-the quadrupole expansion at theta = 0.5)."""
+the quadrupole expansion at theta = 0.5).  The FP32-mixed walk takes the same
+decisions (equal interaction counts) and agrees within the FP32 acceleration
+tolerance, 1e-4 of max|g|."""
 import numpy as np
 import pytest
 
@@ -12,11 +14,13 @@ import sph_inputs
 pytestmark = pytest.mark.gpu
 
 EPS = 1e-3
+TOL32 = 1e-4     # FP32-mixed acceleration tolerance, relative to max |g|
 
 
-def _gpu(s, theta, G=1.0, eps=EPS):
+def _gpu(s, theta, G=1.0, eps=EPS, precision="fp64"):
     from paper_2005_02656_gb300 import Params, SphSim
-    sim = SphSim(s, Params(box_lo=s["lo"], box_hi=s["hi"], periodic=s["periodic"]))
+    sim = SphSim(s, Params(box_lo=s["lo"], box_hi=s["hi"], periodic=s["periodic"],
+                           precision=precision))
     g, counts = sim.gravity(G, eps, theta)
     g = g.cpu().numpy()
     ids = sim.t["id"].cpu().numpy()
@@ -46,6 +50,32 @@ def test_tree_matches_oracle_tree(theta):
     np.testing.assert_array_equal(counts, st)
 
 
+@pytest.mark.parametrize("theta", [0.0, 0.5, 0.8])
+def test_fp32_matches_oracle_tree(theta):
+    s = sph_inputs.uniform_sphere(22, seed_index=81)
+    g, counts = _gpu(s, theta, precision="fp32_mixed")
+    rc, ref, st = oracle.gravity_tree(s, eps=EPS, theta=theta)
+    assert rc == 0
+    ref_by_id = np.empty_like(ref)
+    ref_by_id[s["id"]] = ref
+    scale = np.abs(ref_by_id).max()
+    err = np.abs(g - ref_by_id).max() / scale
+    assert err <= TOL32, err
+    assert err > 0.0           # FP32 arithmetic did run
+    np.testing.assert_array_equal(counts, st)
+
+
+def test_fp32_decisions_on_an_exact_lattice():
+    """Unjittered lattice points lie on cell faces and at equal distances, so
+    many FP32 decisions fall inside the margin and are taken in FP64: the
+    counts still equal the FP64 walk's."""
+    s = sph_inputs.uniform_sphere(24, seed_index=85, jitter=0.0)
+    g64, c64 = _gpu(s, 0.5)
+    g32, c32 = _gpu(s, 0.5, precision="fp32_mixed")
+    np.testing.assert_array_equal(c32, c64)
+    assert np.abs(g32 - g64).max() <= TOL32 * np.abs(g64).max()
+
+
 def test_tree_error_against_direct_sum():
     s = sph_inputs.uniform_sphere(22, seed_index=82)
     g, _ = _gpu(s, 0.5)
@@ -72,6 +102,22 @@ def test_full_size_sampled():
     e = np.linalg.norm(g[sample_ids] - d, axis=1) / np.linalg.norm(d, axis=1)
     assert np.sqrt((e ** 2).mean()) < 1e-3
     assert counts[0] > 0 and counts[1] > 0
+
+
+def test_fp32_full_size_sampled():
+    s = sph_inputs.uniform_sphere(124, seed_index=83)
+    n = s["x"].shape[0]
+    g, counts = _gpu(s, 0.5, precision="fp32_mixed")
+    rng = np.random.default_rng(5)
+    sample_ids = rng.choice(n, 300, replace=False)
+    pos = np.empty(n, dtype=np.int64)
+    pos[s["id"]] = np.arange(n)
+    rc, ref, _ = oracle.gravity_tree(s, eps=EPS, theta=0.5, targets=pos[sample_ids])
+    assert rc == 0
+    assert np.abs(g[sample_ids] - ref).max() <= TOL32 * np.abs(ref).max()
+    g64, c64 = _gpu(s, 0.5)
+    np.testing.assert_array_equal(counts, c64)
+    assert np.abs(g - g64).max() <= TOL32 * np.abs(g64).max()
 
 
 def test_periodic_box_is_rejected():
