@@ -293,34 +293,45 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_walk(const Node* nodes, int
 }
 
 // ---- FP32-mixed walk ------------------------------------------------------
-// The node and particle terms in FP32, the opening decisions exact.  Node
-// coordinates are stored relative to the grid origin lo (so |value| <= L, the
-// grid's largest extent) and each particle relative to its leaf's centre of
-// mass; a lane forms p - c_leaf in FP64 once per opened leaf.
+// The node and particle terms in FP32, the opening decisions exact, and no
+// FP64 operation inside the walk (the FP64 pipe runs at 1/64 of the FP32
+// rate).  Coordinates are taken relative to the grid origin lo and split into
+// an FP32 head and tail (v = hi + lo to about 2^-48 |v|), so r = x_a - c is
+// (hi_a - hi_c) + (lo_a - lo_c) with FP32 rounding relative to |r| instead of
+// to the box.  Each particle is stored relative to its leaf's centre of mass,
+// so a lane that opens a leaf forms x_a - x_b as r - (x_b - c).
 
 struct NodeF {     // 96 B, read with uniform (broadcast) loads
-  float4 cm;       // c - lo, M
+  float4 cm;       // hi(c - lo), M
+  float4 q1;       // Q yz zz, size, lo(c - lo).x
+  float4 lo;       // box_lo - lo, lo(c - lo).y
+  float4 hi;       // box_hi - lo, lo(c - lo).z
   float4 q0;       // Q xx xy xz yy
-  float4 q1;       // Q yz zz, size, 0
-  float4 lo;       // box_lo - lo, 0
-  float4 hi;       // box_hi - lo, 0
   int4 t;          // first, nchild, p0, np
 };
+
+__device__ __forceinline__ void split2(double v, float& hi, float& lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
 
 __global__ void k_nodes32(const Node* nodes, int64_t nn, double lx, double ly, double lz,
                           NodeF* out) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nn;
        k += (int64_t)gridDim.x * blockDim.x) {
     const Node& nd = nodes[k];
+    float ch[3], cl[3];
+    split2(nd.c[0] - lx, ch[0], cl[0]);
+    split2(nd.c[1] - ly, ch[1], cl[1]);
+    split2(nd.c[2] - lz, ch[2], cl[2]);
     NodeF f;
-    f.cm = make_float4((float)(nd.c[0] - lx), (float)(nd.c[1] - ly), (float)(nd.c[2] - lz),
-                       (float)nd.M);
-    f.q0 = make_float4((float)nd.Q[0], (float)nd.Q[1], (float)nd.Q[2], (float)nd.Q[3]);
-    f.q1 = make_float4((float)nd.Q[4], (float)nd.Q[5], (float)nd.size, 0.f);
+    f.cm = make_float4(ch[0], ch[1], ch[2], (float)nd.M);
+    f.q1 = make_float4((float)nd.Q[4], (float)nd.Q[5], (float)nd.size, cl[0]);
     f.lo = make_float4((float)(nd.box_lo[0] - lx), (float)(nd.box_lo[1] - ly),
-                       (float)(nd.box_lo[2] - lz), 0.f);
+                       (float)(nd.box_lo[2] - lz), cl[1]);
     f.hi = make_float4((float)(nd.box_hi[0] - lx), (float)(nd.box_hi[1] - ly),
-                       (float)(nd.box_hi[2] - lz), 0.f);
+                       (float)(nd.box_hi[2] - lz), cl[2]);
+    f.q0 = make_float4((float)nd.Q[0], (float)nd.Q[1], (float)nd.Q[2], (float)nd.Q[3]);
     f.t = make_int4(nd.first, nd.nchild, nd.p0, nd.np);
     out[k] = f;
   }
@@ -337,18 +348,26 @@ __global__ void k_leaf_offsets(const Node* nodes, int64_t n_leaves, StateView s,
   }
 }
 
+// Constants of the FP32 walk, converted on the host.
+struct Walk32Consts {
+  double lx, ly, lz;   // grid origin
+  double theta;        // for the FP64 decision
+  float G, eps2, th;
+  float mb;            // box-face margin: covers the FP32 rounding of box and head
+  float aL;            // absolute distance margin
+};
+
 // Same warp walk as k_walk.  The FP32 decision uses margins that cover the
-// rounding of the stored coordinates (each <= L 2^-24 absolute) and of the
-// FP32 distance (relative 2^-22 with rsqrtf): mb on a box face, aL + 2e-6 R
-// on the distance.  A lane inside a margin takes the FP64 decision of k_walk
-// (accept64 on the FP64 node), so every lane accepts and opens exactly the
-// nodes that the FP64 walk does.
+// rounding of the stored box faces and of the particle's head (each <= L
+// 2^-24, L the grid's largest extent) and of the FP32 distance (relative
+// 2^-22 with rsqrtf): mb on a box face, aL + 2e-6 R on the distance.  A lane
+// inside a margin takes the FP64 decision of k_walk (accept64 on the FP64
+// node), so every lane accepts and opens exactly the nodes that the FP64 walk
+// does.
 __global__ void __launch_bounds__(32 * kWalkWarps) k_walk32(const Node* nodes,
                                                             const NodeF* nf, const float4* po,
                                                             int32_t root, StateView s,
-                                                            int64_t n, double lx, double ly,
-                                                            double lz, double L, double G,
-                                                            double eps, double theta,
+                                                            int64_t n, Walk32Consts k32,
                                                             double* gx, double* gy, double* gz,
                                                             unsigned long long* stats,
                                                             uint32_t* err) {
@@ -356,16 +375,16 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_walk32(const Node* nodes,
   __shared__ uint32_t st_mask[kWalkWarps][kStack];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned long long nodes_used = 0, pairs = 0;
-  const float eps2 = (float)(eps * eps), Gf = (float)G, th = (float)theta;
-  const float mb = (float)(4.0 * L * 5.9604644775390625e-8);   // 4 L 2^-24
-  const float aL = (float)(8.0 * L * 5.9604644775390625e-8);   // 8 L 2^-24
   const int64_t tiles = (n + 31) / 32;
   for (int64_t tile = blockIdx.x * (int64_t)kWalkWarps + w; tile < tiles;
        tile += (int64_t)gridDim.x * kWalkWarps) {
     const int64_t a = tile * 32 + lane;
     const bool valid = a < n;
-    const double p[3] = {valid ? s.x[a] : 0.0, valid ? s.y[a] : 0.0, valid ? s.z[a] : 0.0};
-    const float pf[3] = {(float)(p[0] - lx), (float)(p[1] - ly), (float)(p[2] - lz)};
+    const int32_t a32 = valid ? (int32_t)a : -1;
+    float ph[3], pl[3];
+    split2((valid ? s.x[a] : 0.0) - k32.lx, ph[0], pl[0]);
+    split2((valid ? s.y[a] : 0.0) - k32.ly, ph[1], pl[1]);
+    split2((valid ? s.z[a] : 0.0) - k32.lz, ph[2], pl[2]);
     float acc[3] = {0.f, 0.f, 0.f};
     const uint32_t all = __ballot_sync(0xffffffffu, valid);
     if (lane == 0) {
@@ -383,38 +402,43 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_walk32(const Node* nodes,
       const NodeF* f = nf + k;
       const float4 cm = __ldg(&f->cm);
       const float4 q1 = __ldg(&f->q1);
+      const float4 blo = __ldg(&f->lo), bhi = __ldg(&f->hi);
       const int4 t = __ldg(&f->t);
       const bool live = (mask >> lane) & 1u;
       bool open = false;
+      float r[3];
+      r[0] = (ph[0] - cm.x) + (pl[0] - q1.w);
+      r[1] = (ph[1] - cm.y) + (pl[1] - blo.w);
+      r[2] = (ph[2] - cm.z) + (pl[2] - bhi.w);
       if (live) {
-        const float4 blo = __ldg(&f->lo), bhi = __ldg(&f->hi);
-        const float r[3] = {pf[0] - cm.x, pf[1] - cm.y, pf[2] - cm.z};
         const float R2 = fmaf(r[2], r[2], fmaf(r[1], r[1], r[0] * r[0]));
         const float inv_R = rsqrtf(R2);
         const float Rf = R2 * inv_R;
-        const float size = q1.z;
+        const float size = q1.z, mb = k32.mb;
         // the box: certainly outside, certainly inside, or within mb of a face
-        const bool out_c = pf[0] < blo.x - mb || pf[0] > bhi.x + mb || pf[1] < blo.y - mb ||
-                           pf[1] > bhi.y + mb || pf[2] < blo.z - mb || pf[2] > bhi.z + mb;
-        const bool in_c = pf[0] >= blo.x + mb && pf[0] <= bhi.x - mb && pf[1] >= blo.y + mb &&
-                          pf[1] <= bhi.y - mb && pf[2] >= blo.z + mb && pf[2] <= bhi.z - mb;
-        const bool acc_c = size * (1.f + 1e-6f) < th * (Rf * (1.f - 2e-6f) - aL);
-        const bool rej_c = size * (1.f - 1e-6f) > th * (Rf * (1.f + 2e-6f) + aL);
+        const bool out_c = ph[0] < blo.x - mb || ph[0] > bhi.x + mb || ph[1] < blo.y - mb ||
+                           ph[1] > bhi.y + mb || ph[2] < blo.z - mb || ph[2] > bhi.z + mb;
+        const bool in_c = ph[0] >= blo.x + mb && ph[0] <= bhi.x - mb && ph[1] >= blo.y + mb &&
+                          ph[1] <= bhi.y - mb && ph[2] >= blo.z + mb && ph[2] <= bhi.z - mb;
+        const bool acc_c = size * (1.f + 1e-6f) < k32.th * (Rf * (1.f - 2e-6f) - k32.aL);
+        const bool rej_c = size * (1.f - 1e-6f) > k32.th * (Rf * (1.f + 2e-6f) + k32.aL);
         bool accept;
         if (in_c || rej_c) {
           accept = false;
         } else if (out_c && acc_c) {
           accept = true;
         } else {
+          // FP64 positions are reloaded here rather than kept live across the walk
+          const double p[3] = {s.x[a], s.y[a], s.z[a]};
           double r64[3], R2_64, R64;
-          accept = accept64(nodes[k], p, theta, r64, R2_64, R64);
+          accept = accept64(nodes[k], p, k32.theta, r64, R2_64, R64);
         }
         if (accept) {
           const float4 q0 = __ldg(&f->q0);
-          const float inv_s = eps2 > 0.f ? rsqrtf(R2 + eps2) : inv_R;
-          const float mono = Gf * cm.w * (inv_s * inv_s * inv_s);
+          const float inv_s = rsqrtf(R2 + k32.eps2);
+          const float mono = k32.G * cm.w * (inv_s * inv_s * inv_s);
           const float inv_R2 = inv_R * inv_R;
-          const float g5 = Gf * (inv_R2 * inv_R2 * inv_R);
+          const float g5 = k32.G * (inv_R2 * inv_R2 * inv_R);
           const float Qr[3] = {q0.x * r[0] + q0.y * r[1] + q0.z * r[2],
                                q0.y * r[0] + q0.w * r[1] + q1.x * r[2],
                                q0.z * r[0] + q1.x * r[1] + q1.y * r[2]};
@@ -429,16 +453,14 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_walk32(const Node* nodes,
       const uint32_t omask = __ballot_sync(0xffffffffu, open);
       if (omask == 0) continue;
       if (t.x < 0) {
-        // an opened leaf: p - c_leaf once in FP64, then its particles in FP32
-        const Node& nd = nodes[k];
-        const float q[3] = {(float)(p[0] - nd.c[0]), (float)(p[1] - nd.c[1]),
-                            (float)(p[2] - nd.c[2])};
+        // an opened leaf: x_a - x_b = r - (x_b - c), its particles in order
         for (int32_t b = t.z; b < t.z + t.w; ++b) {
           const float4 o = __ldg(po + b);
-          if (open && b != a) {
-            const float d[3] = {q[0] - o.x, q[1] - o.y, q[2] - o.z};
-            const float inv = rsqrtf(fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0])) + eps2);
-            const float fb = Gf * o.w * (inv * inv * inv);
+          if (open && b != a32) {
+            const float d[3] = {r[0] - o.x, r[1] - o.y, r[2] - o.z};
+            const float inv =
+                rsqrtf(fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0])) + k32.eps2);
+            const float fb = k32.G * o.w * (inv * inv * inv);
             for (int c = 0; c < 3; ++c) acc[c] -= fb * d[c];
             ++pairs;
           }
@@ -619,9 +641,18 @@ extern "C" int sph_gravity(sph_ctx* ctx, sph_state* state, double G, double eps,
         nodes, noff, g.lo[0], g.lo[1], g.lo[2], nf);
     sph::grav::k_leaf_offsets<<<sph::grav::blocks_for(n_occ, sm, 128), 128, 0, st>>>(
         nodes, n_occ, in, po);
+    sph::grav::Walk32Consts k32;
+    k32.lx = g.lo[0];
+    k32.ly = g.lo[1];
+    k32.lz = g.lo[2];
+    k32.theta = theta;
+    k32.G = (float)G;
+    k32.eps2 = (float)(eps * eps);
+    k32.th = (float)theta;
+    k32.mb = (float)(4.0 * L * 5.9604644775390625e-8);  // 4 L 2^-24
+    k32.aL = (float)(8.0 * L * 5.9604644775390625e-8);  // 8 L 2^-24
     sph::grav::k_walk32<<<wb, 32 * sph::grav::kWalkWarps, 0, st>>>(
-        nodes, nf, po, root, in, n, g.lo[0], g.lo[1], g.lo[2], L, G, eps, theta, gx, gy, gz,
-        stats, ctx->err);
+        nodes, nf, po, root, in, n, k32, gx, gy, gz, stats, ctx->err);
     ctx->launches += 3;
   } else {
     sph::grav::k_walk<<<wb, 32 * sph::grav::kWalkWarps, 0, st>>>(nodes, root, in, n, G, eps,
