@@ -17,6 +17,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -171,6 +172,14 @@ def whole_job_rate(n_per_rank, world, ms_max):
     return n_per_rank * world / (ms_max * 1e-3)
 
 
+def conservation(d0, d1, steps):
+    """Drift over the timed steps from the sums {Px, Py, Pz, E_kin, E_int, ...}
+    before and after them."""
+    e0, e1 = d0[3] + d0[4], d1[3] + d1[4]
+    return {"energy_rel_change_per_step": (e1 - e0) / abs(e0) / steps,
+            "momentum_change": [float(d1[i] - d0[i]) for i in range(3)]}
+
+
 def run_gpu(args, world, rank, local):
     import numpy as np
     import torch
@@ -206,6 +215,7 @@ def run_gpu(args, world, rank, local):
         for _ in range(args.warmup):
             sim.step()
         torch.cuda.synchronize()
+        d0 = sim.diagnostics()
         sim.profile(True)
         sim.stage_times()
         st0 = sim.stats()
@@ -229,6 +239,7 @@ def run_gpu(args, world, rank, local):
         launches = sim.launch_count() - l0
         flags = sim.error_word()
         diag = sim.last_diagnostics()
+        d1 = sim.diagnostics()
         sim.close()
         del sim
         torch.cuda.empty_cache()
@@ -237,7 +248,8 @@ def run_gpu(args, world, rank, local):
         exact = (st1["exact_tests"] - st0["exact_tests"]) / steps
         return {"ms": ms, "stages": {k: v / max(nsteps, 1) for k, v in stages.items()},
                 "pairs": pairs, "candidates": cands, "exact_tests": exact, "launches": launches,
-                "flags": flags, "dt": float(diag[8])}
+                "flags": flags, "dt": float(diag[8]),
+                "conservation": conservation(d0, d1, steps)}
 
     r32 = timed("fp32_mixed")
     r64 = None if args.no_fp64 else timed("fp64")
@@ -502,10 +514,64 @@ def cpu_baseline(max_seconds=20.0, max_steps=5):
         el = time.perf_counter() - t0
         if el >= max_seconds or steps >= max_steps:
             break
-    return {"value": n * steps / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "neighbor_pairs_per_s": pairs / el, "seconds": el,
-            "sample": f"{steps} full oracle step(s) of the Kelvin-Helmholtz recipe at 1/8 scale "
-                      f"(outer lattice {SAMPLE_NX}, {n} particles), FP64, OpenMP"}
+    out = {"value": n * steps / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "neighbor_pairs_per_s": pairs / el, "seconds": el,
+           "sample": f"{steps} full oracle step(s) of the Kelvin-Helmholtz recipe at 1/8 scale "
+                     f"(outer lattice {SAMPLE_NX}, {n} particles), FP64, OpenMP",
+           "host": host_cpu()}
+    out["small_box"] = oracle_threads_sample()
+    return out
+
+
+def host_cpu():
+    """Core count and CPU model of this host, read at run time."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
+def oracle_threads_sample(steps=3):
+    """The oracle on the 8,000-particle periodic box (jittered 20^3 lattice):
+    full steps on one thread and on all cores."""
+    import numpy as np
+
+    import oracle
+    import sph_inputs
+    s0 = sph_inputs.jittered_box(20, seed_index=0)
+    n = s0["x"].shape[0]
+    box = oracle.Box(s0["lo"], s0["hi"], s0["periodic"])
+    p = oracle.Params()
+    all_cores = oracle.num_threads()
+    res = {"workload": f"jittered_box_{n}", "steps": steps}
+    for label, threads in (("one_thread", 1), ("all_cores", all_cores)):
+        used = oracle.set_num_threads(threads)
+        s = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in s0.items()}
+        dt_prev, pairs = 0.0, 0
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            rc, dt_prev, out = oracle.step(box, s, p, dt_prev)
+            pairs += int(np.asarray(out["nn"]).sum())
+        el = time.perf_counter() - t0
+        res[label] = {"threads": used, "value": n * steps / el, "unit": UNIT,
+                      "neighbor_pairs_per_s": pairs / el}
+    oracle.set_num_threads(all_cores)
+    return res
 
 
 def main():
@@ -536,6 +602,7 @@ def main():
         "gpu_launches": r32["launches"],
         "clocks": r32["clocks"],
         "error_flags": r32["flags"],
+        "conservation": r32["conservation"],
         "search": {"candidates_per_step": r32["candidates"], "exact_tests_per_step": r32["exact_tests"],
                    "pairs_per_step": r32["pairs"]},
     }
@@ -545,7 +612,7 @@ def main():
                         "neighbor_pairs_per_s": r64["pairs"] * world / (ms64 * 1e-3),
                         "stages_ms": r64["stages"], "roofline": roofline(r64, n, "fp64"),
                         "gpu_launches": r64["launches"], "error_flags": r64["flags"],
-                        "clocks": r64["clocks"]}
+                        "conservation": r64["conservation"], "clocks": r64["clocks"]}
         line["fp32_mixed_over_fp64"] = ms64 / ms
     line["e2e"] = res["e2e"]
     if res.get("ensemble") is not None:

@@ -88,6 +88,8 @@ def _load():
         lib.oracle_gravity_tree.argtypes = [i64, P, P, P, P, P, d, d, d, i64, P, P, P, P, P]
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = cint
+        lib.oracle_set_num_threads.argtypes = [cint]
+        lib.oracle_set_num_threads.restype = cint
         lib.oracle_any_nonfinite.argtypes = [i64, P]
         _lib = lib
     return _lib
@@ -133,6 +135,11 @@ class Params:
 def num_threads() -> int:
     """Threads the oracle's per-particle loops run on."""
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> int:
+    """Sets the threads of the per-particle loops; returns the count in effect."""
+    return int(_load().oracle_set_num_threads(int(n)))
 
 
 def kernel_norm(sinc_n: float = 6.0) -> float:

@@ -668,6 +668,17 @@ int oracle_num_threads(void) {
 #endif
 }
 
+/* Sets the thread count of the per-particle loops (results do not depend on
+ * it); returns the count now in effect. */
+int oracle_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+  return oracle_num_threads();
+}
+
 /* Non-finite scan helper: returns 1 if any of the n values is NaN or inf. */
 int oracle_any_nonfinite(int64_t n, const double* v) {
   for (int64_t i = 0; i < n; ++i)

@@ -613,3 +613,27 @@ def test_gravity_tree_reduces_to_direct_and_converges(oracle_mod):
         rms.append(np.sqrt((e ** 2).mean()))
     assert rms[1] < 1e-3
     assert rms[1] / rms[0] > 6 and rms[2] / rms[1] > 6, rms
+
+
+def test_oracle_results_do_not_depend_on_thread_count(oracle_mod):
+    """Every per-particle loop writes only its own particle, so one thread and
+    all threads give bit-identical steps."""
+    s0 = sph_inputs.jittered_box(10, seed_index=0)
+    box = Box(s0["lo"], s0["hi"], s0["periodic"])
+    all_threads = oracle_mod.num_threads()
+    runs = []
+    try:
+        for threads in (1, all_threads):
+            assert oracle_mod.set_num_threads(threads) == threads
+            s = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in s0.items()}
+            rc, dt, out = oracle_mod.step(box, s, Params(), 0.0)
+            assert rc == oracle_mod.OK
+            runs.append((dt, s, out))
+    finally:
+        oracle_mod.set_num_threads(all_threads)
+    (dt1, s1, o1), (dt2, s2, o2) = runs
+    assert dt1 == dt2
+    for k in ("x", "y", "z", "vx", "u", "h"):
+        np.testing.assert_array_equal(s1[k], s2[k])
+    for k in ("rho", "ax", "du"):
+        np.testing.assert_array_equal(o1[k], o2[k])
