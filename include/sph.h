@@ -295,7 +295,8 @@ SPH_API void sph_ens_default_config(sph_ens_config* c);
  * box_hi (3 per box) and box_periodic (3 per box) describe it, box_alpha[b] is
  * its viscosity coefficient (Eq. 5).  common: gamma, courant, dt_growth,
  * ng_target, max_nb, sinc_n and precision (must be SPH_FP32_MIXED) shared by
- * all boxes.  All pointers are HOST arrays.  Allocates the device scratch
+ * all boxes.  All pointers are HOST arrays.  Every box_n[b] must be >= 1 and
+ * n_boxes >= 1 (SPH_ERR_INVALID_ARG otherwise).  Allocates the device scratch
  * (about 1 KB per particle at max_nb = 160). */
 SPH_API int sph_ensemble_init(const sph_params* common, int n_boxes, const int64_t* box_n,
                               const double* box_lo, const double* box_hi,

@@ -530,8 +530,7 @@ extern "C" int sph_gravity(sph_ctx* ctx, sph_state* state, double G, double eps,
                            sph_stream_t stream) {
   using sph::grav::Node;
   if (!ctx) return SPH_ERR_INVALID_ARG;
-  if (!state || !gx || !gy || !gz)
-    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "NULL state or output");
+  if (!state) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "NULL state");
   const int64_t n = state->n;
   if (n < 0 || n > ctx->n_max)
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "n = %lld outside [0, n_max]", (long long)n);
@@ -541,10 +540,11 @@ extern "C" int sph_gravity(sph_ctx* ctx, sph_state* state, double G, double eps,
     if (ctx->prm.periodic[k])
       return sph::set_error(ctx, SPH_ERR_INVALID_ARG,
                             "self-gravity needs open boundaries on every axis");
-  if (n == 0) {
+  if (n == 0) {  // nothing to read or write: the arrays may be NULL
     if (interactions) interactions[0] = interactions[1] = 0;
     return SPH_OK;
   }
+  if (!gx || !gy || !gz) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "NULL output");
   const double* req[] = {state->x, state->y, state->z, state->vx, state->vy, state->vz,
                          state->vxh, state->vyh, state->vzh, state->h, state->m, state->u,
                          state->du_prev};

@@ -130,6 +130,11 @@ def test_bad_config_is_rejected():
     with pytest.raises(_lib.SphError):
         ens.set_config(find_window=512, threads_per_particle=3)
     ens.close()
+    s = sph_inputs.jittered_box(8, seed_index=310)
+    empty = {k: (v[:0].copy() if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+    with pytest.raises(_lib.SphError) as e:
+        Ensemble([(s, 1.0), (empty, 1.0)])
+    assert e.value.code == _lib.SPH_ERR_INVALID_ARG
 
 
 def test_autotune_picks_a_configuration():

@@ -128,3 +128,48 @@ def test_periodic_box_is_rejected():
         sim.gravity()
     assert e.value.code == _lib.SPH_ERR_INVALID_ARG
     sim.close()
+
+
+def _few(xyz, m, h=0.1):
+    n = len(m)
+    s = {k: np.zeros(n) for k in ("x", "y", "z", "vx", "vy", "vz", "vxh", "vyh", "vzh",
+                                  "du_prev")}
+    s["x"], s["y"], s["z"] = (np.array(c, dtype=np.float64) for c in zip(*xyz)) if n else \
+        (np.zeros(0), np.zeros(0), np.zeros(0))
+    s["m"] = np.asarray(m, dtype=np.float64)
+    s["h"] = np.full(n, h)
+    s["u"] = np.ones(n)
+    s["id"] = np.arange(n, dtype=np.int64)
+    s["lo"], s["hi"], s["periodic"] = (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), (0, 0, 0)
+    return s
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+def test_two_bodies_closed_form(precision):
+    """Two bodies 0.5 apart along a diagonal: the softened Newtonian pull,
+    equal and opposite momentum (the leaves are opened, so the sum is direct)."""
+    s = _few([(0.1, 0.2, 0.3), (0.4, 0.6, 0.3)], [2.0, 0.5])
+    G, eps = 1.5, 0.1
+    g, counts = _gpu(s, 0.5, G=G, eps=eps, precision=precision)
+    d = np.array([0.3, 0.4, 0.0])
+    f = G / (0.25 + eps * eps) ** 1.5
+    tol = 1e-14 if precision == "fp64" else 1e-6
+    np.testing.assert_allclose(g[0], f * 0.5 * d, rtol=tol, atol=tol * f)
+    np.testing.assert_allclose(g[1], -f * 2.0 * d, rtol=tol, atol=tol * f)
+    assert counts[1] == 2
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+def test_single_particle_and_empty(precision):
+    g, counts = _gpu(_few([(0.1, 0.2, 0.3)], [1.0]), 0.5, precision=precision)
+    np.testing.assert_array_equal(g, np.zeros((1, 3)))
+    np.testing.assert_array_equal(counts, [0, 0])
+    from paper_2005_02656_gb300 import Params, SphSim
+    s = _few([], [])
+    sim = SphSim(s, Params(box_lo=s["lo"], box_hi=s["hi"], periodic=s["periodic"],
+                           precision=precision), n_max=4)
+    g, counts = sim.gravity(1.0, EPS, 0.5)
+    assert g.shape == (0, 3)
+    np.testing.assert_array_equal(counts, [0, 0])
+    assert sim.error_word() == 0
+    sim.close()
