@@ -38,6 +38,14 @@ SAMPLE_NX = 112        # the same recipe at 1/8 scale for the CPU oracle (1,067,
 # momentum read W_ab(h_a) cached by the density pass.
 FLOPS = {"find": 14, "density": 37, "iad": 57, "momentum": 140}
 FLOPS64 = {"find": 14, "density": 43, "iad": 19, "momentum": 131}
+# Algorithmic HBM bytes of one step, each array read or written once: per
+# particle (sort/gather 344, find 20, density 100, IAD 132, momentum 116,
+# dt 16, update 244) and per list entry (the int32 list written by the search
+# and read by density, IAD and momentum; the FP64 path also writes W_ab(h_a)
+# per entry and reads it twice).  Neighbour data gathered by the pair kernels
+# is counted once per particle, as the record it is read from.
+STEP_BYTES = {"fp32_mixed": {"particle": 972, "entry": 16},
+              "fp64": {"particle": 972, "entry": 40}}
 # Derived non-tensor peaks: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz, and
 # the FP64 pipe at 1/64 of that rate.
 SM, LANES, MHZ = 152, 128, 2070.0
@@ -471,6 +479,31 @@ def _gravity_one(dev, windows, calls, theta, precision):
                          "flops_per_call": flops}}
 
 
+def step_roofline(r, n, precision, ms_step):
+    """The whole step against max(bytes / HBM bandwidth, pipe time of its
+    flops): the search on the FP32 pipe, the pair sums on the pipe of the
+    path's precision; the kernels run one after another, so pipe times add."""
+    hbm = peaks().get("hbm_gbs")
+    entries = r["pairs"]
+    b = STEP_BYTES[precision]
+    bytes_step = b["particle"] * n + b["entry"] * entries
+    find_ms = FLOPS["find"] * r["candidates"] / (FP32_PEAK_TFLOPS * 1e12) * 1e3
+    if precision == "fp64":
+        pair_flops = sum(FLOPS64[k] for k in ("density", "iad", "momentum")) * entries
+        pair_ms = pair_flops / (FP64_PEAK_TFLOPS * 1e12) * 1e3
+    else:
+        pair_flops = sum(FLOPS[k] for k in ("density", "iad", "momentum")) * entries
+        pair_ms = pair_flops / (FP32_PEAK_TFLOPS * 1e12) * 1e3
+    alu_ms = find_ms + pair_ms
+    hbm_ms = bytes_step / (hbm * 1e9) * 1e3 if hbm else None
+    bound = "alu" if hbm_ms is None or alu_ms >= hbm_ms else "hbm"
+    t = max(alu_ms, hbm_ms or 0.0)
+    return {"bound": bound, "time_ms": t, "alu_ms": alu_ms, "hbm_ms": hbm_ms,
+            "frac": t / ms_step, "bytes_per_step": bytes_step,
+            "flops_per_step": FLOPS["find"] * r["candidates"] + pair_flops,
+            "hbm_peak_gbs": hbm, "peak_source": "HBM: MEASURED_PEAKS.json copy; pipes derived"}
+
+
 def roofline(r, n, precision):
     """Dominant kernel's achieved vs peak under the flop model above."""
     st = r["stages"]
@@ -599,6 +632,7 @@ def main():
         "neighbor_pairs_per_s": r32["pairs"] * world / (ms * 1e-3),
         "stages_ms": r32["stages"],
         "roofline": roofline(r32, n, "fp32_mixed"),
+        "step_roofline": step_roofline(r32, n, "fp32_mixed", ms),
         "gpu_launches": r32["launches"],
         "clocks": r32["clocks"],
         "error_flags": r32["flags"],
@@ -611,6 +645,7 @@ def main():
         line["fp64"] = {"value": whole_job_rate(n, world, ms64), "unit": UNIT, "ms_per_step": ms64,
                         "neighbor_pairs_per_s": r64["pairs"] * world / (ms64 * 1e-3),
                         "stages_ms": r64["stages"], "roofline": roofline(r64, n, "fp64"),
+                        "step_roofline": step_roofline(r64, n, "fp64", ms64),
                         "gpu_launches": r64["launches"], "error_flags": r64["flags"],
                         "conservation": r64["conservation"], "clocks": r64["clocks"]}
         line["fp32_mixed_over_fp64"] = ms64 / ms
