@@ -5,7 +5,14 @@
 //
 // The cell's stencil particles are staged in the warp's shared-memory window
 // as FP32 positions relative to the cell's origin (offset to their own cell +
-// the stencil shift).  Lane t owns target t of the cell (32 at a time) and
+// the stencil shift).  Only candidates within reach of some target are staged:
+// the distance from the candidate to the bounding box of the cell's targets
+// must be below the largest 2 h_a among them (plus the FP32 error bound), which
+// every neighbour of every target satisfies.  With cells of side >= 2 h_max this
+// keeps about three quarters of the 27-cell stencil where h is near h_max and
+// about half where h is smaller; the staged candidates keep their stencil-slot
+// order, so the lists are the same sequences as without the filter.
+// Lane t owns target t of the cell (32 at a time) and
 // walks the staged candidates in blocks of 64, all lanes reading the same
 // candidate pair (broadcast loads, paired FP32 arithmetic on candidates j and
 // j + 32 of the block):
@@ -130,22 +137,89 @@ __device__ __forceinline__ void find_cell(const Grid& g, uint32_t code, const St
     __syncwarp();
     return;
   }
-  for (int w0 = 0; w0 < P; w0 += WIN) {
-    const int wn = min(WIN, P - w0);
-    const int wpad = (wn + 63) & ~63;
-    // stage slots [w0, w0 + wn) cell by cell (no per-slot search)
-    for (int sc = 0; sc < S.ncell; ++sc) {
-      const int lo = max(S.off[sc], w0), hi = min(S.off[sc + 1], w0 + wn);
-      const float sx = S.shift[sc][0], sy = S.shift[sc][1], sz = S.shift[sc][2];
-      for (int J = lo + lane; J < hi; J += 32) {
-        const float4 p = pos32[S.start[sc] + (J - S.off[sc])];
-        const int q = pair_index(J - w0);
-        W.cx[q] = p.x + sx;
-        W.cy[q] = p.y + sy;
-        W.cz[q] = p.z + sz;
-        W.entry[J - w0] = entry_make(S.scode[sc], S.start[sc] + (J - S.off[sc]));
+  // bounding box of the targets (cell-relative FP32) and their largest h
+  {
+    float bl[3] = {kFar, kFar, kFar}, bh[3] = {-kFar, -kFar, -kFar}, hm = 0.0f;
+    for (int t = lane; t < na; t += 32) {
+      const float4 p = pos32[a0 + t];
+      bl[0] = fminf(bl[0], p.x);
+      bl[1] = fminf(bl[1], p.y);
+      bl[2] = fminf(bl[2], p.z);
+      bh[0] = fmaxf(bh[0], p.x);
+      bh[1] = fmaxf(bh[1], p.y);
+      bh[2] = fmaxf(bh[2], p.z);
+      hm = fmaxf(hm, p.w);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      for (int ax = 0; ax < 3; ++ax) {
+        bl[ax] = fminf(bl[ax], __shfl_xor_sync(0xffffffffu, bl[ax], o));
+        bh[ax] = fmaxf(bh[ax], __shfl_xor_sync(0xffffffffu, bh[ax], o));
+      }
+      hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+    }
+    // generous: 2 h in FP32 can be below 2 h_a by 2^-23 relative, and each
+    // candidate and target coordinate carries at most err32 per axis
+    const float reach = 2.0f * hm * 1.0001f + 4.0f * esum;
+    if (lane == 0) {
+      for (int ax = 0; ax < 3; ++ax) {
+        S.box_lo[ax] = bl[ax];
+        S.box_hi[ax] = bh[ax];
+      }
+      S.reach2 = reach * reach;
+    }
+    __syncwarp();
+  }
+
+  int wn = 0;           // slots staged in the current window
+  int wbase = 0;        // staged slots before the current window
+  int gself = -1;       // staged index of the target cell's first particle
+  bool first = true;
+  int sc = 0, j0 = 0;   // next source: stencil cell and particle within it
+  const uint32_t lt = (1u << lane) - 1u;
+  for (;;) {
+    // stage candidates within reach, cell by cell in stencil order, until the
+    // window cannot take another 32 or the stencil is exhausted
+    while (sc < S.ncell && wn + 32 <= WIN) {
+      const int cnt = S.off[sc + 1] - S.off[sc];
+      const bool own = sc == S.self_cell;
+      if (own && j0 == 0) gself = wbase + wn;
+      const int st = S.start[sc];
+      const int j = j0 + lane;
+      bool keep = false;
+      float cx = 0.f, cy = 0.f, cz = 0.f;
+      if (j < cnt) {
+        const float4 p = pos32[st + j];
+        cx = p.x + S.shift[sc][0];
+        cy = p.y + S.shift[sc][1];
+        cz = p.z + S.shift[sc][2];
+        if (WRAP || own) {
+          keep = true;
+        } else {
+          const float dx = fmaxf(fmaxf(S.box_lo[0] - cx, cx - S.box_hi[0]), 0.0f);
+          const float dy = fmaxf(fmaxf(S.box_lo[1] - cy, cy - S.box_hi[1]), 0.0f);
+          const float dz = fmaxf(fmaxf(S.box_lo[2] - cz, cz - S.box_hi[2]), 0.0f);
+          keep = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < S.reach2;
+        }
+      }
+      const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const int q = wn + __popc(bal & lt);
+        const int pq = pair_index(q);
+        W.cx[pq] = cx;
+        W.cy[pq] = cy;
+        W.cz[pq] = cz;
+        W.entry[q] = entry_make(S.scode[sc], st + j);
+      }
+      wn += __popc(bal);
+      j0 += 32;
+      if (j0 >= cnt) {
+        ++sc;
+        j0 = 0;
       }
     }
+    // the targets of the cell against the staged window
+    const int wpad = (wn + 63) & ~63;
     for (int i = wn + lane; i < wpad; i += 32) {
       const int q = pair_index(i);
       W.cx[q] = kFar;
@@ -164,8 +238,9 @@ __device__ __forceinline__ void find_cell(const Grid& g, uint32_t code, const St
       const float lo_lim = lim - margin, hi_lim = lim + margin;
       const float2 npx = make_float2(-pa.x, -pa.x), npy = make_float2(-pa.y, -pa.y),
                    npz = make_float2(-pa.z, -pa.z);
-      const int self = active ? S.self_slot0 + t - w0 : -1;
-      int k = (w0 == 0 || !active) ? 0 : nn[a];
+      const int gs = gself >= 0 ? gself + t - wbase : -1;
+      const int self = (active && gs >= 0 && gs < wn) ? gs : -1;
+      int k = (first || !active) ? 0 : nn[a];
       for (int jb = 0; jb < wpad; jb += 64) {
         uint64_t hit, unc;
         block_masks<WRAP>(g, W.cx + jb, W.cy + jb, W.cz + jb, npx, npy, npz, lo_lim, hi_lim,
@@ -192,10 +267,14 @@ __device__ __forceinline__ void find_cell(const Grid& g, uint32_t code, const St
       if (active) {
         nn[a] = k;
         if (k > max_nb) raise_flag(err, SPH_FLAG_NB_OVERFLOW);
-        tested += (unsigned long long)wn - (self >= 0 && self < wn ? 1 : 0);
+        tested += (unsigned long long)wn - (self >= 0 ? 1 : 0);
       }
     }
     __syncwarp();
+    first = false;
+    if (sc >= S.ncell) break;
+    wbase += wn;
+    wn = 0;
   }
 }
 

@@ -44,6 +44,7 @@ __device__ __forceinline__ void entry_shift(uint32_t e, const Grid& g, float& sx
 
 struct alignas(16) Stencil {
   int ncell;
+  int self_cell;                  // stencil index of the target cell
   int self_slot0;                 // slot of the target cell's first particle
   int a0, na;                     // target cell: first sorted index, population
   int start[kMaxStencil];         // first sorted index of each stencil cell
@@ -51,6 +52,8 @@ struct alignas(16) Stencil {
   float shift[kMaxStencil][3];    // stencil-cell origin minus target-cell origin (FP32)
   int scode[kMaxStencil];         // shift code of each stencil cell (list entries)
   int maxpop;                     // largest stencil-cell population
+  float box_lo[3], box_hi[3];     // bounding box of the target cell's particles (FP32)
+  float reach2;                   // squared staging reach (find_cell)
 };
 
 // Distinct stencil cells along one axis for a target cell at index ic: their
@@ -131,6 +134,7 @@ __device__ __forceinline__ void build_stencil_warp(const Grid& g, uint32_t code,
   if (lane < ncell) S.off[lane] = incl - cnt;
   if (lane == ncell - 1) S.off[ncell] = incl;
   if (self) {
+    S.self_cell = lane;
     S.self_slot0 = incl - cnt;
     S.a0 = S.start[lane];
     S.na = cnt;
