@@ -362,6 +362,7 @@ def run_ensemble(args, dev, windows):
             "phase_ms_per_step": {k: round(v, 4) for k, v in phase_ms.items()},
             "phase_steps": phase_steps,
             "autotune": {k: tune[k] for k in ("cell_factor", "find_window", "threads_per_particle",
+                                              "momentum_threads",
                                               "blocks_per_sm", "seconds_per_step", "tried")}}
 
 

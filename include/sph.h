@@ -284,8 +284,11 @@ typedef struct {
                           staged per warp, 128, 256 or 512 [512]; smaller
                           windows leave more of the SM's L1 to the pair phases */
   int threads_per_particle; /* lanes sharing one particle's neighbour list in
-                          the density, IAD and momentum phases: 1, 2 or 4 [1];
-                          with 1 a box's results equal a single-box sph_step */
+                          the density and IAD phases: 1, 2 or 4 [1] */
+  int momentum_threads;  /* lanes sharing one particle's neighbour list in the
+                          momentum phase: 1, 2 or 4 [4].  With the defaults
+                          (1 and 4, the single-box kernels' split) a box's
+                          results equal a single-box sph_step */
 } sph_ens_config;
 
 SPH_API void sph_ens_default_config(sph_ens_config* c);

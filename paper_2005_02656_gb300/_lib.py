@@ -70,7 +70,7 @@ class SphParams(C.Structure):
 class EnsConfig(C.Structure):
     _fields_ = [("cell_factor", C.c_double), ("blocks_per_sm", C.c_int),
                 ("test_skip_block", C.c_int), ("find_window", C.c_int),
-                ("threads_per_particle", C.c_int)]
+                ("threads_per_particle", C.c_int), ("momentum_threads", C.c_int)]
 
 
 class SphError(RuntimeError):

@@ -100,7 +100,8 @@ struct Args {
   float Bn;
   double cell_factor;    // cells of side >= cell_factor * 2 h_max
   int skip_block;        // test hook (sph_ens_config::test_skip_block)
-  int tpp;               // threads per particle of the pair phases (1, 2, 4)
+  int tpp;               // threads per particle of the density and IAD phases (1, 2, 4)
+  int tpm;               // threads per particle of the momentum phase (1, 2, 4)
 };
 
 // --- ordered-integer encodings of doubles for atomic min/max ---
@@ -548,9 +549,9 @@ __device__ void ph_iad(const Args& A) {
     ph_iad_t<1>(A);
 }
 __device__ void ph_momentum(const Args& A) {
-  if (A.tpp == 4)
+  if (A.tpm == 4)
     ph_momentum_t<4>(A);
-  else if (A.tpp == 2)
+  else if (A.tpm == 2)
     ph_momentum_t<2>(A);
   else
     ph_momentum_t<1>(A);
@@ -804,6 +805,7 @@ Args args_of(sph_ens* e, const sph_state* st, double* dt_dev) {
   A.cell_factor = e->cfg.cell_factor;
   A.skip_block = e->cfg.test_skip_block;
   A.tpp = e->cfg.threads_per_particle;
+  A.tpm = e->cfg.momentum_threads;
   return A;
 }
 
@@ -891,6 +893,7 @@ void sph_ens_default_config(sph_ens_config* c) {
   c->test_skip_block = -1;
   c->find_window = 512;
   c->threads_per_particle = 1;
+  c->momentum_threads = 4;
 }
 
 int sph_ensemble_init(const sph_params* common, int n_boxes, const int64_t* box_n,
@@ -1009,6 +1012,8 @@ int sph_ensemble_set_config(sph_ens* e, const sph_ens_config* c) {
   if (c->threads_per_particle != 1 && c->threads_per_particle != 2 &&
       c->threads_per_particle != 4)
     return ens_fail(e, SPH_ERR_INVALID_ARG, "threads_per_particle must be 1, 2 or 4");
+  if (c->momentum_threads != 1 && c->momentum_threads != 2 && c->momentum_threads != 4)
+    return ens_fail(e, SPH_ERR_INVALID_ARG, "momentum_threads must be 1, 2 or 4");
   e->cfg = *c;
   if (e->graph) {
     cudaGraphExecDestroy(e->graph);

@@ -66,7 +66,7 @@ class Ensemble:
             raise _lib.SphError(rc, (self.lib.sph_ensemble_last_error(self.ctx) or b"").decode())
 
     def set_config(self, cell_factor=None, blocks_per_sm=None, test_skip_block=None,
-                   find_window=None, threads_per_particle=None):
+                   find_window=None, threads_per_particle=None, momentum_threads=None):
         if cell_factor is not None:
             self.cfg.cell_factor = float(cell_factor)
         if blocks_per_sm is not None:
@@ -77,6 +77,8 @@ class Ensemble:
             self.cfg.find_window = int(find_window)
         if threads_per_particle is not None:
             self.cfg.threads_per_particle = int(threads_per_particle)
+        if momentum_threads is not None:
+            self.cfg.momentum_threads = int(momentum_threads)
         with torch.cuda.device(self.device):
             self._err(self.lib.sph_ensemble_set_config(self.ctx, C.byref(self.cfg)))
 
@@ -135,7 +137,8 @@ class Ensemble:
         order = np.argsort(out["id"], kind="stable")
         return {k: v[order] for k, v in out.items()}
 
-    KNOBS = ("cell_factor", "find_window", "threads_per_particle", "blocks_per_sm")
+    KNOBS = ("cell_factor", "find_window", "threads_per_particle", "momentum_threads",
+             "blocks_per_sm")
 
     def _time(self, steps, knobs):
         """Seconds per step of `steps` steps of a copy of the current state
@@ -155,13 +158,14 @@ class Ensemble:
         return sec
 
     def autotune(self, steps: int = 2, cell_factors=(1.0, 1.15, 1.3), find_windows=(128, 256, 512),
-                 threads_per_particle=(1, 2, 4), blocks_per_sm=(0,)):
+                 threads_per_particle=(1, 2, 4), momentum_threads=(4, 2), blocks_per_sm=(0,)):
         """Picks the ensemble kernel's configuration by timing `steps` steps
         of a copy of the current state per candidate: the tile shape of the
         neighbour search (find_window) and the threads per particle of the
-        pair phases over their full grid at the first cell factor, then the
-        cell-size factor and the persistent CTAs per SM one at a time around
-        the best.  The ensemble's own state is not advanced."""
+        density and IAD phases over their full grid at the first cell factor
+        and momentum split, then the momentum split, the cell-size factor and
+        the persistent CTAs per SM one at a time around the best.  The
+        ensemble's own state is not advanced."""
         results = []
 
         def trial(**knobs):
@@ -173,11 +177,13 @@ class Ensemble:
         for w in find_windows:
             for tp in threads_per_particle:
                 k = {"cell_factor": cell_factors[0], "find_window": w,
-                     "threads_per_particle": tp, "blocks_per_sm": blocks_per_sm[0]}
+                     "threads_per_particle": tp, "momentum_threads": momentum_threads[0],
+                     "blocks_per_sm": blocks_per_sm[0]}
                 sec = trial(**k)
                 if best is None or sec < best[0]:
                     best = (sec, k)
-        for name, values in (("cell_factor", cell_factors[1:]), ("blocks_per_sm", blocks_per_sm[1:])):
+        for name, values in (("momentum_threads", momentum_threads[1:]),
+                             ("cell_factor", cell_factors[1:]), ("blocks_per_sm", blocks_per_sm[1:])):
             for v in values:
                 k = dict(best[1], **{name: v})
                 sec = trial(**k)

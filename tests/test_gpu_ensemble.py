@@ -95,15 +95,15 @@ def test_barrier_timeout_is_reported_and_context_recovers():
     ens.close()
 
 
-@pytest.mark.parametrize("find_window,tpp", [(128, 1), (256, 2), (512, 4)])
-def test_tile_shape_and_threads_per_particle_against_oracle(find_window, tpp):
+@pytest.mark.parametrize("find_window,tpp,tpm", [(128, 1, 1), (256, 2, 2), (512, 4, 4), (256, 1, 4)])
+def test_tile_shape_and_threads_per_particle_against_oracle(find_window, tpp, tpm):
     """Every tile shape and thread count gives the same neighbour sets and
     sums within the FP32-mixed tolerances (the split changes only the
     summation order)."""
     from paper_2005_02656_gb300 import Ensemble
     boxes = _boxes()
     ens = Ensemble(boxes)
-    ens.set_config(find_window=find_window, threads_per_particle=tpp)
+    ens.set_config(find_window=find_window, threads_per_particle=tpp, momentum_threads=tpm)
     ens.step(1)
     assert ens.error_word() == 0
     for b in (0, 5):
@@ -129,6 +129,8 @@ def test_bad_config_is_rejected():
         ens.set_config(find_window=200)
     with pytest.raises(_lib.SphError):
         ens.set_config(find_window=512, threads_per_particle=3)
+    with pytest.raises(_lib.SphError):
+        ens.set_config(threads_per_particle=1, momentum_threads=3)
     ens.close()
     s = sph_inputs.jittered_box(8, seed_index=310)
     empty = {k: (v[:0].copy() if isinstance(v, np.ndarray) else v) for k, v in s.items()}
@@ -142,10 +144,11 @@ def test_autotune_picks_a_configuration():
     ens = Ensemble(_boxes())
     before = ens.box_numpy(3)
     res = ens.autotune(steps=1, cell_factors=(1.0, 1.3), find_windows=(128, 512),
-                       threads_per_particle=(1, 2))
+                       threads_per_particle=(1, 2), momentum_threads=(4, 2))
     assert res["cell_factor"] in (1.0, 1.3) and res["seconds_per_step"] > 0
     assert res["find_window"] in (128, 512) and res["threads_per_particle"] in (1, 2)
-    assert len(res["tried"]) == 5
+    assert res["momentum_threads"] in (4, 2)
+    assert len(res["tried"]) == 6
     after = ens.box_numpy(3)
     np.testing.assert_array_equal(before["x"], after["x"])   # tuning leaves the state alone
     ens.step(1)
