@@ -60,3 +60,59 @@ def test_null_arguments_are_rejected(lib):
     assert lib.sph_step(None, None, None, None) == -1
     assert lib.sph_error_word(None, None) == -1
     assert lib.sph_last_error(None) == b"no context"
+
+
+def _params(lib, **kw):
+    from paper_2005_02656_gb300._lib import SphParams
+    p = SphParams()
+    lib.sph_default_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("field,value", [
+    ("gamma", 1.0), ("alpha", -0.1), ("courant", 0.0), ("dt_growth", 0.9), ("ng_target", -1),
+    ("max_nb", 0), ("max_nb", 162), ("max_nb", 4100), ("sinc_n", 0.5), ("sinc_n", 6.5),
+    ("sinc_n", 13.0), ("precision", 7), ("kernel_mode", 3), ("gradh", 2)])
+def test_invalid_params_are_rejected_before_any_device_work(lib, field, value):
+    # sph_init validates its parameters on the host and returns before any
+    # CUDA call, so this runs without a GPU
+    from paper_2005_02656_gb300._lib import SPH_ERR_INVALID_ARG
+    p = _params(lib, **{field: value})
+    ctx = C.c_void_p(1)
+    assert lib.sph_init(C.byref(p), 1000, C.byref(ctx)) == SPH_ERR_INVALID_ARG
+    assert not ctx.value
+
+
+def test_param_combinations_and_sizes_are_rejected(lib):
+    from paper_2005_02656_gb300._lib import SPH_ERR_INVALID_ARG, SPH_KERNEL_TABLE
+    ctx = C.c_void_p()
+    p = _params(lib, gradh=1, kernel_mode=SPH_KERNEL_TABLE)     # grad-h needs the exact kernel
+    assert lib.sph_init(C.byref(p), 1000, C.byref(ctx)) == SPH_ERR_INVALID_ARG
+    p = _params(lib)
+    p.periodic[1] = 1
+    p.box_lo[1], p.box_hi[1] = 1.0, 1.0                          # periodic axis of zero length
+    assert lib.sph_init(C.byref(p), 1000, C.byref(ctx)) == SPH_ERR_INVALID_ARG
+    p = _params(lib)
+    for n_max in (0, -5, (1 << 27) + 1):                         # list entries hold 27-bit indices
+        assert lib.sph_init(C.byref(p), n_max, C.byref(ctx)) == SPH_ERR_INVALID_ARG
+    assert not ctx.value
+
+
+def test_ensemble_defaults_and_host_checks(lib):
+    from paper_2005_02656_gb300._lib import EnsConfig, SPH_ERR_INVALID_ARG, SPH_FP32_MIXED
+    c = EnsConfig()
+    lib.sph_ens_default_config(C.byref(c))
+    assert (c.cell_factor, c.blocks_per_sm, c.test_skip_block, c.find_window,
+            c.threads_per_particle, c.momentum_threads) == (1.0, 0, -1, 512, 1, 4)
+    p = _params(lib, precision=SPH_FP32_MIXED)
+    n = (C.c_int64 * 1)(100)
+    d3 = (C.c_double * 3)(0, 0, 0)
+    i3 = (C.c_int * 3)(1, 1, 1)
+    a1 = (C.c_double * 1)(1.0)
+    e = C.c_void_p()
+    assert lib.sph_ensemble_init(C.byref(p), 0, n, d3, d3, i3, a1, C.byref(e)) == SPH_ERR_INVALID_ARG
+    p64 = _params(lib)                                           # the ensemble is FP32-mixed only
+    assert lib.sph_ensemble_init(C.byref(p64), 1, n, d3, d3, i3, a1, C.byref(e)) == SPH_ERR_INVALID_ARG
+    assert not e.value
