@@ -3,7 +3,8 @@
 // grid-stride over the sorted particles, walking its neighbour list (entries:
 // sph_tile.cuh) and gathering the neighbours' FP64 fields through L1/L2
 // (particles are in Morton cell order, so a warp's neighbours share lines).
-// Separations are FP64 minimum-image differences of the positions.  On this
+// Separations are FP64 minimum-image differences of the positions, the image
+// taken from the list entry's cell shift (sep64).  On this
 // part the FP64 pipe bounds these kernels, so per-pair divisions are hoisted
 // into per-particle arrays (m/rho, P/rho^2, 1/rho, 1/h^2, B_n/h^3), and the
 // kernel value W_ab(h_a) of each list entry is evaluated once, by the density
@@ -21,6 +22,7 @@ namespace {
 constexpr int kThreads64 = 128;
 
 struct Aux64 {
+  const int32_t* cell3;  // packed cell coordinates of each sorted particle
   double* vol;     // m / rho
   double* X;       // P / rho^2
   double* inv_rho;
@@ -36,11 +38,37 @@ struct Lists64 {
   int max_nb;
 };
 
-__device__ __forceinline__ void sep64(const Grid& g, double xa, double ya, double za, double xb,
-                                      double yb, double zb, double& dx, double& dy, double& dz) {
-  dx = min_image(xb - xa, g.Lbox[0], g.halfL[0], g.periodic[0]);
-  dy = min_image(yb - ya, g.Lbox[1], g.halfL[1], g.periodic[1]);
-  dz = min_image(zb - za, g.Lbox[2], g.halfL[2], g.periodic[2]);
+// FP64 minimum-image separation x_b - x_a of a list entry.  With at least
+// three cells on every periodic axis (Grid::wrap32 == 0) the image is known
+// from the entry's cell shift: the neighbour's cell is ca + shift before
+// wrapping, and an index below 0 or past the last cell means its image lies
+// one period down or up.  That is the same subtraction or addition of the
+// period that the minimum-image test would pick for a neighbour (closer than
+// 2h < L/2), decided by integer arithmetic instead of six FP64 comparisons
+// (the FP64 pipe bounds these kernels).  Otherwise the comparisons decide.
+__device__ __forceinline__ void sep64(const Grid& g, const int ca[3], uint32_t e, double xa,
+                                      double ya, double za, double xb, double yb, double zb,
+                                      double& dx, double& dy, double& dz) {
+  dx = xb - xa;
+  dy = yb - ya;
+  dz = zb - za;
+  if (g.wrap32) {
+    dx = min_image(dx, g.Lbox[0], g.halfL[0], g.periodic[0]);
+    dy = min_image(dy, g.Lbox[1], g.halfL[1], g.periodic[1]);
+    dz = min_image(dz, g.Lbox[2], g.halfL[2], g.periodic[2]);
+    return;
+  }
+  const int c = (int)(e >> kIndexBits);
+  const int sz = c / 9, sy = (c - 9 * sz) / 3, sx = c - 9 * sz - 3 * sy;
+  const int u[3] = {ca[0] + sx - 1, ca[1] + sy - 1, ca[2] + sz - 1};
+  double* d[3] = {&dx, &dy, &dz};
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    if (u[ax] < 0)
+      *d[ax] = __dsub_rn(*d[ax], g.Lbox[ax]);
+    else if (u[ax] >= g.nc[ax])
+      *d[ax] = __dadd_rn(*d[ax], g.Lbox[ax]);
+  }
 }
 
 // GRADH: also the grad-h terms, Omega_a = 1 + h_a/(3 rho_a) sum_b m_b dW/dh_a.
@@ -57,6 +85,8 @@ __global__ void __launch_bounds__(kThreads64) k_density64(const Grid* gp, StateV
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
        a += (int64_t)gridDim.x * blockDim.x) {
     const double xa = s.x[a], ya = s.y[a], za = s.z[a], ha = s.h[a];
+    int cell_a[3];
+    unpack_cell(aux.cell3[a], cell_a[0], cell_a[1], cell_a[2]);
     const double hinv2 = 1.0 / (ha * ha);
     const double norm = Bn * hinv2 / ha;
     const int cnt = min(L.nn[a], L.max_nb);
@@ -64,9 +94,10 @@ __global__ void __launch_bounds__(kThreads64) k_density64(const Grid* gp, StateV
     double* wrow = L.w + a * L.max_nb;
     double acc = 0.0, gsum = 0.0;
     for (int k = 0; k < cnt; ++k) {
-      const int64_t b = entry_index(list[k]);
+      const uint32_t e = list[k];
+      const int64_t b = entry_index(e);
       double dx, dy, dz;
-      sep64(g, xa, ya, za, s.x[b], s.y[b], s.z[b], dx, dy, dz);
+      sep64(g, cell_a, e, xa, ya, za, s.x[b], s.y[b], s.z[b], dx, dy, dz);
       const double r2 = dx * dx + dy * dy + dz * dz;
       const double t = fmin(r2 * hinv2, 4.0);
       if (GRADH) {
@@ -110,14 +141,17 @@ __global__ void __launch_bounds__(kThreads64) k_iad64(const Grid* gp, StateView 
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
        a += (int64_t)gridDim.x * blockDim.x) {
     const double xa = s.x[a], ya = s.y[a], za = s.z[a];
+    int cell_a[3];
+    unpack_cell(aux.cell3[a], cell_a[0], cell_a[1], cell_a[2]);
     const int cnt = min(L.nn[a], L.max_nb);
     const uint32_t* list = L.nbr + a * L.max_nb;
     const double* wrow = L.w + a * L.max_nb;
     double t00 = 0, t01 = 0, t02 = 0, t11 = 0, t12 = 0, t22 = 0;
     for (int k = 0; k < cnt; ++k) {
-      const int64_t b = entry_index(list[k]);
+      const uint32_t e = list[k];
+      const int64_t b = entry_index(e);
       double dx, dy, dz;
-      sep64(g, xa, ya, za, s.x[b], s.y[b], s.z[b], dx, dy, dz);
+      sep64(g, cell_a, e, xa, ya, za, s.x[b], s.y[b], s.z[b], dx, dy, dz);
       const double w = aux.vol[b] * wrow[k];
       const double wx = w * dx, wy = w * dy, wz = w * dz;
       t00 += wx * dx;
@@ -161,6 +195,8 @@ __global__ void __launch_bounds__(kThreads64) k_momentum64(const Grid* gp, State
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
        a += (int64_t)gridDim.x * blockDim.x) {
     const double xa = s.x[a], ya = s.y[a], za = s.z[a];
+    int cell_a[3];
+    unpack_cell(aux.cell3[a], cell_a[0], cell_a[1], cell_a[2]);
     const double vxa = s.vx[a], vya = s.vy[a], vza = s.vz[a];
     const double Xa = aux.X[a], ira = aux.inv_rho[a], ca = o.c[a];
     const double* Ca = o.iad + 6 * a;
@@ -170,9 +206,10 @@ __global__ void __launch_bounds__(kThreads64) k_momentum64(const Grid* gp, State
     const double* wrow = L.w + a * L.max_nb;
     double accx = 0, accy = 0, accz = 0, du = 0;
     for (int k = 0; k < cnt; ++k) {
-      const int64_t b = entry_index(list[k]);
+      const uint32_t e = list[k];
+      const int64_t b = entry_index(e);
       double dx, dy, dz;
-      sep64(g, xa, ya, za, s.x[b], s.y[b], s.z[b], dx, dy, dz);
+      sep64(g, cell_a, e, xa, ya, za, s.x[b], s.y[b], s.z[b], dx, dy, dz);
       const double r2 = dx * dx + dy * dy + dz * dz;
       const double Wa = wrow[k];
       const double tb = r2 * aux.hinv2[b];
@@ -216,6 +253,7 @@ __global__ void __launch_bounds__(kThreads64) k_momentum64(const Grid* gp, State
 
 inline Aux64 aux_of(sph_ctx* ctx) {
   Aux64 a;
+  a.cell3 = ctx->cell3;
   a.vol = ctx->vol;
   a.X = ctx->X;
   a.inv_rho = ctx->inv_rho;
