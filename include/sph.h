@@ -195,8 +195,13 @@ SPH_API int sph_step(sph_ctx* ctx, sph_state* state, double* dt_inout, sph_strea
 
 /* sph_step for callers whose state lives in HOST memory (pinned or pageable):
  * copies the state in, steps, copies the new state and the outputs back and
- * synchronises the stream.  dt_inout is a HOST pointer.  Uses device mirrors
- * owned by the context (allocated on first use). */
+ * synchronises the stream.  dt_inout is a HOST pointer.  Uses device mirrors,
+ * a second stream and events owned by the context (created on first use):
+ * velocities and the integrator history are copied in on the second stream
+ * while the sort and the neighbour search run, and m, id and du_prev are
+ * copied out as soon as the step has produced them, so pinned buffers let
+ * copies and kernels overlap.  The call returns after every copy has
+ * completed. */
 SPH_API int sph_step_host(sph_ctx* ctx, sph_state* host_state, double* dt_inout, sph_stream_t stream);
 
 /* Conservation sums of a state {Px, Py, Pz, E_kin, E_int, Lx, Ly, Lz}

@@ -238,22 +238,34 @@ void run_momentum(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
     sph::launch_momentum_f64(ctx, s, o, n, st);
 }
 
+// Step events per ring slot: marks 0..SPH_NSTAGE at the stage boundaries and
+// mark SPH_NSTAGE + 1 after the second gather part, which runs between the
+// search and density and is counted with the sort.
+constexpr int kProfMarks = SPH_NSTAGE + 2;
+constexpr int kMarkGatherB = SPH_NSTAGE + 1;
+
 inline void prof_mark(sph_ctx* ctx, int k, cudaStream_t st) {
-  if (ctx->prof) cudaEventRecord(ctx->prof_ev[ctx->prof_slot * (SPH_NSTAGE + 1) + k], st);
+  if (ctx->prof) cudaEventRecord(ctx->prof_ev[ctx->prof_slot * kProfMarks + k], st);
 }
 
 // Folds the recorded event sets into prof_ms (synchronises on them).
 int prof_fold(sph_ctx* ctx) {
   for (int slot = 0; slot < ctx->prof_slot; ++slot) {
-    cudaEvent_t* e = ctx->prof_ev + slot * (SPH_NSTAGE + 1);
+    cudaEvent_t* e = ctx->prof_ev + slot * kProfMarks;
     cudaError_t err = cudaEventSynchronize(e[SPH_NSTAGE]);
     if (err != cudaSuccess) return sph::cuda_fail(ctx, err, "profile events");
     for (int k = 0; k < SPH_NSTAGE; ++k) {
+      // density (stage 2) starts after the second gather part
+      const cudaEvent_t from = k == 2 ? e[kMarkGatherB] : e[k];
       float ms = 0.0f;
-      err = cudaEventElapsedTime(&ms, e[k], e[k + 1]);
+      err = cudaEventElapsedTime(&ms, from, e[k + 1]);
       if (err != cudaSuccess) return sph::cuda_fail(ctx, err, "profile events");
       ctx->prof_ms[k] += ms;
     }
+    float gb = 0.0f;  // the second gather part belongs to the sort
+    err = cudaEventElapsedTime(&gb, e[2], e[kMarkGatherB]);
+    if (err != cudaSuccess) return sph::cuda_fail(ctx, err, "profile events");
+    ctx->prof_ms[0] += gb;
     ctx->prof_steps += 1;
   }
   ctx->prof_slot = 0;
@@ -376,10 +388,13 @@ void sph_destroy(sph_ctx* ctx) {
   if (!ctx) return;
   cudaDeviceSynchronize();
   if (ctx->prof_ev) {
-    for (int k = 0; k < sph::kProfRing * (SPH_NSTAGE + 1); ++k)
+    for (int k = 0; k < sph::kProfRing * kProfMarks; ++k)
       if (ctx->prof_ev[k]) cudaEventDestroy(ctx->prof_ev[k]);
     free(ctx->prof_ev);
   }
+  if (ctx->hs_stream) cudaStreamDestroy(ctx->hs_stream);
+  for (cudaEvent_t ev : ctx->hs_ev)
+    if (ev) cudaEventDestroy(ev);
   free_all(ctx);
   free(ctx);
 }
@@ -483,15 +498,22 @@ int sph_step(sph_ctx* ctx, sph_state* state, double* dt_inout, sph_stream_t stre
   }
   prof_mark(ctx, 0, st);
   sph::launch_grid(ctx, in, n, st);
-  sph::launch_sort_gather(ctx, in, n, st);
+  sph::launch_sort(ctx, in, n, st);
+  if (ctx->hook_sorted) cudaEventRecord(ctx->hook_sorted, st);
   prof_mark(ctx, 1, st);
   sph::launch_find_neighbors(ctx, ctx->s, n, st);
   prof_mark(ctx, 2, st);
+  // velocities and integrator history: a host caller may still be copying
+  // them in while the search runs
+  if (ctx->hook_wait) cudaStreamWaitEvent(st, ctx->hook_wait, 0);
+  sph::launch_gather_b(ctx, in, n, st);
+  prof_mark(ctx, kMarkGatherB, st);
   run_density(ctx, ctx->s, o, n, st);
   prof_mark(ctx, 3, st);
   run_iad(ctx, ctx->s, o, n, st);
   prof_mark(ctx, 4, st);
   run_momentum(ctx, ctx->s, o, n, st);
+  if (ctx->hook_mom) cudaEventRecord(ctx->hook_mom, st);
   prof_mark(ctx, 5, st);
   sph::launch_timestep(ctx, ctx->s, o, n, dt_inout, st);
   prof_mark(ctx, 6, st);
@@ -511,13 +533,20 @@ int sph_step_host(sph_ctx* ctx, sph_state* hs, double* dt_inout, sph_stream_t st
   if (!dt_inout) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "dt_inout is NULL");
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = hs->n;
+  if (n == 0) return SPH_OK;  // nothing to advance; dt is left unchanged
   const int64_t nm = ctx->n_max;
   cudaError_t e = cudaSuccess;
   if (!ctx->hm_buf) {
     e = cudaMalloc((void**)&ctx->hm_buf, sizeof(double) * (size_t)nm * 26);
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->hm_id, sizeof(int64_t) * (size_t)nm);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->hs_stream, cudaStreamNonBlocking);
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+      e = cudaEventCreateWithFlags(&ctx->hs_ev[k], cudaEventDisableTiming);
     if (e != cudaSuccess) return sph::cuda_fail(ctx, e, "sph_step_host mirrors");
   }
+  cudaStream_t cs = ctx->hs_stream;
+  cudaEvent_t ev_start = ctx->hs_ev[0], ev_in = ctx->hs_ev[1], ev_sorted = ctx->hs_ev[2],
+              ev_mom = ctx->hs_ev[3], ev_done = ctx->hs_ev[4];
   sph_state ds;
   memset(&ds, 0, sizeof(ds));  // omega stays NULL: not mirrored
   double* base = ctx->hm_buf;
@@ -528,24 +557,59 @@ int sph_step_host(sph_ctx* ctx, sph_state* hs, double* dt_inout, sph_stream_t st
   ds.iad = base + (size_t)20 * nm;  // 6 * nm
   ds.id = ctx->hm_id;
   ds.n = n;
-  double* hin[13] = {hs->x, hs->y, hs->z, hs->vx, hs->vy, hs->vz, hs->h, hs->m, hs->u,
-                     hs->vxh, hs->vyh, hs->vzh, hs->du_prev};
-  double* din[13] = {ds.x, ds.y, ds.z, ds.vx, ds.vy, ds.vz, ds.h, ds.m, ds.u,
-                     ds.vxh, ds.vyh, ds.vzh, ds.du_prev};
   const size_t b = sizeof(double) * (size_t)n;
-  for (int k = 0; k < 13 && e == cudaSuccess; ++k)
-    e = cudaMemcpyAsync(din[k], hin[k], b, cudaMemcpyHostToDevice, st);
+  // Copies in: what the sort, search and density read on the caller's
+  // stream; velocities and the integrator history on the second stream,
+  // overlapping the sort and the search (the step waits for them before its
+  // second gather part).  The second stream starts after all earlier work of
+  // the caller's stream, so the device mirrors are free.
+  double* hin_a[6] = {hs->x, hs->y, hs->z, hs->h, hs->m, hs->u};
+  double* din_a[6] = {ds.x, ds.y, ds.z, ds.h, ds.m, ds.u};
+  double* hin_b[7] = {hs->vx, hs->vy, hs->vz, hs->vxh, hs->vyh, hs->vzh, hs->du_prev};
+  double* din_b[7] = {ds.vx, ds.vy, ds.vz, ds.vxh, ds.vyh, ds.vzh, ds.du_prev};
+  e = cudaEventRecord(ev_start, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_start, 0);
+  for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync(din_a[k], hin_a[k], b, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ds.id, hs->id, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->dt_dev, dt_inout, sizeof(double), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return sph::cuda_fail(ctx, e, "sph_step_host copy in");
+  for (int k = 0; k < 7 && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync(din_b[k], hin_b[k], b, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(ev_in, cs);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(cs);
+    return sph::cuda_fail(ctx, e, "sph_step_host copy in");
+  }
+  ctx->hook_wait = ev_in;
+  ctx->hook_sorted = ev_sorted;
+  ctx->hook_mom = ev_mom;
   rc = sph_step(ctx, &ds, ctx->dt_dev, stream);
-  if (rc != SPH_OK) return rc;
-  for (int k = 0; k < 13 && e == cudaSuccess; ++k)
-    e = cudaMemcpyAsync(hin[k], din[k], b, cudaMemcpyDeviceToHost, st);
+  ctx->hook_wait = ctx->hook_sorted = ctx->hook_mom = nullptr;
+  if (rc != SPH_OK) {
+    cudaStreamSynchronize(cs);
+    return rc;
+  }
+  // Copies out on the second stream as soon as their values are final: m and
+  // id after the sort (the sorted scratch holds what the update writes back),
+  // du_prev = du after the momentum pass.  Their copies in (earlier on the
+  // same stream or before the sort) have completed by then.
+  e = cudaStreamWaitEvent(cs, ev_sorted, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hs->m, ctx->s.m, b, cudaMemcpyDeviceToHost, cs);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(hs->id, ds.id, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(hs->id, ctx->s.id, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost,
+                        cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_mom, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hs->du_prev, ds.du, b, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(ev_done, cs);
+  // the rest after the update, on the caller's stream
+  double* hout_s[10] = {hs->x, hs->y, hs->z, hs->vx, hs->vy, hs->vz, hs->vxh, hs->vyh, hs->vzh,
+                        hs->u};
+  double* dout_s[10] = {ds.x, ds.y, ds.z, ds.vx, ds.vy, ds.vz, ds.vxh, ds.vyh, ds.vzh, ds.u};
+  for (int k = 0; k < 10 && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync(hout_s[k], dout_s[k], b, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hs->h, ds.h, b, cudaMemcpyDeviceToHost, st);
   double* hout[7] = {hs->rho, hs->p, hs->c, hs->ax, hs->ay, hs->az, hs->du};
   double* dout[7] = {ds.rho, ds.p, ds.c, ds.ax, ds.ay, ds.az, ds.du};
   for (int k = 0; k < 7 && e == cudaSuccess; ++k)
@@ -554,8 +618,12 @@ int sph_step_host(sph_ctx* ctx, sph_state* hs, double* dt_inout, sph_stream_t st
     e = cudaMemcpyAsync(hs->iad, ds.iad, 6 * b, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dt_inout, ctx->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_done, 0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return sph::cuda_fail(ctx, e, "sph_step_host copy out");
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(cs);
+    return sph::cuda_fail(ctx, e, "sph_step_host copy out");
+  }
   return SPH_OK;
 }
 
@@ -607,7 +675,7 @@ int sph_stats(sph_ctx* ctx, uint64_t* out) {
 int sph_profile(sph_ctx* ctx, int enable) {
   if (!ctx) return SPH_ERR_INVALID_ARG;
   if (enable && !ctx->prof_ev) {
-    const int total = sph::kProfRing * (SPH_NSTAGE + 1);
+    const int total = sph::kProfRing * kProfMarks;
     ctx->prof_ev = (cudaEvent_t*)calloc(total, sizeof(cudaEvent_t));
     if (!ctx->prof_ev) return sph::set_error(ctx, SPH_ERR_OOM, "profile events");
     for (int k = 0; k < total; ++k) {

@@ -127,7 +127,7 @@ struct sph_ctx {
   // per-stage timing (sph_profile): a ring of event sets, one per step
   int prof;
   int prof_slot;
-  cudaEvent_t* prof_ev;   // kProfRing * (SPH_NSTAGE + 1)
+  cudaEvent_t* prof_ev;   // kProfRing * (SPH_NSTAGE + 2)
   double prof_ms[SPH_NSTAGE];
   int64_t prof_steps;
 
@@ -137,6 +137,12 @@ struct sph_ctx {
 
   // host-step mirrors
   double* hm_buf;       // device mirror storage for sph_step_host
+  cudaStream_t hs_stream;  // sph_step_host: second stream for the overlapped copies
+  cudaEvent_t hs_ev[5];    // sph_step_host: start, inputs in, sorted, momentum done, copies done
+  // set by sph_step_host around its sph_step call: wait for hook_wait before
+  // the second gather part; record hook_sorted after the sort and hook_mom
+  // after the momentum pass
+  cudaEvent_t hook_wait, hook_sorted, hook_mom;
   int64_t* hm_id;
   int64_t hm_n;
 };
@@ -152,6 +158,10 @@ int cuda_fail(sph_ctx* ctx, cudaError_t e, const char* what);
 void launch_grid(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st);
 // Counting sort by Morton cell code, deterministic order within cells; gathers
 // `in` into the sorted scratch ctx->s and builds pos32 / cell3 / cell_of.
+// Sort and gather: launch_sort (cells, order, first gather part) then
+// launch_gather_b (velocities, integrator history); launch_sort_gather does both.
+void launch_sort(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st);
+void launch_gather_b(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st);
 void launch_sort_gather(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st);
 // Recompute pos32 / cell3 for an already-sorted state (no permutation).
 void launch_copy_state(const StateView& dst, const StateView& src, int64_t n, cudaStream_t st,

@@ -12,8 +12,10 @@
 //                  list of occupied cells in Morton order
 //   k_scatter      particle -> provisional sorted position
 //   k_cell_order   per cell: rank members by source index (deterministic order)
-//   k_gather       copy the persistent state into sorted scratch, and build
-//                  the FP32 cell-relative positions
+//   k_gather_a     copy positions, h, m, u and id into sorted scratch, and
+//                  build the FP32 cell-relative positions
+//   k_gather_b     copy velocities and the integrator history (first read by
+//                  the momentum pass)
 #include <cuda_runtime.h>
 
 #include "sph_device.cuh"
@@ -324,9 +326,11 @@ __device__ __forceinline__ uint32_t compact3(uint32_t v) {
   return v;
 }
 
-__global__ void k_gather(StateView in, StateView out, int64_t n, const Grid* gp,
-                         const int32_t* perm, const uint32_t* code, float4* pos32,
-                         int32_t* cell3, float4* rec_d, float4* rec_m) {
+// Gather, first part: what the search, density and IAD read (positions, h,
+// m, u, id and the FP32 cell-relative positions).
+__global__ void k_gather_a(StateView in, StateView out, int64_t n, const Grid* gp,
+                           const int32_t* perm, const uint32_t* code, float4* pos32,
+                           int32_t* cell3, float4* rec_d) {
   const Grid g = *gp;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
@@ -336,16 +340,9 @@ __global__ void k_gather(StateView in, StateView out, int64_t n, const Grid* gp,
     out.y[p] = y;
     out.z[p] = z;
     out.h[p] = h;
-    const double vx = in.vx[s], vy = in.vy[s], vz = in.vz[s], m = in.m[s];
-    out.vx[p] = vx;
-    out.vy[p] = vy;
-    out.vz[p] = vz;
-    out.vxh[p] = in.vxh[s];
-    out.vyh[p] = in.vyh[s];
-    out.vzh[p] = in.vzh[s];
+    const double m = in.m[s];
     out.m[p] = m;
     out.u[p] = in.u[s];
-    out.du_prev[p] = in.du_prev[s];
     out.id[p] = in.id[s];
     uint32_t c = code[s];
     int ix = compact3(c), iy = compact3(c >> 1), iz = compact3(c >> 2);
@@ -355,7 +352,26 @@ __global__ void k_gather(StateView in, StateView out, int64_t n, const Grid* gp,
     pos32[p] = make_float4(ox, oy, oz, (float)h);
     cell3[p] = pack_cell(ix, iy, iz);
     rec_d[p] = make_float4(ox, oy, oz, (float)m);
-    rec_m[5 * p + 1] = make_float4((float)vx, (float)vy, (float)vz, (float)m);
+  }
+}
+
+// Gather, second part: velocities and the integrator history, first read by
+// the momentum pass (so a caller may still be copying them in while the
+// search runs).
+__global__ void k_gather_b(StateView in, StateView out, int64_t n, const int32_t* perm,
+                           float4* rec_m) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int64_t s = perm[p];
+    const double vx = in.vx[s], vy = in.vy[s], vz = in.vz[s];
+    out.vx[p] = vx;
+    out.vy[p] = vy;
+    out.vz[p] = vz;
+    out.vxh[p] = in.vxh[s];
+    out.vyh[p] = in.vyh[s];
+    out.vzh[p] = in.vzh[s];
+    out.du_prev[p] = in.du_prev[s];
+    rec_m[5 * p + 1] = make_float4((float)vx, (float)vy, (float)vz, (float)out.m[p]);
   }
 }
 
@@ -378,7 +394,7 @@ void launch_grid(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st) 
   ctx->launches += 2;
 }
 
-void launch_sort_gather(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st) {
+void launch_sort(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st) {
   int pb = grid_for(n, 256, ctx->sm_count);
   k_cell_count<<<pb, 256, 0, st>>>(in, n, ctx->grid, ctx->tbl_count, ctx->code, ctx->slot);
   const int scan_blocks = kMaxTable / kScanItems;
@@ -390,9 +406,20 @@ void launch_sort_gather(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream
   k_cell_order<<<ctx->sm_count * 8, 256, 0, st>>>(ctx->grid, ctx->occ, ctx->tbl_start,
                                                   ctx->tbl_count, ctx->perm_tmp, ctx->perm,
                                                   ctx->cell_of);
-  k_gather<<<pb, 256, 0, st>>>(in, ctx->s, n, ctx->grid, ctx->perm, ctx->code, ctx->pos32,
-                               ctx->cell3, ctx->rec_d, ctx->rec_m);
+  k_gather_a<<<pb, 256, 0, st>>>(in, ctx->s, n, ctx->grid, ctx->perm, ctx->code, ctx->pos32,
+                                 ctx->cell3, ctx->rec_d);
   ctx->launches += 7;
+}
+
+void launch_gather_b(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st) {
+  k_gather_b<<<grid_for(n, 256, ctx->sm_count), 256, 0, st>>>(in, ctx->s, n, ctx->perm,
+                                                              ctx->rec_m);
+  ctx->launches += 1;
+}
+
+void launch_sort_gather(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st) {
+  launch_sort(ctx, in, n, st);
+  launch_gather_b(ctx, in, n, st);
 }
 
 void launch_copy_state(const StateView& dst, const StateView& src, int64_t n, cudaStream_t st,
