@@ -498,7 +498,7 @@ int sph_step(sph_ctx* ctx, sph_state* state, double* dt_inout, sph_stream_t stre
   }
   prof_mark(ctx, 0, st);
   sph::launch_grid(ctx, in, n, st);
-  sph::launch_sort(ctx, in, n, st);
+  sph::launch_sort(ctx, in, n, st, ctx->hook_wait_a);
   if (ctx->hook_sorted) cudaEventRecord(ctx->hook_sorted, st);
   prof_mark(ctx, 1, st);
   sph::launch_find_neighbors(ctx, ctx->s, n, st);
@@ -540,13 +540,13 @@ int sph_step_host(sph_ctx* ctx, sph_state* hs, double* dt_inout, sph_stream_t st
     e = cudaMalloc((void**)&ctx->hm_buf, sizeof(double) * (size_t)nm * 26);
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->hm_id, sizeof(int64_t) * (size_t)nm);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->hs_stream, cudaStreamNonBlocking);
-    for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
       e = cudaEventCreateWithFlags(&ctx->hs_ev[k], cudaEventDisableTiming);
     if (e != cudaSuccess) return sph::cuda_fail(ctx, e, "sph_step_host mirrors");
   }
   cudaStream_t cs = ctx->hs_stream;
-  cudaEvent_t ev_start = ctx->hs_ev[0], ev_in = ctx->hs_ev[1], ev_sorted = ctx->hs_ev[2],
-              ev_mom = ctx->hs_ev[3], ev_done = ctx->hs_ev[4];
+  cudaEvent_t ev_start = ctx->hs_ev[0], ev_in_a = ctx->hs_ev[1], ev_in = ctx->hs_ev[2],
+              ev_sorted = ctx->hs_ev[3], ev_mom = ctx->hs_ev[4], ev_done = ctx->hs_ev[5];
   sph_state ds;
   memset(&ds, 0, sizeof(ds));  // omega stays NULL: not mirrored
   double* base = ctx->hm_buf;
@@ -558,23 +558,27 @@ int sph_step_host(sph_ctx* ctx, sph_state* hs, double* dt_inout, sph_stream_t st
   ds.id = ctx->hm_id;
   ds.n = n;
   const size_t b = sizeof(double) * (size_t)n;
-  // Copies in: what the sort, search and density read on the caller's
-  // stream; velocities and the integrator history on the second stream,
-  // overlapping the sort and the search (the step waits for them before its
-  // second gather part).  The second stream starts after all earlier work of
-  // the caller's stream, so the device mirrors are free.
-  double* hin_a[6] = {hs->x, hs->y, hs->z, hs->h, hs->m, hs->u};
-  double* din_a[6] = {ds.x, ds.y, ds.z, ds.h, ds.m, ds.u};
+  // Copies in: x, y, z, h (read by the cell keys) on the caller's stream;
+  // m, u and id on the second stream, overlapping the cell keys and order
+  // (the step waits for them before its first gather part); velocities and
+  // the integrator history after them, overlapping the search (waited for
+  // before the second gather part).  The second stream starts after all
+  // earlier work of the caller's stream, so the device mirrors are free.
+  double* hin_a[4] = {hs->x, hs->y, hs->z, hs->h};
+  double* din_a[4] = {ds.x, ds.y, ds.z, ds.h};
   double* hin_b[7] = {hs->vx, hs->vy, hs->vz, hs->vxh, hs->vyh, hs->vzh, hs->du_prev};
   double* din_b[7] = {ds.vx, ds.vy, ds.vz, ds.vxh, ds.vyh, ds.vzh, ds.du_prev};
   e = cudaEventRecord(ev_start, st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_start, 0);
-  for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k)
     e = cudaMemcpyAsync(din_a[k], hin_a[k], b, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ds.id, hs->id, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->dt_dev, dt_inout, sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ds.m, hs->m, b, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ds.u, hs->u, b, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ds.id, hs->id, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(ev_in_a, cs);
   for (int k = 0; k < 7 && e == cudaSuccess; ++k)
     e = cudaMemcpyAsync(din_b[k], hin_b[k], b, cudaMemcpyHostToDevice, cs);
   if (e == cudaSuccess) e = cudaEventRecord(ev_in, cs);
@@ -582,11 +586,12 @@ int sph_step_host(sph_ctx* ctx, sph_state* hs, double* dt_inout, sph_stream_t st
     cudaStreamSynchronize(cs);
     return sph::cuda_fail(ctx, e, "sph_step_host copy in");
   }
+  ctx->hook_wait_a = ev_in_a;
   ctx->hook_wait = ev_in;
   ctx->hook_sorted = ev_sorted;
   ctx->hook_mom = ev_mom;
   rc = sph_step(ctx, &ds, ctx->dt_dev, stream);
-  ctx->hook_wait = ctx->hook_sorted = ctx->hook_mom = nullptr;
+  ctx->hook_wait_a = ctx->hook_wait = ctx->hook_sorted = ctx->hook_mom = nullptr;
   if (rc != SPH_OK) {
     cudaStreamSynchronize(cs);
     return rc;
@@ -594,7 +599,7 @@ int sph_step_host(sph_ctx* ctx, sph_state* hs, double* dt_inout, sph_stream_t st
   // Copies out on the second stream as soon as their values are final: m and
   // id after the sort (the sorted scratch holds what the update writes back),
   // du_prev = du after the momentum pass.  Their copies in (earlier on the
-  // same stream or before the sort) have completed by then.
+  // same stream) have completed by then.
   e = cudaStreamWaitEvent(cs, ev_sorted, 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(hs->m, ctx->s.m, b, cudaMemcpyDeviceToHost, cs);
   if (e == cudaSuccess)

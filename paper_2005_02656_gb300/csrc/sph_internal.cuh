@@ -138,11 +138,11 @@ struct sph_ctx {
   // host-step mirrors
   double* hm_buf;       // device mirror storage for sph_step_host
   cudaStream_t hs_stream;  // sph_step_host: second stream for the overlapped copies
-  cudaEvent_t hs_ev[5];    // sph_step_host: start, inputs in, sorted, momentum done, copies done
-  // set by sph_step_host around its sph_step call: wait for hook_wait before
-  // the second gather part; record hook_sorted after the sort and hook_mom
-  // after the momentum pass
-  cudaEvent_t hook_wait, hook_sorted, hook_mom;
+  cudaEvent_t hs_ev[6];    // sph_step_host: start, inputs in (2), sorted, momentum done, copies done
+  // set by sph_step_host around its sph_step call: wait for hook_wait_a
+  // before the first gather part and hook_wait before the second; record
+  // hook_sorted after the sort and hook_mom after the momentum pass
+  cudaEvent_t hook_wait_a, hook_wait, hook_sorted, hook_mom;
   int64_t* hm_id;
   int64_t hm_n;
 };
@@ -160,7 +160,10 @@ void launch_grid(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st);
 // `in` into the sorted scratch ctx->s and builds pos32 / cell3 / cell_of.
 // Sort and gather: launch_sort (cells, order, first gather part) then
 // launch_gather_b (velocities, integrator history); launch_sort_gather does both.
-void launch_sort(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st);
+// wait_gather (may be null): an event the first gather part waits for (the
+// cell keys and order only read x, y, z and h)
+void launch_sort(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st,
+                 cudaEvent_t wait_gather = nullptr);
 void launch_gather_b(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st);
 void launch_sort_gather(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st);
 // Recompute pos32 / cell3 for an already-sorted state (no permutation).

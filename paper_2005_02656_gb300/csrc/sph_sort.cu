@@ -394,7 +394,8 @@ void launch_grid(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st) 
   ctx->launches += 2;
 }
 
-void launch_sort(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st) {
+void launch_sort(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st,
+                 cudaEvent_t wait_gather) {
   int pb = grid_for(n, 256, ctx->sm_count);
   k_cell_count<<<pb, 256, 0, st>>>(in, n, ctx->grid, ctx->tbl_count, ctx->code, ctx->slot);
   const int scan_blocks = kMaxTable / kScanItems;
@@ -406,6 +407,7 @@ void launch_sort(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st) 
   k_cell_order<<<ctx->sm_count * 8, 256, 0, st>>>(ctx->grid, ctx->occ, ctx->tbl_start,
                                                   ctx->tbl_count, ctx->perm_tmp, ctx->perm,
                                                   ctx->cell_of);
+  if (wait_gather) cudaStreamWaitEvent(st, wait_gather, 0);
   k_gather_a<<<pb, 256, 0, st>>>(in, ctx->s, n, ctx->grid, ctx->perm, ctx->code, ctx->pos32,
                                  ctx->cell3, ctx->rec_d);
   ctx->launches += 7;
