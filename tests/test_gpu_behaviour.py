@@ -112,22 +112,29 @@ def test_conservation_to_rounding_common_h():
     sim.close()
 
 
-def test_host_step_equals_device_step():
-    """sph_step_host on pinned host arrays gives the device step's results."""
+@pytest.mark.parametrize("precision,side", [("fp32_mixed", 16), ("fp32_mixed", 27), ("fp64", 19)])
+def test_host_step_equals_device_step(precision, side):
+    """sph_step_host on pinned host arrays gives the device step's results,
+    step after step: its copies run on two streams (positions first, m, u, id
+    and then the velocities and integrator history while the sort and search
+    run; m, id and du_prev copied out early), so every field is checked."""
     from paper_2005_02656_gb300 import HostStepper, Params
-    s = sph_inputs.jittered_box(16, seed_index=46, vel_sigma=0.1)
-    dev = _sim(s, precision="fp32_mixed")
-    dev.step(2)
+    s = sph_inputs.jittered_box(side, seed_index=46, vel_sigma=0.1)
+    steps = 3
+    dev = _sim(s, precision=precision)
+    dev.step(steps)
     d = dev.to_numpy()
     dev.close()
     hs = HostStepper(s, Params(box_lo=s["lo"], box_hi=s["hi"], periodic=s["periodic"],
-                               precision="fp32_mixed"), outputs=True)
-    hs.step()
-    hs.step()
+                               precision=precision), outputs=True)
+    for _ in range(steps):
+        hs.step()
     h = {k: v.numpy() for k, v in hs.h.items()}
     order = np.argsort(h["id"])
-    for k in ("x", "y", "z", "vx", "u", "h", "rho", "ax", "du"):
-        np.testing.assert_array_equal(h[k][order], d[k])
+    np.testing.assert_array_equal(h["id"][order], np.arange(side ** 3))
+    for k in ("x", "y", "z", "vx", "vy", "vz", "vxh", "vyh", "vzh", "u", "du_prev", "h", "m",
+              "rho", "ax", "du"):
+        np.testing.assert_array_equal(h[k][order], d[k], err_msg=k)
     hs.close()
 
 
