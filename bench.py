@@ -554,7 +554,26 @@ def cpu_baseline(max_seconds=20.0, max_steps=5):
                      f"(outer lattice {SAMPLE_NX}, {n} particles), FP64, OpenMP",
            "host": host_cpu()}
     out["small_box"] = oracle_threads_sample()
+    out["square_patch"] = oracle_square_patch_sample()
     return out
+
+
+def oracle_square_patch_sample():
+    """One full oracle step of the 10^6-particle rotating square patch (x, y
+    open, z periodic) on all cores."""
+    import numpy as np
+
+    import oracle
+    import sph_inputs
+    s = sph_inputs.square_patch(100, shuffle=False)
+    n = s["x"].shape[0]
+    box = oracle.Box(s["lo"], s["hi"], s["periodic"])
+    t0 = time.perf_counter()
+    rc, _, out = oracle.step(box, s, oracle.Params(), 0.0)
+    el = time.perf_counter() - t0
+    return {"workload": f"square_patch_{n}", "steps": 1, "threads": oracle.num_threads(),
+            "value": n / el, "unit": UNIT,
+            "neighbor_pairs_per_s": int(np.asarray(out["nn"]).sum()) / el, "rc": rc}
 
 
 def host_cpu():
