@@ -136,6 +136,7 @@ struct sph_ctx {
   size_t grav_bytes;
 
   // host-step mirrors
+  int find_blocks;      // persistent CTAs of the neighbour search (occupancy x SMs)
   double* hm_buf;       // device mirror storage for sph_step_host
   cudaStream_t hs_stream;  // sph_step_host: second stream for the overlapped copies
   cudaEvent_t hs_ev[6];    // sph_step_host: start, inputs in (2), sorted, momentum done, copies done

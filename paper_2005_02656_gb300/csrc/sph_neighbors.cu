@@ -69,14 +69,12 @@ __global__ void k_export(int64_t n, const int32_t* nn, const uint32_t* nbr, int 
   }
 }
 
-int g_find_blocks = 0;
-
 }  // namespace
 
 void launch_find_neighbors(sph_ctx* ctx, const StateView& s, int64_t n, cudaStream_t st) {
   (void)n;
   const size_t smem = kFindWarps * sizeof(FindWarpSmem);
-  if (!g_find_blocks) {
+  if (!ctx->find_blocks) {  // once per context, on its device
     int per_sm = 0;
     cudaFuncSetAttribute(k_find_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
@@ -84,12 +82,12 @@ void launch_find_neighbors(sph_ctx* ctx, const StateView& s, int64_t n, cudaStre
                          (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_find_tile<false>, kFindThreads,
                                                   smem);
-    g_find_blocks = (per_sm > 0 ? per_sm : 1) * ctx->sm_count;
+    ctx->find_blocks = (per_sm > 0 ? per_sm : 1) * ctx->sm_count;
   }
-  k_find_tile<false><<<g_find_blocks, kFindThreads, smem, st>>>(
+  k_find_tile<false><<<ctx->find_blocks, kFindThreads, smem, st>>>(
       ctx->grid, s, ctx->pos32, ctx->occ, ctx->tbl_start, ctx->tbl_count, ctx->nn, ctx->nbr,
       ctx->prm.max_nb, ctx->err, ctx->stats);
-  k_find_tile<true><<<g_find_blocks, kFindThreads, smem, st>>>(
+  k_find_tile<true><<<ctx->find_blocks, kFindThreads, smem, st>>>(
       ctx->grid, s, ctx->pos32, ctx->occ, ctx->tbl_start, ctx->tbl_count, ctx->nn, ctx->nbr,
       ctx->prm.max_nb, ctx->err, ctx->stats);
   ctx->launches += 2;
