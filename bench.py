@@ -230,18 +230,18 @@ def run_gpu(args, world, rank, local):
         l0 = sim.launch_count()
         barrier()
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         tw0 = time.time()
-        e0.record(stream)
-        for _ in range(steps):
+        ev[0].record(stream)
+        for i in range(steps):
             sim.step()
-        e1.record(stream)
+            ev[i + 1].record(stream)
         torch.cuda.synchronize()
         tw1 = time.time()
         barrier()
         windows[key] = (tw0, tw1)
-        ms = e0.elapsed_time(e1) / steps
+        ms = ev[0].elapsed_time(ev[steps]) / steps
+        ms_median = statistics.median(ev[i].elapsed_time(ev[i + 1]) for i in range(steps))
         stages, nsteps = sim.stage_times()
         st1 = sim.stats()
         launches = sim.launch_count() - l0
@@ -254,7 +254,8 @@ def run_gpu(args, world, rank, local):
         pairs = (st1["pairs"] - st0["pairs"]) / steps
         cands = (st1["candidates"] - st0["candidates"]) / steps
         exact = (st1["exact_tests"] - st0["exact_tests"]) / steps
-        return {"ms": ms, "stages": {k: v / max(nsteps, 1) for k, v in stages.items()},
+        return {"ms": ms, "ms_median": ms_median,
+                "stages": {k: v / max(nsteps, 1) for k, v in stages.items()},
                 "pairs": pairs, "candidates": cands, "exact_tests": exact, "launches": launches,
                 "flags": flags, "dt": float(diag[8]),
                 "conservation": conservation(d0, d1, steps)}
@@ -650,6 +651,7 @@ def main():
                    "neighbors_target": 100, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "no flush: state + lists ~7 GB >> 129 MB L2"},
         "neighbor_pairs_per_s": r32["pairs"] * world / (ms * 1e-3),
+        "ms_per_step_median": r32["ms_median"],
         "stages_ms": r32["stages"],
         "roofline": roofline(r32, n, "fp32_mixed"),
         "step_roofline": step_roofline(r32, n, "fp32_mixed", ms),
@@ -663,6 +665,7 @@ def main():
     if r64 is not None:
         ms64 = res["ms64"]
         line["fp64"] = {"value": whole_job_rate(n, world, ms64), "unit": UNIT, "ms_per_step": ms64,
+                        "ms_per_step_median": r64["ms_median"],
                         "neighbor_pairs_per_s": r64["pairs"] * world / (ms64 * 1e-3),
                         "stages_ms": r64["stages"], "roofline": roofline(r64, n, "fp64"),
                         "step_roofline": step_roofline(r64, n, "fp64", ms64),
