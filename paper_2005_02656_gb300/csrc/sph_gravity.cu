@@ -415,11 +415,15 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_walk32(const Node* nodes,
         const float inv_R = rsqrtf(R2);
         const float Rf = R2 * inv_R;
         const float size = q1.z, mb = k32.mb;
-        // the box: certainly outside, certainly inside, or within mb of a face
-        const bool out_c = ph[0] < blo.x - mb || ph[0] > bhi.x + mb || ph[1] < blo.y - mb ||
-                           ph[1] > bhi.y + mb || ph[2] < blo.z - mb || ph[2] > bhi.z + mb;
-        const bool in_c = ph[0] >= blo.x + mb && ph[0] <= bhi.x - mb && ph[1] >= blo.y + mb &&
-                          ph[1] <= bhi.y - mb && ph[2] >= blo.z + mb && ph[2] <= bhi.z - mb;
+        // the box: certainly outside, certainly inside, or within mb of a face.
+        // dmin is the smallest signed distance of the particle to a face
+        // (negative outside); its own rounding (<= L 2^-24) adds to the
+        // stored faces' and the head's, all within mb = 4 L 2^-24.
+        const float dmin =
+            fminf(fminf(fminf(ph[0] - blo.x, bhi.x - ph[0]), fminf(ph[1] - blo.y, bhi.y - ph[1])),
+                  fminf(ph[2] - blo.z, bhi.z - ph[2]));
+        const bool out_c = dmin < -mb;
+        const bool in_c = dmin >= mb;
         const bool acc_c = size * (1.f + 1e-6f) < k32.th * (Rf * (1.f - 2e-6f) - k32.aL);
         const bool rej_c = size * (1.f - 1e-6f) > k32.th * (Rf * (1.f + 2e-6f) + k32.aL);
         bool accept;
