@@ -154,3 +154,22 @@ def test_autotune_picks_a_configuration():
     ens.step(1)
     assert ens.error_word() == 0
     ens.close()
+
+
+def test_gradh_boxes_match_their_single_box_runs():
+    """With the grad-h terms on (Omega in X = P / (Omega rho^2)), each box of
+    the ensemble still equals its own single-box FP32-mixed run bit for bit."""
+    from paper_2005_02656_gb300 import Ensemble, Params, SphSim
+    boxes = _boxes()[:4]
+    ens = Ensemble(boxes, Params(precision="fp32_mixed", gradh=1))
+    ens.step(2)
+    assert ens.error_word() == 0
+    for b, (s, alpha) in enumerate(boxes):
+        sim = SphSim(s, precision="fp32_mixed", alpha=alpha, gradh=1)
+        sim.step(2)
+        ref = sim.to_numpy()
+        got = ens.box_numpy(b)
+        for k in ("x", "vx", "u", "h", "rho", "ax", "du"):
+            np.testing.assert_array_equal(got[k], ref[k], err_msg=f"box {b} field {k}")
+        sim.close()
+    ens.close()

@@ -36,12 +36,12 @@ def _by_id(s):
     return {k: (v[order] if isinstance(v, np.ndarray) else v) for k, v in s.items()}
 
 
-@pytest.mark.parametrize("theta", [0.0, 0.5, 0.8])
-def test_tree_matches_oracle_tree(theta):
+@pytest.mark.parametrize("theta,eps", [(0.0, EPS), (0.5, EPS), (0.8, EPS), (0.5, 0.0)])
+def test_tree_matches_oracle_tree(theta, eps):
     s = sph_inputs.uniform_sphere(22, seed_index=81)
-    g, counts = _gpu(s, theta)
+    g, counts = _gpu(s, theta, eps=eps)
     # the oracle sees the arrays in the order the GPU received them
-    rc, ref, st = oracle.gravity_tree(s, eps=EPS, theta=theta)
+    rc, ref, st = oracle.gravity_tree(s, eps=eps, theta=theta)
     assert rc == 0
     ref_by_id = np.empty_like(ref)
     ref_by_id[s["id"]] = ref
@@ -50,11 +50,11 @@ def test_tree_matches_oracle_tree(theta):
     np.testing.assert_array_equal(counts, st)
 
 
-@pytest.mark.parametrize("theta", [0.0, 0.5, 0.8])
-def test_fp32_matches_oracle_tree(theta):
+@pytest.mark.parametrize("theta,eps", [(0.0, EPS), (0.5, EPS), (0.8, EPS), (0.5, 0.0)])
+def test_fp32_matches_oracle_tree(theta, eps):
     s = sph_inputs.uniform_sphere(22, seed_index=81)
-    g, counts = _gpu(s, theta, precision="fp32_mixed")
-    rc, ref, st = oracle.gravity_tree(s, eps=EPS, theta=theta)
+    g, counts = _gpu(s, theta, eps=eps, precision="fp32_mixed")
+    rc, ref, st = oracle.gravity_tree(s, eps=eps, theta=theta)
     assert rc == 0
     ref_by_id = np.empty_like(ref)
     ref_by_id[s["id"]] = ref
