@@ -200,8 +200,10 @@ SPH_API int sph_step(sph_ctx* ctx, sph_state* state, double* dt_inout, sph_strea
  * velocities and the integrator history are copied in on the second stream
  * while the sort and the neighbour search run, and m, id and du_prev are
  * copied out as soon as the step has produced them, so pinned buffers let
- * copies and kernels overlap.  The call returns after every copy has
- * completed. */
+ * copies and kernels overlap.  When x, y, z, vx, vy, vz, vxh, vyh, vzh, u and h
+ * are pinned (page-locked, device-accessible) host memory, the update kernel
+ * writes the new state straight into them; otherwise they are copied back.
+ * The call returns after every copy and write has completed. */
 SPH_API int sph_step_host(sph_ctx* ctx, sph_state* host_state, double* dt_inout, sph_stream_t stream);
 
 /* Conservation sums of a state {Px, Py, Pz, E_kin, E_int, Lx, Ly, Lz}

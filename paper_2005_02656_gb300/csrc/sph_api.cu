@@ -517,7 +517,8 @@ int sph_step(sph_ctx* ctx, sph_state* state, double* dt_inout, sph_stream_t stre
   prof_mark(ctx, 5, st);
   sph::launch_timestep(ctx, ctx->s, o, n, dt_inout, st);
   prof_mark(ctx, 6, st);
-  sph::launch_update(ctx, ctx->s, o, in, n, dt_inout, st);
+  sph::launch_update(ctx, ctx->s, o, ctx->hook_update_dst ? *ctx->hook_update_dst : in, n,
+                     dt_inout, st);
   prof_mark(ctx, 7, st);
   if (ctx->prof) ctx->prof_slot += 1;
   rc = finish(ctx, "sph_step");
@@ -586,12 +587,45 @@ int sph_step_host(sph_ctx* ctx, sph_state* hs, double* dt_inout, sph_stream_t st
     cudaStreamSynchronize(cs);
     return sph::cuda_fail(ctx, e, "sph_step_host copy in");
   }
+  // Pinned caller arrays can be written by the update kernel itself, so the
+  // new state crosses the host link while the update runs instead of after
+  // it.  Pageable arrays take the copy path.
+  double* hout_s[11] = {hs->x, hs->y, hs->z, hs->vx, hs->vy, hs->vz, hs->vxh, hs->vyh, hs->vzh,
+                        hs->u, hs->h};
+  double* zc[11];
+  bool direct = true;
+  for (int k = 0; k < 11 && direct; ++k) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, hout_s[k]) != cudaSuccess || at.type != cudaMemoryTypeHost ||
+        !at.devicePointer)
+      direct = false;
+    else
+      zc[k] = (double*)at.devicePointer;
+  }
+  cudaGetLastError();  // a failed attribute query is not an error of this call
+  sph::StateView zdst;
+  memset(&zdst, 0, sizeof(zdst));
+  if (direct) {
+    zdst.x = zc[0];
+    zdst.y = zc[1];
+    zdst.z = zc[2];
+    zdst.vx = zc[3];
+    zdst.vy = zc[4];
+    zdst.vz = zc[5];
+    zdst.vxh = zc[6];
+    zdst.vyh = zc[7];
+    zdst.vzh = zc[8];
+    zdst.u = zc[9];
+    zdst.h = zc[10];
+  }
   ctx->hook_wait_a = ev_in_a;
   ctx->hook_wait = ev_in;
   ctx->hook_sorted = ev_sorted;
   ctx->hook_mom = ev_mom;
+  ctx->hook_update_dst = direct ? &zdst : nullptr;
   rc = sph_step(ctx, &ds, ctx->dt_dev, stream);
   ctx->hook_wait_a = ctx->hook_wait = ctx->hook_sorted = ctx->hook_mom = nullptr;
+  ctx->hook_update_dst = nullptr;
   if (rc != SPH_OK) {
     cudaStreamSynchronize(cs);
     return rc;
@@ -608,13 +642,11 @@ int sph_step_host(sph_ctx* ctx, sph_state* hs, double* dt_inout, sph_stream_t st
   if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_mom, 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(hs->du_prev, ds.du, b, cudaMemcpyDeviceToHost, cs);
   if (e == cudaSuccess) e = cudaEventRecord(ev_done, cs);
-  // the rest after the update, on the caller's stream
-  double* hout_s[10] = {hs->x, hs->y, hs->z, hs->vx, hs->vy, hs->vz, hs->vxh, hs->vyh, hs->vzh,
-                        hs->u};
-  double* dout_s[10] = {ds.x, ds.y, ds.z, ds.vx, ds.vy, ds.vz, ds.vxh, ds.vyh, ds.vzh, ds.u};
-  for (int k = 0; k < 10 && e == cudaSuccess; ++k)
+  // the rest after the update, on the caller's stream (already written by
+  // the update kernel when the arrays are pinned)
+  double* dout_s[11] = {ds.x, ds.y, ds.z, ds.vx, ds.vy, ds.vz, ds.vxh, ds.vyh, ds.vzh, ds.u, ds.h};
+  for (int k = 0; k < 11 && e == cudaSuccess && !direct; ++k)
     e = cudaMemcpyAsync(hout_s[k], dout_s[k], b, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hs->h, ds.h, b, cudaMemcpyDeviceToHost, st);
   double* hout[7] = {hs->rho, hs->p, hs->c, hs->ax, hs->ay, hs->az, hs->du};
   double* dout[7] = {ds.rho, ds.p, ds.c, ds.ax, ds.ay, ds.az, ds.du};
   for (int k = 0; k < 7 && e == cudaSuccess; ++k)

@@ -144,6 +144,9 @@ struct sph_ctx {
   // before the first gather part and hook_wait before the second; record
   // hook_sorted after the sort and hook_mom after the momentum pass
   cudaEvent_t hook_wait_a, hook_wait, hook_sorted, hook_mom;
+  // set by sph_step_host when the caller's arrays are pinned: the update
+  // writes the new state straight into them (m, id and du_prev NULL)
+  const sph::StateView* hook_update_dst;
   int64_t* hm_id;
   int64_t hm_n;
 };

@@ -189,10 +189,10 @@ __global__ void __launch_bounds__(kThreads) k_update(StateView s, OutView o, Sta
     d.vyh[p] = vhn[1];
     d.vzh[p] = vhn[2];
     d.u[p] = un;
-    d.du_prev[p] = du;
+    if (d.du_prev) d.du_prev[p] = du;  // NULL: the caller takes du_prev, m and id elsewhere
     d.h[p] = h;
-    d.m[p] = m;
-    d.id[p] = s.id[p];
+    if (d.m) d.m[p] = m;
+    if (d.id) d.id[p] = s.id[p];
     acc[0] += m * vn[0];
     acc[1] += m * vn[1];
     acc[2] += m * vn[2];

@@ -219,7 +219,7 @@ class HostStepper:
     whose state lives in host memory)."""
 
     def __init__(self, state: dict, params: Params | None = None, n_max: int | None = None,
-                 device: str = "cuda:0", outputs: bool = False):
+                 device: str = "cuda:0", outputs: bool = False, pinned: bool = True):
         self.lib = _lib.load()
         self.device = torch.device(device)
         if params is None:
@@ -231,15 +231,18 @@ class HostStepper:
             self._cp = params.c()
             check(self.lib, None, self.lib.sph_init(C.byref(self._cp), int(n_max or self.n),
                                                     C.byref(self.ctx)))
+        # pinned arrays let the library overlap its copies and write the new
+        # state from the update kernel; pageable ones take plain copies
+        pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t.clone())
         self.h = {}
         for k in PERSISTENT:
-            self.h[k] = torch.as_tensor(np.ascontiguousarray(state[k], dtype=np.float64)).pin_memory()
-        self.h["id"] = torch.as_tensor(np.ascontiguousarray(state["id"], dtype=np.int64)).pin_memory()
+            self.h[k] = pin(torch.as_tensor(np.ascontiguousarray(state[k], dtype=np.float64)))
+        self.h["id"] = pin(torch.as_tensor(np.ascontiguousarray(state["id"], dtype=np.int64)))
         self.outputs = outputs
         if outputs:
             for k in OUTPUTS:
-                self.h[k] = torch.zeros(self.n, dtype=torch.float64).pin_memory()
-            self.h["iad"] = torch.zeros(6 * self.n, dtype=torch.float64).pin_memory()
+                self.h[k] = pin(torch.zeros(self.n, dtype=torch.float64))
+            self.h["iad"] = pin(torch.zeros(6 * self.n, dtype=torch.float64))
         self.dt = np.zeros(1)
         self._st = SphState()
         for k in _lib.STATE_FIELDS:

@@ -112,12 +112,15 @@ def test_conservation_to_rounding_common_h():
     sim.close()
 
 
-@pytest.mark.parametrize("precision,side", [("fp32_mixed", 16), ("fp32_mixed", 27), ("fp64", 19)])
-def test_host_step_equals_device_step(precision, side):
+@pytest.mark.parametrize("precision,side,pinned", [("fp32_mixed", 16, True), ("fp32_mixed", 27, True),
+                                                   ("fp64", 19, True), ("fp32_mixed", 17, False)])
+def test_host_step_equals_device_step(precision, side, pinned):
     """sph_step_host on pinned host arrays gives the device step's results,
     step after step: its copies run on two streams (positions first, m, u, id
     and then the velocities and integrator history while the sort and search
-    run; m, id and du_prev copied out early), so every field is checked."""
+    run; m, id and du_prev copied out early; with pinned arrays the update
+    kernel writes the rest straight into them, with pageable ones they are
+    copied), so every field is checked."""
     from paper_2005_02656_gb300 import HostStepper, Params
     s = sph_inputs.jittered_box(side, seed_index=46, vel_sigma=0.1)
     steps = 3
@@ -126,7 +129,7 @@ def test_host_step_equals_device_step(precision, side):
     d = dev.to_numpy()
     dev.close()
     hs = HostStepper(s, Params(box_lo=s["lo"], box_hi=s["hi"], periodic=s["periodic"],
-                               precision=precision), outputs=True)
+                               precision=precision), outputs=True, pinned=pinned)
     for _ in range(steps):
         hs.step()
     h = {k: v.numpy() for k, v in hs.h.items()}
