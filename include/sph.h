@@ -401,7 +401,8 @@ SPH_API const char* sph_adjoint_last_error(const sph_adj* a);
 
 /* Stages of sph_step timed by sph_profile. */
 enum {
-  SPH_STAGE_SORT = 0,     /* grid, Morton counting sort, gather          */
+  SPH_STAGE_SORT = 0,     /* grid, Morton counting sort, both gather
+                             parts (the second runs after the search)   */
   SPH_STAGE_FIND = 1,     /* neighbour lists                             */
   SPH_STAGE_DENSITY = 2,  /* density + EOS                               */
   SPH_STAGE_IAD = 3,      /* IAD matrix                                  */
