@@ -207,8 +207,10 @@ SPH_API int sph_step(sph_ctx* ctx, sph_state* state, double* dt_inout, sph_strea
 SPH_API int sph_step_host(sph_ctx* ctx, sph_state* host_state, double* dt_inout, sph_stream_t stream);
 
 /* Conservation sums of a state {Px, Py, Pz, E_kin, E_int, Lx, Ly, Lz}
- * (section 4.2: total momentum and energy), FP64 with compensated block
- * sums.  out: HOST array of 8.  Synchronises the stream. */
+ * (section 4.2: total momentum and energy) in FP64: per-thread partial sums,
+ * then fixed-shape warp, block and grid trees, so the result is the same on
+ * every run (within 1e-13 relative of an exactly rounded sum on the tested
+ * states).  out: HOST array of 8.  Synchronises the stream. */
 SPH_API int sph_diagnostics(sph_ctx* ctx, const sph_state* state, double* out, sph_stream_t stream);
 
 /* Conservation sums accumulated by the last sph_step (of its new state) and
