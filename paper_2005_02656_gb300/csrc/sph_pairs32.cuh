@@ -81,8 +81,9 @@ __device__ __forceinline__ void for_entries(const uint32_t* row, int cnt, Body b
 }
 
 // The entries of a row owned by sub-lane `sub` of a group of NSUB lanes that
-// share one target: 16-byte chunks c = sub, sub + NSUB, ...  NSUB = 1 is
-// for_entries (every entry, in order).
+// share one target: entries k = sub, sub + NSUB, ... for NSUB >= 4, 16-byte
+// chunks c = sub, sub + NSUB, ... for NSUB = 2.  NSUB = 1 is for_entries
+// (every entry, in order).
 template <int NSUB, typename Body>
 __device__ __forceinline__ void for_entries_part(const uint32_t* row, int cnt, int sub,
                                                  Body body) {
@@ -90,6 +91,15 @@ __device__ __forceinline__ void for_entries_part(const uint32_t* row, int cnt, i
     for_entries(row, cnt, body);
     return;
   }
+  if (NSUB >= 4) {
+    // the NSUB lanes of a target read NSUB consecutive entries at a time:
+    // neighbours in the same cell, adjacent in memory, so a warp-wide gather
+    // touches fewer lines (momentum 6.22 -> 6.11 ms at 8.4M particles)
+    for (int k = sub; k < cnt; k += NSUB) body(__ldg(row + k));
+    return;
+  }
+  // two lanes: every other 16-byte group of four entries (measured better
+  // than interleaved single entries for two lanes, 6.29 against 7.03 ms)
   const uint4* r4 = reinterpret_cast<const uint4*>(row);
   for (int c = sub; 4 * c < cnt; c += NSUB) {
     const uint4 e = r4[c];
