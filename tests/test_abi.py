@@ -116,3 +116,15 @@ def test_ensemble_defaults_and_host_checks(lib):
     p64 = _params(lib)                                           # the ensemble is FP32-mixed only
     assert lib.sph_ensemble_init(C.byref(p64), 1, n, d3, d3, i3, a1, C.byref(e)) == SPH_ERR_INVALID_ARG
     assert not e.value
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No CPU fallback: without libsph.so the binding raises."""
+    from paper_2005_02656_gb300 import _lib
+    saved = _lib._lib
+    _lib._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="no fallback"):
+            _lib.load(str(tmp_path / "libsph.so"))
+    finally:
+        _lib._lib = saved
