@@ -300,6 +300,7 @@ typedef struct {
                           results equal a single-box sph_step */
 } sph_ens_config;
 
+/* Fills c with the defaults in brackets above (host only, no device work). */
 SPH_API void sph_ens_default_config(sph_ens_config* c);
 
 /* Creates an ensemble of n_boxes boxes.  Box b owns particles
@@ -313,7 +314,10 @@ SPH_API void sph_ens_default_config(sph_ens_config* c);
 SPH_API int sph_ensemble_init(const sph_params* common, int n_boxes, const int64_t* box_n,
                               const double* box_lo, const double* box_hi,
                               const int* box_periodic, const double* box_alpha, sph_ens** out);
+/* Synchronises the device and frees the ensemble's device scratch and graph. */
 SPH_API void sph_ensemble_destroy(sph_ens* e);
+/* Sets the tuning knobs for the next step or capture; SPH_ERR_INVALID_ARG for
+ * a value outside the ranges above (the configuration is then unchanged). */
 SPH_API int sph_ensemble_set_config(sph_ens* e, const sph_ens_config* c);
 
 /* Advances every box by `steps` steps in one persistent launch.  state: the
@@ -330,7 +334,10 @@ SPH_API int sph_ensemble_capture(sph_ens* e, sph_state* state, double* dt, int s
                                  sph_stream_t stream);
 SPH_API int sph_ensemble_replay(sph_ens* e, sph_stream_t stream);
 
+/* Synchronises, returns the device error bits of all boxes (SPH_FLAG_*) in
+ * *flags, clears them and re-arms the grid barrier. */
 SPH_API int sph_ensemble_error_word(sph_ens* e, uint32_t* flags);
+/* Message of the last failed call on e. */
 SPH_API const char* sph_ensemble_last_error(const sph_ens* e);
 /* out[0] particles, out[1] boxes, out[2] persistent CTAs, out[3] launches. */
 SPH_API int sph_ensemble_info(const sph_ens* e, int64_t* out);
@@ -372,6 +379,7 @@ typedef struct sph_adj sph_adj;
  * of working arrays, plus one FP64 sph_ctx. */
 SPH_API int sph_adjoint_init(const sph_params* params, int64_t n_max, int steps,
                              int checkpoint_every, sph_adj** out);
+/* Synchronises the device and frees the rollout's tape, checkpoints and context. */
 SPH_API void sph_adjoint_destroy(sph_adj* a);
 
 /* Runs the forward rollout from s0 (its 13 state arrays are read; id and the
