@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--no-table", action="store_true", help="skip the lookup-table kernel leg")
     ap.add_argument("--no-gravity", action="store_true", help="skip the self-gravity leg")
     ap.add_argument("--adjoint-side", type=int, default=100)
+    ap.add_argument("--pair-mode", choices=["staged", "lists"], default="staged",
+                    help="FP32-mixed pair sums: cell-staged candidates with hit masks, or "
+                         "int32 neighbour lists")
     return ap.parse_args()
 
 
@@ -218,7 +221,8 @@ def run_gpu(args, world, rank, local):
     def timed(precision, kernel_mode="exact", steps=None, key=None):
         steps = steps or args.steps
         key = key or precision
-        sim = SphSim(state, precision=precision, device=dev, kernel_mode=kernel_mode)
+        sim = SphSim(state, precision=precision, device=dev, kernel_mode=kernel_mode,
+                     pair_mode=args.pair_mode)
         stream = torch.cuda.current_stream()
         for _ in range(args.warmup):
             sim.step()

@@ -86,6 +86,27 @@ enum { SPH_KERNEL_EXACT = 0, SPH_KERNEL_TABLE = 1 };
  * ~1e-8; gradh, the ensemble and the differentiable rollout require
  * SPH_KERNEL_EXACT. */
 
+/* How the FP32-mixed pair sums reach the neighbours (SPH_FP64 always uses
+ * SPH_PAIRS_LISTS).
+ *  SPH_PAIRS_STAGED: the neighbour search records, per occupied cell, the
+ *    candidates it staged (the particles of the cell's 3x3x3 stencil within
+ *    reach of the cell's targets, in stencil order) and, per target, one
+ *    64-bit hit mask per 64 staged candidates (bit set: r^2 < (2 h_a)^2
+ *    decided exactly as by sph_find_neighbors).  Density, IAD and momentum
+ *    then work cell by cell: the cell's staged candidate records are copied
+ *    into shared memory once and each target's sum runs over its hit bits.
+ *    The masks and staged entries live in the list buffer and a 108-byte-per-
+ *    particle entry buffer; a state whose masks do not fit (more than
+ *    max_nb / 2 mask words per particle on average) raises
+ *    SPH_FLAG_NB_OVERFLOW.
+ *  SPH_PAIRS_LISTS: the search writes int32 neighbour lists (max_nb per
+ *    particle) and every pair kernel gathers its neighbours' records from
+ *    global memory; the batched ensemble uses this form, and a single box
+ *    run with it equals the ensemble's result for that box bit for bit.
+ * Both give the same neighbour sets and the same sums up to FP32 summation
+ * order. */
+enum { SPH_PAIRS_STAGED = 0, SPH_PAIRS_LISTS = 1 };
+
 /* Particle state: structure of arrays of caller-owned device memory.
  *  inputs (persistent state): x y z (positions), vx vy vz (velocity at integer
  *    time, v^n), vxh vyh vzh (half-step velocity v^{n-1/2}; set equal to v
@@ -128,6 +149,8 @@ typedef struct {
                                   sum_b m_b dW_ab(h_a)/dh_a in the density pass
                                   (self term included) and uses P/(Omega rho^2)
                                   in momentum and energy [0]                    */
+  int pair_mode;               /* SPH_PAIRS_STAGED or SPH_PAIRS_LISTS, read by
+                                  SPH_FP32_MIXED contexts [SPH_PAIRS_STAGED]     */
 } sph_params;
 
 /* Fills *p with the defaults above and a periodic unit box. */
@@ -226,22 +249,24 @@ SPH_API int sph_error_word(sph_ctx* ctx, uint32_t* flags);
 SPH_API const char* sph_last_error(const sph_ctx* ctx);
 
 /* The conservation sums of sph_diagnostics for callers that cannot allocate
- * device memory: code that runs while a CUDA graph is being captured (an
- * allocation there would fail the capture), code inside a host callback, or a
- * host that owns the whole device memory through its own pool and forbids
- * other allocations.  No context is needed and nothing is allocated: the
- * per-block partial sums live in a file-scope static device array of about
- * 512 KB that every device loading the library holds until the process exits.
- * The paper has no counterpart; it is an interface convenience.
+ * device memory: a host program that owns the whole device memory through its
+ * own pool and forbids any other allocation, or a component that holds no
+ * sph_ctx and must not create one.  No context is needed and nothing is
+ * allocated: the per-block partial sums live in a file-scope static device
+ * array of about 512 KB that every device loading the library holds until the
+ * process exits.  The paper has no counterpart; it is an interface
+ * convenience.
  *   state: as for sph_diagnostics; only x y z vx vy vz m u and n are read
  *          (device arrays); n must be <= 16,777,216, larger states are
  *          rejected with SPH_ERR_INVALID_ARG.
  *   out:   HOST array of 8, filled as by sph_diagnostics.
- * The first call on a device, with that device current, looks up the static
- * array's device address; make that first call before any stream capture.
- * All calls share the static array: calls that overlap on the GPU (other
- * streams or host threads) race.  Synchronises the stream.  Returns SPH_OK,
- * SPH_ERR_INVALID_ARG or SPH_ERR_CUDA. */
+ * The call copies the sums to the host and synchronises the stream, so it
+ * cannot run on a stream that is being captured into a CUDA graph: such a
+ * stream is refused with SPH_ERR_INVALID_ARG before any other CUDA call, and
+ * the capture is left intact.  The first call on a device, with that device
+ * current, looks up the static array's device address.  All calls share the
+ * static array: calls that overlap on the GPU (other streams or host threads)
+ * race.  Returns SPH_OK, SPH_ERR_INVALID_ARG or SPH_ERR_CUDA. */
 SPH_API int sph_diagnostics_noalloc(const sph_state* state, double* out, sph_stream_t stream);
 
 /* Self-gravity (section 4.1: a multipolar expansion evaluated on the tree

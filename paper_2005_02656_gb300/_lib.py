@@ -32,6 +32,8 @@ SPH_FP64 = 0
 SPH_FP32_MIXED = 1
 SPH_KERNEL_EXACT = 0
 SPH_KERNEL_TABLE = 1
+SPH_PAIRS_STAGED = 0
+SPH_PAIRS_LISTS = 1
 
 STATE_FIELDS = ("x", "y", "z", "vx", "vy", "vz", "h", "m", "u", "vxh", "vyh", "vzh", "du_prev",
                 "rho", "p", "c", "iad", "ax", "ay", "az", "du", "omega")
@@ -63,7 +65,7 @@ class SphParams(C.Structure):
         ("gamma", C.c_double), ("alpha", C.c_double), ("courant", C.c_double),
         ("dt_growth", C.c_double), ("ng_target", C.c_int), ("max_nb", C.c_int),
         ("sinc_n", C.c_double), ("precision", C.c_int), ("kernel_mode", C.c_int),
-        ("gradh", C.c_int),
+        ("gradh", C.c_int), ("pair_mode", C.c_int),
     ]
 
 

@@ -46,6 +46,7 @@ class Rollout:
         if rc != _lib.SPH_OK:
             raise _lib.SphError(rc, "sph_adjoint_init")
         self._n = 0
+        self.forwards = 0       # forward rollouts run so far (the tape holds the last one)
 
     def _err(self, rc):
         if rc != _lib.SPH_OK:
@@ -70,6 +71,7 @@ class Rollout:
                                                    float(alpha), C.c_void_p(out.data_ptr()),
                                                    _stream_ptr()))
         self._n = n
+        self.forwards += 1
         return out
 
     def backward(self, g_final: torch.Tensor):
@@ -124,6 +126,7 @@ class SphRolloutFn(torch.autograd.Function):
         state = {k: v.detach().contiguous() for k, v in state.items()}
         fin = ro.forward(state, float(alpha), float(dt_prev0))
         ctx.ro = ro
+        ctx.forward_id = ro.forwards
         x = fin[0:3].t().contiguous()
         v = fin[3:6].t().contiguous()
         return x, v, fin[6].clone(), fin[7].clone()
@@ -131,6 +134,11 @@ class SphRolloutFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gx, gv, gu, grho):
         ro = ctx.ro
+        if ro.forwards != ctx.forward_id:
+            # the Rollout's tape holds a newer forward than this graph's
+            raise RuntimeError("this Rollout ran another forward since the one being "
+                               "differentiated; a Rollout holds the tape of its last forward "
+                               "only (use one Rollout per pending backward)")
         n = ro._n
         dev = ro.device
 

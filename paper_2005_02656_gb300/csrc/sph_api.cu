@@ -81,6 +81,8 @@ int check_params(sph_ctx* ctx, const sph_params* p) {
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "gradh must be 0 or 1");
   if (p->gradh && p->kernel_mode != SPH_KERNEL_EXACT)
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "gradh needs SPH_KERNEL_EXACT");
+  if (p->pair_mode != SPH_PAIRS_STAGED && p->pair_mode != SPH_PAIRS_LISTS)
+    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "unknown pair_mode %d", p->pair_mode);
   return SPH_OK;
 }
 
@@ -203,28 +205,34 @@ void free_all(sph_ctx* ctx) {
                   ctx->ktab32, ctx->code, ctx->slot,
                   ctx->perm_tmp, ctx->perm, ctx->tbl_count, ctx->tbl_start, ctx->occ,
                   ctx->scan_part, ctx->cell_of, ctx->s.x, ctx->s_id_buf, ctx->pos32,
-                  ctx->cell3, ctx->nn, ctx->nbr, ctx->wcache, ctx->vol, ctx->rec_d, ctx->rec_i, ctx->rec_m, ctx->red.part, ctx->red.counter, ctx->stats, ctx->hm_buf, ctx->hm_id,
-                  ctx->grav_buf};
+                  ctx->cell3, ctx->nn, ctx->nbr, ctx->wcache, ctx->vol, ctx->rec_d, ctx->rec_i,
+                  ctx->rec_m, ctx->cmeta, ctx->sent, ctx->masks, ctx->salloc, ctx->recA, ctx->recV,
+                  ctx->recQ, ctx->recC, ctx->recC2, ctx->red.part, ctx->red.counter, ctx->stats,
+                  ctx->hm_buf, ctx->hm_id, ctx->grav_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
 
-int run_find(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st) {
-  sph::launch_grid(ctx, in, n, st);
-  sph::launch_sort_gather(ctx, in, n, st);
-  sph::launch_find_neighbors(ctx, ctx->s, n, st);
-  return finish(ctx, "neighbour search launch");
+void run_search(sph_ctx* ctx, const StateView& s, int64_t n, cudaStream_t st) {
+  if (sph::staged_pairs(ctx))
+    sph::launch_find_masks(ctx, s, n, st);
+  else
+    sph::launch_find_neighbors(ctx, s, n, st);
 }
 
 void run_density(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n, cudaStream_t st) {
-  if (ctx->prm.precision == SPH_FP32_MIXED)
+  if (sph::staged_pairs(ctx))
+    sph::launch_density_staged(ctx, s, o, n, st);
+  else if (ctx->prm.precision == SPH_FP32_MIXED)
     sph::launch_density_f32(ctx, s, o, n, st);
   else
     sph::launch_density_f64(ctx, s, o, n, st);
 }
 
 void run_iad(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n, cudaStream_t st) {
-  if (ctx->prm.precision == SPH_FP32_MIXED)
+  if (sph::staged_pairs(ctx))
+    sph::launch_iad_staged(ctx, s, o, n, st);
+  else if (ctx->prm.precision == SPH_FP32_MIXED)
     sph::launch_iad_f32(ctx, s, o, n, st);
   else
     sph::launch_iad_f64(ctx, s, o, n, st);
@@ -232,7 +240,9 @@ void run_iad(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n, cuda
 
 void run_momentum(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
                   cudaStream_t st) {
-  if (ctx->prm.precision == SPH_FP32_MIXED)
+  if (sph::staged_pairs(ctx))
+    sph::launch_momentum_staged(ctx, s, o, n, st);
+  else if (ctx->prm.precision == SPH_FP32_MIXED)
     sph::launch_momentum_f32(ctx, s, o, n, st);
   else
     sph::launch_momentum_f64(ctx, s, o, n, st);
@@ -294,6 +304,7 @@ void sph_default_params(sph_params* p) {
   p->precision = SPH_FP64;
   p->kernel_mode = SPH_KERNEL_EXACT;
   p->gradh = 0;
+  p->pair_mode = SPH_PAIRS_STAGED;
 }
 
 int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {
@@ -350,6 +361,19 @@ int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {
   ALLOC(ctx->rec_d, n);
   ALLOC(ctx->rec_i, n);
   ALLOC(ctx->rec_m, 5 * n);
+  // cell-staged pair passes: at most 27 n staged entries (a cell appears in
+  // at most 27 stencils) and kMaskWords hit-mask words per particle
+  ctx->sent_cap = 27 * n;
+  ctx->mask_cap = (int64_t)sph::kMaskWords * n;
+  ALLOC(ctx->cmeta, n);
+  ALLOC(ctx->sent, (size_t)ctx->sent_cap);
+  ALLOC(ctx->masks, (size_t)ctx->mask_cap);
+  ALLOC(ctx->salloc, 2);
+  ALLOC(ctx->recA, n);
+  ALLOC(ctx->recV, n);
+  ALLOC(ctx->recQ, n);
+  ALLOC(ctx->recC, n);
+  ALLOC(ctx->recC2, n);
   ALLOC(ctx->red.part, sph::kReduceBlocks * 16);
   ALLOC(ctx->red.counter, 8);
   ALLOC(ctx->stats, 4);
@@ -414,7 +438,10 @@ int sph_set_params(sph_ctx* ctx, const sph_params* params) {
       return sph::cuda_fail(ctx, e, "sph_set_params: FP64 kernel-value cache");
     }
   }
+  const bool staged_before = sph::staged_pairs(ctx);
   ctx->prm = *params;
+  // the masks of the staged form are not lists (and the other way round)
+  if (sph::staged_pairs(ctx) != staged_before) ctx->have_lists = 0;
   ctx->have_density = ctx->have_iad = 0;
   return build_kernel_table(ctx);
 }
@@ -434,7 +461,7 @@ int sph_find_neighbors(sph_ctx* ctx, sph_state* state, sph_stream_t stream) {
   sph::launch_grid(ctx, in, state->n, st);
   sph::launch_sort_gather(ctx, in, state->n, st);
   sph::launch_copy_state(in, ctx->s, state->n, st, ctx);
-  sph::launch_find_neighbors(ctx, in, state->n, st);
+  run_search(ctx, in, state->n, st);
   rc = finish(ctx, "sph_find_neighbors");
   ctx->have_lists = rc == SPH_OK;
   ctx->have_density = ctx->have_iad = 0;
@@ -448,8 +475,11 @@ int sph_get_neighbors(sph_ctx* ctx, const sph_state* state, int32_t* counts, int
   if (!counts || !ids) return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "NULL output");
   if (!ctx->have_lists)
     return sph::set_error(ctx, SPH_ERR_ORDER, "no neighbour lists: call sph_find_neighbors");
-  sph::launch_export_neighbors(ctx, view_of(state), state->n, counts, ids,
-                               (cudaStream_t)stream);
+  if (sph::staged_pairs(ctx))
+    sph::launch_export_masks(ctx, view_of(state), state->n, counts, ids, (cudaStream_t)stream);
+  else
+    sph::launch_export_neighbors(ctx, view_of(state), state->n, counts, ids,
+                                 (cudaStream_t)stream);
   return finish(ctx, "sph_get_neighbors");
 }
 
@@ -501,7 +531,7 @@ int sph_step(sph_ctx* ctx, sph_state* state, double* dt_inout, sph_stream_t stre
   sph::launch_sort(ctx, in, n, st, ctx->hook_wait_a);
   if (ctx->hook_sorted) cudaEventRecord(ctx->hook_sorted, st);
   prof_mark(ctx, 1, st);
-  sph::launch_find_neighbors(ctx, ctx->s, n, st);
+  run_search(ctx, ctx->s, n, st);
   prof_mark(ctx, 2, st);
   // velocities and integrator history: a host caller may still be copying
   // them in while the search runs

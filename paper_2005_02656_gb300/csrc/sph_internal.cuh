@@ -16,6 +16,7 @@ constexpr int kScanItems = 4096;                // cell-table entries per scan b
 constexpr int kProfRing = 64;                   // step event sets kept before folding
 constexpr int kHTab = 4097;                     // h factors tabulated for counts 0..4096
 constexpr int kKernelTableN = 20000;            // kernel values of SPH_KERNEL_TABLE
+constexpr int kMaskWords = 32;                  // hit-mask words per particle (staged pairs)
 
 // Cell grid of the current step, computed on the device from the particles'
 // extent and h_max, read by every later kernel of the step.
@@ -120,6 +121,26 @@ struct sph_ctx {
   float4* rec_i;        // offset x, y, z, m/rho           (density)
   float4* rec_m;        // 5 float4 per particle           (gather, density, IAD)
 
+  // SPH_PAIRS_STAGED (sph_staged.cu): per occupied cell (slot_base,
+  // mask_base, a0, S << 16 | na); staged candidate entries; hit masks
+  // (mask_cap 64-bit words); two allocation counters.  Cells in list form
+  // use nbr.
+  uint4* cmeta;
+  uint32_t* sent;
+  unsigned long long* masks;
+  unsigned long long* salloc;
+  int64_t sent_cap;
+  int64_t mask_cap;
+  // momentum records as planes: (offset, 1/h^2), (v, m),
+  // (B_n/h^3, P/(Omega rho^2), c, 1/rho), (C00 C01 C02 C11), (C12 C22)
+  float4* recA;
+  float4* recV;
+  float4* recQ;
+  float4* recC;
+  float2* recC2;
+  int find_mask_blocks;   // persistent CTAs of the mask-writing search
+  int pass_blocks[3];     // persistent CTAs of the density, IAD, momentum passes
+
   // reductions
   sph::Reduce red;
   unsigned long long* stats;  // 4 cumulative counters (sph_stats)
@@ -185,6 +206,22 @@ void launch_density_f64(sph_ctx* ctx, const StateView& s, const OutView& o, int6
 void launch_iad_f64(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n, cudaStream_t st);
 void launch_momentum_f64(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
                          cudaStream_t st);
+
+// --- sph_staged.cu (SPH_FP32_MIXED with SPH_PAIRS_STAGED) ---
+void launch_find_masks(sph_ctx* ctx, const StateView& s, int64_t n, cudaStream_t st);
+void launch_density_staged(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
+                           cudaStream_t st);
+void launch_iad_staged(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
+                       cudaStream_t st);
+void launch_momentum_staged(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
+                            cudaStream_t st);
+void launch_export_masks(sph_ctx* ctx, const StateView& s, int64_t n, int32_t* counts,
+                         int64_t* ids, cudaStream_t st);
+
+// True when the context's pair sums run on cell-staged candidates.
+inline bool staged_pairs(const sph_ctx* ctx) {
+  return ctx->prm.precision == SPH_FP32_MIXED && ctx->prm.pair_mode == SPH_PAIRS_STAGED;
+}
 
 // --- sph_pairs_fp32.cu ---
 void launch_density_f32(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,

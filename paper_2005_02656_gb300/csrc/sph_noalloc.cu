@@ -10,10 +10,18 @@
 // Host code must not pass the symbol itself to a kernel (on the host it is a
 // stand-in, not a device address): the first call on a device, with that
 // device current, looks the address up with cudaGetSymbolAddress and caches
-// it per device.  All calls share the array, so calls that overlap on the GPU
-// (different streams, or different host threads) race and give wrong sums.
+// it per device (an atomic slot, so host threads making their first calls at
+// the same time store the same address without a data race).  All calls
+// share the array, so calls that overlap on the GPU (different streams, or
+// different host threads) race and give wrong sums.
+//
+// The call ends by copying the sums to the host and synchronising the
+// stream, which a stream under graph capture does not allow: a capturing
+// stream is refused before any other CUDA call, leaving the capture intact.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <atomic>
 
 #include "../../include/sph.h"
 
@@ -34,7 +42,7 @@ constexpr int kNaDoubles = kNaCounter + 2;
 static __device__ __align__(256) double g_na_scratch[kNaDoubles];
 
 constexpr int kMaxDevices = 64;
-double* g_na_ptr[kMaxDevices] = {nullptr};
+std::atomic<double*> g_na_ptr[kMaxDevices] = {};
 
 __global__ void __launch_bounds__(kNaThreads) k_diag_noalloc(
     const double* x, const double* y, const double* z, const double* vx, const double* vy,
@@ -100,15 +108,24 @@ extern "C" int sph_diagnostics_noalloc(const sph_state* state, double* out, sph_
   if (state->n > 0 && (!state->x || !state->y || !state->z || !state->vx || !state->vy ||
                        !state->vz || !state->m || !state->u))
     return SPH_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  // a stream under capture cannot be synchronised: refuse it untouched
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SPH_ERR_INVALID_ARG;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return SPH_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SPH_ERR_CUDA;
-  if (!g_na_ptr[dev]) {
+  double* scratch = g_na_ptr[dev].load(std::memory_order_acquire);
+  if (!scratch) {
     // once per device, with that device current: the scratch's device address
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) return SPH_ERR_CUDA;
-    g_na_ptr[dev] = static_cast<double*>(p);
+    scratch = static_cast<double*>(p);
+    g_na_ptr[dev].store(scratch, std::memory_order_release);
   }
-  cudaStream_t st = (cudaStream_t)stream;
   if (state->n == 0) {
     for (int k = 0; k < kNaSums; ++k) out[k] = 0.0;
     return SPH_OK;
@@ -116,10 +133,10 @@ extern "C" int sph_diagnostics_noalloc(const sph_state* state, double* out, sph_
   const int blocks = (int)((state->n + kNaChunk - 1) / kNaChunk);
   k_diag_noalloc<<<blocks, kNaThreads, 0, st>>>(state->x, state->y, state->z, state->vx,
                                                 state->vy, state->vz, state->m, state->u,
-                                                state->n, g_na_ptr[dev]);
+                                                state->n, scratch);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(out, g_na_ptr[dev] + kNaResult, kNaSums * sizeof(double),
+    e = cudaMemcpyAsync(out, scratch + kNaResult, kNaSums * sizeof(double),
                         cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;

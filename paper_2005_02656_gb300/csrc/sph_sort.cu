@@ -359,7 +359,7 @@ __global__ void k_gather_a(StateView in, StateView out, int64_t n, const Grid* g
 // the momentum pass (so a caller may still be copying them in while the
 // search runs).
 __global__ void k_gather_b(StateView in, StateView out, int64_t n, const int32_t* perm,
-                           float4* rec_m) {
+                           float4* rec_m, float4* recV) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     int64_t s = perm[p];
@@ -371,7 +371,11 @@ __global__ void k_gather_b(StateView in, StateView out, int64_t n, const int32_t
     out.vyh[p] = in.vyh[s];
     out.vzh[p] = in.vzh[s];
     out.du_prev[p] = in.du_prev[s];
-    rec_m[5 * p + 1] = make_float4((float)vx, (float)vy, (float)vz, (float)out.m[p]);
+    const float4 vm = make_float4((float)vx, (float)vy, (float)vz, (float)out.m[p]);
+    if (recV)
+      recV[p] = vm;  // the staged pair passes' velocity plane
+    else
+      rec_m[5 * p + 1] = vm;
   }
 }
 
@@ -414,8 +418,8 @@ void launch_sort(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st,
 }
 
 void launch_gather_b(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st) {
-  k_gather_b<<<grid_for(n, 256, ctx->sm_count), 256, 0, st>>>(in, ctx->s, n, ctx->perm,
-                                                              ctx->rec_m);
+  k_gather_b<<<grid_for(n, 256, ctx->sm_count), 256, 0, st>>>(
+      in, ctx->s, n, ctx->perm, ctx->rec_m, staged_pairs(ctx) ? ctx->recV : nullptr);
   ctx->launches += 1;
 }
 

@@ -32,6 +32,8 @@ class Params:
     precision: str = "fp64"   # "fp64" | "fp32_mixed"
     gradh: int = 0            # 1: grad-h terms Omega in Eqs. 2-3
     kernel_mode: str = "exact"  # "exact" | "table" (section 4.5: 20,000-entry table)
+    pair_mode: str = "staged"   # FP32-mixed pair sums: "staged" (cell-staged candidates
+                                # and hit masks) | "lists" (int32 neighbour lists)
 
     def c(self) -> SphParams:
         p = SphParams()
@@ -44,6 +46,7 @@ class Params:
         p.precision = {"fp64": _lib.SPH_FP64, "fp32_mixed": _lib.SPH_FP32_MIXED}[self.precision]
         p.kernel_mode = {"exact": _lib.SPH_KERNEL_EXACT, "table": _lib.SPH_KERNEL_TABLE}[self.kernel_mode]
         p.gradh = int(self.gradh)
+        p.pair_mode = {"staged": _lib.SPH_PAIRS_STAGED, "lists": _lib.SPH_PAIRS_LISTS}[self.pair_mode]
         return p
 
 

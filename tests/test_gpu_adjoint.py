@@ -185,6 +185,34 @@ def test_autograd_function_gives_the_same_gradients(small):
     ro.close()
 
 
+def test_stale_graph_backward_is_refused():
+    """A Rollout keeps the tape of its last forward only: the backward of an
+    earlier graph after a newer forward on the same Rollout raises instead of
+    returning the newer rollout's gradients."""
+    from paper_2005_02656_gb300 import Params, Rollout, rollout
+    s, _ = _case(side=8, seed=72)
+    n = s["x"].shape[0]
+    dev = torch.device("cuda:0")
+    ro = Rollout(n, 2, 1, Params(box_lo=s["lo"], box_hi=s["hi"], periodic=s["periodic"]))
+    h = torch.tensor(s["h"], device=dev)
+    m = torch.tensor(s["m"], device=dev)
+
+    def run(scale):
+        x0 = torch.tensor(np.stack([s["x"], s["y"], s["z"]], 1), device=dev, requires_grad=True)
+        v0 = torch.tensor(scale * np.stack([s["vx"], s["vy"], s["vz"]], 1), device=dev,
+                          requires_grad=True)
+        u0 = torch.tensor(s["u"], device=dev, requires_grad=True)
+        x, v, u, rho = rollout(x0, v0, u0, 1.0, ro, h, m)
+        return ((rho - 1.0) ** 2).sum() + 0.5 * (m * (v * v).sum(1)).sum()
+
+    first = run(1.0)
+    second = run(2.0)
+    with pytest.raises(RuntimeError, match="another forward"):
+        first.backward()
+    second.backward()                     # the newest graph still differentiates
+    ro.close()
+
+
 def test_backward_before_forward_and_overflow_are_errors():
     from paper_2005_02656_gb300 import Params, Rollout, _lib
     s, _ = _case(side=8, seed=71)

@@ -18,10 +18,11 @@ def _sim(s, **kw):
     return SphSim(s, **kw)
 
 
-def test_neighbor_overflow_flag_and_true_counts():
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+def test_neighbor_overflow_flag_and_true_counts(precision):
     from paper_2005_02656_gb300 import _lib
     s = sph_inputs.jittered_box(16, seed_index=40)
-    sim = _sim(s, max_nb=32, ng_target=0)
+    sim = _sim(s, max_nb=32, ng_target=0, precision=precision)
     sim.find_neighbors()
     counts, _ = sim.get_neighbors()
     assert sim.error_word() & _lib.FLAG_NB_OVERFLOW

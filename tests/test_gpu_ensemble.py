@@ -26,7 +26,7 @@ def test_each_box_matches_its_single_box_run():
     ens.step(3)
     assert ens.error_word() == 0
     for b, (s, alpha) in enumerate(boxes):
-        sim = SphSim(s, precision="fp32_mixed", alpha=alpha)
+        sim = SphSim(s, precision="fp32_mixed", alpha=alpha, pair_mode="lists")
         sim.step(3)
         ref = sim.to_numpy()
         got = ens.box_numpy(b)
@@ -165,7 +165,7 @@ def test_gradh_boxes_match_their_single_box_runs():
     ens.step(2)
     assert ens.error_word() == 0
     for b, (s, alpha) in enumerate(boxes):
-        sim = SphSim(s, precision="fp32_mixed", alpha=alpha, gradh=1)
+        sim = SphSim(s, precision="fp32_mixed", alpha=alpha, gradh=1, pair_mode="lists")
         sim.step(2)
         ref = sim.to_numpy()
         got = ens.box_numpy(b)

@@ -39,9 +39,23 @@ def _cases():
 CASES = _cases()
 
 
-def _gpu(s, precision="fp64", **kw):
+def _big_cells():
+    """Cells far above the pair passes' shared-memory sizes: a few particles
+    with 1.8 h make the cells (side >= 2 h_max) hold ~150 targets each (three
+    rounds of 64), their stencils ~1,400 staged candidates (two windows), and
+    the large-h particles ~590 neighbours (several list passes of 128)."""
+    s = sph_inputs.jittered_box(16, seed_index=8)
+    s["h"][[7, 2000]] *= 1.8
+    return s
+
+
+BIG_CELLS = _big_cells()
+BIG_MAX_NB = 1024
+
+
+def _gpu(s, precision="fp64", max_nb=MAX_NB, **kw):
     from paper_2005_02656_gb300 import SphSim
-    sim = SphSim(s, precision=precision, max_nb=MAX_NB, **kw)
+    sim = SphSim(s, precision=precision, max_nb=max_nb, **kw)
     sim.find_neighbors()
     sim.density()
     sim.iad()
@@ -56,11 +70,15 @@ def _gpu(s, precision="fp64", **kw):
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_neighbors_bit_exact(name):
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+def test_neighbors_bit_exact(name, precision):
+    """Sorted id lists equal the oracle's: from the int32 lists (FP64 and the
+    FP32-mixed "lists" form share that search) and from the hit masks of the
+    FP32-mixed staged form."""
     s = CASES[name]
     rc, ref_s, ref = oracle_outputs(s, ng_target=0, max_nb=MAX_NB)
     assert rc == 0
-    got, counts, ids, flags = _gpu(s)
+    got, counts, ids, flags = _gpu(s, precision=precision)
     assert flags == 0
     np.testing.assert_array_equal(counts, ref["nn"])
     mb = ids.shape[1]
@@ -83,17 +101,39 @@ def test_fp64_fields(name):
         assert e[k] <= FP64_TOL, (k, e)
 
 
-@pytest.mark.parametrize("name", ["box20", "patch20", "kh32", "box16_varh"])
-def test_fp32_mixed_fields(name):
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("pair_mode", ["staged", "lists"])
+def test_fp32_mixed_fields(name, pair_mode):
     s = CASES[name]
     rc, ref_s, ref = oracle_outputs(s, ng_target=0, max_nb=MAX_NB)
     assert rc == 0
-    got, counts, _, flags = _gpu(s, precision="fp32_mixed")
+    got, counts, _, flags = _gpu(s, precision="fp32_mixed", pair_mode=pair_mode)
     assert flags == 0
     np.testing.assert_array_equal(counts, ref["nn"])   # lists are exact in both precisions
     e = field_errors(got, ref)
     for k, tol in FP32_TOL.items():
         assert e[k] <= tol, (k, e)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+def test_big_cells_rounds_windows_and_list_passes(precision):
+    """Neighbour sets bit-exact and fields within tolerance when cells exceed
+    every shared-memory size of the staged pair passes (several target
+    rounds, candidate windows and list-expansion passes per cell)."""
+    s = BIG_CELLS
+    rc, ref_s, ref = oracle_outputs(s, ng_target=0, max_nb=BIG_MAX_NB)
+    assert rc == 0
+    assert ref["nn"].max() > 3 * 128          # several list passes for the large-h targets
+    got, counts, ids, flags = _gpu(s, precision=precision, max_nb=BIG_MAX_NB)
+    assert flags == 0
+    np.testing.assert_array_equal(counts, ref["nn"])
+    for a in range(counts.shape[0]):
+        k = counts[a]
+        np.testing.assert_array_equal(ids[a, :k], ref["nbr"][a, :k])
+    e = field_errors(got, ref)
+    tol = ({k: FP64_TOL for k in ("rho", "a", "du")} if precision == "fp64" else FP32_TOL)
+    for k, t in tol.items():
+        assert e[k] <= t, (k, e)
 
 
 @pytest.mark.parametrize("name", ["box20", "box16_varh", "kh32"])
