@@ -456,13 +456,28 @@ SPH_API int sph_profile(sph_ctx* ctx, int enable);
  * Synchronises on the last recorded event. */
 SPH_API int sph_stage_times(sph_ctx* ctx, double* ms, int64_t* steps);
 
-/* Cumulative device counters since sph_init (synchronous read):
+/* Cumulative device counters since sph_init (synchronous read), HOST array
+ * of 6:
  * out[0] (target, candidate) pairs tested by the neighbour search,
  * out[1] of which decided by the exact FP64 criterion (inside the FP32
  *        prefilter's error margin),
  * out[2] neighbour pairs found by sph_step (sum over steps of sum_a nn_a),
- * out[3] particle updates done by sph_step (sum over steps of n). */
+ * out[3] particle updates done by sph_step (sum over steps of n),
+ * out[4] staged candidate slots recorded by the SPH_PAIRS_STAGED search
+ *        (sum over cells of S, one 4-byte entry each),
+ * out[5] hit-mask words it wrote (sum over cells of na ceil(S / 64), 8 bytes
+ *        each). */
 SPH_API int sph_stats(sph_ctx* ctx, uint64_t* out);
+
+/* The FP32 fused-multiply-add rate of the current device in TFLOP/s,
+ * measured by the library's own kernel: every thread of SMs x 8 blocks of 256
+ * runs 8 independent chains of 65,536 dependent FFMAs, timed with CUDA events
+ * on `stream` after one untimed launch (2 flops per FFMA).  It is the
+ * measured denominator of the FP32-pipe roofline of the pair sums.  The paper
+ * has no counterpart; it is a measurement utility.  Synchronous; allocates
+ * nothing but two events.  Returns SPH_OK, SPH_ERR_INVALID_ARG (NULL
+ * tflops) or SPH_ERR_CUDA. */
+SPH_API int sph_measure_fp32_peak(double* tflops, sph_stream_t stream);
 
 /* Number of kernels the library launched on this context so far. */
 SPH_API int64_t sph_launch_count(const sph_ctx* ctx);

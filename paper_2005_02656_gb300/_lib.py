@@ -49,7 +49,7 @@ EXPORTS = ("sph_default_params", "sph_init", "sph_destroy", "sph_set_params", "s
            "sph_ensemble_replay", "sph_ensemble_error_word", "sph_ensemble_last_error",
            "sph_ensemble_info", "sph_ensemble_phase_times", "sph_gravity", "sph_adjoint_init", "sph_adjoint_destroy", "sph_adjoint_forward",
            "sph_adjoint_backward", "sph_adjoint_info", "sph_adjoint_time_steps",
-           "sph_adjoint_last_error")
+           "sph_adjoint_last_error", "sph_measure_fp32_peak")
 STAGES = ("sort", "find", "density", "iad", "momentum", "dt", "update")
 ENS_PHASES = ("reset", "extent", "grid", "count", "scan", "items", "scatter", "order", "gather",
               "find", "density", "iad", "momentum", "dt", "update")
@@ -174,6 +174,8 @@ def load(path: str = LIB_PATH):
     lib.sph_profile.restype = I
     lib.sph_stage_times.argtypes = [ctxp, P, P]
     lib.sph_stage_times.restype = I
+    lib.sph_measure_fp32_peak.argtypes = [P, P]
+    lib.sph_measure_fp32_peak.restype = I
     _lib = lib
     return lib
 

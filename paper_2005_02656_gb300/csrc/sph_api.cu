@@ -206,7 +206,7 @@ void free_all(sph_ctx* ctx) {
                   ctx->perm_tmp, ctx->perm, ctx->tbl_count, ctx->tbl_start, ctx->occ,
                   ctx->scan_part, ctx->cell_of, ctx->s.x, ctx->s_id_buf, ctx->pos32,
                   ctx->cell3, ctx->nn, ctx->nbr, ctx->wcache, ctx->vol, ctx->rec_d, ctx->rec_i,
-                  ctx->rec_m, ctx->cmeta, ctx->sent, ctx->masks, ctx->salloc, ctx->recA, ctx->recV,
+                  ctx->rec_m, ctx->cmeta, ctx->sent, ctx->masks, ctx->salloc, ctx->cells, ctx->recA, ctx->recV,
                   ctx->recQ, ctx->recC, ctx->recC2, ctx->red.part, ctx->red.counter, ctx->stats,
                   ctx->hm_buf, ctx->hm_id, ctx->grav_buf};
   for (void* p : ptrs)
@@ -368,7 +368,8 @@ int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {
   ALLOC(ctx->cmeta, n);
   ALLOC(ctx->sent, (size_t)ctx->sent_cap);
   ALLOC(ctx->masks, (size_t)ctx->mask_cap);
-  ALLOC(ctx->salloc, 2);
+  ALLOC(ctx->salloc, 4);
+  ALLOC(ctx->cells, 2 * n);
   ALLOC(ctx->recA, n);
   ALLOC(ctx->recV, n);
   ALLOC(ctx->recQ, n);
@@ -376,7 +377,7 @@ int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {
   ALLOC(ctx->recC2, n);
   ALLOC(ctx->red.part, sph::kReduceBlocks * 16);
   ALLOC(ctx->red.counter, 8);
-  ALLOC(ctx->stats, 4);
+  ALLOC(ctx->stats, sph::kStats);
 #undef ALLOC
   if (sbuf) {
     double** f[13] = {&ctx->s.x, &ctx->s.y, &ctx->s.z, &ctx->s.vx, &ctx->s.vy, &ctx->s.vz,
@@ -393,7 +394,7 @@ int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {
     e = cudaMemset(ctx->err, 0, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(ctx->red.counter, 0, 8 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(ctx->diag, 0, 32 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMemset(ctx->stats, 0, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->stats, 0, sph::kStats * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(ctx->tbl_count, 0, sph::kMaxTable * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) rc = sph::cuda_fail(ctx, e, "init");
@@ -734,7 +735,8 @@ int sph_stats(sph_ctx* ctx, uint64_t* out) {
   if (!ctx || !out) return SPH_ERR_INVALID_ARG;
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess)
-    e = cudaMemcpy(out, ctx->stats, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    e = cudaMemcpy(out, ctx->stats, sph::kStats * sizeof(unsigned long long),
+                   cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return sph::cuda_fail(ctx, e, "sph_stats");
   return SPH_OK;
 }

@@ -17,6 +17,7 @@ constexpr int kProfRing = 64;                   // step event sets kept before f
 constexpr int kHTab = 4097;                     // h factors tabulated for counts 0..4096
 constexpr int kKernelTableN = 20000;            // kernel values of SPH_KERNEL_TABLE
 constexpr int kMaskWords = 32;                  // hit-mask words per particle (staged pairs)
+constexpr int kStats = 6;                       // cumulative device counters (sph_stats)
 
 // Cell grid of the current step, computed on the device from the particles'
 // extent and h_max, read by every later kernel of the step.
@@ -128,7 +129,8 @@ struct sph_ctx {
   uint4* cmeta;
   uint32_t* sent;
   unsigned long long* masks;
-  unsigned long long* salloc;
+  unsigned long long* salloc;  // [0] entries, [1] mask words, [2] fast cells, [3] other cells
+  uint32_t* cells;             // 2 n_max: the pipelined passes' cells, then the others
   int64_t sent_cap;
   int64_t mask_cap;
   // momentum records as planes: (offset, 1/h^2), (v, m),
@@ -139,11 +141,12 @@ struct sph_ctx {
   float4* recC;
   float2* recC2;
   int find_mask_blocks;   // persistent CTAs of the mask-writing search
-  int pass_blocks[3];     // persistent CTAs of the density, IAD, momentum passes
+  int pass_blocks[6];     // persistent CTAs of the density, IAD, momentum passes (general
+                          // kernels, then pipelined ones at +3)
 
   // reductions
   sph::Reduce red;
-  unsigned long long* stats;  // 4 cumulative counters (sph_stats)
+  unsigned long long* stats;  // kStats cumulative counters (sph_stats)
 
   // per-stage timing (sph_profile): a ring of event sets, one per step
   int prof;

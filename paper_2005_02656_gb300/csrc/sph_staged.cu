@@ -54,6 +54,10 @@ using find::pair_index;
 
 // ------------------------------------------------------------------ search --
 
+constexpr int kTR = 64;         // targets per round of the pair passes
+constexpr int kLC = 128;        // list entries per target and list pass
+constexpr int kPipeWin = 832;   // staged candidates of a cell the pipelined passes take
+
 // A cell is staged (hit masks) when its stencil holds at most kStagedMaxP
 // particles, so a target's mask row is at most kStagedMaxP / 64 words and the
 // mask buffer (kMaskWords per particle) cannot overflow; larger stencils (a
@@ -62,6 +66,12 @@ using find::pair_index;
 constexpr int kStagedMaxP = 64 * kMaskWords;
 constexpr uint32_t kListForm = 0xffffffffu;
 
+// Targets of a cell (bit 15 of a staged cell's field is its pipelined-pass flag).
+__device__ __forceinline__ int cell_na(uint4 md) {
+  return (int)(md.w & (md.y == kListForm ? 0xffffu : 0x7fffu));
+}
+__device__ __forceinline__ int cell_S(uint4 md) { return (int)(md.w >> 16); }
+
 struct MaskOut {
   uint4* meta;                  // per occupied cell
   uint32_t* sent;               // staged candidate entries
@@ -69,7 +79,18 @@ struct MaskOut {
   unsigned long long* alloc;    // [0] entries taken, [1] mask words taken
   unsigned long long sent_cap;  // capacities of sent and masks
   unsigned long long mask_cap;
+  uint16_t* slist;              // staged-slot lists (rows of max_nb entries)
+  uint32_t* fcells;             // cells of the pipelined passes (alloc[2] of them)
+  uint32_t* scells;             // the other cells (alloc[3])
 };
+
+// Row of particle a in the staged-slot lists: max_nb uint16 entries inside the
+// particle's int32 list row (a particle's cell is either staged or in list
+// form, so the row serves one of the two).  16-byte aligned: max_nb is a
+// multiple of 4.
+__device__ __forceinline__ uint16_t* slot_row(uint16_t* slist, int64_t a, int max_nb) {
+  return slist + 2 * a * max_nb;
+}
 
 template <bool WRAP, int WIN>
 __device__ __forceinline__ void find_cell_masks(const Grid& g, uint32_t cell, uint32_t code,
@@ -80,7 +101,9 @@ __device__ __forceinline__ void find_cell_masks(const Grid& g, uint32_t cell, ui
                                                 uint32_t* nbr, int max_nb, const MaskOut& mo,
                                                 uint32_t* err,
                                                 FindWarpSmemT<WIN>& W, unsigned long long& tested,
-                                                unsigned long long& exact) {
+                                                unsigned long long& exact,
+                                                unsigned long long& slots,
+                                                unsigned long long& words) {
   const int lane = threadIdx.x & 31;
   Stencil& S = W.S;
   const float esum = g.err32[0] + g.err32[1] + g.err32[2];
@@ -108,7 +131,10 @@ __device__ __forceinline__ void find_cell_masks(const Grid& g, uint32_t cell, ui
     __syncwarp();
     find::find_cell<WRAP, WIN>(g, code, s, pos32, tbl_start, tbl_count, nn, nbr, max_nb, err,
                                W, tested, exact);
-    if (lane == 0) mo.meta[cell] = make_uint4(0u, kListForm, (uint32_t)a0, (uint32_t)na & 0xffffu);
+    if (lane == 0) {
+      mo.meta[cell] = make_uint4(0u, kListForm, (uint32_t)a0, (uint32_t)na & 0xffffu);
+      mo.scells[atomicAdd(mo.alloc + 3, 1ull)] = cell;
+    }
     __syncwarp();
     return;
   }
@@ -263,10 +289,78 @@ __device__ __forceinline__ void find_cell_masks(const Grid& g, uint32_t cell, ui
     wn = rem;
     __syncwarp();
   }
+  const uint32_t staged = 64u * gb + (uint32_t)wn;
   if (lane == 0) {
-    const uint32_t staged = 64u * gb + (uint32_t)wn;
-    mo.meta[cell] = make_uint4(slot_base, mask_base, (uint32_t)a0,
-                               (staged << 16) | ((uint32_t)na & 0xffffu));
+    slots += staged;
+    words += (unsigned long long)na * ((staged + 63) >> 6);
+  }
+  // The staged-slot lists: lane t walks the hit masks it wrote for target t
+  // (still in L2) in one loop over words and bits, packing slot indices into
+  // a 128-bit register eight at a time and storing each full group with one
+  // 16-byte store; the rest, up to max_nb entries, one by one.
+  // The round's mask words are first copied (coalesced) into the window,
+  // which is free now: nblk <= kStagedMaxP / 64 = 32 words per target.
+  const int nblk = (int)((staged + 63) >> 6);
+  static_assert(kStagedMaxP / 64 * 32 * 8 <= 4 * WIN * 4, "mask copy fits the window");
+  unsigned long long* mcopy = reinterpret_cast<unsigned long long*>(W.cx);
+  int kl = 0, kmax = 0;  // this lane's count and its largest over the rounds
+  for (int t0 = 0; t0 < na; t0 += 32, kmax = max(kmax, kl), kl = 0) {
+    const int t = t0 + lane;
+    __syncwarp();
+#pragma unroll 4
+    for (int blk = 0; blk < nblk; ++blk)
+      mcopy[blk * 32 + lane] =
+          t < na ? mo.masks[mask_base + (uint32_t)blk * (uint32_t)na + (uint32_t)t] : 0ull;
+    __syncwarp();
+    if (t >= na) continue;
+    uint16_t* row = slot_row(mo.slist, (int64_t)a0 + t, max_nb);
+    int& k = kl;
+    uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;  // entries k-8..k-1 of the group being filled
+    k = 0;
+    int blk = 0;
+    uint64_t w = nblk > 0 ? mcopy[lane] : 0;
+    for (;;) {
+      if (!w) {
+        if (++blk >= nblk) break;
+        w = mcopy[blk * 32 + lane];
+        continue;
+      }
+      const int q = __clzll((long long)w);
+      w ^= kTop >> q;
+      const uint32_t e = (uint32_t)(64 * blk + q);
+      b0 = __funnelshift_r(b0, b1, 16);
+      b1 = __funnelshift_r(b1, b2, 16);
+      b2 = __funnelshift_r(b2, b3, 16);
+      b3 = (b3 >> 16) | (e << 16);
+      ++k;
+      if ((k & 7) == 0) {
+        if (k <= max_nb) {
+          *reinterpret_cast<uint4*>(row + (k - 8)) = make_uint4(b0, b1, b2, b3);
+        } else if (k - 8 < max_nb) {  // a group across max_nb (max_nb = 4 mod 8)
+          const uint32_t bb[4] = {b0, b1, b2, b3};
+          for (int i = 0; k - 8 + i < max_nb; ++i)
+            row[k - 8 + i] = (uint16_t)(bb[i >> 1] >> (16 * (i & 1)));
+        }
+      }
+    }
+    // the last, partial group (entries (k & ~7) .. k - 1, at the top of b)
+    const int r = k & 7;
+    const uint32_t bb[4] = {b0, b1, b2, b3};
+    for (int i = 0; i < r; ++i) {
+      const int pos = (k & ~7) + i, src = 8 - r + i;
+      if (pos < max_nb) row[pos] = (uint16_t)(bb[src >> 1] >> (16 * (src & 1)));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+  // cells the pipelined passes take whole: one round of targets, one window
+  // of staged candidates, one list chunk per target
+  const bool fast = na <= kTR && (int)staged <= kPipeWin && kmax <= kLC;
+  if (lane == 0) {
+    mo.meta[cell] = make_uint4(slot_base, (uint32_t)gself, (uint32_t)a0,
+                               (staged << 16) | (fast ? 0x8000u : 0u) | (uint32_t)na);
+    const unsigned long long q = atomicAdd(mo.alloc + (fast ? 2 : 3), 1ull);
+    (fast ? mo.fcells : mo.scells)[q] = cell;
   }
   __syncwarp();
 }
@@ -282,11 +376,11 @@ __global__ void __launch_bounds__(kFindThreads, 4) k_find_mask(
   FindWarpSmem& W = reinterpret_cast<FindWarpSmem*>(smem_raw)[warp];
   const Grid g = *gp;
   if ((g.wrap32 != 0) != WRAP) return;
-  unsigned long long tested = 0, exact = 0;
+  unsigned long long tested = 0, exact = 0, slots = 0, words = 0;
   const uint32_t gw = blockIdx.x * kFindWarps + warp, nw = gridDim.x * kFindWarps;
   for (uint32_t cell = gw; cell < g.n_occ; cell += nw)
     find_cell_masks<WRAP, kFindWindow>(g, cell, occ[cell], s, pos32, tbl_start, tbl_count, nn,
-                                       nbr, max_nb, mo, err, W, tested, exact);
+                                       nbr, max_nb, mo, err, W, tested, exact, slots, words);
   for (int o = 16; o > 0; o >>= 1) {
     tested += __shfl_xor_sync(0xffffffffu, tested, o);
     exact += __shfl_xor_sync(0xffffffffu, exact, o);
@@ -294,15 +388,15 @@ __global__ void __launch_bounds__(kFindThreads, 4) k_find_mask(
   if (lane == 0) {
     atomicAdd(stats + 0, tested);
     atomicAdd(stats + 1, exact);
+    atomicAdd(stats + 4, slots);   // lane 0 alone counted its cells' slots and words
+    atomicAdd(stats + 5, words);
   }
 }
 
 // ------------------------------------------------------------- pair passes --
 
-constexpr int kPT = 256;        // threads per CTA (pair passes)
-constexpr int kTR = 64;         // targets per round
-constexpr int kLC = 128;        // list entries per target and expansion pass
-constexpr int kLS = kLC + 2;    // list row stride (uint16): rows start in different banks
+constexpr int kPT = 256;        // threads per CTA (general pair passes)
+constexpr int kLS = kLC + 8;    // list row stride (uint16): 16-byte aligned rows, in different banks
 constexpr int kMaxSub = 32;     // threads sharing one target, at most
 
 __device__ __forceinline__ float wrap32(float d, const Grid& g, int ax) {
@@ -333,6 +427,73 @@ __device__ __forceinline__ float s_pow(float t, int n, const float2* tab) {
   return tab ? kernel_w32_tab(t, 1.0f, tab) : kernel_w32(t, 1.0f, n);
 }
 
+// Paired FP32: two pairs per instruction (f32x2 arithmetic of sm_100+), each
+// component rounded exactly as the scalar operation.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// s_pow for two arguments: the polynomial and the powers in paired FP32.
+__device__ __forceinline__ float2 s_pow2(float2 t, int n, const float2* tab) {
+  if (tab) return make_float2(kernel_w32_tab(t.x, 1.0f, tab), kernel_w32_tab(t.y, 1.0f, tab));
+  t = make_float2(fminf(t.x, 4.0f), fminf(t.y, 4.0f));
+  constexpr SincCoefs<kSincTerms32> C{};
+  float2 s = f2((float)C.c[kSincTerms32 - 1]);
+#pragma unroll
+  for (int k = kSincTerms32 - 2; k >= 0; --k) s = __ffma2_rn(s, t, f2((float)C.c[k]));
+  if (n == 6) {
+    const float2 s2 = __fmul2_rn(s, s);
+    return __fmul2_rn(__fmul2_rn(s2, s2), s2);
+  }
+  return make_float2(ipow(s.x, n), ipow(s.y, n));
+}
+
+// Separations b - a of two neighbours (paired), with the FP32 minimum image
+// on periodic axes of fewer than 3 cells.
+__device__ __forceinline__ void sep2(const Grid& g, float4 b0, float4 b1, float ax_, float ay,
+                                     float az, float2& dx, float2& dy, float2& dz) {
+  dx = __fadd2_rn(f2(b0.x, b1.x), f2(-ax_));
+  dy = __fadd2_rn(f2(b0.y, b1.y), f2(-ay));
+  dz = __fadd2_rn(f2(b0.z, b1.z), f2(-az));
+  if (g.wrap32) {
+    if (g.periodic[0]) dx = make_float2(wrap32(dx.x, g, 0), wrap32(dx.y, g, 0));
+    if (g.periodic[1]) dy = make_float2(wrap32(dy.x, g, 1), wrap32(dy.y, g, 1));
+    if (g.periodic[2]) dz = make_float2(wrap32(dz.x, g, 2), wrap32(dz.y, g, 2));
+  }
+}
+
+// Asynchronous global -> shared copies (cp.async, no register staging): the
+// pipelined passes copy the next cell's records and lists while the current
+// cell is computed.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Adds the cell shift of entry e to the position of staged record j (plane 0).
+__device__ __forceinline__ void add_shift(float4* rec, int j, uint32_t e, const Grid& g) {
+  float sx, sy, sz;
+  entry_shift(e, g, sx, sy, sz);
+  float4 r = rec[j];
+  r.x += sx;
+  r.y += sy;
+  r.z += sz;
+  rec[j] = r;
+}
+
 // --- density + EOS (Eq. 1, self term included) ---
 struct DensityPass {
   static constexpr int kWin = 1024;   // staged slots held in shared memory
@@ -340,6 +501,11 @@ struct DensityPass {
   static constexpr int kV = 2;        // reduced values: sum m S^n, grad-h sum
   static constexpr int kMinBlocks = 4;
   static constexpr int kStageU = 4;   // staged records loaded per thread at once
+  static constexpr bool kPaired = true;  // two pairs per iteration in paired FP32
+  static constexpr int kPipeThreads = 256;
+  static constexpr int kPipeMinBlocks = 3;
+  static constexpr bool kTargetSmem = false;
+  static constexpr bool kPipePaired = true;
   const float4* rec_d;   // (offset, m) per particle
   const float4* pos32;   // (offset, h)
   const double* u;
@@ -368,6 +534,7 @@ struct DensityPass {
   }
   static __device__ void store(float4* rec, int j, const Rec& r) { rec[j] = r.r; }
   static __device__ Rec fetch(const float4* rec, int j) { return {rec[j]}; }
+  static __device__ void target_from(float4*, int, Target&) {}
   __device__ void load_target(int64_t a, Target& T) const {
     const float4 p = pos32[a];
     T.x = p.x;
@@ -383,14 +550,34 @@ struct DensityPass {
     acc[0] = fmaf(r.w, s_pow(tt, sinc_n, ktab), acc[0]);
     if (gradh) acc[1] = fmaf(r.w, kernel_tdw32(tt, 1.0f, sinc_n), acc[1]);
   }
-  __device__ void finish(int64_t a, const float* acc) const {
-    const float4 p = pos32[a];
+  __device__ void pair2(const Target& T, const Rec& R0, const Rec& R1, const Grid& g,
+                        float2* acc) const {
+    float2 dx, dy, dz;
+    sep2(g, R0.r, R1.r, T.x, T.y, T.z, dx, dy, dz);
+    const float2 tt =
+        __fmul2_rn(__ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx))), f2(T.hinv2));
+    const float2 m = f2(R0.r.w, R1.r.w);
+    acc[0] = __ffma2_rn(m, s_pow2(tt, sinc_n, ktab), acc[0]);
+    if (gradh)
+      acc[1] = __ffma2_rn(m, make_float2(kernel_tdw32(tt.x, 1.0f, sinc_n),
+                                         kernel_tdw32(tt.y, 1.0f, sinc_n)), acc[1]);
+  }
+  __device__ void copy_async(float4* rec, int j, int b) const { cp_async16(rec + j, rec_d + b); }
+  struct FinishIn {
+    float4 p;
+    float m;
+    double u;
+  };
+  __device__ FinishIn prefin(int64_t a) const { return {pos32[a], rec_d[a].w, u[a]}; }
+  __device__ void finish(int64_t a, const float* acc) const { finish2(a, acc, prefin(a)); }
+  __device__ void finish2(int64_t a, const float* acc, const FinishIn& fin) const {
+    const float4 p = fin.p;
     const float hinv2 = 1.0f / (p.w * p.w);
     const float norm = Bn * hinv2 / p.w;
-    const float ma = rec_d[a].w;
+    const float ma = fin.m;
     const float rho = norm * (ma + acc[0]);  // self term: S(0)^n = 1
     const double rho64 = (double)rho;
-    const double pr = (gamma - 1.0) * rho64 * u[a];
+    const double pr = (gamma - 1.0) * rho64 * fin.u;
     const double c = sqrt(gamma * pr / rho64);
     o.rho[a] = rho64;
     o.p[a] = pr;
@@ -416,6 +603,11 @@ struct IadPass {
   static constexpr int kV = 6;
   static constexpr int kMinBlocks = 4;
   static constexpr int kStageU = 4;
+  static constexpr bool kPaired = true;
+  static constexpr int kPipeThreads = 256;
+  static constexpr int kPipeMinBlocks = 3;
+  static constexpr bool kTargetSmem = false;
+  static constexpr bool kPipePaired = true;
   const float4* rec_i;   // (offset, m / rho)
   const float4* recA;    // (offset, 1 / h^2)
   const float4* recQ;    // (B_n / h^3, ...)
@@ -440,6 +632,7 @@ struct IadPass {
   }
   static __device__ void store(float4* rec, int j, const Rec& r) { rec[j] = r.r; }
   static __device__ Rec fetch(const float4* rec, int j) { return {rec[j]}; }
+  static __device__ void target_from(float4*, int, Target&) {}
   __device__ void load_target(int64_t a, Target& T) const {
     const float4 p = recA[a];
     T.x = p.x;
@@ -466,9 +659,34 @@ struct IadPass {
     acc[4] = fmaf(wy, dz, acc[4]);
     acc[5] = fmaf(wz, dz, acc[5]);
   }
-  __device__ void finish(int64_t a, const float* acc) const {
-    const float hinv2 = recA[a].w;
-    const float norm = recQ[a].x;
+  __device__ void pair2(const Target& T, const Rec& R0, const Rec& R1, const Grid& g,
+                        float2* acc) const {
+    float2 dx, dy, dz;
+    sep2(g, R0.r, R1.r, T.x, T.y, T.z, dx, dy, dz);
+    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+    const float2 tt = __fmul2_rn(r2, f2(T.hinv2));
+    const float2 ih = f2(T.inv_h);
+    dx = __fmul2_rn(dx, ih);
+    dy = __fmul2_rn(dy, ih);
+    dz = __fmul2_rn(dz, ih);
+    const float2 w = __fmul2_rn(f2(R0.r.w, R1.r.w), s_pow2(tt, sinc_n, ktab));
+    const float2 wx = __fmul2_rn(w, dx), wy = __fmul2_rn(w, dy), wz = __fmul2_rn(w, dz);
+    acc[0] = __ffma2_rn(wx, dx, acc[0]);
+    acc[1] = __ffma2_rn(wx, dy, acc[1]);
+    acc[2] = __ffma2_rn(wx, dz, acc[2]);
+    acc[3] = __ffma2_rn(wy, dy, acc[3]);
+    acc[4] = __ffma2_rn(wy, dz, acc[4]);
+    acc[5] = __ffma2_rn(wz, dz, acc[5]);
+  }
+  __device__ void copy_async(float4* rec, int j, int b) const { cp_async16(rec + j, rec_i + b); }
+  struct FinishIn {
+    float hinv2, norm;
+  };
+  __device__ FinishIn prefin(int64_t a) const { return {recA[a].w, recQ[a].x}; }
+  __device__ void finish(int64_t a, const float* acc) const { finish2(a, acc, prefin(a)); }
+  __device__ void finish2(int64_t a, const float* acc, const FinishIn& fin) const {
+    const float hinv2 = fin.hinv2;
+    const float norm = fin.norm;
     const float t00 = norm * acc[0], t01 = norm * acc[1], t02 = norm * acc[2];
     const float t11 = norm * acc[3], t12 = norm * acc[4], t22 = norm * acc[5];
     const float c00 = t11 * t22 - t12 * t12;
@@ -502,10 +720,15 @@ struct IadPass {
 
 // --- momentum and energy with artificial viscosity (Eqs. 2-5) ---
 struct MomentumPass {
-  static constexpr int kWin = 768;
+  static constexpr int kWin = kPipeWin;  // plane stride of the staged records
   static constexpr int kRecBytes = 72;  // four float4 planes and one float2 plane
   static constexpr int kV = 4;
-  static constexpr int kMinBlocks = 3;
+  static constexpr int kMinBlocks = 2;
+  static constexpr bool kPaired = false;  // the general kernel: scalar pairs
+  static constexpr int kPipeThreads = 512;  // pipelined kernel: one CTA of 16 warps per SM
+  static constexpr int kPipeMinBlocks = 1;
+  static constexpr bool kTargetSmem = true;  // target records from the staged window
+  static constexpr bool kPipePaired = true;  // 512 threads per CTA leave room for ~120 registers
   static constexpr int kStageU = 2;
   const float4* recA;    // (offset, 1 / h^2)
   const float4* recV;    // (v, m)
@@ -598,6 +821,71 @@ struct MomentumPass {
     acc[3] = fmaf(mb, fmaf(Wa * fmaf(0.25f * Pi, ira, T.q.y), vCa, 0.25f * Pi * irb * Wb * vCb),
                   acc[3]);
   }
+  __device__ void pair2(const Target& T, const Rec& R0, const Rec& R1, const Grid& g,
+                        float2* acc) const {
+    // two pairs of Eqs. 2-5, the operations of pair() in paired FP32
+    float2 dx, dy, dz;
+    sep2(g, R0.p, R1.p, T.p.x, T.p.y, T.p.z, dx, dy, dz);
+    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+    const float2 Wa = __fmul2_rn(f2(T.q.x), s_pow2(__fmul2_rn(r2, f2(T.p.w)), sinc_n, ktab));
+    const float2 Wb = __fmul2_rn(f2(R0.q.x, R1.q.x),
+                                 s_pow2(__fmul2_rn(r2, f2(R0.p.w, R1.p.w)), sinc_n, ktab));
+    const float2 Cadx = __ffma2_rn(f2(T.c02), dz, __ffma2_rn(f2(T.c01), dy, __fmul2_rn(f2(T.c00), dx)));
+    const float2 Cady = __ffma2_rn(f2(T.c12), dz, __ffma2_rn(f2(T.c11), dy, __fmul2_rn(f2(T.c01), dx)));
+    const float2 Cadz = __ffma2_rn(f2(T.c22), dz, __ffma2_rn(f2(T.c12), dy, __fmul2_rn(f2(T.c02), dx)));
+    const float2 b00 = f2(R0.c.x, R1.c.x), b01 = f2(R0.c.y, R1.c.y), b02 = f2(R0.c.z, R1.c.z);
+    const float2 b11 = f2(R0.c.w, R1.c.w), b12 = f2(R0.c2.x, R1.c2.x), b22 = f2(R0.c2.y, R1.c2.y);
+    const float2 Cbdx = __ffma2_rn(b02, dz, __ffma2_rn(b01, dy, __fmul2_rn(b00, dx)));
+    const float2 Cbdy = __ffma2_rn(b12, dz, __ffma2_rn(b11, dy, __fmul2_rn(b01, dx)));
+    const float2 Cbdz = __ffma2_rn(b22, dz, __ffma2_rn(b12, dy, __fmul2_rn(b02, dx)));
+    const float2 vabx = __fadd2_rn(f2(T.v.x), f2(-R0.v.x, -R1.v.x));
+    const float2 vaby = __fadd2_rn(f2(T.v.y), f2(-R0.v.y, -R1.v.y));
+    const float2 vabz = __fadd2_rn(f2(T.v.z), f2(-R0.v.z, -R1.v.z));
+    const float2 xvn = __ffma2_rn(dz, vabz, __ffma2_rn(dy, vaby, __fmul2_rn(dx, vabx)));
+    const float2 xv = make_float2(-xvn.x, -xvn.y);
+    // Eq. 5 without a branch: w_ab = x_ab.v_ab / r, Pi = 0 unless approaching
+    const float2 w = __fmul2_rn(xv, make_float2(rsqrtf(r2.x), rsqrtf(r2.y)));
+    const float2 vsig = __fadd2_rn(__fadd2_rn(f2(T.q.z), f2(R0.q.z, R1.q.z)),
+                                   __fmul2_rn(f2(-3.0f), w));
+    const float2 pv = __fmul2_rn(__fmul2_rn(f2(-0.5f * alpha), vsig), w);
+    const float2 Pi = make_float2(xv.x < 0.0f ? pv.x : 0.0f, xv.y < 0.0f ? pv.y : 0.0f);
+    const float2 irb = f2(R0.q.w, R1.q.w);
+    const float2 mb = f2(R0.v.w, R1.v.w);
+    const float2 hP = __fmul2_rn(f2(0.5f), Pi), qP = __fmul2_rn(f2(0.25f), Pi);
+    const float2 fa = __fmul2_rn(__fmul2_rn(mb, Wa), __ffma2_rn(hP, f2(T.q.w), f2(T.q.y)));
+    const float2 fb = __fmul2_rn(__fmul2_rn(mb, Wb), __ffma2_rn(hP, irb, f2(R0.q.y, R1.q.y)));
+    acc[0] = __ffma2_rn(f2(-1.0f), __ffma2_rn(fa, Cadx, __fmul2_rn(fb, Cbdx)), acc[0]);
+    acc[1] = __ffma2_rn(f2(-1.0f), __ffma2_rn(fa, Cady, __fmul2_rn(fb, Cbdy)), acc[1]);
+    acc[2] = __ffma2_rn(f2(-1.0f), __ffma2_rn(fa, Cadz, __fmul2_rn(fb, Cbdz)), acc[2]);
+    const float2 vCa = __ffma2_rn(vabz, Cadz, __ffma2_rn(vaby, Cady, __fmul2_rn(vabx, Cadx)));
+    const float2 vCb = __ffma2_rn(vabz, Cbdz, __ffma2_rn(vaby, Cbdy, __fmul2_rn(vabx, Cbdx)));
+    const float2 i1 = __fmul2_rn(Wa, __ffma2_rn(qP, f2(T.q.w), f2(T.q.y)));
+    const float2 i2 = __fmul2_rn(__fmul2_rn(__fmul2_rn(qP, irb), Wb), vCb);
+    acc[3] = __ffma2_rn(mb, __ffma2_rn(i1, vCa, i2), acc[3]);
+  }
+  __device__ void copy_async(float4* rec, int j, int b) const {
+    cp_async16(plane(rec, 0) + j, recA + b);
+    cp_async16(plane(rec, 1) + j, recV + b);
+    cp_async16(plane(rec, 2) + j, recQ + b);
+    cp_async16(plane(rec, 3) + j, recC + b);
+    cp_async8(plane2(rec) + j, recC2 + b);
+  }
+  // The target's data is its own staged record (its cell's shift is zero).
+  static __device__ void target_from(float4* rec, int j, Target& T) {
+    const Rec R = fetch(rec, j);
+    T.p = R.p;
+    T.v = R.v;
+    T.q = R.q;
+    T.c00 = R.c.x;
+    T.c01 = R.c.y;
+    T.c02 = R.c.z;
+    T.c11 = R.c.w;
+    T.c12 = R.c2.x;
+    T.c22 = R.c2.y;
+  }
+  struct FinishIn {};
+  __device__ FinishIn prefin(int64_t) const { return {}; }
+  __device__ void finish2(int64_t a, const float* acc, const FinishIn&) const { finish(a, acc); }
   __device__ void finish(int64_t a, const float* acc) const {
     o.ax[a] = acc[0];
     o.ay[a] = acc[1];
@@ -613,13 +901,11 @@ struct MomentumPass {
 // targets' totals.
 template <class Pass>
 struct PassSmem {
-  static constexpr int kWB = Pass::kWin / 64;
   static constexpr size_t kRec = (size_t)Pass::kWin * Pass::kRecBytes;
   static constexpr size_t kLists = (size_t)kTR * kLS * sizeof(uint16_t);
   static constexpr size_t kPart = (size_t)kPT * Pass::kV * sizeof(float);
   static constexpr size_t kListsOrPart = kLists > kPart ? kLists : kPart;
-  static constexpr size_t kCnt = (size_t)kTR * kWB * sizeof(int);
-  static constexpr size_t kBytes = kRec + ((kListsOrPart + 15) & ~(size_t)15) + kCnt +
+  static constexpr size_t kBytes = kRec + ((kListsOrPart + 15) & ~(size_t)15) +
                                    (size_t)kTR * sizeof(int);
   static_assert(kRec % 16 == 0, "record planes keep 16-byte alignment");
 };
@@ -627,12 +913,38 @@ struct PassSmem {
 // Neighbour source of one pass launch.
 struct Src {
   const uint4* meta;                 // per occupied cell
+  const uint32_t* cells;             // the cells of this launch
+  const unsigned long long* ncells;  // their number (device counter)
   const uint32_t* sent;              // staged candidate entries
-  const unsigned long long* masks;   // hit masks
-  const int32_t* nn;                 // list-form cells: counts and int32 lists
-  const uint32_t* nbr;
+  const int32_t* nn;                 // exact neighbour counts
+  const uint32_t* nbr;               // list-form cells: int32 lists
+  const uint16_t* slist;             // staged cells: staged-slot lists (same rows as nbr)
   int max_nb;
 };
+
+// Values of the next cell loaded while the current one is computed: the
+// neighbour counts of its first targets and its first staged entries.
+template <int U>
+struct Prefetch {
+  int nn;          // thread tid < kTR: count of target tid of the first round
+  uint32_t e[U];   // staged entries tid + u kPT of the first window
+};
+
+template <class Pass>
+__device__ __forceinline__ void prefetch_cell(const Src& src, uint4 md,
+                                              Prefetch<Pass::kStageU>& pf) {
+  const int tid = threadIdx.x;
+  const int S = cell_S(md), na = cell_na(md);
+  const bool staged = md.y != kListForm;
+  pf.nn = (staged && tid < kTR && tid < na) ? __ldg(src.nn + md.z + tid) : 0;
+  (void)S;
+  const int wn = min(Pass::kWin, S);
+#pragma unroll
+  for (int u = 0; u < Pass::kStageU; ++u) {
+    const int j = tid + u * kPT;
+    pf.e[u] = (staged && j < wn) ? __ldg(src.sent + md.x + (uint32_t)j) : 0u;
+  }
+}
 
 template <class Pass>
 __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, const Grid* gp,
@@ -643,18 +955,26 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
   float4* rec = reinterpret_cast<float4*>(smem_raw);
   uint16_t* lists = reinterpret_cast<uint16_t*>(smem_raw + SM::kRec);
   float* part = reinterpret_cast<float*>(smem_raw + SM::kRec);
-  int* cnt = reinterpret_cast<int*>(smem_raw + SM::kRec + ((SM::kListsOrPart + 15) & ~(size_t)15));
-  int* tot = cnt + kTR * SM::kWB;
+  int* tot = reinterpret_cast<int*>(smem_raw + SM::kRec + ((SM::kListsOrPart + 15) & ~(size_t)15));
   const Grid g = *gp;
-  const uint32_t n_occ = g.n_occ;
+  const uint32_t n_cells = (uint32_t)*src.ncells;
+  const uint32_t G = gridDim.x;
   const int tid = threadIdx.x;
-  uint4 md_next = blockIdx.x < n_occ ? __ldg(src.meta + blockIdx.x) : make_uint4(0, 0, 0, 0);
-  for (uint32_t cell = blockIdx.x; cell < n_occ; cell += gridDim.x) {
+  const uint4 zero4 = make_uint4(0u, kListForm, 0u, 0u);
+  auto meta_of = [&](uint32_t q) { return q < n_cells ? __ldg(src.meta + src.cells[q]) : zero4; };
+  uint4 md_next = meta_of(blockIdx.x);
+  uint4 md_after = meta_of(blockIdx.x + G);
+  Prefetch<U> pf;
+  prefetch_cell<Pass>(src, md_next, pf);
+  for (uint32_t q = blockIdx.x; q < n_cells; q += G) {
     const uint4 md = md_next;
-    if (cell + gridDim.x < n_occ) md_next = __ldg(src.meta + cell + gridDim.x);
-    const uint32_t slot_base = md.x, mask_base = md.y, a0 = md.z;
-    const int S = (int)(md.w >> 16), na = (int)(md.w & 0xffffu);
-    const bool list_form = mask_base == kListForm;
+    const Prefetch<U> cur = pf;
+    md_next = md_after;
+    md_after = meta_of(q + 2 * G);
+    prefetch_cell<Pass>(src, md_next, pf);  // lands while this cell is computed
+    const uint32_t slot_base = md.x, a0 = md.z;
+    const int S = cell_S(md), na = cell_na(md);
+    const bool list_form = md.y == kListForm;
     int staged_w0 = -1;
     for (int r0 = 0; r0 < na; r0 += kTR) {
       const int nr = min(kTR, na - r0);
@@ -662,80 +982,80 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
       if (nsub > kMaxSub) nsub = kMaxSub;
       const int t = tid / nsub, sub = tid - t * nsub;
       const bool active = t < nr;
+      const int64_t a = (int64_t)a0 + r0 + (active ? t : 0);
       typename Pass::Target T;
       float acc[Pass::kV];
+      float2 acc2[Pass::kV];  // paired partial sums, folded into acc at the end
 #pragma unroll
-      for (int v = 0; v < Pass::kV; ++v) acc[v] = 0.0f;
-      if (active) pass.load_target((int64_t)a0 + r0 + t, T);
+      for (int v = 0; v < Pass::kV; ++v) {
+        acc[v] = 0.0f;
+        acc2[v] = make_float2(0.0f, 0.0f);
+      }
+      if (active) pass.load_target(a, T);
       if (list_form) {
         // a cell whose stencil exceeds the staged form's limits: int32 lists,
         // neighbour records read from global memory
-        if (active) {
-          const int64_t a = (int64_t)a0 + r0 + t;
-          const int c = min(src.nn[a], src.max_nb);
-          const uint32_t* row = src.nbr + a * src.max_nb;
-          for (int k = sub; k < c; k += nsub) pass.pair(T, pass.load(__ldg(row + k), g), g, acc);
-        }
-      }
-      for (int w0 = 0; !list_form && w0 < S; w0 += Pass::kWin) {
-        const int wn = min(Pass::kWin, S - w0);
-        const int wb = (wn + 63) >> 6;
-        if (w0 != staged_w0) {
-          __syncthreads();  // the previous window's readers are done
-          const uint32_t* es = src.sent + slot_base + (uint32_t)w0;
-          for (int j0 = 0; j0 < wn; j0 += U * kPT) {
-            uint32_t e[U];
+        const int c = active ? min(__ldg(src.nn + a), src.max_nb) : 0;
+        const uint32_t* row = src.nbr + a * src.max_nb;
+        for (int k = sub; k < c; k += nsub) pass.pair(T, pass.load(__ldg(row + k), g), g, acc);
+      } else {
+        // the targets' staged-slot lists (ascending slots), kLC entries per
+        // target at a time in shared memory, walked window by window
+        if (tid < nr)
+          tot[tid] = min(r0 == 0 ? cur.nn : __ldg(src.nn + a0 + r0 + tid), src.max_nb);
+        for (int lp = 0;; ++lp) {
+          __syncthreads();  // tot written; the previous readers are done
+          for (int i = tid; i < nr * (kLC / 4); i += kPT) {
+            const int tt = i / (kLC / 4), k4 = 4 * (i - tt * (kLC / 4));
+            const int kk = lp * kLC + k4;
+            if (kk < tot[tt])  // 8-byte chunks: max_nb and kLC are multiples of 4
+              *reinterpret_cast<uint2*>(lists + tt * kLS + k4) = __ldg(reinterpret_cast<const uint2*>(
+                  slot_row(const_cast<uint16_t*>(src.slist), (int64_t)a0 + r0 + tt, src.max_nb) + kk));
+          }
+          const int nl = active ? min(tot[t] - lp * kLC, kLC) : 0;
+          int k = sub;
+          for (int w0 = 0; w0 < S; w0 += Pass::kWin) {
+            const int wn = min(Pass::kWin, S - w0);
+            if (w0 != staged_w0) {
+              if (w0 > 0) __syncthreads();  // the previous window's readers are done
+              const uint32_t* es = src.sent + slot_base + (uint32_t)w0;
+              const bool pre = w0 == 0 && r0 == 0 && lp == 0;  // entries already loaded
+              for (int j0 = 0; j0 < wn; j0 += U * kPT) {
+                uint32_t e[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-              const int j = j0 + u * kPT + tid;
-              e[u] = j < wn ? __ldg(es + j) : 0u;
-            }
+                for (int u = 0; u < U; ++u) {
+                  const int j = j0 + u * kPT + tid;
+                  e[u] = (pre && j0 == 0) ? cur.e[u] : (j < wn ? __ldg(es + j) : 0u);
+                }
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-              if (j0 + u * kPT + tid < wn) Pass::store(rec, j0 + u * kPT + tid, pass.load(e[u], g));
-          }
-          staged_w0 = w0;
-        }
-        const uint32_t mrow = mask_base + (uint32_t)(w0 >> 6) * (uint32_t)na + (uint32_t)r0;
-        for (int ep = 0;; ++ep) {
-          __syncthreads();  // records staged; lists free
-          for (int i = tid; i < nr * wb; i += kPT) {
-            const int tt = i % nr, jb = i / nr;
-            cnt[jb * kTR + tt] = __popcll(__ldg(src.masks + mrow + (uint32_t)jb * na + tt));
-          }
-          __syncthreads();
-          for (int i = tid; i < nr * wb; i += kPT) {
-            const int tt = i % nr, jb = i / nr;
-            int pos = -ep * kLC;
-            for (int j = 0; j < jb; ++j) pos += cnt[j * kTR + tt];
-            if (jb == 0) {
-              int sum = 0;
-              for (int j = 0; j < wb; ++j) sum += cnt[j * kTR + tt];
-              tot[tt] = sum;
+                for (int u = 0; u < U; ++u)
+                  if (j0 + u * kPT + tid < wn)
+                    Pass::store(rec, j0 + u * kPT + tid, pass.load(e[u], g));
+              }
+              staged_w0 = w0;
             }
-            uint64_t w = __ldg(src.masks + mrow + (uint32_t)jb * na + tt);
-            uint16_t* row = lists + tt * kLS;
-            while (w && pos < kLC) {
-              const int q = __clzll((long long)w);
-              w ^= kTop >> q;
-              if (pos >= 0) row[pos] = (uint16_t)(64 * jb + q);
-              ++pos;
-            }
-          }
-          __syncthreads();
-          if (active) {
-            const int nl = min(tot[t] - ep * kLC, kLC);
+            __syncthreads();  // lists copied, records staged
             const uint16_t* row = lists + t * kLS;
-            for (int k = sub; k < nl; k += nsub) pass.pair(T, Pass::fetch(rec, row[k]), g, acc);
+            const int wend = w0 + wn;
+            for (; Pass::kPaired && k + nsub < nl; k += 2 * nsub) {  // two entries at a time
+              const int s0 = row[k], s1 = row[k + nsub];
+              if (s1 >= wend) break;                 // ascending: s0 < s1
+              pass.pair2(T, Pass::fetch(rec, s0 - w0), Pass::fetch(rec, s1 - w0), g, acc2);
+            }
+            for (; k < nl; k += nsub) {
+              const int slot = row[k];
+              if (slot >= wend) break;
+              pass.pair(T, Pass::fetch(rec, slot - w0), g, acc);
+            }
           }
-          const int more = __syncthreads_or(active && sub == 0 && tot[t] > (ep + 1) * kLC);
+          const int more = __syncthreads_or(active && sub == 0 && tot[t] > (lp + 1) * kLC);
           if (!more) break;
         }
       }
       // the nsub partial sums of each target, added in a fixed order
       __syncthreads();
 #pragma unroll
-      for (int v = 0; v < Pass::kV; ++v) part[v * kPT + tid] = acc[v];
+      for (int v = 0; v < Pass::kV; ++v) part[v * kPT + tid] = acc[v] + (acc2[v].x + acc2[v].y);
       __syncthreads();
       if (tid < nr) {
         float sm[Pass::kV];
@@ -749,6 +1069,212 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
       }
     }
   }
+}
+
+// ------------------------------------------------- pipelined pair passes --
+//
+// The cells the search marked (one round of at most kTR targets, at most
+// kPipeWin staged candidates, lists of at most kLC entries) are processed by a
+// two-stage software pipeline: while a CTA computes cell i from one half of a
+// double buffer, the records and lists of cell i + 1 are arriving in the other
+// half by cp.async, and the staged entries and counts of cell i + 2 by plain
+// loads into registers.  Each thread adds the cell shifts to the records it
+// copied itself once they have landed, so one barrier per cell publishes the
+// cell's data and one more the per-target partial sums.
+
+template <class Pass>
+struct PipeSmem {
+  static constexpr int PT = Pass::kPipeThreads;
+  static constexpr size_t kRec = (size_t)kPipeWin * Pass::kRecBytes;  // one buffer
+  static constexpr size_t kList = (size_t)kTR * kLS * sizeof(uint16_t);
+  static constexpr size_t kPart = (size_t)PT * Pass::kV * sizeof(float);
+  static constexpr size_t kBytes = 2 * kRec + 2 * kList + kPart + 2 * (size_t)kTR * sizeof(int);
+  static_assert(kRec % 16 == 0 && kList % 16 == 0 && kPart % 16 == 0, "16-byte aligned parts");
+};
+
+template <class Pass>
+__global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_cellpipe(
+    Pass pass, const Grid* gp, Src src) {
+  using SM = PipeSmem<Pass>;
+  constexpr int PT = Pass::kPipeThreads;
+  constexpr int U = (kPipeWin + PT - 1) / PT;  // staged slots per thread
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // the two halves of the double buffer: records, lists and counts of half h
+  auto rbuf = [&](int h) { return reinterpret_cast<float4*>(smem_raw + h * SM::kRec); };
+  auto lbuf = [&](int h) {
+    return reinterpret_cast<uint16_t*>(smem_raw + 2 * SM::kRec + h * SM::kList);
+  };
+  float* part = reinterpret_cast<float*>(smem_raw + 2 * SM::kRec + 2 * SM::kList);
+  int* tc0 = reinterpret_cast<int*>(smem_raw + 2 * SM::kRec + 2 * SM::kList + SM::kPart);
+  auto tcnt = [&](int h) { return tc0 + h * kTR; };
+  const Grid g = *gp;
+  const uint32_t n_cells = (uint32_t)*src.ncells;
+  const uint32_t G = gridDim.x;
+  const int tid = threadIdx.x;
+  uint32_t q = blockIdx.x;
+  if (q >= n_cells) return;
+  const uint4 none = make_uint4(0u, kListForm, 0u, 0u);
+  auto meta_of = [&](uint32_t qq) { return qq < n_cells ? __ldg(src.meta + src.cells[qq]) : none; };
+  // staged entries of a cell's slots tid + u PT, and count of its target tid
+  auto load_entries = [&](uint4 md, uint32_t* e) {
+    const int S = md.y == kListForm ? 0 : cell_S(md);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = tid + u * PT;
+      e[u] = j < S ? __ldg(src.sent + md.x + (uint32_t)j) : 0u;
+    }
+  };
+  auto load_count = [&](uint4 md) {
+    const int na = md.y == kListForm ? 0 : cell_na(md);
+    return tid < na ? min(__ldg(src.nn + md.z + tid), src.max_nb) : 0;
+  };
+  auto issue_records = [&](uint4 md, const uint32_t* e, float4* rec) {
+    const int S = cell_S(md);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = tid + u * PT;
+      if (j < S) pass.copy_async(rec, j, entry_index(e[u]));
+    }
+  };
+  auto issue_lists = [&](uint4 md, const int* cnt, uint16_t* lst) {
+    const int na = cell_na(md);
+    for (int i = tid; i < na * (kLC / 8); i += PT) {
+      const int tt = i / (kLC / 8), k8 = 8 * (i - tt * (kLC / 8));
+      if (k8 >= cnt[tt]) continue;
+      const uint16_t* grow =
+          slot_row(const_cast<uint16_t*>(src.slist), (int64_t)md.z + tt, src.max_nb) + k8;
+      if (k8 + 8 <= src.max_nb)
+        cp_async16(lst + tt * kLS + k8, grow);
+      else  // the last 4 entries of a row of max_nb = 4 mod 8
+        cp_async8(lst + tt * kLS + k8, grow);
+    }
+  };
+  // prologue: the first cell's copies, the second cell's entries and counts
+  uint4 md_cur = meta_of(q), md_nxt = meta_of(q + G), md_nn = meta_of(q + 2 * G);
+  uint32_t e_cur[U], e_nxt[U];
+  load_entries(md_cur, e_cur);
+  {
+    const int c0 = load_count(md_cur);
+    issue_records(md_cur, e_cur, rbuf(0));
+    if (tid < kTR) tcnt(0)[tid] = c0;
+    __syncthreads();
+    issue_lists(md_cur, tcnt(0), lbuf(0));
+    cp_async_commit();
+  }
+  load_entries(md_nxt, e_nxt);
+  int c_nxt = load_count(md_nxt);
+  typename Pass::Target T_cur, T_nxt;
+  auto target_map = [&](uint4 md, int& t, int& sub, int& nsub) {
+    const int na = cell_na(md);
+    nsub = na > 0 ? min(PT / na, kMaxSub) : 1;
+    t = tid / nsub;
+    sub = tid - t * nsub;
+  };
+  if (!Pass::kTargetSmem) {
+    int t, sub, nsub;
+    target_map(md_cur, t, sub, nsub);
+    if (t < cell_na(md_cur)) pass.load_target((int64_t)md_cur.z + t, T_cur);
+  }
+  int buf = 0;
+  for (;;) {
+    // this cell's records and lists have landed (the copies this thread made):
+    // add the cell shifts to the records this thread copied
+    cp_async_wait_all();
+    {
+      const int S = cell_S(md_cur);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = tid + u * PT;
+        if (j < S) add_shift(rbuf(buf), j, e_cur[u], g);
+      }
+    }
+    const bool has_nxt = q + G < n_cells;
+    if (has_nxt && tid < kTR) tcnt(buf ^ 1)[tid] = c_nxt;
+    __syncthreads();  // this cell's data published; the next cell's counts too
+    if (has_nxt) {
+      issue_records(md_nxt, e_nxt, rbuf(buf ^ 1));
+      issue_lists(md_nxt, tcnt(buf ^ 1), lbuf(buf ^ 1));
+    }
+    cp_async_commit();
+    // registers for the cell after next
+    uint32_t e_nn[U];
+    load_entries(md_nn, e_nn);
+    const int c_nn = load_count(md_nn);
+    const uint4 md_nnn = meta_of(q + 3 * G);
+    if (!Pass::kTargetSmem && has_nxt) {
+      int t, sub, nsub;
+      target_map(md_nxt, t, sub, nsub);
+      if (t < cell_na(md_nxt)) pass.load_target((int64_t)md_nxt.z + t, T_nxt);
+    }
+    // compute this cell
+    const int na = cell_na(md_cur);
+    const uint32_t a0 = md_cur.z;
+    int t, sub, nsub;
+    target_map(md_cur, t, sub, nsub);
+    const bool active = t < na;
+    typename Pass::FinishIn fin;
+    if (tid < na) fin = pass.prefin((int64_t)a0 + tid);
+    if (Pass::kTargetSmem && active) Pass::target_from(rbuf(buf), (int)md_cur.y + t, T_cur);
+    float acc[Pass::kV];
+    float2 acc2[Pass::kV];
+#pragma unroll
+    for (int v = 0; v < Pass::kV; ++v) {
+      acc[v] = 0.0f;
+      acc2[v] = make_float2(0.0f, 0.0f);
+    }
+    if (active) {
+      const uint16_t* row = lbuf(buf) + t * kLS;
+      const int nl = tcnt(buf)[t];
+      float4* rec = rbuf(buf);
+      int k = sub;
+      if (Pass::kPipePaired)
+        for (; k + nsub < nl; k += 2 * nsub)
+          pass.pair2(T_cur, Pass::fetch(rec, row[k]), Pass::fetch(rec, row[k + nsub]), g, acc2);
+      for (; k < nl; k += nsub) pass.pair(T_cur, Pass::fetch(rec, row[k]), g, acc);
+    }
+#pragma unroll
+    for (int v = 0; v < Pass::kV; ++v) part[v * PT + tid] = acc[v] + (acc2[v].x + acc2[v].y);
+    __syncthreads();  // partial sums published
+    if (tid < na) {
+      float sm[Pass::kV];
+#pragma unroll
+      for (int v = 0; v < Pass::kV; ++v) {
+        float x = 0.0f;
+        for (int qq = 0; qq < nsub; ++qq) x += part[v * PT + tid * nsub + qq];
+        sm[v] = x;
+      }
+      pass.finish2((int64_t)a0 + tid, sm, fin);
+    }
+    q += G;
+    if (q >= n_cells) break;
+    md_cur = md_nxt;
+    md_nxt = md_nn;
+    md_nn = md_nnn;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      e_cur[u] = e_nxt[u];
+      e_nxt[u] = e_nn[u];
+    }
+    c_nxt = c_nn;
+    if (!Pass::kTargetSmem) T_cur = T_nxt;
+    buf ^= 1;
+  }
+}
+
+template <class Pass>
+int pipe_blocks(sph_ctx* ctx, int* cache) {
+  if (!*cache) {  // once per context, on its device
+    using SM = PipeSmem<Pass>;
+    cudaFuncSetAttribute(k_cellpipe<Pass>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)SM::kBytes);
+    cudaFuncSetAttribute(k_cellpipe<Pass>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cellpipe<Pass>, SM::PT,
+                                                  SM::kBytes);
+    *cache = (per_sm > 0 ? per_sm : 1) * ctx->sm_count;
+  }
+  return *cache;
 }
 
 template <class Pass>
@@ -768,16 +1294,23 @@ int pass_blocks(sph_ctx* ctx, int* cache) {
 
 template <class Pass>
 void launch_pass(sph_ctx* ctx, const Pass& p, int* cache, cudaStream_t st) {
-  const int blocks = pass_blocks<Pass>(ctx, cache);
   Src src;
   src.meta = ctx->cmeta;
   src.sent = ctx->sent;
-  src.masks = ctx->masks;
   src.nn = ctx->nn;
   src.nbr = ctx->nbr;
+  src.slist = reinterpret_cast<uint16_t*>(ctx->nbr);
   src.max_nb = ctx->prm.max_nb;
-  k_cellpass<Pass><<<blocks, kPT, PassSmem<Pass>::kBytes, st>>>(p, ctx->grid, src);
-  ctx->launches += 1;
+  // the cells the search marked for the pipeline, then the others
+  src.cells = ctx->cells;
+  src.ncells = ctx->salloc + 2;
+  k_cellpipe<Pass><<<pipe_blocks<Pass>(ctx, cache + 3), Pass::kPipeThreads,
+                     PipeSmem<Pass>::kBytes, st>>>(p, ctx->grid, src);
+  src.cells = ctx->cells + ctx->n_max;
+  src.ncells = ctx->salloc + 3;
+  k_cellpass<Pass><<<pass_blocks<Pass>(ctx, cache), kPT, PassSmem<Pass>::kBytes, st>>>(
+      p, ctx->grid, src);
+  ctx->launches += 2;
 }
 
 // ----------------------------------------------------------------- export --
@@ -793,31 +1326,23 @@ __device__ __forceinline__ void insert_sorted(int64_t* row, int m, int64_t v) {
   row[k + 1] = v;
 }
 
-__global__ void k_export_masks(int64_t n, const int32_t* nn, const uint32_t* cell_of,
-                               const uint4* meta, const uint32_t* sent,
-                               const unsigned long long* masks, const uint32_t* nbr, int max_nb,
-                               const int64_t* id, int32_t* counts, int64_t* ids) {
+// The lists of a particle as sorted ids: staged cells from the staged-slot
+// list (slot -> staged entry -> particle), list-form cells from the int32 list.
+__global__ void k_export_lists(int64_t n, const int32_t* nn, const uint32_t* cell_of,
+                               const uint4* meta, const uint32_t* sent, const uint16_t* slist,
+                               const uint32_t* nbr, int max_nb, const int64_t* id,
+                               int32_t* counts, int64_t* ids) {
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
        a += (int64_t)gridDim.x * blockDim.x) {
     counts[a] = nn[a];
     const uint4 md = meta[cell_of[a]];
     int64_t* row = ids + a * max_nb;
-    if (md.y == kListForm) {  // a list-form cell: its int32 list
-      const int c = min(nn[a], max_nb);
+    const int c = min(nn[a], max_nb);
+    if (md.y == kListForm) {
       for (int k = 0; k < c; ++k) insert_sorted(row, k, id[entry_index(nbr[a * max_nb + k])]);
-      continue;
-    }
-    const int S = (int)(md.w >> 16), na = (int)(md.w & 0xffffu);
-    const int t = (int)(a - (int64_t)md.z);
-    int m = 0;
-    for (int blk = 0; 64 * blk < S; ++blk) {
-      uint64_t w = masks[md.y + (uint32_t)blk * na + t];
-      while (w && m < max_nb) {
-        const int q = __clzll((long long)w);
-        w ^= kTop >> q;
-        insert_sorted(row, m, id[entry_index(sent[md.x + 64u * blk + q])]);
-        ++m;
-      }
+    } else {
+      const uint16_t* srow = slist + 2 * a * max_nb;
+      for (int k = 0; k < c; ++k) insert_sorted(row, k, id[entry_index(sent[md.x + srow[k]])]);
     }
   }
 }
@@ -850,7 +1375,10 @@ void launch_find_masks(sph_ctx* ctx, const StateView& s, int64_t n, cudaStream_t
   mo.alloc = ctx->salloc;
   mo.sent_cap = (unsigned long long)ctx->sent_cap;
   mo.mask_cap = (unsigned long long)ctx->mask_cap;
-  cudaMemsetAsync(ctx->salloc, 0, 2 * sizeof(unsigned long long), st);
+  mo.slist = reinterpret_cast<uint16_t*>(ctx->nbr);
+  mo.fcells = ctx->cells;
+  mo.scells = ctx->cells + ctx->n_max;
+  cudaMemsetAsync(ctx->salloc, 0, 4 * sizeof(unsigned long long), st);
   k_find_mask<false><<<ctx->find_mask_blocks, kFindThreads, smem, st>>>(
       ctx->grid, s, ctx->pos32, ctx->occ, ctx->tbl_start, ctx->tbl_count, ctx->nn, ctx->nbr,
       ctx->prm.max_nb, mo, ctx->err, ctx->stats);
@@ -920,9 +1448,9 @@ void launch_export_masks(sph_ctx* ctx, const StateView& s, int64_t n, int32_t* c
   int64_t b = (n + 127) / 128;
   if (b > (int64_t)ctx->sm_count * 32) b = ctx->sm_count * 32;
   if (b < 1) b = 1;
-  k_export_masks<<<(int)b, 128, 0, st>>>(n, ctx->nn, ctx->cell_of, ctx->cmeta, ctx->sent,
-                                         ctx->masks, ctx->nbr, ctx->prm.max_nb, s.id, counts,
-                                         ids);
+  k_export_lists<<<(int)b, 128, 0, st>>>(n, ctx->nn, ctx->cell_of, ctx->cmeta, ctx->sent,
+                                         reinterpret_cast<const uint16_t*>(ctx->nbr), ctx->nbr,
+                                         ctx->prm.max_nb, s.id, counts, ids);
   ctx->launches += 1;
 }
 

@@ -182,10 +182,11 @@ class SphSim:
         return int(self.lib.sph_launch_count(self.ctx))
 
     def stats(self) -> dict:
-        out = np.zeros(4, dtype=np.uint64)
+        out = np.zeros(6, dtype=np.uint64)
         self._call(self.lib.sph_stats, out.ctypes.data_as(C.c_void_p))
         return {"candidates": int(out[0]), "exact_tests": int(out[1]), "pairs": int(out[2]),
-                "particle_updates": int(out[3])}
+                "particle_updates": int(out[3]), "staged_slots": int(out[4]),
+                "mask_words": int(out[5])}
 
     def profile(self, enable: bool = True):
         self._call(self.lib.sph_profile, 1 if enable else 0)
