@@ -502,6 +502,7 @@ struct DensityPass {
   static constexpr int kMinBlocks = 4;
   static constexpr int kStageU = 4;   // staged records loaded per thread at once
   static constexpr bool kPaired = true;  // two pairs per iteration in paired FP32
+  static constexpr bool kPipe = true;  // marked cells in the pipelined kernel
   static constexpr int kPipeThreads = 256;
   static constexpr int kPipeMinBlocks = 3;
   static constexpr bool kTargetSmem = false;
@@ -576,23 +577,27 @@ struct DensityPass {
     const float norm = Bn * hinv2 / p.w;
     const float ma = fin.m;
     const float rho = norm * (ma + acc[0]);  // self term: S(0)^n = 1
-    const double rho64 = (double)rho;
-    const double pr = (gamma - 1.0) * rho64 * fin.u;
-    const double c = sqrt(gamma * pr / rho64);
-    o.rho[a] = rho64;
-    o.p[a] = pr;
-    o.c[a] = c;
+    // the ideal-gas equation of state in FP32 (from the FP32 density; FP64
+    // division and square root run at 1/64 of the FP32 rate on this part):
+    // P = (gamma - 1) rho u, c = sqrt(gamma P / rho) = sqrt(gamma (gamma - 1) u),
+    // X = P / rho^2 = (gamma - 1) u / rho
+    const float uf = (float)fin.u, g1 = (float)(gamma - 1.0);
+    const float pr = g1 * rho * uf;
+    const float c = sqrtf((float)gamma * g1 * uf);
     const float inv_rho = 1.0f / rho;
+    float X = g1 * uf * inv_rho;
+    o.rho[a] = (double)rho;
+    o.p[a] = (double)pr;
+    o.c[a] = (double)c;
     rec_i[a] = make_float4(p.x, p.y, p.z, ma * inv_rho);
     recA[a] = make_float4(p.x, p.y, p.z, hinv2);
-    double X = pr / (rho64 * rho64);
     if (gradh) {
-      const double omega = -2.0 * (double)(norm * acc[1]) / (3.0 * rho64);
+      const float omega = -2.0f * norm * acc[1] * inv_rho * (1.0f / 3.0f);
       X /= omega;
-      if (o.omega) o.omega[a] = omega;
+      if (o.omega) o.omega[a] = (double)omega;
     }
-    recQ[a] = make_float4(norm, (float)X, (float)c, inv_rho);
-    if (!isfinite(rho64) || !isfinite(c)) raise_flag(err, SPH_FLAG_NONFINITE);
+    recQ[a] = make_float4(norm, X, c, inv_rho);
+    if (!isfinite(rho) || !isfinite(c)) raise_flag(err, SPH_FLAG_NONFINITE);
   }
 };
 
@@ -604,6 +609,7 @@ struct IadPass {
   static constexpr int kMinBlocks = 4;
   static constexpr int kStageU = 4;
   static constexpr bool kPaired = true;
+  static constexpr bool kPipe = true;
   static constexpr int kPipeThreads = 256;
   static constexpr int kPipeMinBlocks = 3;
   static constexpr bool kTargetSmem = false;
@@ -720,15 +726,18 @@ struct IadPass {
 
 // --- momentum and energy with artificial viscosity (Eqs. 2-5) ---
 struct MomentumPass {
-  static constexpr int kWin = kPipeWin;  // plane stride of the staged records
+  static constexpr int kWin = 768;  // staged slots (plane stride): three CTAs of 73 KB per SM
   static constexpr int kRecBytes = 72;  // four float4 planes and one float2 plane
   static constexpr int kV = 4;
-  static constexpr int kMinBlocks = 2;
-  static constexpr bool kPaired = false;  // the general kernel: scalar pairs
-  static constexpr int kPipeThreads = 512;  // pipelined kernel: one CTA of 16 warps per SM
+  static constexpr int kMinBlocks = 3;
+  static constexpr bool kPaired = false;  // the paired body needs ~120 registers: scalar pairs
+                                          // keep three CTAs per SM
+  static constexpr bool kPipe = false;    // 72-byte records leave no room for a double buffer
+                                          // beside more than one CTA per SM (measured slower)
+  static constexpr int kPipeThreads = 512;
   static constexpr int kPipeMinBlocks = 1;
   static constexpr bool kTargetSmem = true;  // target records from the staged window
-  static constexpr bool kPipePaired = true;  // 512 threads per CTA leave room for ~120 registers
+  static constexpr bool kPipePaired = true;
   static constexpr int kStageU = 2;
   const float4* recA;    // (offset, 1 / h^2)
   const float4* recV;    // (v, m)
@@ -1301,11 +1310,16 @@ void launch_pass(sph_ctx* ctx, const Pass& p, int* cache, cudaStream_t st) {
   src.nbr = ctx->nbr;
   src.slist = reinterpret_cast<uint16_t*>(ctx->nbr);
   src.max_nb = ctx->prm.max_nb;
-  // the cells the search marked for the pipeline, then the others
+  // the cells the search marked: the pipelined kernel (passes with kPipe)
+  // or the general one; then the others in the general kernel
   src.cells = ctx->cells;
   src.ncells = ctx->salloc + 2;
-  k_cellpipe<Pass><<<pipe_blocks<Pass>(ctx, cache + 3), Pass::kPipeThreads,
-                     PipeSmem<Pass>::kBytes, st>>>(p, ctx->grid, src);
+  if constexpr (Pass::kPipe)
+    k_cellpipe<Pass><<<pipe_blocks<Pass>(ctx, cache + 3), Pass::kPipeThreads,
+                       PipeSmem<Pass>::kBytes, st>>>(p, ctx->grid, src);
+  else
+    k_cellpass<Pass><<<pass_blocks<Pass>(ctx, cache), kPT, PassSmem<Pass>::kBytes, st>>>(
+        p, ctx->grid, src);
   src.cells = ctx->cells + ctx->n_max;
   src.ncells = ctx->salloc + 3;
   k_cellpass<Pass><<<pass_blocks<Pass>(ctx, cache), kPT, PassSmem<Pass>::kBytes, st>>>(
