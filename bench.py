@@ -34,23 +34,54 @@ SAMPLE_NX = 112        # the same recipe at 1/8 scale for the CPU oracle (1,067,
 # Flop model per directed neighbour pair (add/sub/mul = 1, FMA = 2,
 # rsqrt/div = 1), counted on the operations of each pair loop as written; the
 # neighbour search counts per (target, candidate) test.  The FP64 kernels
-# evaluate a 15-term series for W (32 flops, 9 terms in FP32) and IAD and
+# evaluate a 15-term series for W (32 flops, 7 terms in FP32) and IAD and
 # momentum read W_ab(h_a) cached by the density pass.
 FLOPS = {"find": 14, "density": 37, "iad": 57, "momentum": 140}
 FLOPS64 = {"find": 14, "density": 43, "iad": 19, "momentum": 131}
-# Algorithmic HBM bytes of one step, each array read or written once: per
-# particle (sort/gather 344, find 20, density 100, IAD 132, momentum 116,
-# dt 16, update 244) and per list entry (the int32 list written by the search
-# and read by density, IAD and momentum; the FP64 path also writes W_ab(h_a)
-# per entry and reads it twice).  Neighbour data gathered by the pair kernels
-# is counted once per particle, as the record it is read from.
-STEP_BYTES = {"fp32_mixed": {"particle": 972, "entry": 16},
-              "fp64": {"particle": 972, "entry": 40}}
+# Algorithmic HBM bytes of each kernel launch, every array it touches read or
+# written once: per particle (its own fields in and out; the records of
+# neighbours counted once, as the particle's own record), per staged slot (the
+# 4-byte candidate entry, FP32-mixed), per hit-mask word (8 bytes, FP32-mixed)
+# and per list entry (the int32 list and, FP64, the cached W_ab(h_a)).
+#   FP32-mixed  find: pos32 16 in, nn 4 out; entries and mask words written.
+#               density: rec_d 16, pos32 16, u 8 in; rho, p, c 24, rec_i,
+#               recA, recQ 48 out.  IAD: rec_i, recA, recQ 48 in; iad 48,
+#               recC 16, recC2 8 out.  momentum: recA, recV, recQ, recC, recC2
+#               72 in; ax, ay, az, du 32 out.  Each pass reads the entries and
+#               mask words once.
+#   FP64        find: pos32 16 in, nn 4 out, the list written.  density: x, y,
+#               z, h, m, u 48 in, rho, p, c 24 out, the list read and W
+#               written.  IAD: x, y, z, h, m, rho 48 in, iad 48 out.  momentum:
+#               17 fields 136 in, 32 out; both read the list and W.
+KERNEL_BYTES = {
+    "fp32_mixed": {"find": {"particle": 20, "slot": 4, "word": 8, "entry": 0},
+                   "density": {"particle": 112, "slot": 4, "word": 8, "entry": 0},
+                   "iad": {"particle": 120, "slot": 4, "word": 8, "entry": 0},
+                   "momentum": {"particle": 104, "slot": 4, "word": 8, "entry": 0}},
+    "fp64": {"find": {"particle": 20, "slot": 0, "word": 0, "entry": 4},
+             "density": {"particle": 72, "slot": 0, "word": 0, "entry": 12},
+             "iad": {"particle": 96, "slot": 0, "word": 0, "entry": 12},
+             "momentum": {"particle": 168, "slot": 0, "word": 0, "entry": 12}},
+}
+# Per particle, the rest of the step (sort and gather 344, dt 16, update 244).
+OTHER_BYTES = 604
+PAIR_KERNELS = ("find", "density", "iad", "momentum")
+# The survey's step model: about 25 kflop and 1.9 KB of HBM traffic per
+# particle for the FP32-mixed step at 100 neighbours.
+SURVEY_MODEL = {"flops_per_particle": 25_000, "bytes_per_particle": 1_900}
 # Derived non-tensor peaks: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz, and
 # the FP64 pipe at 1/64 of that rate.
 SM, LANES, MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM * LANES * 2 * MHZ * 1e6 / 1e12
 FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
+FP32_SRC = "fp32 pipe, derived: 152 SMs x 128 lanes x 2 x 2070 MHz"
+FP64_SRC = "fp64 pipe, derived: 1/64 of 152 SMs x 128 lanes x 2 x 2070 MHz"
+# DRAM traffic of the pair-path kernels: an ncu capture (dram__bytes_read.sum,
+# dram__bytes_write.sum per launch) of the FP32-mixed step on the 1/8-scale KH
+# box, committed with the hash of the kernel sources it was taken on.
+TRAFFIC_META = os.path.join("profiles", "ncu_dram_kh1m.json")
+STAGE_KERNELS = {"find": ("k_find_mask",), "density": ("DensityPass",), "iad": ("IadPass",),
+                 "momentum": ("MomentumPass",)}
 
 
 def parse():
@@ -154,17 +185,61 @@ def source_hash(names):
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel_key):
-    """DRAM bytes per launch of a kernel from the committed ncu summary, or
-    None when the kernel's source changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+def read_ncu_csv(path):
+    """Per-launch metrics of an `ncu --csv --print-units base` log: a list of
+    (launch id, kernel name, {metric: value}) in launch order."""
+    import csv
+    rows = []
+    with open(path, newline="") as f:
+        lines = [ln for ln in f if not ln.startswith("==")]
+    start = next((i for i, ln in enumerate(lines) if ln.startswith('"ID"')), None)
+    if start is None:
+        return []
+    launches = {}
+    for rec in csv.DictReader(lines[start:]):
+        try:
+            lid = int(rec["ID"])
+            val = float(rec["Metric Value"].replace(",", ""))
+        except (KeyError, ValueError):
+            continue
+        unit = rec.get("Metric Unit", "")
+        scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1.0,
+                 "usecond": 1e3, "msecond": 1e6}.get(unit, 1.0)
+        launches.setdefault(lid, (rec["Kernel Name"], {}))[1][rec["Metric Name"]] = val * scale
+    for lid in sorted(launches):
+        rows.append((lid, launches[lid][0], launches[lid][1]))
+    return rows
+
+
+def stage_traffic(rows):
+    """DRAM bytes (read + write) per stage of the last captured step: for each
+    kernel of a stage its last launch, summed over the stage's kernels."""
+    last = {}
+    for lid, name, m in rows:
+        if "dram__bytes_read.sum" in m and "dram__bytes_write.sum" in m:
+            last[name] = m["dram__bytes_read.sum"] + m["dram__bytes_write.sum"]
+    out = {}
+    for stage, keys in STAGE_KERNELS.items():
+        hits = [b for name, b in last.items() if any(k in name for k in keys)]
+        if hits:
+            out[stage] = sum(hits)
+    return out
+
+
+def traffic_for(stage, n):
+    """DRAM bytes per launch of a stage's kernels at n particles, from the
+    committed ncu capture scaled by the particle count (the cell populations
+    and neighbour counts do not depend on the box size), or None when the
+    capture is absent or its kernel sources changed since it was taken."""
     try:
-        t = json.load(open(path))[kernel_key]
+        meta = json.load(open(os.path.join(ROOT, TRAFFIC_META)))
     except Exception:
         return None
-    if t.get("source_sha") != source_hash(t["source"]):
+    if meta.get("source_sha") != source_hash(meta["source"]):
         return None
-    return t["bytes_per_launch"]
+    rows = read_ncu_csv(os.path.join(ROOT, "profiles", meta["csv"]))
+    b = stage_traffic(rows).get(stage)
+    return None if b is None else b * n / meta["n_particles"]
 
 
 def reduce_max(value, dist, device):
@@ -215,6 +290,8 @@ def run_gpu(args, world, rank, local):
     clocks = Clocks(local)
     clocks.start()
     windows = {}
+    from paper_2005_02656_gb300 import measure_fp32_peak
+    fp32_measured = max(measure_fp32_peak() for _ in range(3))   # the FFMA probe, best of 3
     state = sph_inputs.kelvin_helmholtz(args.nx, seed_index=2)
     n = int(state["x"].shape[0])
 
@@ -258,9 +335,12 @@ def run_gpu(args, world, rank, local):
         pairs = (st1["pairs"] - st0["pairs"]) / steps
         cands = (st1["candidates"] - st0["candidates"]) / steps
         exact = (st1["exact_tests"] - st0["exact_tests"]) / steps
+        slots = (st1["staged_slots"] - st0["staged_slots"]) / steps
+        words = (st1["mask_words"] - st0["mask_words"]) / steps
         return {"ms": ms, "ms_median": ms_median,
                 "stages": {k: v / max(nsteps, 1) for k, v in stages.items()},
-                "pairs": pairs, "candidates": cands, "exact_tests": exact, "launches": launches,
+                "pairs": pairs, "candidates": cands, "exact_tests": exact, "slots": slots,
+                "words": words, "launches": launches,
                 "flags": flags, "dt": float(diag[8]),
                 "conservation": conservation(d0, d1, steps)}
 
@@ -319,6 +399,7 @@ def run_gpu(args, world, rank, local):
             r["clocks"] = clocks.summary(*windows[key])
     ms32 = max_over_ranks(r32["ms"])
     res = {"n": n, "r32": r32, "r64": r64, "ms32": ms32, "e2e": e2e, "ensemble": ens,
+           "fp32_measured": fp32_measured,
            "adjoint": adjoint, "table": tab, "gravity": gravity}
     if r64 is not None:
         res["ms64"] = max_over_ranks(r64["ms"])
@@ -485,15 +566,53 @@ def _gravity_one(dev, windows, calls, theta, precision):
                          "flops_per_call": flops}}
 
 
+def kernel_bytes(r, n, precision, kern):
+    b = KERNEL_BYTES[precision][kern]
+    return (b["particle"] * n + b["slot"] * r.get("slots", 0) + b["word"] * r.get("words", 0) +
+            b["entry"] * r["pairs"])
+
+
+def kernel_rooflines(r, n, precision, fp32_measured=None):
+    """Each pair-path kernel (search, density, IAD, momentum) against both
+    roofs: its flops on the pipe of its precision (derived peak, and the
+    probe's measured FP32 rate) and its algorithmic bytes on the measured HBM
+    copy bandwidth; `bound` names the nearer roof."""
+    hbm = peaks().get("hbm_gbs")
+    units = {"find": r["candidates"], "density": r["pairs"], "iad": r["pairs"],
+             "momentum": r["pairs"]}
+    out = {}
+    for k in PAIR_KERNELS:
+        ms = r["stages"][k]
+        fp64 = precision == "fp64" and k != "find"
+        flops = (FLOPS64 if fp64 else FLOPS)[k] * units[k]
+        tflops = flops / (ms * 1e-3) / 1e12
+        peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+        alu = {"achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+               "peak_source": FP64_SRC if fp64 else FP32_SRC, "flops_per_launch": flops}
+        if not fp64 and fp32_measured:
+            alu["peak_measured"] = fp32_measured
+            alu["frac_measured"] = tflops / fp32_measured
+        nbytes = kernel_bytes(r, n, precision, k)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        mem = {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm if hbm else None,
+               "bytes_per_launch": nbytes,
+               "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)" if hbm else None}
+        bound = "alu" if mem["frac"] is None or alu["frac"] >= mem["frac"] else "hbm"
+        out[k] = {"ms_per_launch": ms, "bound": bound, "alu": alu, "hbm": mem,
+                  "traffic": traffic_for(k, n) if precision == "fp32_mixed" else None}
+    return out
+
+
 def step_roofline(r, n, precision, ms_step):
     """The whole step against max(bytes / HBM bandwidth, pipe time of its
     flops): the search on the FP32 pipe, the pair sums on the pipe of the
-    path's precision; the kernels run one after another, so pipe times add."""
+    path's precision; the kernels run one after another, so pipe times add.
+    The survey's model (25 kflop, 1.9 KB per particle, all on the FP32 pipe)
+    is given beside it."""
     hbm = peaks().get("hbm_gbs")
-    entries = r["pairs"]
-    b = STEP_BYTES[precision]
-    bytes_step = b["particle"] * n + b["entry"] * entries
+    bytes_step = OTHER_BYTES * n + sum(kernel_bytes(r, n, precision, k) for k in PAIR_KERNELS)
     find_ms = FLOPS["find"] * r["candidates"] / (FP32_PEAK_TFLOPS * 1e12) * 1e3
+    entries = r["pairs"]
     if precision == "fp64":
         pair_flops = sum(FLOPS64[k] for k in ("density", "iad", "momentum")) * entries
         pair_ms = pair_flops / (FP64_PEAK_TFLOPS * 1e12) * 1e3
@@ -504,33 +623,37 @@ def step_roofline(r, n, precision, ms_step):
     hbm_ms = bytes_step / (hbm * 1e9) * 1e3 if hbm else None
     bound = "alu" if hbm_ms is None or alu_ms >= hbm_ms else "hbm"
     t = max(alu_ms, hbm_ms or 0.0)
+    sv_alu = SURVEY_MODEL["flops_per_particle"] * n / (FP32_PEAK_TFLOPS * 1e12) * 1e3
+    sv_hbm = SURVEY_MODEL["bytes_per_particle"] * n / (hbm * 1e9) * 1e3 if hbm else None
+    sv_t = max(sv_alu, sv_hbm or 0.0)
     return {"bound": bound, "time_ms": t, "alu_ms": alu_ms, "hbm_ms": hbm_ms,
             "frac": t / ms_step, "bytes_per_step": bytes_step,
             "flops_per_step": FLOPS["find"] * r["candidates"] + pair_flops,
-            "hbm_peak_gbs": hbm, "peak_source": "HBM: MEASURED_PEAKS.json copy; pipes derived"}
+            "hbm_peak_gbs": hbm, "peak_source": "HBM: MEASURED_PEAKS.json copy; pipes derived",
+            "survey_model": dict(SURVEY_MODEL, alu_ms=sv_alu, hbm_ms=sv_hbm, time_ms=sv_t,
+                                 bound="alu" if sv_hbm is None or sv_alu >= sv_hbm else "hbm",
+                                 frac=sv_t / ms_step)}
 
 
-def roofline(r, n, precision):
-    """Dominant kernel's achieved vs peak under the flop model above."""
-    st = r["stages"]
-    units = {"find": r["candidates"], "density": r["pairs"], "iad": r["pairs"],
-             "momentum": r["pairs"]}
-    kern = max(("find", "density", "iad", "momentum"), key=lambda k: st[k])
-    flops = (FLOPS64 if precision == "fp64" else FLOPS)[kern] * units[kern]
-    ms = st[kern]
-    achieved = flops / (ms * 1e-3) / 1e12
-    if precision == "fp64" and kern != "find":
-        peak, pk = FP64_PEAK_TFLOPS, "fp64 pipe, derived: 1/64 of 152 SMs x 128 lanes x 2 x 2070 MHz"
+def roofline(r, n, precision, fp32_measured=None):
+    """The contract's roofline record: the dominant kernel (longest of the
+    four pair-path stages) against its nearer roof."""
+    ks = kernel_rooflines(r, n, precision, fp32_measured)
+    kern = max(PAIR_KERNELS, key=lambda k: r["stages"][k])
+    k = ks[kern]
+    roof = k["alu"] if k["bound"] == "alu" else k["hbm"]
+    out = {"kernel": f"{kern} ({precision})", "bound": k["bound"], "achieved": roof["achieved"],
+           "peak": roof["peak"], "unit": roof["unit"], "frac": roof["frac"],
+           "peak_source": roof["peak_source"], "ms_per_launch": k["ms_per_launch"],
+           "traffic": k["traffic"]}
+    if k["bound"] == "alu":
+        out["flops_per_launch"] = roof["flops_per_launch"]
+        for key in ("peak_measured", "frac_measured"):
+            if key in roof:
+                out[key] = roof[key]
     else:
-        peak, pk = FP32_PEAK_TFLOPS, "fp32 pipe, derived: 152 SMs x 128 lanes x 2 x 2070 MHz"
-    src = {"find": "sph_neighbors.cu", "density": "sph_pairs_fp32.cu", "iad": "sph_pairs_fp32.cu",
-           "momentum": "sph_pairs_fp32.cu"}[kern]
-    if precision == "fp64" and kern != "find":
-        src = "sph_pairs_fp64.cu"
-    return {"kernel": f"{kern} ({precision})", "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": pk,
-            "flops_per_launch": flops, "ms_per_launch": ms,
-            "traffic": traffic_for(f"{kern}_{precision}") if src else None}
+        out["bytes_per_launch"] = roof["bytes_per_launch"]
+    return out
 
 
 def cpu_baseline(max_seconds=20.0, max_steps=5):
@@ -657,14 +780,19 @@ def main():
         "neighbor_pairs_per_s": r32["pairs"] * world / (ms * 1e-3),
         "ms_per_step_median": r32["ms_median"],
         "stages_ms": r32["stages"],
-        "roofline": roofline(r32, n, "fp32_mixed"),
+        "roofline": roofline(r32, n, "fp32_mixed", res["fp32_measured"]),
+        "kernels_roofline": kernel_rooflines(r32, n, "fp32_mixed", res["fp32_measured"]),
         "step_roofline": step_roofline(r32, n, "fp32_mixed", ms),
+        "fp32_peak": {"derived_tflops": FP32_PEAK_TFLOPS, "measured_tflops": res["fp32_measured"],
+                      "measured_by": "sph_measure_fp32_peak: dependent-FMA chains, 8 per thread, "
+                                     "8 CTAs of 256 threads per SM, best of 3"},
         "gpu_launches": r32["launches"],
         "clocks": r32["clocks"],
         "error_flags": r32["flags"],
         "conservation": r32["conservation"],
         "search": {"candidates_per_step": r32["candidates"], "exact_tests_per_step": r32["exact_tests"],
-                   "pairs_per_step": r32["pairs"]},
+                   "pairs_per_step": r32["pairs"], "staged_slots_per_step": r32["slots"],
+                   "mask_words_per_step": r32["words"]},
     }
     if r64 is not None:
         ms64 = res["ms64"]
@@ -672,6 +800,7 @@ def main():
                         "ms_per_step_median": r64["ms_median"],
                         "neighbor_pairs_per_s": r64["pairs"] * world / (ms64 * 1e-3),
                         "stages_ms": r64["stages"], "roofline": roofline(r64, n, "fp64"),
+                        "kernels_roofline": kernel_rooflines(r64, n, "fp64"),
                         "step_roofline": step_roofline(r64, n, "fp64", ms64),
                         "gpu_launches": r64["launches"], "error_flags": r64["flags"],
                         "conservation": r64["conservation"], "clocks": r64["clocks"]}

@@ -151,6 +151,12 @@ typedef struct {
                                   in momentum and energy [0]                    */
   int pair_mode;               /* SPH_PAIRS_STAGED or SPH_PAIRS_LISTS, read by
                                   SPH_FP32_MIXED contexts [SPH_PAIRS_STAGED]     */
+  double energy_dt;            /* energy-rate limit of the time step (a reading;
+                                  section 4.2 names only a global minimum):
+                                  dt_n <= energy_dt * min_a u_a / |du_a| over
+                                  the particles with du_a != 0; 0 turns it off
+                                  [0].  Must be >= 0; not used by the ensemble
+                                  (sph_ensemble_init rejects a nonzero value)   */
 } sph_params;
 
 /* Fills *p with the defaults above and a periodic unit box. */
@@ -208,6 +214,7 @@ SPH_API int sph_momentum_energy(sph_ctx* ctx, sph_state* state, sph_stream_t str
 
 /* One full step: neighbour search, density + EOS, IAD, momentum/energy, the
  * global time step dt_n = min(courant * min_a h_a/c_a, dt_growth * dt_{n-1})
+ * (and energy_dt * min_a u_a/|du_a| when energy_dt > 0)
  * (no cap when dt_{n-1} = 0), and the update (half-step velocity kick by
  * (dt_n + dt_{n-1})/2, drift, predicted velocity, Adams-Bashforth energy,
  * periodic wrap, h <- h (1 + (ng_target/max(nn,1))^(1/3)) / 2).

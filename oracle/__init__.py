@@ -77,6 +77,8 @@ def _load():
                                                P, P]
         lib.oracle_timestep.restype = d
         lib.oracle_timestep.argtypes = [i64, P, P, d, d, d]
+        lib.oracle_timestep_u.restype = d
+        lib.oracle_timestep_u.argtypes = [i64, P, P, P, P, d, d, d, d]
         lib.oracle_update.restype = None
         lib.oracle_update.argtypes = [C.POINTER(_Box), i64] + [P] * 17 + [d, d, cint]
         lib.oracle_diagnostics.restype = None
@@ -130,6 +132,7 @@ class Params:
     max_nb: int = 160
     gradh: int = 0          # 1: grad-h terms Omega in Eqs. 2-3
     kernel_mode: int = 0    # 0: exact sinc kernel; 1: 20,000-entry table (section 4.5)
+    energy_dt: float = 0.0  # > 0: dt <= energy_dt * min u / |du| (opt-in reading)
 
 
 def num_threads() -> int:
@@ -260,9 +263,14 @@ def momentum_energy(box: Box, s: dict, rho_full, p_full, c_full, iad_full, nn, n
     return out
 
 
-def timestep(h, c, params: Params, dt_prev: float) -> float:
-    """Courant time step with growth cap."""
+def timestep(h, c, params: Params, dt_prev: float, u=None, du=None) -> float:
+    """Courant time step with growth cap; with params.energy_dt > 0 also the
+    energy-rate limit energy_dt * min u / |du| (u, du required then)."""
     h, c = _f64(h), _f64(c)
+    if params.energy_dt > 0.0:
+        u, du = _f64(u), _f64(du)
+        return _load().oracle_timestep_u(h.shape[0], _p(h), _p(c), _p(u), _p(du), params.courant,
+                                         float(params.energy_dt), params.dt_growth, float(dt_prev))
     return _load().oracle_timestep(h.shape[0], _p(h), _p(c), params.courant, params.dt_growth,
                                    float(dt_prev))
 
@@ -324,7 +332,7 @@ def step(box: Box, s: dict, params: Params, dt_prev: float, brute=False, record_
     rc, out = outputs(box, s, params, brute=brute, record_av=record_av)
     if rc not in (OK,):
         return rc, float("nan"), out
-    dt = timestep(s["h"], out["c"], params, dt_prev)
+    dt = timestep(s["h"], out["c"], params, dt_prev, u=s["u"], du=out["du"])
     update(box, s, out["ax"], out["ay"], out["az"], out["du"], out["nn"], dt, dt_prev,
            params.ng_target)
     return OK, dt, out

@@ -576,6 +576,35 @@ double oracle_timestep(int64_t n, const double* h, const double* c, double coura
   return dt;
 }
 
+/* Reading (opt-in, energy_dt > 0): the step is also limited by the rate of    */
+/* change of the internal energy, dt <= energy_dt * min_a u_a / |du_a| over   */
+/* the particles with du_a != 0, so that one forward-Euler step changes no u   */
+/* by more than the fraction energy_dt of itself.  Applied before the growth  */
+/* cap; energy_dt = 0 gives oracle_timestep.                                 */
+double oracle_timestep_u(int64_t n, const double* h, const double* c, const double* u,
+                         const double* du, double courant, double energy_dt, double dt_growth,
+                         double dt_prev) {
+  double mn = INFINITY, mu = INFINITY;
+  for (int64_t i = 0; i < n; ++i) {
+    double q = h[i] / c[i];
+    mn = q < mn ? q : mn;
+    if (energy_dt > 0.0 && du[i] != 0.0) {
+      double r = u[i] / fabs(du[i]);
+      mu = r < mu ? r : mu;
+    }
+  }
+  double dt = courant * mn;
+  if (energy_dt > 0.0) {
+    double du_lim = energy_dt * mu;
+    dt = du_lim < dt ? du_lim : dt;
+  }
+  if (dt_prev > 0.0) {
+    double cap = dt_growth * dt_prev;
+    dt = cap < dt ? cap : dt;
+  }
+  return dt;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Update (section 4.1: positions and velocities by a second-order Press     */
 /* method, energy by second-order Adams-Bashforth; no formulas printed).      */

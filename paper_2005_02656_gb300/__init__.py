@@ -9,7 +9,7 @@ from ._build import build  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("SphSim", "Params", "HostStepper"):
+    if name in ("SphSim", "Params", "HostStepper", "measure_fp32_peak"):
         from . import sim
         return getattr(sim, name)
     if name == "Ensemble":

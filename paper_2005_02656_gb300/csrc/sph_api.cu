@@ -83,6 +83,8 @@ int check_params(sph_ctx* ctx, const sph_params* p) {
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "gradh needs SPH_KERNEL_EXACT");
   if (p->pair_mode != SPH_PAIRS_STAGED && p->pair_mode != SPH_PAIRS_LISTS)
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "unknown pair_mode %d", p->pair_mode);
+  if (!(p->energy_dt >= 0.0) || !isfinite(p->energy_dt))
+    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "energy_dt must be finite and >= 0");
   return SPH_OK;
 }
 
@@ -305,6 +307,7 @@ void sph_default_params(sph_params* p) {
   p->kernel_mode = SPH_KERNEL_EXACT;
   p->gradh = 0;
   p->pair_mode = SPH_PAIRS_STAGED;
+  p->energy_dt = 0.0;
 }
 
 int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {

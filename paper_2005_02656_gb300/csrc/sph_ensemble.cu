@@ -905,7 +905,7 @@ int sph_ensemble_init(const sph_params* common, int n_boxes, const int64_t* box_
   *out = nullptr;
   if (common->precision != SPH_FP32_MIXED || common->max_nb % 4 != 0 || common->max_nb < 4 ||
       !(common->sinc_n >= 1.0 && common->sinc_n <= 12.0) ||
-      common->kernel_mode != SPH_KERNEL_EXACT)
+      common->kernel_mode != SPH_KERNEL_EXACT || common->energy_dt != 0.0)
     return SPH_ERR_INVALID_ARG;
   sph_ens* e = (sph_ens*)calloc(1, sizeof(sph_ens));
   if (!e) return SPH_ERR_OOM;

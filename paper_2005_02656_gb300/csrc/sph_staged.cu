@@ -65,6 +65,7 @@ constexpr int kPipeWin = 832;   // staged candidates of a cell the pipelined pas
 // int32 lists, marked by mask_base = kListForm.
 constexpr int kStagedMaxP = 64 * kMaskWords;
 constexpr uint32_t kListForm = 0xffffffffu;
+constexpr uint32_t kNoCell = 0xffffffffu;  // past the end of a launch's cell list
 
 // Targets of a cell (bit 15 of a staged cell's field is its pipelined-pass flag).
 __device__ __forceinline__ int cell_na(uint4 md) {
@@ -971,15 +972,19 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
   const int tid = threadIdx.x;
   const uint4 zero4 = make_uint4(0u, kListForm, 0u, 0u);
   auto meta_of = [&](uint32_t q) { return q < n_cells ? __ldg(src.meta + src.cells[q]) : zero4; };
+  auto cell_at = [&](uint32_t q) { return q < n_cells ? __ldg(src.cells + q) : kNoCell; };
+  auto meta_at = [&](uint32_t c) { return c != kNoCell ? __ldg(src.meta + c) : zero4; };
   uint4 md_next = meta_of(blockIdx.x);
   uint4 md_after = meta_of(blockIdx.x + G);
+  uint32_t c_ahead = cell_at(blockIdx.x + 2 * G);  // meta loaded one cell later
   Prefetch<U> pf;
   prefetch_cell<Pass>(src, md_next, pf);
   for (uint32_t q = blockIdx.x; q < n_cells; q += G) {
     const uint4 md = md_next;
     const Prefetch<U> cur = pf;
     md_next = md_after;
-    md_after = meta_of(q + 2 * G);
+    md_after = meta_at(c_ahead);
+    c_ahead = cell_at(q + 3 * G);
     prefetch_cell<Pass>(src, md_next, pf);  // lands while this cell is computed
     const uint32_t slot_base = md.x, a0 = md.z;
     const int S = cell_S(md), na = cell_na(md);
@@ -1124,6 +1129,10 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
   if (q >= n_cells) return;
   const uint4 none = make_uint4(0u, kListForm, 0u, 0u);
   auto meta_of = [&](uint32_t qq) { return qq < n_cells ? __ldg(src.meta + src.cells[qq]) : none; };
+  // the cell index is loaded one iteration before its meta, so that neither
+  // load waits for the other inside an iteration
+  auto cell_at = [&](uint32_t qq) { return qq < n_cells ? __ldg(src.cells + qq) : kNoCell; };
+  auto meta_at = [&](uint32_t c) { return c != kNoCell ? __ldg(src.meta + c) : none; };
   // staged entries of a cell's slots tid + u PT, and count of its target tid
   auto load_entries = [&](uint4 md, uint32_t* e) {
     const int S = md.y == kListForm ? 0 : cell_S(md);
@@ -1160,6 +1169,7 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
   };
   // prologue: the first cell's copies, the second cell's entries and counts
   uint4 md_cur = meta_of(q), md_nxt = meta_of(q + G), md_nn = meta_of(q + 2 * G);
+  uint32_t c_nnn = cell_at(q + 3 * G);
   uint32_t e_cur[U], e_nxt[U];
   load_entries(md_cur, e_cur);
   {
@@ -1173,6 +1183,8 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
   load_entries(md_nxt, e_nxt);
   int c_nxt = load_count(md_nxt);
   typename Pass::Target T_cur, T_nxt;
+  typename Pass::FinishIn fin_cur, fin_nxt;
+  if (tid < cell_na(md_cur)) fin_cur = pass.prefin((int64_t)md_cur.z + tid);
   auto target_map = [&](uint4 md, int& t, int& sub, int& nsub) {
     const int na = cell_na(md);
     nsub = na > 0 ? min(PT / na, kMaxSub) : 1;
@@ -1209,20 +1221,20 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
     uint32_t e_nn[U];
     load_entries(md_nn, e_nn);
     const int c_nn = load_count(md_nn);
-    const uint4 md_nnn = meta_of(q + 3 * G);
+    const uint4 md_nnn = meta_at(c_nnn);
+    c_nnn = cell_at(q + 4 * G);
     if (!Pass::kTargetSmem && has_nxt) {
       int t, sub, nsub;
       target_map(md_nxt, t, sub, nsub);
       if (t < cell_na(md_nxt)) pass.load_target((int64_t)md_nxt.z + t, T_nxt);
     }
+    if (has_nxt && tid < cell_na(md_nxt)) fin_nxt = pass.prefin((int64_t)md_nxt.z + tid);
     // compute this cell
     const int na = cell_na(md_cur);
     const uint32_t a0 = md_cur.z;
     int t, sub, nsub;
     target_map(md_cur, t, sub, nsub);
     const bool active = t < na;
-    typename Pass::FinishIn fin;
-    if (tid < na) fin = pass.prefin((int64_t)a0 + tid);
     if (Pass::kTargetSmem && active) Pass::target_from(rbuf(buf), (int)md_cur.y + t, T_cur);
     float acc[Pass::kV];
     float2 acc2[Pass::kV];
@@ -1252,7 +1264,7 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
         for (int qq = 0; qq < nsub; ++qq) x += part[v * PT + tid * nsub + qq];
         sm[v] = x;
       }
-      pass.finish2((int64_t)a0 + tid, sm, fin);
+      pass.finish2((int64_t)a0 + tid, sm, fin_cur);
     }
     q += G;
     if (q >= n_cells) break;
@@ -1266,6 +1278,7 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
     }
     c_nxt = c_nn;
     if (!Pass::kTargetSmem) T_cur = T_nxt;
+    fin_cur = fin_nxt;
     buf ^= 1;
   }
 }

@@ -1,6 +1,8 @@
 // Global time step, integrator update and conservation sums, all FP64.
 //
-// k_timestep  dt_n = min(courant * min_a h_a / c_a, dt_growth * dt_{n-1})
+// k_timestep  dt_n = min(courant * min_a h_a / c_a, dt_growth * dt_{n-1}),
+//             and, when energy_dt > 0, at most energy_dt * min_a u_a / |du_a|
+//             over du_a != 0 (the opt-in energy-rate limit, a reading)
 //             (section 4.2: the global minimum time step; the paper's
 //             MPI_Allreduce becomes a block reduction plus a last-block
 //             finalisation, so the result never leaves the device)
@@ -93,31 +95,44 @@ __device__ void finalize_block(const double* part, int nblocks, const Op (&op)[N
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads) k_timestep(const double* h, const double* c, int64_t n,
-                                                       double courant, double growth,
-                                                       double* dt_io, double* diag, double* part,
+__global__ void __launch_bounds__(kThreads) k_timestep(const double* h, const double* c,
+                                                       const double* u, const double* du,
+                                                       int64_t n, double courant, double growth,
+                                                       double energy_dt, double* dt_io,
+                                                       double* diag, double* part,
                                                        unsigned int* counter, uint32_t* err) {
-  double mn = INFINITY;
+  double mn = INFINITY, mu = INFINITY;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
+       i += (int64_t)gridDim.x * blockDim.x) {
     mn = fmin(mn, h[i] / c[i]);
+    if (energy_dt > 0.0 && du[i] != 0.0) mu = fmin(mu, u[i] / fabs(du[i]));
+  }
   mn = warp_min(mn);
-  __shared__ double sh[kThreads / 32];
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mn;
+  mu = warp_min(mu);
+  __shared__ double sh[2][kThreads / 32];
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = mn;
+    sh[1][threadIdx.x >> 5] = mu;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < kThreads / 32; ++w) mn = fmin(mn, sh[w]);
+    for (int w = 1; w < kThreads / 32; ++w) {
+      mn = fmin(mn, sh[0][w]);
+      mu = fmin(mu, sh[1][w]);
+    }
     part[blockIdx.x * kParts] = mn;
+    part[blockIdx.x * kParts + 1] = mu;
   }
   if (!block_last(counter)) return;
   __threadfence();
-  __shared__ double res[1];
-  const Op ops[1] = {Op::kMin};
-  finalize_block<1>(part, gridDim.x, ops, res);
+  __shared__ double res[2];
+  const Op ops[2] = {Op::kMin, Op::kMin};
+  finalize_block<2>(part, gridDim.x, ops, res);
   if (threadIdx.x == 0) {
     const double m = res[0];
     const double prev = *dt_io;
     double dt = courant * m;
+    if (energy_dt > 0.0) dt = fmin(dt, energy_dt * res[1]);  // no du != 0: res[1] = inf
     if (prev > 0.0) dt = fmin(dt, growth * prev);
     if (!isfinite(dt) || !(dt > 0.0)) raise_flag(err, SPH_FLAG_NONFINITE);
     diag[12] = prev;
@@ -282,8 +297,8 @@ inline int red_blocks(int64_t n, int sm) {
 void launch_timestep(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n, double* dt_io,
                      cudaStream_t st) {
   k_timestep<<<red_blocks(n, ctx->sm_count), kThreads, 0, st>>>(
-      s.h, o.c, n, ctx->prm.courant, ctx->prm.dt_growth, dt_io, ctx->diag, ctx->red.part,
-      ctx->red.counter + 1, ctx->err);
+      s.h, o.c, s.u, o.du, n, ctx->prm.courant, ctx->prm.dt_growth, ctx->prm.energy_dt, dt_io,
+      ctx->diag, ctx->red.part, ctx->red.counter + 1, ctx->err);
   ctx->launches += 1;
 }
 

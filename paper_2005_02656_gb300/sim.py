@@ -34,6 +34,7 @@ class Params:
     kernel_mode: str = "exact"  # "exact" | "table" (section 4.5: 20,000-entry table)
     pair_mode: str = "staged"   # FP32-mixed pair sums: "staged" (cell-staged candidates
                                 # and hit masks) | "lists" (int32 neighbour lists)
+    energy_dt: float = 0.0      # > 0: dt <= energy_dt * min u / |du| (opt-in energy-rate limit)
 
     def c(self) -> SphParams:
         p = SphParams()
@@ -47,11 +48,21 @@ class Params:
         p.kernel_mode = {"exact": _lib.SPH_KERNEL_EXACT, "table": _lib.SPH_KERNEL_TABLE}[self.kernel_mode]
         p.gradh = int(self.gradh)
         p.pair_mode = {"staged": _lib.SPH_PAIRS_STAGED, "lists": _lib.SPH_PAIRS_LISTS}[self.pair_mode]
+        p.energy_dt = float(self.energy_dt)
         return p
 
 
 def _stream_ptr():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def measure_fp32_peak() -> float:
+    """FP32 fused-multiply-add rate of the current device in TFLOP/s, measured
+    by the library's probe kernel on the current stream (sph_measure_fp32_peak)."""
+    lib = _lib.load()
+    out = C.c_double(0.0)
+    check(lib, None, lib.sph_measure_fp32_peak(C.byref(out), _stream_ptr()))
+    return float(out.value)
 
 
 class SphSim:

@@ -13,9 +13,12 @@ sum_a dL/dx_a = 0 and sum_a dL/dv_a = sum_a m_a v_a(K).
 
 Tolerance: the gradients are exact derivatives of the same function on both
 sides, so they differ by FP64 rounding of the pair sums amplified through K
-steps; 1e-6 relative (of the largest component, or of the directional
-derivative with every term in magnitude) is the bar, measured differences
-are far below it."""
+steps.  "Relative 1e-6" is read per field as max |g - g_ref| <= 1e-6
+max |g_ref| (a component that is zero by symmetry has no relative error),
+and in addition per component, |g_i - g_ref,i| <= 1e-6 |g_ref,i|, for every
+component at least 1e-4 of the field's largest; against central differences
+it is 1e-6 of the directional derivative with every term in magnitude.
+Measured differences are far below these bars."""
 import numpy as np
 import pytest
 import torch
@@ -84,8 +87,14 @@ def test_forward_matches_oracle_and_time_steps(small):
 @pytest.mark.parametrize("field", ["x", "v", "u"])
 def test_gradient_matches_reference_adjoint(small, field):
     *_, ref, gpu = small
-    err = np.abs(gpu[field] - ref[field]).max()
-    assert err <= TOL * np.abs(ref[field]).max(), (field, err, np.abs(ref[field]).max())
+    g, r = np.asarray(gpu[field]), np.asarray(ref[field])
+    err = np.abs(g - r).max()
+    assert err <= TOL * np.abs(r).max(), (field, err, np.abs(r).max())
+    # component by component where the component is not tiny
+    big = np.abs(r) >= 1e-4 * np.abs(r).max()
+    assert big.sum() > 0.5 * big.size
+    rel = np.abs(g - r)[big] / np.abs(r)[big]
+    assert rel.max() <= TOL, (field, rel.max())
 
 
 def test_alpha_gradient_matches_reference_adjoint(small):

@@ -8,7 +8,9 @@ sample).
   the oracle and the step's outputs are compared on a sample (the two
   trajectories separate at rounding level, so each step is checked on
   identical inputs).
-* Kelvin-Helmholtz box, 8,416,298 particles: one FP64 and one FP32-mixed step.
+* Kelvin-Helmholtz box, 8,416,298 particles: one FP64 and one FP32-mixed step;
+  the sampled particles' neighbour lists (exact in both precisions), density,
+  IAD matrix C, accelerations and du.
 """
 import numpy as np
 import pytest
@@ -18,6 +20,12 @@ import sph_inputs
 from helpers import sym
 
 pytestmark = pytest.mark.gpu
+
+# FP32-mixed C: max_ij |C - C_ref| / max_ij |C_ref| per particle; tau is a sum
+# of ~100 FP32 terms on 1/h-scaled separations (relative ~1e-6) and the
+# cofactor inverse multiplies by the condition number of tau (<~ 10 on these
+# lattices)
+FP32_IAD_TOL = 1e-4
 
 
 def _sample_errors(got, ref, sample_ids):
@@ -105,9 +113,18 @@ def test_kelvin_helmholtz_8m_sampled(precision):
     before.update(lo=s["lo"], hi=s["hi"], periodic=s["periodic"])
     rng = np.random.default_rng(6)
     sample = rng.choice(before["x"].shape[0], 200, replace=False)
+    # the search of the step's pre-step state: sampled lists bit-exact
+    sim.find_neighbors()
+    counts, ids = _lists_for_sample(sim, sample)
+    rc, nn_ref, nbr_ref = oracle.find_neighbors(box, before["x"], before["y"], before["z"],
+                                               before["h"], targets=sample, max_nb=params.max_nb)
+    assert rc == 0
+    np.testing.assert_array_equal(counts, nn_ref)
+    for i in range(sample.shape[0]):
+        np.testing.assert_array_equal(ids[i, :counts[i]], nbr_ref[i, :counts[i]])
     sim.step()
     assert sim.error_word() == 0
-    tol = ({"rho": 1e-12, "a": 1e-12, "du": 1e-12} if precision == "fp64"
-           else {"rho": 1e-5, "a": 1e-4, "du": 1e-4})
+    tol = ({"rho": 1e-12, "iad": 1e-12, "a": 1e-12, "du": 1e-12} if precision == "fp64"
+           else {"rho": 1e-5, "iad": FP32_IAD_TOL, "a": 1e-4, "du": 1e-4})
     _check_step(sim, before, box, params, sample, tol, params.max_nb)
     sim.close()

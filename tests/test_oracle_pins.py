@@ -361,6 +361,35 @@ def test_timestep_rule(oracle_mod):
     assert oracle_mod.timestep(h, c, p, 0.1) == pytest.approx(0.005, rel=1e-15)
 
 
+def test_energy_rate_limit_off_is_the_courant_rule(oracle_mod):
+    rng = np.random.default_rng(31)
+    h, c = rng.uniform(0.01, 0.1, 50), rng.uniform(0.5, 2.0, 50)
+    u, du = rng.uniform(0.1, 2.0, 50), rng.normal(0.0, 5.0, 50)
+    for prev in (0.0, 1e-3, 1.0):
+        p0 = Params(courant=0.2, dt_growth=1.1)
+        p1 = Params(courant=0.2, dt_growth=1.1, energy_dt=1e300)    # active, never binding
+        assert oracle_mod.timestep(h, c, p1, prev, u=u, du=du) == oracle_mod.timestep(h, c, p0, prev)
+
+
+@pytest.mark.parametrize("cu", [0.02, 0.1])
+def test_energy_rate_limit_bounds_the_first_euler_step(oracle_mod, cu):
+    """Reading: dt <= C_u min u/|du|.  On the first step the energy update is
+    forward Euler, so no particle's u changes by more than the fraction C_u of
+    itself, and the particle that sets dt changes by exactly that fraction."""
+    s = sph_inputs.jittered_box(10, seed_index=41, vel_sigma=0.5)
+    box = box_of(s)
+    s0 = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+    p = Params(energy_dt=cu)
+    rc, dt, out = oracle_mod.step(box, s, p, 0.0)
+    assert rc == 0
+    dt_courant = oracle_mod.timestep(s0["h"], out["c"], Params(), 0.0)
+    assert dt < dt_courant                       # the limit binds here
+    frac = np.abs(s["u"] - s0["u"]) / s0["u"]
+    assert frac.max() <= cu * (1 + 1e-12)
+    assert frac.max() == pytest.approx(cu, rel=1e-12)
+    assert (s["u"] > 0).all()
+
+
 # ------------------------------------------------------------- integrator --
 def _blank_state(n):
     rng = np.random.default_rng(9)
