@@ -371,8 +371,8 @@ int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {
   ALLOC(ctx->cmeta, n);
   ALLOC(ctx->sent, (size_t)ctx->sent_cap);
   ALLOC(ctx->masks, (size_t)ctx->mask_cap);
-  ALLOC(ctx->salloc, 4);
-  ALLOC(ctx->cells, 2 * n);
+  ALLOC(ctx->salloc, 5);
+  ALLOC(ctx->cells, 3 * n);
   ALLOC(ctx->recA, n);
   ALLOC(ctx->recV, n);
   ALLOC(ctx->recQ, n);

@@ -129,8 +129,11 @@ struct sph_ctx {
   uint4* cmeta;
   uint32_t* sent;
   unsigned long long* masks;
-  unsigned long long* salloc;  // [0] entries, [1] mask words, [2] fast cells, [3] other cells
-  uint32_t* cells;             // 2 n_max: the pipelined passes' cells, then the others
+  unsigned long long* salloc;  // [0] entries, [1] mask words, cells of the lists of cells[]:
+                               // [2] S <= 448, [3] the rest, [4] 448 < S <= 832
+  uint32_t* cells;             // 3 n_max: cells staging at most 448 candidates (all pipelined
+                               // passes), the others, cells staging 449..832 (pipelined
+                               // density and IAD)
   int64_t sent_cap;
   int64_t mask_cap;
   // momentum records as planes: (offset, 1/h^2), (v, m),

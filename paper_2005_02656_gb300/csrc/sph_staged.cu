@@ -57,6 +57,7 @@ using find::pair_index;
 constexpr int kTR = 64;         // targets per round of the pair passes
 constexpr int kLC = 128;        // list entries per target and list pass
 constexpr int kPipeWin = 832;   // staged candidates of a cell the pipelined passes take
+constexpr int kPipeWinM = 448;  // ... the pipelined momentum pass takes (72-byte records)
 
 // A cell is staged (hit masks) when its stencil holds at most kStagedMaxP
 // particles, so a target's mask row is at most kStagedMaxP / 64 words and the
@@ -81,8 +82,9 @@ struct MaskOut {
   unsigned long long sent_cap;  // capacities of sent and masks
   unsigned long long mask_cap;
   uint16_t* slist;              // staged-slot lists (rows of max_nb entries)
-  uint32_t* fcells;             // cells of the pipelined passes (alloc[2] of them)
+  uint32_t* fcells;             // cells of every pipelined pass (alloc[2] of them)
   uint32_t* scells;             // the other cells (alloc[3])
+  uint32_t* mcells;             // cells of the pipelined density and IAD passes only (alloc[4])
 };
 
 // Row of particle a in the staged-slot lists: max_nb uint16 entries inside the
@@ -354,14 +356,16 @@ __device__ __forceinline__ void find_cell_masks(const Grid& g, uint32_t cell, ui
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-  // cells the pipelined passes take whole: one round of targets, one window
-  // of staged candidates, one list chunk per target
-  const bool fast = na <= kTR && (int)staged <= kPipeWin && kmax <= kLC;
+  // cells the pipelined passes take whole: one round of at most kTR targets,
+  // lists of at most kLC entries and one window of staged candidates (448
+  // for momentum, 832 for the others)
+  const int cls =
+      na > kTR || kmax > kLC || (int)staged > kPipeWin ? 1 : ((int)staged <= kPipeWinM ? 0 : 2);
   if (lane == 0) {
     mo.meta[cell] = make_uint4(slot_base, (uint32_t)gself, (uint32_t)a0,
-                               (staged << 16) | (fast ? 0x8000u : 0u) | (uint32_t)na);
-    const unsigned long long q = atomicAdd(mo.alloc + (fast ? 2 : 3), 1ull);
-    (fast ? mo.fcells : mo.scells)[q] = cell;
+                               (staged << 16) | (cls != 1 ? 0x8000u : 0u) | (uint32_t)na);
+    const unsigned long long q = atomicAdd(mo.alloc + 2 + cls, 1ull);
+    (cls == 0 ? mo.fcells : (cls == 1 ? mo.scells : mo.mcells))[q] = cell;
   }
   __syncwarp();
 }
@@ -503,9 +507,11 @@ struct DensityPass {
   static constexpr int kMinBlocks = 4;
   static constexpr int kStageU = 4;   // staged records loaded per thread at once
   static constexpr bool kPaired = true;  // two pairs per iteration in paired FP32
-  static constexpr bool kPipe = true;  // marked cells in the pipelined kernel
   static constexpr int kPipeThreads = 256;
   static constexpr int kPipeMinBlocks = 3;
+  static constexpr int kPipeW = kPipeWin;  // its window (staged slots per buffer)
+  static constexpr bool kPipeAll = true;   // cells of up to kPipeWin candidates
+  static constexpr bool kSmemLists = true; // lists copied with the records
   static constexpr bool kTargetSmem = false;
   static constexpr bool kPipePaired = true;
   const float4* rec_d;   // (offset, m) per particle
@@ -534,8 +540,11 @@ struct DensityPass {
     const float4 r = rec_d[entry_index(e)];
     return {make_float4(r.x + sx, r.y + sy, r.z + sz, r.w)};
   }
+  template <int W>
   static __device__ void store(float4* rec, int j, const Rec& r) { rec[j] = r.r; }
+  template <int W>
   static __device__ Rec fetch(const float4* rec, int j) { return {rec[j]}; }
+  template <int W>
   static __device__ void target_from(float4*, int, Target&) {}
   __device__ void load_target(int64_t a, Target& T) const {
     const float4 p = pos32[a];
@@ -564,6 +573,7 @@ struct DensityPass {
       acc[1] = __ffma2_rn(m, make_float2(kernel_tdw32(tt.x, 1.0f, sinc_n),
                                          kernel_tdw32(tt.y, 1.0f, sinc_n)), acc[1]);
   }
+  template <int W>
   __device__ void copy_async(float4* rec, int j, int b) const { cp_async16(rec + j, rec_d + b); }
   struct FinishIn {
     float4 p;
@@ -610,9 +620,11 @@ struct IadPass {
   static constexpr int kMinBlocks = 4;
   static constexpr int kStageU = 4;
   static constexpr bool kPaired = true;
-  static constexpr bool kPipe = true;
   static constexpr int kPipeThreads = 256;
   static constexpr int kPipeMinBlocks = 3;
+  static constexpr int kPipeW = kPipeWin;
+  static constexpr bool kPipeAll = true;
+  static constexpr bool kSmemLists = true;
   static constexpr bool kTargetSmem = false;
   static constexpr bool kPipePaired = true;
   const float4* rec_i;   // (offset, m / rho)
@@ -637,8 +649,11 @@ struct IadPass {
     const float4 r = rec_i[entry_index(e)];
     return {make_float4(r.x + sx, r.y + sy, r.z + sz, r.w)};
   }
+  template <int W>
   static __device__ void store(float4* rec, int j, const Rec& r) { rec[j] = r.r; }
+  template <int W>
   static __device__ Rec fetch(const float4* rec, int j) { return {rec[j]}; }
+  template <int W>
   static __device__ void target_from(float4*, int, Target&) {}
   __device__ void load_target(int64_t a, Target& T) const {
     const float4 p = recA[a];
@@ -685,6 +700,7 @@ struct IadPass {
     acc[4] = __ffma2_rn(wy, dz, acc[4]);
     acc[5] = __ffma2_rn(wz, dz, acc[5]);
   }
+  template <int W>
   __device__ void copy_async(float4* rec, int j, int b) const { cp_async16(rec + j, rec_i + b); }
   struct FinishIn {
     float hinv2, norm;
@@ -733,12 +749,15 @@ struct MomentumPass {
   static constexpr int kMinBlocks = 3;
   static constexpr bool kPaired = false;  // the paired body needs ~120 registers: scalar pairs
                                           // keep three CTAs per SM
-  static constexpr bool kPipe = false;    // 72-byte records leave no room for a double buffer
-                                          // beside more than one CTA per SM (measured slower)
-  static constexpr int kPipeThreads = 512;
-  static constexpr int kPipeMinBlocks = 1;
+  // pipelined kernel: cells of up to kPipeWinM candidates, a double buffer of
+  // 2 x 32 KB, three CTAs per SM
+  static constexpr int kPipeThreads = 256;
+  static constexpr int kPipeMinBlocks = 3;
+  static constexpr int kPipeW = kPipeWinM;
+  static constexpr bool kPipeAll = false;    // the cells of 449..832 candidates: general kernel
+  static constexpr bool kSmemLists = false;  // lists read through L1
   static constexpr bool kTargetSmem = true;  // target records from the staged window
-  static constexpr bool kPipePaired = true;
+  static constexpr bool kPipePaired = false;
   static constexpr int kStageU = 2;
   const float4* recA;    // (offset, 1 / h^2)
   const float4* recV;    // (v, m)
@@ -755,10 +774,12 @@ struct MomentumPass {
     float4 p, v, q;
     float c00, c01, c02, c11, c12, c22;
   };
-  // shared-memory planes of a window: A, V, Q, C (float4) then C2 (float2)
-  static __device__ __forceinline__ float4* plane(float4* rec, int k) { return rec + k * kWin; }
+  // shared-memory planes of a window of W slots: A, V, Q, C (float4) then C2 (float2)
+  template <int W>
+  static __device__ __forceinline__ float4* plane(float4* rec, int k) { return rec + k * W; }
+  template <int W>
   static __device__ __forceinline__ float2* plane2(float4* rec) {
-    return reinterpret_cast<float2*>(rec + 4 * kWin);
+    return reinterpret_cast<float2*>(rec + 4 * W);
   }
   struct Rec {
     float4 p, v, q, c;  // (position relative to the target's cell, 1/h^2), (v, m), Q, C
@@ -771,16 +792,18 @@ struct MomentumPass {
     const float4 p = recA[b];
     return {make_float4(p.x + sx, p.y + sy, p.z + sz, p.w), recV[b], recQ[b], recC[b], recC2[b]};
   }
+  template <int W>
   static __device__ void store(float4* rec, int j, const Rec& r) {
-    plane(rec, 0)[j] = r.p;
-    plane(rec, 1)[j] = r.v;
-    plane(rec, 2)[j] = r.q;
-    plane(rec, 3)[j] = r.c;
-    plane2(rec)[j] = r.c2;
+    plane<W>(rec, 0)[j] = r.p;
+    plane<W>(rec, 1)[j] = r.v;
+    plane<W>(rec, 2)[j] = r.q;
+    plane<W>(rec, 3)[j] = r.c;
+    plane2<W>(rec)[j] = r.c2;
   }
+  template <int W>
   static __device__ Rec fetch(float4* rec, int j) {
-    return {plane(rec, 0)[j], plane(rec, 1)[j], plane(rec, 2)[j], plane(rec, 3)[j],
-            plane2(rec)[j]};
+    return {plane<W>(rec, 0)[j], plane<W>(rec, 1)[j], plane<W>(rec, 2)[j], plane<W>(rec, 3)[j],
+            plane2<W>(rec)[j]};
   }
   __device__ void load_target(int64_t a, Target& T) const {
     T.p = recA[a];
@@ -873,16 +896,18 @@ struct MomentumPass {
     const float2 i2 = __fmul2_rn(__fmul2_rn(__fmul2_rn(qP, irb), Wb), vCb);
     acc[3] = __ffma2_rn(mb, __ffma2_rn(i1, vCa, i2), acc[3]);
   }
+  template <int W>
   __device__ void copy_async(float4* rec, int j, int b) const {
-    cp_async16(plane(rec, 0) + j, recA + b);
-    cp_async16(plane(rec, 1) + j, recV + b);
-    cp_async16(plane(rec, 2) + j, recQ + b);
-    cp_async16(plane(rec, 3) + j, recC + b);
-    cp_async8(plane2(rec) + j, recC2 + b);
+    cp_async16(plane<W>(rec, 0) + j, recA + b);
+    cp_async16(plane<W>(rec, 1) + j, recV + b);
+    cp_async16(plane<W>(rec, 2) + j, recQ + b);
+    cp_async16(plane<W>(rec, 3) + j, recC + b);
+    cp_async8(plane2<W>(rec) + j, recC2 + b);
   }
   // The target's data is its own staged record (its cell's shift is zero).
+  template <int W>
   static __device__ void target_from(float4* rec, int j, Target& T) {
-    const Rec R = fetch(rec, j);
+    const Rec R = fetch<W>(rec, j);
     T.p = R.p;
     T.v = R.v;
     T.q = R.q;
@@ -1044,7 +1069,7 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
 #pragma unroll
                 for (int u = 0; u < U; ++u)
                   if (j0 + u * kPT + tid < wn)
-                    Pass::store(rec, j0 + u * kPT + tid, pass.load(e[u], g));
+                    Pass::template store<Pass::kWin>(rec, j0 + u * kPT + tid, pass.load(e[u], g));
               }
               staged_w0 = w0;
             }
@@ -1054,12 +1079,13 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
             for (; Pass::kPaired && k + nsub < nl; k += 2 * nsub) {  // two entries at a time
               const int s0 = row[k], s1 = row[k + nsub];
               if (s1 >= wend) break;                 // ascending: s0 < s1
-              pass.pair2(T, Pass::fetch(rec, s0 - w0), Pass::fetch(rec, s1 - w0), g, acc2);
+              pass.pair2(T, Pass::template fetch<Pass::kWin>(rec, s0 - w0),
+                         Pass::template fetch<Pass::kWin>(rec, s1 - w0), g, acc2);
             }
             for (; k < nl; k += nsub) {
               const int slot = row[k];
               if (slot >= wend) break;
-              pass.pair(T, Pass::fetch(rec, slot - w0), g, acc);
+              pass.pair(T, Pass::template fetch<Pass::kWin>(rec, slot - w0), g, acc);
             }
           }
           const int more = __syncthreads_or(active && sub == 0 && tot[t] > (lp + 1) * kLC);
@@ -1087,73 +1113,127 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
 
 // ------------------------------------------------- pipelined pair passes --
 //
-// The cells the search marked (one round of at most kTR targets, at most
-// kPipeWin staged candidates, lists of at most kLC entries) are processed by a
-// two-stage software pipeline: while a CTA computes cell i from one half of a
-// double buffer, the records and lists of cell i + 1 are arriving in the other
-// half by cp.async, and the staged entries and counts of cell i + 2 by plain
-// loads into registers.  Each thread adds the cell shifts to the records it
-// copied itself once they have landed, so one barrier per cell publishes the
-// cell's data and one more the per-target partial sums.
+// Cells staging at most kPipeW candidates are processed by a two-stage
+// software pipeline: while a CTA computes cell i from one half of a double
+// buffer, the records of cell i + 1 arrive in the other half by cp.async, the
+// staged entries of cell i + 2 and the meta of cell i + 3 by plain loads into
+// registers.  Each thread adds the cell shifts (a 27-entry table) to the
+// records it copied itself once they have landed, so one barrier per cell
+// publishes the records and one more the per-target partial sums.
+//
+// Thread (t, s) of target t takes entries s, s + nsub, ... of t's staged-slot
+// list, so the threads of a warp step through their lists in lockstep.  The
+// lists come from shared memory (passes with 16-byte records: the next cell's
+// lists are copied by cp.async with its records) or from global memory
+// through L1 (momentum, whose 72-byte records leave no room for list buffers:
+// the next cell's list rows are prefetched into L1).
 
 template <class Pass>
 struct PipeSmem {
   static constexpr int PT = Pass::kPipeThreads;
-  static constexpr size_t kRec = (size_t)kPipeWin * Pass::kRecBytes;  // one buffer
-  static constexpr size_t kList = (size_t)kTR * kLS * sizeof(uint16_t);
+  static constexpr int W = Pass::kPipeW;
+  static constexpr bool L = Pass::kSmemLists;
+  static constexpr size_t kRec = (size_t)W * Pass::kRecBytes;  // one buffer
+  static constexpr size_t kList = L ? (size_t)kTR * kLS * sizeof(uint16_t) : 0;
+  static constexpr size_t kCnt = L ? (size_t)kTR * sizeof(int) : 0;
   static constexpr size_t kPart = (size_t)PT * Pass::kV * sizeof(float);
-  static constexpr size_t kBytes = 2 * kRec + 2 * kList + kPart + 2 * (size_t)kTR * sizeof(int);
-  static_assert(kRec % 16 == 0 && kList % 16 == 0 && kPart % 16 == 0, "16-byte aligned parts");
+  static constexpr size_t kTab = 27 * sizeof(float4) + 48 * sizeof(int) + 272;  // shifts, 1/nsub, nsub(na)
+  static constexpr size_t oList = 2 * kRec;
+  static constexpr size_t oCnt = oList + 2 * kList;
+  static constexpr size_t oPart = oCnt + 2 * kCnt;
+  static constexpr size_t oTab = oPart + kPart;
+  static constexpr size_t kBytes = oTab + kTab;
+  static_assert(kRec % 16 == 0 && kList % 16 == 0 && kCnt % 16 == 0 && kPart % 16 == 0,
+                "16-byte aligned parts");
+  static_assert(PT <= 256, "nsub table sized for at most 256 targets");
 };
+
+// Cells of a pipelined launch: list 0 then list 1 (optional).
+struct PipeSrc {
+  const uint4* meta;
+  const uint32_t* cells0;
+  const unsigned long long* n0;
+  const uint32_t* cells1;
+  const unsigned long long* n1;
+  const uint32_t* sent;
+  const int32_t* nn;
+  const uint16_t* slist;
+  int max_nb;
+};
+
+// This thread's share of a cell's targets: target t (-1: none), its lane sub
+// of nsub and the length of t's list (global-list passes).
+struct Share {
+  int t, sub, nsub, cnt;
+};
+
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
 
 template <class Pass>
 __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_cellpipe(
-    Pass pass, const Grid* gp, Src src) {
+    Pass pass, const Grid* gp, PipeSrc src) {
   using SM = PipeSmem<Pass>;
-  constexpr int PT = Pass::kPipeThreads;
-  constexpr int U = (kPipeWin + PT - 1) / PT;  // staged slots per thread
+  constexpr int PT = SM::PT;
+  constexpr int W = SM::W;
+  constexpr bool kLists = SM::L;
+  constexpr int U = (W + PT - 1) / PT;  // staged slots per thread
+  constexpr int kV = Pass::kV;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // the two halves of the double buffer: records, lists and counts of half h
   auto rbuf = [&](int h) { return reinterpret_cast<float4*>(smem_raw + h * SM::kRec); };
   auto lbuf = [&](int h) {
-    return reinterpret_cast<uint16_t*>(smem_raw + 2 * SM::kRec + h * SM::kList);
+    return reinterpret_cast<uint16_t*>(smem_raw + SM::oList + h * SM::kList);
   };
-  float* part = reinterpret_cast<float*>(smem_raw + 2 * SM::kRec + 2 * SM::kList);
-  int* tc0 = reinterpret_cast<int*>(smem_raw + 2 * SM::kRec + 2 * SM::kList + SM::kPart);
-  auto tcnt = [&](int h) { return tc0 + h * kTR; };
+  auto tcnt = [&](int h) { return reinterpret_cast<int*>(smem_raw + SM::oCnt) + h * kTR; };
+  float* part = reinterpret_cast<float*>(smem_raw + SM::oPart);
+  float4* shtab = reinterpret_cast<float4*>(smem_raw + SM::oTab);
+  int* inv16 = reinterpret_cast<int*>(smem_raw + SM::oTab + 27 * sizeof(float4));
+  unsigned char* nsubtab = smem_raw + SM::oTab + 27 * sizeof(float4) + 48 * sizeof(int);
   const Grid g = *gp;
-  const uint32_t n_cells = (uint32_t)*src.ncells;
-  const uint32_t G = gridDim.x;
   const int tid = threadIdx.x;
+  // per-launch tables: the cell shift of each stencil code, nsub = min(PT / na,
+  // 32) and 1/nsub in 16-bit fixed point (tid / nsub = tid * inv16 >> 16 is
+  // exact for tid < 256 and nsub <= 32)
+  if (tid < 27) {
+    float sx, sy, sz;
+    entry_shift((uint32_t)tid << kIndexBits, g, sx, sy, sz);
+    shtab[tid] = make_float4(sx, sy, sz, 0.0f);
+  }
+  if (tid >= 1 && tid <= kMaxSub) inv16[tid] = (65536 + tid - 1) / tid;
+  for (int na = tid; na <= PT; na += PT)
+    nsubtab[na] = (unsigned char)(na > 0 ? min(PT / na, kMaxSub) : 1);
+  __syncthreads();
+  const uint32_t n0 = (uint32_t)*src.n0;
+  const uint32_t n_cells = n0 + (src.cells1 ? (uint32_t)*src.n1 : 0u);
+  const uint32_t G = gridDim.x;
   uint32_t q = blockIdx.x;
   if (q >= n_cells) return;
   const uint4 none = make_uint4(0u, kListForm, 0u, 0u);
-  auto meta_of = [&](uint32_t qq) { return qq < n_cells ? __ldg(src.meta + src.cells[qq]) : none; };
-  // the cell index is loaded one iteration before its meta, so that neither
-  // load waits for the other inside an iteration
-  auto cell_at = [&](uint32_t qq) { return qq < n_cells ? __ldg(src.cells + qq) : kNoCell; };
+  auto cell_at = [&](uint32_t qq) {
+    return qq < n0 ? __ldg(src.cells0 + qq)
+                   : (qq < n_cells ? __ldg(src.cells1 + (qq - n0)) : kNoCell);
+  };
   auto meta_at = [&](uint32_t c) { return c != kNoCell ? __ldg(src.meta + c) : none; };
-  // staged entries of a cell's slots tid + u PT, and count of its target tid
+  auto present = [&](uint4 md) { return md.y != kListForm; };
+  // staged entries of a cell's slots tid + u PT
   auto load_entries = [&](uint4 md, uint32_t* e) {
-    const int S = md.y == kListForm ? 0 : cell_S(md);
+    const int S = present(md) ? cell_S(md) : 0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int j = tid + u * PT;
       e[u] = j < S ? __ldg(src.sent + md.x + (uint32_t)j) : 0u;
     }
   };
-  auto load_count = [&](uint4 md) {
-    const int na = md.y == kListForm ? 0 : cell_na(md);
-    return tid < na ? min(__ldg(src.nn + md.z + tid), src.max_nb) : 0;
-  };
   auto issue_records = [&](uint4 md, const uint32_t* e, float4* rec) {
     const int S = cell_S(md);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int j = tid + u * PT;
-      if (j < S) pass.copy_async(rec, j, entry_index(e[u]));
+      if (j < S) pass.template copy_async<W>(rec, j, entry_index(e[u]));
     }
   };
+  // the next cell's lists (shared-memory lists): 16-byte chunks of each row
   auto issue_lists = [&](uint4 md, const int* cnt, uint16_t* lst) {
     const int na = cell_na(md);
     for (int i = tid; i < na * (kLC / 8); i += PT) {
@@ -1167,99 +1247,149 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
         cp_async8(lst + tt * kLS + k8, grow);
     }
   };
-  // prologue: the first cell's copies, the second cell's entries and counts
-  uint4 md_cur = meta_of(q), md_nxt = meta_of(q + G), md_nn = meta_of(q + 2 * G);
+  // this thread's target in a cell (nsub threads per target)
+  auto target_of = [&](uint4 md, int& t, int& sub, int& nsub) {
+    const int na = present(md) ? cell_na(md) : 0;
+    nsub = nsubtab[min(na, PT)];
+    t = (tid * inv16[nsub]) >> 16;
+    sub = tid - t * nsub;
+    if (t >= na) t = -1;
+  };
+  // shared-memory lists: the count of target tid; global lists: of this
+  // thread's target
+  auto count_of = [&](uint4 md) {
+    if (kLists) {
+      const int na = present(md) ? cell_na(md) : 0;
+      return tid < na ? min(__ldg(src.nn + md.z + tid), src.max_nb) : 0;
+    }
+    int t, sub, nsub;
+    target_of(md, t, sub, nsub);
+    return t >= 0 ? min(__ldg(src.nn + md.z + t), src.max_nb) : 0;
+  };
+  auto share_of = [&](uint4 md, int cnt) {
+    Share sh;
+    target_of(md, sh.t, sh.sub, sh.nsub);
+    sh.cnt = sh.t >= 0 ? cnt : 0;
+    return sh;
+  };
+  // the 128-byte lines of a cell's list rows (the first 2 max_nb bytes of each)
+  const int lines = (2 * src.max_nb + 127) >> 7;
+  auto prefetch_rows = [&](uint4 md) {
+    const int na = present(md) ? cell_na(md) : 0;
+    for (int i = tid; i < na * lines; i += PT) {
+      const int t = i / lines;
+      prefetch_l1(reinterpret_cast<const unsigned char*>(slot_row(
+                      const_cast<uint16_t*>(src.slist), (int64_t)md.z + t, src.max_nb)) +
+                  128 * (i - t * lines));
+    }
+  };
+  // prologue: the first cell's copies, registers of the next two cells
+  uint4 md_cur = meta_at(cell_at(q)), md_nxt = meta_at(cell_at(q + G));
+  uint4 md_nn = meta_at(cell_at(q + 2 * G));
   uint32_t c_nnn = cell_at(q + 3 * G);
   uint32_t e_cur[U], e_nxt[U];
   load_entries(md_cur, e_cur);
-  {
-    const int c0 = load_count(md_cur);
-    issue_records(md_cur, e_cur, rbuf(0));
-    if (tid < kTR) tcnt(0)[tid] = c0;
+  const int c_cur0 = count_of(md_cur);
+  issue_records(md_cur, e_cur, rbuf(0));
+  if (kLists) {
+    if (tid < kTR) tcnt(0)[tid] = c_cur0;
     __syncthreads();
     issue_lists(md_cur, tcnt(0), lbuf(0));
-    cp_async_commit();
+  } else {
+    prefetch_rows(md_cur);
   }
+  cp_async_commit();
   load_entries(md_nxt, e_nxt);
-  int c_nxt = load_count(md_nxt);
+  Share sh_cur = share_of(md_cur, c_cur0);
+  int cnt_nxt = count_of(md_nxt);
   typename Pass::Target T_cur, T_nxt;
   typename Pass::FinishIn fin_cur, fin_nxt;
+  if (!Pass::kTargetSmem && sh_cur.t >= 0) pass.load_target((int64_t)md_cur.z + sh_cur.t, T_cur);
   if (tid < cell_na(md_cur)) fin_cur = pass.prefin((int64_t)md_cur.z + tid);
-  auto target_map = [&](uint4 md, int& t, int& sub, int& nsub) {
-    const int na = cell_na(md);
-    nsub = na > 0 ? min(PT / na, kMaxSub) : 1;
-    t = tid / nsub;
-    sub = tid - t * nsub;
-  };
-  if (!Pass::kTargetSmem) {
-    int t, sub, nsub;
-    target_map(md_cur, t, sub, nsub);
-    if (t < cell_na(md_cur)) pass.load_target((int64_t)md_cur.z + t, T_cur);
-  }
   int buf = 0;
   for (;;) {
-    // this cell's records and lists have landed (the copies this thread made):
-    // add the cell shifts to the records this thread copied
+    // this cell's records have landed (the copies this thread made): add the
+    // cell shifts to the records this thread copied
     cp_async_wait_all();
     {
       const int S = cell_S(md_cur);
+      float4* rec = rbuf(buf);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int j = tid + u * PT;
-        if (j < S) add_shift(rbuf(buf), j, e_cur[u], g);
+        if (j < S) {
+          const float4 sh = shtab[e_cur[u] >> kIndexBits];
+          float4 r = rec[j];
+          r.x += sh.x;
+          r.y += sh.y;
+          r.z += sh.z;
+          rec[j] = r;
+        }
       }
     }
     const bool has_nxt = q + G < n_cells;
-    if (has_nxt && tid < kTR) tcnt(buf ^ 1)[tid] = c_nxt;
-    __syncthreads();  // this cell's data published; the next cell's counts too
+    if (kLists && has_nxt && tid < kTR) tcnt(buf ^ 1)[tid] = cnt_nxt;
+    __syncthreads();  // this cell's data published; the previous reduction done
     if (has_nxt) {
       issue_records(md_nxt, e_nxt, rbuf(buf ^ 1));
-      issue_lists(md_nxt, tcnt(buf ^ 1), lbuf(buf ^ 1));
+      if (kLists) issue_lists(md_nxt, tcnt(buf ^ 1), lbuf(buf ^ 1));
     }
     cp_async_commit();
-    // registers for the cell after next
+    // registers for the next cells
     uint32_t e_nn[U];
     load_entries(md_nn, e_nn);
-    const int c_nn = load_count(md_nn);
+    const int cnt_nn = count_of(md_nn);
     const uint4 md_nnn = meta_at(c_nnn);
     c_nnn = cell_at(q + 4 * G);
-    if (!Pass::kTargetSmem && has_nxt) {
-      int t, sub, nsub;
-      target_map(md_nxt, t, sub, nsub);
-      if (t < cell_na(md_nxt)) pass.load_target((int64_t)md_nxt.z + t, T_nxt);
-    }
+    const Share sh_nxt = share_of(md_nxt, cnt_nxt);
+    if (!kLists) prefetch_rows(md_nxt);
+    if (!Pass::kTargetSmem && sh_nxt.t >= 0)
+      pass.load_target((int64_t)md_nxt.z + sh_nxt.t, T_nxt);
     if (has_nxt && tid < cell_na(md_nxt)) fin_nxt = pass.prefin((int64_t)md_nxt.z + tid);
     // compute this cell
     const int na = cell_na(md_cur);
     const uint32_t a0 = md_cur.z;
-    int t, sub, nsub;
-    target_map(md_cur, t, sub, nsub);
-    const bool active = t < na;
-    if (Pass::kTargetSmem && active) Pass::target_from(rbuf(buf), (int)md_cur.y + t, T_cur);
-    float acc[Pass::kV];
-    float2 acc2[Pass::kV];
+    float acc[kV];
+    float2 acc2[kV];
 #pragma unroll
-    for (int v = 0; v < Pass::kV; ++v) {
+    for (int v = 0; v < kV; ++v) {
       acc[v] = 0.0f;
       acc2[v] = make_float2(0.0f, 0.0f);
     }
-    if (active) {
-      const uint16_t* row = lbuf(buf) + t * kLS;
-      const int nl = tcnt(buf)[t];
+    if (sh_cur.t >= 0) {
       float4* rec = rbuf(buf);
-      int k = sub;
-      if (Pass::kPipePaired)
-        for (; k + nsub < nl; k += 2 * nsub)
-          pass.pair2(T_cur, Pass::fetch(rec, row[k]), Pass::fetch(rec, row[k + nsub]), g, acc2);
-      for (; k < nl; k += nsub) pass.pair(T_cur, Pass::fetch(rec, row[k]), g, acc);
+      if (Pass::kTargetSmem)
+        Pass::template target_from<W>(rec, (int)md_cur.y + sh_cur.t, T_cur);
+      const int ns = sh_cur.nsub;
+      int k = sh_cur.sub;
+      if (kLists) {
+        const uint16_t* row = lbuf(buf) + sh_cur.t * kLS;
+        const int c = tcnt(buf)[sh_cur.t];
+        if (Pass::kPipePaired)
+          for (; k + ns < c; k += 2 * ns)
+            pass.pair2(T_cur, Pass::template fetch<W>(rec, row[k]),
+                       Pass::template fetch<W>(rec, row[k + ns]), g, acc2);
+        for (; k < c; k += ns) pass.pair(T_cur, Pass::template fetch<W>(rec, row[k]), g, acc);
+      } else {
+        const uint16_t* row =
+            slot_row(const_cast<uint16_t*>(src.slist), (int64_t)a0 + sh_cur.t, src.max_nb);
+        const int c = sh_cur.cnt;
+        if (Pass::kPipePaired)
+          for (; k + ns < c; k += 2 * ns)
+            pass.pair2(T_cur, Pass::template fetch<W>(rec, __ldg(row + k)),
+                       Pass::template fetch<W>(rec, __ldg(row + k + ns)), g, acc2);
+        for (; k < c; k += ns)
+          pass.pair(T_cur, Pass::template fetch<W>(rec, __ldg(row + k)), g, acc);
+      }
     }
 #pragma unroll
-    for (int v = 0; v < Pass::kV; ++v) part[v * PT + tid] = acc[v] + (acc2[v].x + acc2[v].y);
+    for (int v = 0; v < kV; ++v) part[v * PT + tid] = acc[v] + (acc2[v].x + acc2[v].y);
     __syncthreads();  // partial sums published
     if (tid < na) {
-      float sm[Pass::kV];
+      const int nsub = sh_cur.nsub;
+      float sm[kV];
 #pragma unroll
-      for (int v = 0; v < Pass::kV; ++v) {
+      for (int v = 0; v < kV; ++v) {
         float x = 0.0f;
         for (int qq = 0; qq < nsub; ++qq) x += part[v * PT + tid * nsub + qq];
         sm[v] = x;
@@ -1276,7 +1406,8 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
       e_cur[u] = e_nxt[u];
       e_nxt[u] = e_nn[u];
     }
-    c_nxt = c_nn;
+    sh_cur = sh_nxt;
+    cnt_nxt = cnt_nn;
     if (!Pass::kTargetSmem) T_cur = T_nxt;
     fin_cur = fin_nxt;
     buf ^= 1;
@@ -1316,6 +1447,21 @@ int pass_blocks(sph_ctx* ctx, int* cache) {
 
 template <class Pass>
 void launch_pass(sph_ctx* ctx, const Pass& p, int* cache, cudaStream_t st) {
+  // the pipelined kernel: cells of at most 448 staged candidates, and for the
+  // passes with 16-byte records also those of 449..832
+  PipeSrc ps;
+  ps.meta = ctx->cmeta;
+  ps.cells0 = ctx->cells;
+  ps.n0 = ctx->salloc + 2;
+  ps.cells1 = Pass::kPipeAll ? ctx->cells + 2 * ctx->n_max : nullptr;
+  ps.n1 = ctx->salloc + 4;
+  ps.sent = ctx->sent;
+  ps.nn = ctx->nn;
+  ps.slist = reinterpret_cast<uint16_t*>(ctx->nbr);
+  ps.max_nb = ctx->prm.max_nb;
+  k_cellpipe<Pass><<<pipe_blocks<Pass>(ctx, cache + 3), Pass::kPipeThreads,
+                     PipeSmem<Pass>::kBytes, st>>>(p, ctx->grid, ps);
+  // the general kernel: the other cells (for momentum also those of 449..832)
   Src src;
   src.meta = ctx->cmeta;
   src.sent = ctx->sent;
@@ -1323,21 +1469,18 @@ void launch_pass(sph_ctx* ctx, const Pass& p, int* cache, cudaStream_t st) {
   src.nbr = ctx->nbr;
   src.slist = reinterpret_cast<uint16_t*>(ctx->nbr);
   src.max_nb = ctx->prm.max_nb;
-  // the cells the search marked: the pipelined kernel (passes with kPipe)
-  // or the general one; then the others in the general kernel
-  src.cells = ctx->cells;
-  src.ncells = ctx->salloc + 2;
-  if constexpr (Pass::kPipe)
-    k_cellpipe<Pass><<<pipe_blocks<Pass>(ctx, cache + 3), Pass::kPipeThreads,
-                       PipeSmem<Pass>::kBytes, st>>>(p, ctx->grid, src);
-  else
-    k_cellpass<Pass><<<pass_blocks<Pass>(ctx, cache), kPT, PassSmem<Pass>::kBytes, st>>>(
-        p, ctx->grid, src);
   src.cells = ctx->cells + ctx->n_max;
   src.ncells = ctx->salloc + 3;
   k_cellpass<Pass><<<pass_blocks<Pass>(ctx, cache), kPT, PassSmem<Pass>::kBytes, st>>>(
       p, ctx->grid, src);
   ctx->launches += 2;
+  if (!Pass::kPipeAll) {
+    src.cells = ctx->cells + 2 * ctx->n_max;
+    src.ncells = ctx->salloc + 4;
+    k_cellpass<Pass><<<pass_blocks<Pass>(ctx, cache), kPT, PassSmem<Pass>::kBytes, st>>>(
+        p, ctx->grid, src);
+    ctx->launches += 1;
+  }
 }
 
 // ----------------------------------------------------------------- export --
@@ -1405,7 +1548,8 @@ void launch_find_masks(sph_ctx* ctx, const StateView& s, int64_t n, cudaStream_t
   mo.slist = reinterpret_cast<uint16_t*>(ctx->nbr);
   mo.fcells = ctx->cells;
   mo.scells = ctx->cells + ctx->n_max;
-  cudaMemsetAsync(ctx->salloc, 0, 4 * sizeof(unsigned long long), st);
+  mo.mcells = ctx->cells + 2 * ctx->n_max;
+  cudaMemsetAsync(ctx->salloc, 0, 5 * sizeof(unsigned long long), st);
   k_find_mask<false><<<ctx->find_mask_blocks, kFindThreads, smem, st>>>(
       ctx->grid, s, ctx->pos32, ctx->occ, ctx->tbl_start, ctx->tbl_count, ctx->nn, ctx->nbr,
       ctx->prm.max_nb, mo, ctx->err, ctx->stats);
