@@ -534,11 +534,10 @@ struct DensityPass {
   struct Rec {
     float4 r;  // position relative to the target's cell, m
   };
-  __device__ Rec load(uint32_t e, const Grid& g) const {
-    float sx, sy, sz;
-    entry_shift(e, g, sx, sy, sz);
+  __device__ Rec load(uint32_t e, const float4* shtab) const {
+    const float4 sh = shtab[e >> kIndexBits];
     const float4 r = rec_d[entry_index(e)];
-    return {make_float4(r.x + sx, r.y + sy, r.z + sz, r.w)};
+    return {make_float4(r.x + sh.x, r.y + sh.y, r.z + sh.z, r.w)};
   }
   template <int W>
   static __device__ void store(float4* rec, int j, const Rec& r) { rec[j] = r.r; }
@@ -643,11 +642,10 @@ struct IadPass {
   struct Rec {
     float4 r;  // position relative to the target's cell, m / rho
   };
-  __device__ Rec load(uint32_t e, const Grid& g) const {
-    float sx, sy, sz;
-    entry_shift(e, g, sx, sy, sz);
+  __device__ Rec load(uint32_t e, const float4* shtab) const {
+    const float4 sh = shtab[e >> kIndexBits];
     const float4 r = rec_i[entry_index(e)];
-    return {make_float4(r.x + sx, r.y + sy, r.z + sz, r.w)};
+    return {make_float4(r.x + sh.x, r.y + sh.y, r.z + sh.z, r.w)};
   }
   template <int W>
   static __device__ void store(float4* rec, int j, const Rec& r) { rec[j] = r.r; }
@@ -785,12 +783,12 @@ struct MomentumPass {
     float4 p, v, q, c;  // (position relative to the target's cell, 1/h^2), (v, m), Q, C
     float2 c2;
   };
-  __device__ Rec load(uint32_t e, const Grid& g) const {
-    float sx, sy, sz;
-    entry_shift(e, g, sx, sy, sz);
+  __device__ Rec load(uint32_t e, const float4* shtab) const {
+    const float4 sh = shtab[e >> kIndexBits];
     const int b = entry_index(e);
     const float4 p = recA[b];
-    return {make_float4(p.x + sx, p.y + sy, p.z + sz, p.w), recV[b], recQ[b], recC[b], recC2[b]};
+    return {make_float4(p.x + sh.x, p.y + sh.y, p.z + sh.z, p.w), recV[b], recQ[b], recC[b],
+            recC2[b]};
   }
   template <int W>
   static __device__ void store(float4* rec, int j, const Rec& r) {
@@ -931,18 +929,50 @@ struct MomentumPass {
   }
 };
 
+// Per-launch tables in shared memory: the FP32 shift of each of the 27
+// stencil codes (entry_shift), nsub = min(PT / na, kMaxSub) for na <= 256 and
+// 1/nsub in 16-bit fixed point, so that tid / nsub = (tid inv16) >> 16 (exact
+// for tid < 256 and nsub <= 32: the error of the fixed-point reciprocal times
+// tid stays below 1/nsub).
+struct Tabs {
+  static constexpr size_t kBytes = 27 * sizeof(float4) + 48 * sizeof(int) + 272;
+  float4* shift;
+  int* inv16;
+  unsigned char* nsub;
+  __device__ Tabs(unsigned char* base)
+      : shift(reinterpret_cast<float4*>(base)),
+        inv16(reinterpret_cast<int*>(base + 27 * sizeof(float4))),
+        nsub(base + 27 * sizeof(float4) + 48 * sizeof(int)) {}
+  // filled by the whole CTA; followed by a barrier
+  template <int PT>
+  __device__ void fill(const Grid& g) {
+    const int tid = threadIdx.x;
+    if (tid < 27) {
+      float sx, sy, sz;
+      entry_shift((uint32_t)tid << kIndexBits, g, sx, sy, sz);
+      shift[tid] = make_float4(sx, sy, sz, 0.0f);
+    }
+    if (tid >= 1 && tid <= kMaxSub) inv16[tid] = (65536 + tid - 1) / tid;
+    for (int na = tid; na <= PT; na += PT)
+      nsub[na] = (unsigned char)(na > 0 ? min(PT / na, kMaxSub) : 1);
+    __syncthreads();
+  }
+  __device__ int div(int tid, int ns) const { return (tid * inv16[ns]) >> 16; }
+};
+
 // Shared memory of a pass: the records of a window, the expanded lists (also
 // the reduction's partial sums), per-(target, block) hit counts and the
-// targets' totals.
+// targets' totals, and the tables.
 template <class Pass>
 struct PassSmem {
   static constexpr size_t kRec = (size_t)Pass::kWin * Pass::kRecBytes;
   static constexpr size_t kLists = (size_t)kTR * kLS * sizeof(uint16_t);
   static constexpr size_t kPart = (size_t)kPT * Pass::kV * sizeof(float);
   static constexpr size_t kListsOrPart = kLists > kPart ? kLists : kPart;
-  static constexpr size_t kBytes = kRec + ((kListsOrPart + 15) & ~(size_t)15) +
-                                   (size_t)kTR * sizeof(int);
-  static_assert(kRec % 16 == 0, "record planes keep 16-byte alignment");
+  static constexpr size_t oTot = kRec + ((kListsOrPart + 15) & ~(size_t)15);
+  static constexpr size_t oTab = oTot + (size_t)kTR * sizeof(int);
+  static constexpr size_t kBytes = oTab + Tabs::kBytes;
+  static_assert(kRec % 16 == 0 && oTab % 16 == 0, "16-byte aligned parts");
 };
 
 // Neighbour source of one pass launch.
@@ -990,8 +1020,10 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
   float4* rec = reinterpret_cast<float4*>(smem_raw);
   uint16_t* lists = reinterpret_cast<uint16_t*>(smem_raw + SM::kRec);
   float* part = reinterpret_cast<float*>(smem_raw + SM::kRec);
-  int* tot = reinterpret_cast<int*>(smem_raw + SM::kRec + ((SM::kListsOrPart + 15) & ~(size_t)15));
+  int* tot = reinterpret_cast<int*>(smem_raw + SM::oTot);
   const Grid g = *gp;
+  Tabs tb(smem_raw + SM::oTab);
+  tb.fill<kPT>(g);
   const uint32_t n_cells = (uint32_t)*src.ncells;
   const uint32_t G = gridDim.x;
   const int tid = threadIdx.x;
@@ -1017,9 +1049,8 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
     int staged_w0 = -1;
     for (int r0 = 0; r0 < na; r0 += kTR) {
       const int nr = min(kTR, na - r0);
-      int nsub = kPT / nr;
-      if (nsub > kMaxSub) nsub = kMaxSub;
-      const int t = tid / nsub, sub = tid - t * nsub;
+      const int nsub = tb.nsub[nr];
+      const int t = tb.div(tid, nsub), sub = tid - t * nsub;
       const bool active = t < nr;
       const int64_t a = (int64_t)a0 + r0 + (active ? t : 0);
       typename Pass::Target T;
@@ -1036,7 +1067,8 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
         // neighbour records read from global memory
         const int c = active ? min(__ldg(src.nn + a), src.max_nb) : 0;
         const uint32_t* row = src.nbr + a * src.max_nb;
-        for (int k = sub; k < c; k += nsub) pass.pair(T, pass.load(__ldg(row + k), g), g, acc);
+        for (int k = sub; k < c; k += nsub)
+          pass.pair(T, pass.load(__ldg(row + k), tb.shift), g, acc);
       } else {
         // the targets' staged-slot lists (ascending slots), kLC entries per
         // target at a time in shared memory, walked window by window
@@ -1069,7 +1101,7 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
 #pragma unroll
                 for (int u = 0; u < U; ++u)
                   if (j0 + u * kPT + tid < wn)
-                    Pass::template store<Pass::kWin>(rec, j0 + u * kPT + tid, pass.load(e[u], g));
+                    Pass::template store<Pass::kWin>(rec, j0 + u * kPT + tid, pass.load(e[u], tb.shift));
               }
               staged_w0 = w0;
             }
@@ -1137,7 +1169,7 @@ struct PipeSmem {
   static constexpr size_t kList = L ? (size_t)kTR * kLS * sizeof(uint16_t) : 0;
   static constexpr size_t kCnt = L ? (size_t)kTR * sizeof(int) : 0;
   static constexpr size_t kPart = (size_t)PT * Pass::kV * sizeof(float);
-  static constexpr size_t kTab = 27 * sizeof(float4) + 48 * sizeof(int) + 272;  // shifts, 1/nsub, nsub(na)
+  static constexpr size_t kTab = Tabs::kBytes;
   static constexpr size_t oList = 2 * kRec;
   static constexpr size_t oCnt = oList + 2 * kList;
   static constexpr size_t oPart = oCnt + 2 * kCnt;
@@ -1187,23 +1219,11 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
   };
   auto tcnt = [&](int h) { return reinterpret_cast<int*>(smem_raw + SM::oCnt) + h * kTR; };
   float* part = reinterpret_cast<float*>(smem_raw + SM::oPart);
-  float4* shtab = reinterpret_cast<float4*>(smem_raw + SM::oTab);
-  int* inv16 = reinterpret_cast<int*>(smem_raw + SM::oTab + 27 * sizeof(float4));
-  unsigned char* nsubtab = smem_raw + SM::oTab + 27 * sizeof(float4) + 48 * sizeof(int);
   const Grid g = *gp;
   const int tid = threadIdx.x;
-  // per-launch tables: the cell shift of each stencil code, nsub = min(PT / na,
-  // 32) and 1/nsub in 16-bit fixed point (tid / nsub = tid * inv16 >> 16 is
-  // exact for tid < 256 and nsub <= 32)
-  if (tid < 27) {
-    float sx, sy, sz;
-    entry_shift((uint32_t)tid << kIndexBits, g, sx, sy, sz);
-    shtab[tid] = make_float4(sx, sy, sz, 0.0f);
-  }
-  if (tid >= 1 && tid <= kMaxSub) inv16[tid] = (65536 + tid - 1) / tid;
-  for (int na = tid; na <= PT; na += PT)
-    nsubtab[na] = (unsigned char)(na > 0 ? min(PT / na, kMaxSub) : 1);
-  __syncthreads();
+  Tabs tb(smem_raw + SM::oTab);
+  tb.fill<PT>(g);
+  const float4* shtab = tb.shift;
   const uint32_t n0 = (uint32_t)*src.n0;
   const uint32_t n_cells = n0 + (src.cells1 ? (uint32_t)*src.n1 : 0u);
   const uint32_t G = gridDim.x;
@@ -1250,8 +1270,8 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
   // this thread's target in a cell (nsub threads per target)
   auto target_of = [&](uint4 md, int& t, int& sub, int& nsub) {
     const int na = present(md) ? cell_na(md) : 0;
-    nsub = nsubtab[min(na, PT)];
-    t = (tid * inv16[nsub]) >> 16;
+    nsub = tb.nsub[min(na, PT)];
+    t = tb.div(tid, nsub);
     sub = tid - t * nsub;
     if (t >= na) t = -1;
   };
