@@ -42,22 +42,23 @@ FLOPS64 = {"find": 14, "density": 43, "iad": 19, "momentum": 131}
 # written once: per particle (its own fields in and out; the records of
 # neighbours counted once, as the particle's own record), per staged slot (the
 # 4-byte candidate entry, FP32-mixed), per hit-mask word (8 bytes, FP32-mixed)
-# and per list entry (the int32 list and, FP64, the cached W_ab(h_a)).
-#   FP32-mixed  find: pos32 16 in, nn 4 out; entries and mask words written.
-#               density: rec_d 16, pos32 16, u 8 in; rho, p, c 24, rec_i,
-#               recA, recQ 48 out.  IAD: rec_i, recA, recQ 48 in; iad 48,
-#               recC 16, recC2 8 out.  momentum: recA, recV, recQ, recC, recC2
-#               72 in; ax, ay, az, du 32 out.  Each pass reads the entries and
-#               mask words once.
+# and per list entry (FP32-mixed: the 2-byte staged-slot list; FP64: the int32
+# list and the cached W_ab(h_a)).
+#   FP32-mixed  find: pos32 16 in, nn 4 out; entries, mask words and slot lists
+#               written.  density: rec_d 16, pos32 16, u 8 in; rho, p, c 24,
+#               rec_i, recA, recQ 48 out.  IAD: rec_i, recA, recQ 48 in; iad
+#               48, recC 16, recC2 8 out.  momentum: recA, recV, recQ, recC,
+#               recC2 72 in; ax, ay, az, du 32 out.  Each pass reads the
+#               entries and the slot lists once.
 #   FP64        find: pos32 16 in, nn 4 out, the list written.  density: x, y,
 #               z, h, m, u 48 in, rho, p, c 24 out, the list read and W
 #               written.  IAD: x, y, z, h, m, rho 48 in, iad 48 out.  momentum:
 #               17 fields 136 in, 32 out; both read the list and W.
 KERNEL_BYTES = {
-    "fp32_mixed": {"find": {"particle": 20, "slot": 4, "word": 8, "entry": 0},
-                   "density": {"particle": 112, "slot": 4, "word": 8, "entry": 0},
-                   "iad": {"particle": 120, "slot": 4, "word": 8, "entry": 0},
-                   "momentum": {"particle": 104, "slot": 4, "word": 8, "entry": 0}},
+    "fp32_mixed": {"find": {"particle": 20, "slot": 4, "word": 8, "entry": 2},
+                   "density": {"particle": 112, "slot": 4, "word": 0, "entry": 2},
+                   "iad": {"particle": 120, "slot": 4, "word": 0, "entry": 2},
+                   "momentum": {"particle": 104, "slot": 4, "word": 0, "entry": 2}},
     "fp64": {"find": {"particle": 20, "slot": 0, "word": 0, "entry": 4},
              "density": {"particle": 72, "slot": 0, "word": 0, "entry": 12},
              "iad": {"particle": 96, "slot": 0, "word": 0, "entry": 12},
@@ -212,17 +213,23 @@ def read_ncu_csv(path):
 
 
 def stage_traffic(rows):
-    """DRAM bytes (read + write) per stage of the last captured step: for each
-    kernel of a stage its last launch, summed over the stage's kernels."""
-    last = {}
-    for lid, name, m in rows:
-        if "dram__bytes_read.sum" in m and "dram__bytes_write.sum" in m:
-            last[name] = m["dram__bytes_read.sum"] + m["dram__bytes_write.sum"]
+    """DRAM bytes (read + write) per stage of the last captured step.  A step
+    starts where a search launch follows a launch of another stage; every
+    launch of the last step is summed into its stage."""
+    def stage_of(name):
+        return next((st for st, keys in STAGE_KERNELS.items() if any(k in name for k in keys)),
+                    None)
+    start, prev = 0, None
+    for i, (_, name, _) in enumerate(rows):
+        st = stage_of(name)
+        if st == "find" and prev != "find":
+            start = i
+        prev = st
     out = {}
-    for stage, keys in STAGE_KERNELS.items():
-        hits = [b for name, b in last.items() if any(k in name for k in keys)]
-        if hits:
-            out[stage] = sum(hits)
+    for _, name, m in rows[start:]:
+        st = stage_of(name)
+        if st and "dram__bytes_read.sum" in m and "dram__bytes_write.sum" in m:
+            out[st] = out.get(st, 0.0) + m["dram__bytes_read.sum"] + m["dram__bytes_write.sum"]
     return out
 
 

@@ -31,8 +31,8 @@ def test_step_roofline_picks_the_larger_bound():
     out = bench.step_roofline(r, n, "fp32_mixed", ms_step=10.0)
     kb = bench.KERNEL_BYTES["fp32_mixed"]
     expect = bench.OTHER_BYTES * n + sum(
-        kb[k]["particle"] * n + kb[k]["slot"] * r["slots"] + kb[k]["word"] * r["words"]
-        for k in bench.PAIR_KERNELS)
+        kb[k]["particle"] * n + kb[k]["slot"] * r["slots"] + kb[k]["word"] * r["words"] +
+        kb[k]["entry"] * r["pairs"] for k in bench.PAIR_KERNELS)
     assert out["bytes_per_step"] == pytest.approx(expect)
     flops = bench.FLOPS["find"] * r["candidates"] + sum(
         bench.FLOPS[k] for k in ("density", "iad", "momentum")) * r["pairs"]
@@ -120,10 +120,17 @@ def test_ncu_csv_traffic_per_stage(tmp_path):
     assert [r[0] for r in rows] == [0, 1, 2, 3]
     assert rows[3][2]["gpu__time_duration.sum"] == 1200.0
     t = bench.stage_traffic(rows)
-    # the last launch of each kernel: find = k_find_mask<false> (id 2) + <true> (id 3)
+    # the last step starts at the search launch that follows another stage
+    # (id 2): find = k_find_mask<false> (id 2) + <true> (id 3)
     assert t["find"] == pytest.approx(2000 + 600 + 10)
-    assert t["density"] == pytest.approx(5000)
-    assert "momentum" not in t
+    assert "density" not in t and "momentum" not in t
+    rows2 = rows + [(4, "void sph::k_cellwarp<sph::DensityPass>(int)",
+                     {"dram__bytes_read.sum": 7.0, "dram__bytes_write.sum": 1.0}),
+                    (5, "void sph::k_cellpass<sph::DensityPass>(int)",
+                     {"dram__bytes_read.sum": 2.0, "dram__bytes_write.sum": 0.0})]
+    t2 = bench.stage_traffic(rows2)
+    assert t2["density"] == pytest.approx(10.0)      # two launches of one stage add up
+    assert t2["find"] == pytest.approx(2610)
 
 
 def test_committed_traffic_capture_scales_with_particles():

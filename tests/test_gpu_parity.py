@@ -140,6 +140,26 @@ def test_big_cells_rounds_windows_and_list_passes(precision):
         assert e[k] <= t, (k, e)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+def test_lists_with_max_nb_4_mod_8(precision):
+    """max_nb = 36 (4 mod 8) with counts on both sides of it: rows that fit
+    equal the oracle's, overflowing rows keep their true counts.  Exercises
+    the group of 8 entries that straddles max_nb in the list writer and the
+    last 4-entry chunk of a row in the pair passes."""
+    from paper_2005_02656_gb300 import _lib
+    s = sph_inputs.jittered_box(16, seed_index=10)
+    s["h"] *= 0.75                           # counts 31..42
+    rc, ref_s, ref = oracle_outputs(s, ng_target=0, max_nb=MAX_NB)
+    assert rc == 0
+    nn = ref["nn"]
+    assert (nn > 36).any() and ((nn > 32) & (nn <= 36)).any()
+    got, counts, ids, flags = _gpu(s, precision=precision, max_nb=36)
+    assert flags & _lib.FLAG_NB_OVERFLOW
+    np.testing.assert_array_equal(counts, nn)
+    for a in np.nonzero(nn <= 36)[0]:
+        np.testing.assert_array_equal(ids[a, :nn[a]], ref["nbr"][a, :nn[a]])
+
+
 @pytest.mark.parametrize("name", ["box20", "box16_varh", "kh32"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
 def test_gradh_fields(name, precision):
