@@ -65,6 +65,8 @@ constexpr int kPipeWinM = 448;  // ... the pipelined momentum pass takes (72-byt
 // few particles with a much larger h than the rest make every cell large) get
 // int32 lists, marked by mask_base = kListForm.
 constexpr int kStagedMaxP = 64 * kMaskWords;
+// per-warp buffer of one round's hit words of a one-window stencil
+constexpr int kMaskBufWords = kFindWindow / 64 * 32;
 constexpr uint32_t kListForm = 0xffffffffu;
 constexpr uint32_t kNoCell = 0xffffffffu;  // past the end of a launch's cell list
 
@@ -95,6 +97,51 @@ __device__ __forceinline__ uint16_t* slot_row(uint16_t* slist, int64_t a, int ma
   return slist + 2 * a * max_nb;
 }
 
+// Staged-slot list of one target from its hit-mask words (word blk at
+// words[32 blk], bit 63 - q for slot 64 blk + q): one loop over words and
+// bits, slot indices packed into a 128-bit register eight at a time and each
+// full group stored with one 16-byte store, the rest (up to max_nb entries)
+// one by one.  Returns the number of hits.
+__device__ __forceinline__ int write_slot_list(const unsigned long long* words, int nblk,
+                                               uint16_t* row, int max_nb) {
+  uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;  // entries k-8..k-1 of the group being filled
+  int k = 0;
+  int blk = 0;
+  uint64_t w = nblk > 0 ? words[0] : 0;
+  for (;;) {
+    if (!w) {
+      if (++blk >= nblk) break;
+      w = words[32 * blk];
+      continue;
+    }
+    const int q = __clzll((long long)w);
+    w ^= kTop >> q;
+    const uint32_t e = (uint32_t)(64 * blk + q);
+    b0 = __funnelshift_r(b0, b1, 16);
+    b1 = __funnelshift_r(b1, b2, 16);
+    b2 = __funnelshift_r(b2, b3, 16);
+    b3 = (b3 >> 16) | (e << 16);
+    ++k;
+    if ((k & 7) == 0) {
+      if (k <= max_nb) {
+        *reinterpret_cast<uint4*>(row + (k - 8)) = make_uint4(b0, b1, b2, b3);
+      } else if (k - 8 < max_nb) {  // a group across max_nb (max_nb = 4 mod 8)
+        const uint32_t bb[4] = {b0, b1, b2, b3};
+        for (int i = 0; k - 8 + i < max_nb; ++i)
+          row[k - 8 + i] = (uint16_t)(bb[i >> 1] >> (16 * (i & 1)));
+      }
+    }
+  }
+  // the last, partial group (entries (k & ~7) .. k - 1, at the top of b)
+  const int r = k & 7;
+  const uint32_t bb[4] = {b0, b1, b2, b3};
+  for (int i = 0; i < r; ++i) {
+    const int pos = (k & ~7) + i, src = 8 - r + i;
+    if (pos < max_nb) row[pos] = (uint16_t)(bb[src >> 1] >> (16 * (src & 1)));
+  }
+  return k;
+}
+
 template <bool WRAP, int WIN>
 __device__ __forceinline__ void find_cell_masks(const Grid& g, uint32_t cell, uint32_t code,
                                                 const StateView& s,
@@ -106,7 +153,8 @@ __device__ __forceinline__ void find_cell_masks(const Grid& g, uint32_t cell, ui
                                                 FindWarpSmemT<WIN>& W, unsigned long long& tested,
                                                 unsigned long long& exact,
                                                 unsigned long long& slots,
-                                                unsigned long long& words) {
+                                                unsigned long long& words,
+                                                unsigned long long* mbuf) {
   const int lane = threadIdx.x & 31;
   Stencil& S = W.S;
   const float esum = g.err32[0] + g.err32[1] + g.err32[2];
@@ -180,6 +228,11 @@ __device__ __forceinline__ void find_cell_masks(const Grid& g, uint32_t cell, ui
   uint32_t gb = 0;     // staged block of the window's first 64 slots
   int gself = -1;      // staged slot of the target cell's first particle
   bool first = true;
+  // A stencil that fits one window (most cells): each round's hit words stay
+  // in the warp's mask buffer (word jb of lane t at mbuf[32 jb + t]) and the
+  // round's lists are written from there, so its masks never reach memory.
+  bool direct = false;
+  int kmax = 0;        // largest hit count of the cell's targets (direct cells)
   int sc = 0, j0 = 0;  // next source: stencil cell and particle within it
   const uint32_t lt = (1u << lane) - 1u;
   for (;;) {
@@ -236,6 +289,7 @@ __device__ __forceinline__ void find_cell_masks(const Grid& g, uint32_t cell, ui
     }
     __syncwarp();
     const int nproc = done ? wn : 64 * nblk;  // real slots processed now
+    direct = first && done;
     for (int t0 = 0; t0 < na; t0 += 32) {
       const int t = t0 + lane;
       const bool active = t < na;
@@ -264,9 +318,16 @@ __device__ __forceinline__ void find_cell_masks(const Grid& g, uint32_t cell, ui
         const int gblk = (int)gb + jb;
         if (gs >= 0 && (gs >> 6) == gblk) hit &= ~(kTop >> (gs & 63));
         if (active) {
-          mo.masks[mask_base + (uint32_t)gblk * (uint32_t)na + (uint32_t)t] = hit;
+          if (direct)
+            mbuf[32 * jb + lane] = hit;
+          else
+            mo.masks[mask_base + (uint32_t)gblk * (uint32_t)na + (uint32_t)t] = hit;
           k += __popcll(hit);
         }
+      }
+      if (active && direct) {
+        write_slot_list(mbuf + lane, nblk, slot_row(mo.slist, (int64_t)a, max_nb), max_nb);
+        kmax = max(kmax, k);
       }
       if (active) {
         nn[a] = k;
@@ -303,11 +364,11 @@ __device__ __forceinline__ void find_cell_masks(const Grid& g, uint32_t cell, ui
   // 16-byte store; the rest, up to max_nb entries, one by one.
   // The round's mask words are first copied (coalesced) into the window,
   // which is free now: nblk <= kStagedMaxP / 64 = 32 words per target.
-  const int nblk = (int)((staged + 63) >> 6);
+  const int nblk = direct ? 0 : (int)((staged + 63) >> 6);
   static_assert(kStagedMaxP / 64 * 32 * 8 <= 4 * WIN * 4, "mask copy fits the window");
   unsigned long long* mcopy = reinterpret_cast<unsigned long long*>(W.cx);
-  int kl = 0, kmax = 0;  // this lane's count and its largest over the rounds
-  for (int t0 = 0; t0 < na; t0 += 32, kmax = max(kmax, kl), kl = 0) {
+  int kl = 0;  // this lane's count
+  for (int t0 = 0; !direct && t0 < na; t0 += 32, kmax = max(kmax, kl), kl = 0) {
     const int t = t0 + lane;
     __syncwarp();
 #pragma unroll 4
@@ -316,43 +377,7 @@ __device__ __forceinline__ void find_cell_masks(const Grid& g, uint32_t cell, ui
           t < na ? mo.masks[mask_base + (uint32_t)blk * (uint32_t)na + (uint32_t)t] : 0ull;
     __syncwarp();
     if (t >= na) continue;
-    uint16_t* row = slot_row(mo.slist, (int64_t)a0 + t, max_nb);
-    int& k = kl;
-    uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;  // entries k-8..k-1 of the group being filled
-    k = 0;
-    int blk = 0;
-    uint64_t w = nblk > 0 ? mcopy[lane] : 0;
-    for (;;) {
-      if (!w) {
-        if (++blk >= nblk) break;
-        w = mcopy[blk * 32 + lane];
-        continue;
-      }
-      const int q = __clzll((long long)w);
-      w ^= kTop >> q;
-      const uint32_t e = (uint32_t)(64 * blk + q);
-      b0 = __funnelshift_r(b0, b1, 16);
-      b1 = __funnelshift_r(b1, b2, 16);
-      b2 = __funnelshift_r(b2, b3, 16);
-      b3 = (b3 >> 16) | (e << 16);
-      ++k;
-      if ((k & 7) == 0) {
-        if (k <= max_nb) {
-          *reinterpret_cast<uint4*>(row + (k - 8)) = make_uint4(b0, b1, b2, b3);
-        } else if (k - 8 < max_nb) {  // a group across max_nb (max_nb = 4 mod 8)
-          const uint32_t bb[4] = {b0, b1, b2, b3};
-          for (int i = 0; k - 8 + i < max_nb; ++i)
-            row[k - 8 + i] = (uint16_t)(bb[i >> 1] >> (16 * (i & 1)));
-        }
-      }
-    }
-    // the last, partial group (entries (k & ~7) .. k - 1, at the top of b)
-    const int r = k & 7;
-    const uint32_t bb[4] = {b0, b1, b2, b3};
-    for (int i = 0; i < r; ++i) {
-      const int pos = (k & ~7) + i, src = 8 - r + i;
-      if (pos < max_nb) row[pos] = (uint16_t)(bb[src >> 1] >> (16 * (src & 1)));
-    }
+    kl = write_slot_list(mcopy + lane, nblk, slot_row(mo.slist, (int64_t)a0 + t, max_nb), max_nb);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
@@ -379,13 +404,16 @@ __global__ void __launch_bounds__(kFindThreads, 4) k_find_mask(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   FindWarpSmem& W = reinterpret_cast<FindWarpSmem*>(smem_raw)[warp];
+  unsigned long long* mbuf = reinterpret_cast<unsigned long long*>(
+                                 smem_raw + kFindWarps * sizeof(FindWarpSmem)) +
+                             warp * kMaskBufWords;
   const Grid g = *gp;
   if ((g.wrap32 != 0) != WRAP) return;
   unsigned long long tested = 0, exact = 0, slots = 0, words = 0;
   const uint32_t gw = blockIdx.x * kFindWarps + warp, nw = gridDim.x * kFindWarps;
   for (uint32_t cell = gw; cell < g.n_occ; cell += nw)
     find_cell_masks<WRAP, kFindWindow>(g, cell, occ[cell], s, pos32, tbl_start, tbl_count, nn,
-                                       nbr, max_nb, mo, err, W, tested, exact, slots, words);
+                                       nbr, max_nb, mo, err, W, tested, exact, slots, words, mbuf);
   for (int o = 16; o > 0; o >>= 1) {
     tested += __shfl_xor_sync(0xffffffffu, tested, o);
     exact += __shfl_xor_sync(0xffffffffu, exact, o);
@@ -1547,7 +1575,7 @@ inline OutView outs_with_omega(const OutView& o, int gradh) {
 
 void launch_find_masks(sph_ctx* ctx, const StateView& s, int64_t n, cudaStream_t st) {
   (void)n;
-  const size_t smem = kFindWarps * sizeof(FindWarpSmem);
+  const size_t smem = kFindWarps * (sizeof(FindWarpSmem) + kMaskBufWords * sizeof(unsigned long long));
   if (!ctx->find_mask_blocks) {  // once per context, on its device
     int per_sm = 0;
     cudaFuncSetAttribute(k_find_mask<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
