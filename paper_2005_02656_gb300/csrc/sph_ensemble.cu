@@ -46,6 +46,7 @@ struct Box {
   int periodic[3];
   double alpha;
   double dt, dt_prev;
+  double q;             // dt / (2 dt_prev), 0 on the first step (Adams-Bashforth weight)
   unsigned long long hmax_o, xmin_o[3], xmax_o[3];  // ordered-integer reductions
   unsigned long long qmin_o;                         // min h/c
   int64_t item0;        // first global cell item of the box
@@ -93,6 +94,7 @@ struct Args {
   float4* rec_m;
   int32_t* nn;
   uint32_t* nbr;
+  const double* hfac;    // kMaxSlots + 1: 0.5 (1 + cbrt(ng_target / max(k, 1))) for count k
   double* dt_io;         // per box: dt_{n-1} in, dt_n out
   uint32_t* err;
   Sync* sync;
@@ -565,6 +567,7 @@ __device__ void ph_dt(const Args& A) {
     if (B.dt_prev > 0.0) dt = fmin(dt, A.prm.dt_growth * B.dt_prev);
     if (!isfinite(dt) || !(dt > 0.0)) atomicOr(A.err, (uint32_t)SPH_FLAG_NONFINITE);
     B.dt = dt;
+    B.q = B.dt_prev > 0.0 ? dt / (2.0 * B.dt_prev) : 0.0;
     A.dt_io[b] = dt;
   }
 }
@@ -578,7 +581,7 @@ __device__ void ph_update(const Args& A) {
     const Box& B = A.boxes[A.box_of[p]];
     const double dt = B.dt, dt_prev = B.dt_prev;
     const double delta = 0.5 * (dt + dt_prev);
-    const double q = dt_prev > 0.0 ? dt / (2.0 * dt_prev) : 0.0;
+    const double q = B.q;
     const double a3[3] = {A.out.ax[p], A.out.ay[p], A.out.az[p]};
     const double x3[3] = {A.s.x[p], A.s.y[p], A.s.z[p]};
     const double vh3[3] = {A.s.vxh[p], A.s.vyh[p], A.s.vzh[p]};
@@ -601,11 +604,10 @@ __device__ void ph_update(const Args& A) {
     const double u = A.s.u[p];
     const double un = dt_prev > 0.0 ? u + dt * ((1.0 + q) * du - q * A.s.du_prev[p]) : u + dt * du;
     double h = A.s.h[p];
-    if (prm.ng_target > 0) {
-      const int cnt = A.nn[p];
-      const int kk = cnt > 1 ? cnt : 1;
-      h = h * 0.5 * (1.0 + cbrt((double)prm.ng_target / (double)kk));
-    }
+    // h (0.5 (1 + c)) equals (h 0.5) (1 + c) bit for bit (scaling by 0.5 is
+    // exact), so the tabulated factor changes no result; counts are at most
+    // kMaxSlots (a larger stencil is flagged and its counts are 0)
+    if (prm.ng_target > 0) h = h * __ldg(A.hfac + min(max(A.nn[p], 0), kMaxSlots));
     A.in.x[p] = xn[0];
     A.in.y[p] = xn[1];
     A.in.z[p] = xn[2];
@@ -623,8 +625,17 @@ __device__ void ph_update(const Args& A) {
   }
 }
 
+// The h factors of the update for every possible count (the expression of
+// the single-box table, over the counts a stencil can hold).
+__global__ void k_ens_hfac(double* tab, int ng) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= kMaxSlots; k += gridDim.x * blockDim.x) {
+    const int kk = k > 1 ? k : 1;
+    tab[k] = 0.5 * (1.0 + cbrt((double)ng / (double)kk));
+  }
+}
+
 template <int WIN>
-__global__ void __launch_bounds__(kThreads) k_ensemble(Args A, int steps) {
+__global__ void __launch_bounds__(kThreads, 6) k_ensemble(Args A, int steps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   find::FindWarpSmemT<WIN>& W =
       reinterpret_cast<find::FindWarpSmemT<WIN>*>(smem_raw)[threadIdx.x >> 5];
@@ -688,6 +699,7 @@ struct sph_ens {
   float4 *pos32, *rec_d, *rec_i, *rec_m;
   int32_t* nn;
   uint32_t* nbr;
+  double* hfac;
   uint32_t* err;
   sph::ens::Sync* sync;
   int blocks;
@@ -797,6 +809,7 @@ Args args_of(sph_ens* e, const sph_state* st, double* dt_dev) {
   A.rec_m = e->rec_m;
   A.nn = e->nn;
   A.nbr = e->nbr;
+  A.hfac = e->hfac;
   A.dt_io = dt_dev;
   A.err = e->err;
   A.sync = e->sync;
@@ -967,6 +980,7 @@ int sph_ensemble_init(const sph_params* common, int n_boxes, const int64_t* box_
   A((void**)&e->rec_m, 80 * N);
   A((void**)&e->nn, 4 * N);
   A((void**)&e->nbr, 4 * N * (size_t)common->max_nb);
+  A((void**)&e->hfac, 8 * (size_t)(sph::kMaxSlots + 1));
   A((void**)&e->err, 4);
   A((void**)&e->sync, sizeof(sph::ens::Sync));
   if (err == cudaSuccess) {
@@ -979,6 +993,10 @@ int sph_ensemble_init(const sph_params* common, int n_boxes, const int64_t* box_
   if (err == cudaSuccess)
     err = cudaMemcpy(e->boxes, e->boxes_h, sizeof(Box) * n_boxes, cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemset(e->err, 0, 4);
+  if (err == cudaSuccess) {
+    sph::ens::k_ens_hfac<<<64, 256>>>(e->hfac, common->ng_target > 0 ? common->ng_target : 1);
+    err = cudaGetLastError();
+  }
   if (err == cudaSuccess) err = cudaMemset(e->sync, 0, sizeof(sph::ens::Sync));
   if (err == cudaSuccess) err = cudaDeviceSynchronize();
   int rc = err == cudaSuccess ? configure(e) : SPH_ERR_OOM;
@@ -996,7 +1014,7 @@ void sph_ensemble_destroy(sph_ens* e) {
   if (e->graph) cudaGraphExecDestroy(e->graph);
   void* ptrs[] = {e->boxes, e->box_of, e->item_off, e->sbuf, e->s_id, e->code, e->slot,
                   e->perm_tmp, e->perm, e->tbl_count, e->tbl_start, e->occ, e->pos32,
-                  e->rec_d, e->rec_i, e->rec_m, e->nn, e->nbr, e->err, e->sync};
+                  e->rec_d, e->rec_i, e->rec_m, e->nn, e->nbr, e->hfac, e->err, e->sync};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free(e->boxes_h);

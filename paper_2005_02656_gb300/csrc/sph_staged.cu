@@ -291,9 +291,15 @@ __device__ __forceinline__ void find_cell_masks(const Grid& g, uint32_t cell, ui
     const int nproc = done ? wn : 64 * nblk;  // real slots processed now
     direct = first && done;
     for (int t0 = 0; t0 < na; t0 += 32) {
-      const int t = t0 + lane;
-      const bool active = t < na;
-      const int a = a0 + (active ? t : 0);
+      // a round of r targets; with r <= 16, G = 32 / r lanes share each target
+      // and take its blocks round-robin (lane l: target l % r, blocks
+      // jb = l / r, l / r + G, ...)
+      const int r = min(32, na - t0);
+      const int G = 32 / r;
+      const int tl = lane % r, grp = lane / r;
+      const bool active = grp < G;
+      const int t = t0 + tl;
+      const int a = a0 + t;
       const float4 pa = pos32[a];
       const float two_h = 2.0f * pa.w;
       const float lim = two_h * two_h;
@@ -301,9 +307,9 @@ __device__ __forceinline__ void find_cell_masks(const Grid& g, uint32_t cell, ui
       const float lo_lim = lim - margin, hi_lim = lim + margin;
       const float2 npx = make_float2(-pa.x, -pa.x), npy = make_float2(-pa.y, -pa.y),
                    npz = make_float2(-pa.z, -pa.z);
-      const int gs = (active && gself >= 0) ? gself + t : -1;  // own staged slot
-      int k = (first || !active) ? 0 : nn[a];
-      for (int jb = 0; jb < nblk; ++jb) {
+      const int gs = gself >= 0 ? gself + t : -1;  // own staged slot
+      int kp = 0;                                  // this lane's hits
+      for (int jb = active ? grp : nblk; jb < nblk; jb += G) {
         uint64_t hit, unc;
         find::block_masks<WRAP>(g, W.cx + 64 * jb, W.cy + 64 * jb, W.cz + 64 * jb, npx, npy,
                                 npz, lo_lim, hi_lim, hit, unc);
@@ -317,24 +323,29 @@ __device__ __forceinline__ void find_cell_masks(const Grid& g, uint32_t cell, ui
         }
         const int gblk = (int)gb + jb;
         if (gs >= 0 && (gs >> 6) == gblk) hit &= ~(kTop >> (gs & 63));
-        if (active) {
-          if (direct)
-            mbuf[32 * jb + lane] = hit;
-          else
-            mo.masks[mask_base + (uint32_t)gblk * (uint32_t)na + (uint32_t)t] = hit;
-          k += __popcll(hit);
-        }
+        if (direct)
+          mbuf[32 * jb + tl] = hit;
+        else
+          mo.masks[mask_base + (uint32_t)gblk * (uint32_t)na + (uint32_t)t] = hit;
+        kp += __popcll(hit);
       }
-      if (active && direct) {
-        write_slot_list(mbuf + lane, nblk, slot_row(mo.slist, (int64_t)a, max_nb), max_nb);
+      // the target's hits over its G lanes (lanes tl, tl + r, ...)
+      int k = kp;
+      for (int gg = 1; gg < G; ++gg) k += __shfl_sync(0xffffffffu, kp, min(tl + gg * r, 31));
+      const bool lead = grp == 0;  // the lane that owns the target's results
+      if (direct) __syncwarp();    // the round's hit words are in mbuf
+      if (!first && lead) k += nn[a];
+      if (lead && direct) {
+        write_slot_list(mbuf + tl, nblk, slot_row(mo.slist, (int64_t)a, max_nb), max_nb);
         kmax = max(kmax, k);
       }
-      if (active) {
+      if (lead) {
         nn[a] = k;
         if (k > max_nb) raise_flag(err, SPH_FLAG_NB_OVERFLOW);
         const bool self_here = gs >= 0 && gs >= 64 * (int)gb && gs < 64 * (int)gb + nproc;
         tested += (unsigned long long)nproc - (self_here ? 1 : 0);
       }
+      if (direct) __syncwarp();    // mbuf is free for the next round
     }
     __syncwarp();
     first = false;
@@ -851,8 +862,11 @@ struct MomentumPass {
     sep(g, b0.x, b0.y, b0.z, T.p.x, T.p.y, T.p.z, dx, dy, dz);
     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
     const float4 b2 = R.q;
-    const float Wa = T.q.x * s_pow(r2 * T.p.w, sinc_n, ktab);
-    const float Wb = b2.x * s_pow(r2 * b0.w, sinc_n, ktab);  // clamped at t = 4 (S = 0)
+    // W_a and W_b together in paired FP32 (each component rounded as the
+    // scalar operation), clamped at t = 4 (S = 0)
+    const float2 Wab = __fmul2_rn(f2(T.q.x, b2.x),
+                                  s_pow2(__fmul2_rn(f2(r2), f2(T.p.w, b0.w)), sinc_n, ktab));
+    const float Wa = Wab.x, Wb = Wab.y;
     const float Cadx = fmaf(T.c02, dz, fmaf(T.c01, dy, T.c00 * dx));
     const float Cady = fmaf(T.c12, dz, fmaf(T.c11, dy, T.c01 * dx));
     const float Cadz = fmaf(T.c22, dz, fmaf(T.c12, dy, T.c02 * dx));
