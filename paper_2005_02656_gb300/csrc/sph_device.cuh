@@ -172,12 +172,36 @@ __device__ __forceinline__ float kernel_w32(float t, float norm, int n) {
   return norm * ipow(sinc_poly32(t), n);
 }
 
+// kernel_w32 for two arguments at once (W_a and W_b of one pair): the clamp,
+// the series and the powers in paired FP32, each component rounded exactly as
+// the scalar kernel_w32 (the integer power for n = 6 as (s^2 s^2) s^2).
+__device__ __forceinline__ float2 kernel_w32x2(float2 t, float2 norm, int n) {
+  t = make_float2(fminf(t.x, 4.0f), fminf(t.y, 4.0f));
+  constexpr SincCoefs<kSincTerms32> C{};
+  float2 s = make_float2((float)C.c[kSincTerms32 - 1], (float)C.c[kSincTerms32 - 1]);
+#pragma unroll
+  for (int k = kSincTerms32 - 2; k >= 0; --k)
+    s = __ffma2_rn(s, t, make_float2((float)C.c[k], (float)C.c[k]));
+  float2 p;
+  if (n == 6) {
+    const float2 s2 = __fmul2_rn(s, s);
+    p = __fmul2_rn(__fmul2_rn(s2, s2), s2);
+  } else {
+    p = make_float2(ipow(s.x, n), ipow(s.y, n));
+  }
+  return __fmul2_rn(norm, p);
+}
+
 // The kernel of the context's mode: the series, or the table when tab != NULL.
 __device__ __forceinline__ double kw64(double t, double norm, int n, const double2* tab) {
   return tab ? kernel_w64_tab(t, norm, tab) : kernel_w64(t, norm, n);
 }
 __device__ __forceinline__ float kw32(float t, float norm, int n, const float2* tab) {
   return tab ? kernel_w32_tab(t, norm, tab) : kernel_w32(t, norm, n);
+}
+__device__ __forceinline__ float2 kw32x2(float2 t, float2 norm, int n, const float2* tab) {
+  return tab ? make_float2(kernel_w32_tab(t.x, norm.x, tab), kernel_w32_tab(t.y, norm.y, tab))
+             : kernel_w32x2(t, norm, n);
 }
 
 // ---------------------------------------------------------------------------

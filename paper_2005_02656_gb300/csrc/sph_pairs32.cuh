@@ -275,8 +275,10 @@ __device__ __forceinline__ void momentum_one(int64_t a, const Grid& g, const F32
       rel(g, wrap, e, b0, pa, dx, dy, dz);
       const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
       const float4 b2 = rb[2];
-      const float Wa = kw32(r2 * pa.w, qa.x, sinc_n, f.ktab);
-      const float Wb = kw32(r2 * b0.w, b2.x, sinc_n, f.ktab);  // clamped at t = 4 (S = 0)
+      // W_a and W_b together in paired FP32, clamped at t = 4 (S = 0)
+      const float2 Wab = kw32x2(make_float2(r2 * pa.w, r2 * b0.w), make_float2(qa.x, b2.x),
+                                sinc_n, f.ktab);
+      const float Wa = Wab.x, Wb = Wab.y;
       const float Cadx = fmaf(a02, dz, fmaf(a01, dy, a00 * dx));
       const float Cady = fmaf(a12, dz, fmaf(a11, dy, a01 * dx));
       const float Cadz = fmaf(a22, dz, fmaf(a12, dy, a02 * dx));
