@@ -1214,8 +1214,8 @@ struct PipeSmem {
   static constexpr size_t kTab = Tabs::kBytes;
   static constexpr size_t oList = 2 * kRec;
   static constexpr size_t oCnt = oList + 2 * kList;
-  static constexpr size_t oPart = oCnt + 2 * kCnt;
-  static constexpr size_t oTab = oPart + kPart;
+  static constexpr size_t oPart = oCnt + 3 * kCnt;
+  static constexpr size_t oTab = oPart + 2 * kPart;
   static constexpr size_t kBytes = oTab + kTab;
   static_assert(kRec % 16 == 0 && kList % 16 == 0 && kCnt % 16 == 0 && kPart % 16 == 0,
                 "16-byte aligned parts");
@@ -1260,7 +1260,9 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
     return reinterpret_cast<uint16_t*>(smem_raw + SM::oList + h * SM::kList);
   };
   auto tcnt = [&](int h) { return reinterpret_cast<int*>(smem_raw + SM::oCnt) + h * kTR; };
-  float* part = reinterpret_cast<float*>(smem_raw + SM::oPart);
+  auto part = [&](int h) {
+    return reinterpret_cast<float*>(smem_raw + SM::oPart + h * SM::kPart);
+  };
   const Grid g = *gp;
   const int tid = threadIdx.x;
   Tabs tb(smem_raw + SM::oTab);
@@ -1365,11 +1367,30 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
   Share sh_cur = share_of(md_cur, c_cur0);
   int cnt_nxt = count_of(md_nxt);
   typename Pass::Target T_cur, T_nxt;
-  typename Pass::FinishIn fin_cur, fin_nxt;
   if (!Pass::kTargetSmem && sh_cur.t >= 0) pass.load_target((int64_t)md_cur.z + sh_cur.t, T_cur);
-  if (tid < cell_na(md_cur)) fin_cur = pass.prefin((int64_t)md_cur.z + tid);
-  int buf = 0;
+  // the previous cell, whose per-target sums are added after this iteration's
+  // barrier (its partial sums are in the other half of the partial buffer)
+  int na_prv = 0, nsub_prv = 1;
+  uint32_t a0_prv = 0;
+  // the per-target reduction and finish of the previous cell: thread tid < na
+  // adds the nsub partial sums of target tid in a fixed order
+  auto finish_prev = [&](int ph, const typename Pass::FinishIn& fin) {
+    if (tid < na_prv) {
+      const float* pp = part(ph);
+      float sm[kV];
+#pragma unroll
+      for (int v = 0; v < kV; ++v) {
+        float x = 0.0f;
+        for (int qq = 0; qq < nsub_prv; ++qq) x += pp[v * PT + tid * nsub_prv + qq];
+        sm[v] = x;
+      }
+      pass.finish2((int64_t)a0_prv + tid, sm, fin);
+    }
+  };
+  int buf = 0, cb = 0;  // record/list/partial half, count third
   for (;;) {
+    typename Pass::FinishIn fin_prv;
+    if (tid < na_prv) fin_prv = pass.prefin((int64_t)a0_prv + tid);
     // this cell's records have landed (the copies this thread made): add the
     // cell shifts to the records this thread copied
     cp_async_wait_all();
@@ -1390,11 +1411,14 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
       }
     }
     const bool has_nxt = q + G < n_cells;
-    if (kLists && has_nxt && tid < kTR) tcnt(buf ^ 1)[tid] = cnt_nxt;
-    __syncthreads();  // this cell's data published; the previous reduction done
+    const int cb_nxt = cb == 2 ? 0 : cb + 1;
+    // (the counts' third of two cells ago: read by no thread any more)
+    if (kLists && has_nxt && tid < kTR) tcnt(cb_nxt)[tid] = cnt_nxt;
+    __syncthreads();  // this cell's data published; the previous cell computed
+    finish_prev(buf ^ 1, fin_prv);
     if (has_nxt) {
       issue_records(md_nxt, e_nxt, rbuf(buf ^ 1));
-      if (kLists) issue_lists(md_nxt, tcnt(buf ^ 1), lbuf(buf ^ 1));
+      if (kLists) issue_lists(md_nxt, tcnt(cb_nxt), lbuf(buf ^ 1));
     }
     cp_async_commit();
     // registers for the next cells
@@ -1407,7 +1431,6 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
     if (!kLists) prefetch_rows(md_nxt);
     if (!Pass::kTargetSmem && sh_nxt.t >= 0)
       pass.load_target((int64_t)md_nxt.z + sh_nxt.t, T_nxt);
-    if (has_nxt && tid < cell_na(md_nxt)) fin_nxt = pass.prefin((int64_t)md_nxt.z + tid);
     // compute this cell
     const int na = cell_na(md_cur);
     const uint32_t a0 = md_cur.z;
@@ -1426,7 +1449,7 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
       int k = sh_cur.sub;
       if (kLists) {
         const uint16_t* row = lbuf(buf) + sh_cur.t * kLS;
-        const int c = tcnt(buf)[sh_cur.t];
+        const int c = tcnt(cb)[sh_cur.t];
         if (Pass::kPipePaired)
           for (; k + ns < c; k += 2 * ns)
             pass.pair2(T_cur, Pass::template fetch<W>(rec, row[k]),
@@ -1444,22 +1467,23 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
           pass.pair(T_cur, Pass::template fetch<W>(rec, __ldg(row + k)), g, acc);
       }
     }
+    {
+      float* pp = part(buf);
 #pragma unroll
-    for (int v = 0; v < kV; ++v) part[v * PT + tid] = acc[v] + (acc2[v].x + acc2[v].y);
-    __syncthreads();  // partial sums published
-    if (tid < na) {
-      const int nsub = sh_cur.nsub;
-      float sm[kV];
-#pragma unroll
-      for (int v = 0; v < kV; ++v) {
-        float x = 0.0f;
-        for (int qq = 0; qq < nsub; ++qq) x += part[v * PT + tid * nsub + qq];
-        sm[v] = x;
-      }
-      pass.finish2((int64_t)a0 + tid, sm, fin_cur);
+      for (int v = 0; v < kV; ++v) pp[v * PT + tid] = acc[v] + (acc2[v].x + acc2[v].y);
     }
+    na_prv = na;
+    a0_prv = a0;
+    nsub_prv = sh_cur.nsub;
     q += G;
-    if (q >= n_cells) break;
+    if (q >= n_cells) {
+      // the last cell's sums
+      typename Pass::FinishIn fin_last;
+      if (tid < na_prv) fin_last = pass.prefin((int64_t)a0_prv + tid);
+      __syncthreads();
+      finish_prev(buf, fin_last);
+      break;
+    }
     md_cur = md_nxt;
     md_nxt = md_nn;
     md_nn = md_nnn;
@@ -1471,8 +1495,8 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
     sh_cur = sh_nxt;
     cnt_nxt = cnt_nn;
     if (!Pass::kTargetSmem) T_cur = T_nxt;
-    fin_cur = fin_nxt;
     buf ^= 1;
+    cb = cb_nxt;
   }
 }
 
