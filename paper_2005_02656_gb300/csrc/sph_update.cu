@@ -17,6 +17,8 @@
 // every reduction here is deterministic.
 #include <cuda_runtime.h>
 
+#include <climits>
+
 #include "sph_device.cuh"
 #include "sph_internal.cuh"
 
@@ -165,7 +167,10 @@ __global__ void __launch_bounds__(kThreads) k_update(StateView s, OutView o, Sta
   const double delta = 0.5 * (dt + dt_prev);
   const double q = dt_prev > 0.0 ? dt / (2.0 * dt_prev) : 0.0;
   double acc[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  double nmin = INFINITY, nmax = -INFINITY;
+  // neighbour-count statistics in integer arithmetic (FP64 runs at 1/64 of the
+  // FP32 rate on this part); converted once per thread below
+  long long csum = 0;
+  int cmin = INT_MAX, cmax = INT_MIN;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     const double a3[3] = {o.ax[p], o.ay[p], o.az[p]};
@@ -216,12 +221,15 @@ __global__ void __launch_bounds__(kThreads) k_update(StateView s, OutView o, Sta
     acc[5] += m * (xn[1] * vn[2] - xn[2] * vn[1]);
     acc[6] += m * (xn[2] * vn[0] - xn[0] * vn[2]);
     acc[7] += m * (xn[0] * vn[1] - xn[1] * vn[0]);
-    acc[10] += (double)cnt;
-    nmin = fmin(nmin, (double)cnt);
-    nmax = fmax(nmax, (double)cnt);
+    csum += cnt;
+    cmin = min(cmin, cnt);
+    cmax = max(cmax, cnt);
   }
   acc[8] = 0.0;
   acc[9] = 0.0;
+  acc[10] = (double)csum;  // exact: the sum is far below 2^53
+  double nmin = cmin == INT_MAX ? INFINITY : (double)cmin;
+  double nmax = cmax == INT_MIN ? -INFINITY : (double)cmax;
   nmin = warp_min(nmin);
   nmax = warp_max(nmax);
   __shared__ double shm[kThreads / 32][2];
