@@ -197,10 +197,17 @@ __device__ void ph_extent(const Args& A) {
     }
     const int b0 = __shfl_sync(0xffffffffu, b, 0);
     if (__all_sync(0xffffffffu, b == b0 || b < 0) && b0 >= 0) {
+      // one box for the whole warp: reduce only the open axes' extents (the
+      // box decides, so the branches are uniform; FP64 min/max run at 1/64 of
+      // the FP32 rate on this part)
+      const Box& Bw = A.boxes[b0];
       for (int o = 16; o > 0; o >>= 1) {
         h = fmax(h, __shfl_xor_sync(0xffffffffu, h, o));
-        for (int k = 0; k < 3; ++k) v[k] = fmin(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
-        for (int k = 3; k < 6; ++k) v[k] = fmax(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+        for (int k = 0; k < 3; ++k) {
+          if (Bw.periodic[k]) continue;
+          v[k] = fmin(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+          v[3 + k] = fmax(v[3 + k], __shfl_xor_sync(0xffffffffu, v[3 + k], o));
+        }
       }
       if (lane == 0) {
         Box& B = A.boxes[b0];
@@ -296,14 +303,31 @@ __device__ __forceinline__ void cell_of(const Grid& g, double x, double y, doubl
 }
 
 __device__ void ph_count(const Args& A) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < A.n;
+  const int lane = threadIdx.x & 31;
+  // warp-uniform loop (p - lane is the warp's first particle)
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p - lane < A.n;
        p += (int64_t)gridDim.x * blockDim.x) {
-    const Box& B = A.boxes[A.box_of[p]];
-    int ix, iy, iz;
-    cell_of(B.g, A.in.x[p], A.in.y[p], A.in.z[p], ix, iy, iz);
-    const uint32_t c = morton3(ix, iy, iz);
-    A.code[p] = c;
-    A.slot[p] = atomicAdd(&A.tbl_count[B.tbl_off + c], 1u);
+    const bool valid = p < A.n;
+    uint64_t key = ~0ull;
+    uint32_t c = 0;
+    int64_t off = 0;
+    if (valid) {
+      const Box& B = A.boxes[A.box_of[p]];
+      int ix, iy, iz;
+      cell_of(B.g, A.in.x[p], A.in.y[p], A.in.z[p], ix, iy, iz);
+      c = morton3(ix, iy, iz);
+      A.code[p] = c;
+      off = B.tbl_off;
+      key = ((uint64_t)off << 32) | c;
+    }
+    // one atomic per group of lanes with the same box and cell (the slot order
+    // inside a cell does not matter: ph_order ranks by previous index)
+    const unsigned same = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(same) - 1;
+    uint32_t base = 0;
+    if (valid && lane == leader) base = atomicAdd(&A.tbl_count[off + c], (uint32_t)__popc(same));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (valid) A.slot[p] = base + (uint32_t)__popc(same & ((1u << lane) - 1u));
   }
 }
 

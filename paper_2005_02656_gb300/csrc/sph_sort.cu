@@ -34,14 +34,23 @@ __global__ void k_grid_reduce(StateView in, int64_t n, sph_params prm, Grid* g, 
   double v[7] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double x = in.x[i], y = in.y[i], z = in.z[i], h = in.h[i];
-    v[0] = fmin(v[0], x);
-    v[1] = fmin(v[1], y);
-    v[2] = fmin(v[2], z);
-    v[3] = fmax(v[3], x);
-    v[4] = fmax(v[4], y);
-    v[5] = fmax(v[5], z);
-    v[6] = fmax(v[6], h);
+    // the extent is needed on open axes only (periodic axes take the box)
+    if (!prm.periodic[0]) {
+      const double x = in.x[i];
+      v[0] = fmin(v[0], x);
+      v[3] = fmax(v[3], x);
+    }
+    if (!prm.periodic[1]) {
+      const double y = in.y[i];
+      v[1] = fmin(v[1], y);
+      v[4] = fmax(v[4], y);
+    }
+    if (!prm.periodic[2]) {
+      const double z = in.z[i];
+      v[2] = fmin(v[2], z);
+      v[5] = fmax(v[5], z);
+    }
+    v[6] = fmax(v[6], in.h[i]);
   }
   for (int k = 0; k < 3; ++k) v[k] = warp_min(v[k]);
   for (int k = 3; k < 7; ++k) v[k] = warp_max(v[k]);
@@ -150,13 +159,29 @@ __device__ __forceinline__ void cell_coords(const Grid& g, double x, double y, d
 __global__ void k_cell_count(StateView in, int64_t n, const Grid* gp, uint32_t* count,
                              uint32_t* code, uint32_t* slot) {
   const Grid g = *gp;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+  const int lane = threadIdx.x & 31;
+  // the loop is warp-uniform (i - lane is the warp's first index); lanes past
+  // n take no part but the shuffles
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i - lane < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    int ix, iy, iz;
-    cell_coords(g, in.x[i], in.y[i], in.z[i], ix, iy, iz);
-    uint32_t c = morton3(ix, iy, iz);
-    code[i] = c;
-    slot[i] = atomicAdd(&count[c], 1u);
+    const bool valid = i < n;
+    uint32_t c = 0xffffffffu;
+    if (valid) {
+      int ix, iy, iz;
+      cell_coords(g, in.x[i], in.y[i], in.z[i], ix, iy, iz);
+      c = morton3(ix, iy, iz);
+      code[i] = c;
+    }
+    // one atomic per group of lanes with the same cell (the state is in the
+    // previous step's cell order, so neighbouring lanes mostly share a cell);
+    // the slot order inside a cell does not matter (k_cell_order ranks by
+    // previous index)
+    const unsigned same = __match_any_sync(0xffffffffu, c);
+    const int leader = __ffs(same) - 1;
+    uint32_t base = 0;
+    if (valid && lane == leader) base = atomicAdd(&count[c], (uint32_t)__popc(same));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (valid) slot[i] = base + (uint32_t)__popc(same & ((1u << lane) - 1u));
   }
 }
 
