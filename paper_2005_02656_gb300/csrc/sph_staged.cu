@@ -1463,8 +1463,13 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
           for (; k + ns < c; k += 2 * ns)
             pass.pair2(T_cur, Pass::template fetch<W>(rec, __ldg(row + k)),
                        Pass::template fetch<W>(rec, __ldg(row + k + ns)), g, acc2);
-        for (; k < c; k += ns)
-          pass.pair(T_cur, Pass::template fetch<W>(rec, __ldg(row + k)), g, acc);
+        // the next entry's slot is loaded (through L1) while this pair is summed
+        int slot = k < c ? __ldg(row + k) : 0;
+        for (; k < c; k += ns) {
+          const int nxt = k + ns < c ? __ldg(row + k + ns) : 0;
+          pass.pair(T_cur, Pass::template fetch<W>(rec, slot), g, acc);
+          slot = nxt;
+        }
       }
     }
     {
