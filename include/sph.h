@@ -157,6 +157,13 @@ typedef struct {
                                   the particles with du_a != 0; 0 turns it off
                                   [0].  Must be >= 0; not used by the ensemble
                                   (sph_ensemble_init rejects a nonzero value)   */
+  int angular_sums;            /* 1: sph_step also sums the angular momentum
+                                  of the new state (sph_last_diagnostics
+                                  out[5..7]); 0: out[5..7] are NaN and the
+                                  update saves 12 FP64 operations per particle
+                                  (section 4.2 makes the conservation reduction
+                                  optional; momentum and energy are always
+                                  summed) [0].  Must be 0 or 1                   */
 } sph_params;
 
 /* Fills *p with the defaults above and a periodic unit box. */
@@ -244,7 +251,8 @@ SPH_API int sph_step_host(sph_ctx* ctx, sph_state* host_state, double* dt_inout,
 SPH_API int sph_diagnostics(sph_ctx* ctx, const sph_state* state, double* out, sph_stream_t stream);
 
 /* Conservation sums accumulated by the last sph_step (of its new state) and
- * its dt, without a separate pass: out[0..7] as sph_diagnostics, out[8] = dt,
+ * its dt, without a separate pass: out[0..7] as sph_diagnostics (out[5..7]
+ * NaN unless params.angular_sums = 1), out[8] = dt,
  * out[9] = min nn, out[10] = max nn, out[11] = sum nn.  HOST array of 12;
  * synchronises the stream. */
 SPH_API int sph_last_diagnostics(sph_ctx* ctx, double* out, sph_stream_t stream);

@@ -66,6 +66,7 @@ class SphParams(C.Structure):
         ("dt_growth", C.c_double), ("ng_target", C.c_int), ("max_nb", C.c_int),
         ("sinc_n", C.c_double), ("precision", C.c_int), ("kernel_mode", C.c_int),
         ("gradh", C.c_int), ("pair_mode", C.c_int), ("energy_dt", C.c_double),
+        ("angular_sums", C.c_int),
     ]
 
 

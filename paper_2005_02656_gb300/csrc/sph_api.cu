@@ -85,6 +85,8 @@ int check_params(sph_ctx* ctx, const sph_params* p) {
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "unknown pair_mode %d", p->pair_mode);
   if (!(p->energy_dt >= 0.0) || !isfinite(p->energy_dt))
     return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "energy_dt must be finite and >= 0");
+  if (p->angular_sums != 0 && p->angular_sums != 1)
+    return sph::set_error(ctx, SPH_ERR_INVALID_ARG, "angular_sums must be 0 or 1");
   return SPH_OK;
 }
 
@@ -203,7 +205,8 @@ int dalloc(sph_ctx* ctx, T** p, size_t count, size_t* total) {
 }
 
 void free_all(sph_ctx* ctx) {
-  void* ptrs[] = {ctx->grid, ctx->err, ctx->dt_dev, ctx->diag, ctx->hfac, ctx->ktab64,
+  void* ptrs[] = {ctx->grid, ctx->err, ctx->dt_dev, ctx->diag, ctx->hfac, ctx->cell_org,
+                  ctx->ktab64,
                   ctx->ktab32, ctx->code, ctx->slot,
                   ctx->perm_tmp, ctx->perm, ctx->tbl_count, ctx->tbl_start, ctx->occ,
                   ctx->scan_part, ctx->cell_of, ctx->s.x, ctx->s_id_buf, ctx->pos32,
@@ -308,6 +311,7 @@ void sph_default_params(sph_params* p) {
   p->gradh = 0;
   p->pair_mode = SPH_PAIRS_STAGED;
   p->energy_dt = 0.0;
+  p->angular_sums = 0;
 }
 
 int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {
@@ -343,6 +347,7 @@ int sph_init(const sph_params* params, int64_t n_max, sph_ctx** out) {
   ALLOC(ctx->dt_dev, 1);
   ALLOC(ctx->diag, 32);
   ALLOC(ctx->hfac, sph::kHTab);
+  ALLOC(ctx->cell_org, 3 << sph::kMaxCellBits);
   ALLOC(ctx->code, n);
   ALLOC(ctx->slot, n);
   ALLOC(ctx->perm_tmp, n);

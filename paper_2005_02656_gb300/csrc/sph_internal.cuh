@@ -99,6 +99,7 @@ struct sph_ctx {
   int64_t* s_id_buf;
 
   // per-particle FP32 cell-relative data (sorted order)
+  double* cell_org;     // cell origins lo + i cs per axis (3 x 2^kMaxCellBits)
   float4* pos32;        // offset from the cell origin (x, y, z) and h
   int32_t* cell3;       // packed cell coordinates (10 bits per axis)
 

@@ -4,8 +4,9 @@
 // Morton code and particles within a cell keep their previous relative order).
 //
 // Pipeline (all on the device, no host synchronisation):
-//   k_grid_reduce  block min/max of x, y, z and max h; the last block derives
-//                  the grid (Grid) and validates the periodic box
+//   k_grid_reduce  block min/max of x, y, z (open axes) and max h, on ordered
+//                  integer keys; the last block derives the grid (Grid) and
+//                  validates the periodic box
 //   k_zero_table   clear the per-code particle counts
 //   k_cell_count   Morton code per particle, arrival slot by atomicAdd
 //   k_scan_*       exclusive scan of counts over codes -> cell start, and the
@@ -27,41 +28,53 @@ namespace {
 
 constexpr int kRedThreads = 256;
 
-__global__ void k_grid_reduce(StateView in, int64_t n, sph_params prm, Grid* g, double* part,
+// The extent and h_max reductions run on ordered integer keys (okey) in
+// integer arithmetic: FP64 runs at 1/64 of the FP32 rate on this part.
+__device__ __forceinline__ long long warp_min_ll(long long v) {
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ long long warp_max_ll(long long v) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Keys k[0..2] (minima of x, y, z), k[3..5] (maxima) and k[6] (max h, whose
+// negative values are ignored as fmax from 0 would) of one block, reduced on
+// the open axes only (periodic axes take the box and keep the neutral keys).
+__global__ void k_grid_reduce(StateView in, int64_t n, sph_params prm, Grid* g, long long* part,
                               unsigned int* counter, uint32_t* err) {
-  __shared__ double sh[kRedThreads / 32][7];
+  __shared__ long long sh[kRedThreads / 32][7];
   __shared__ bool last;
-  double v[7] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0};
+  const bool open[3] = {!prm.periodic[0], !prm.periodic[1], !prm.periodic[2]};
+  long long v[7] = {kKeyInf, kKeyInf, kKeyInf, -kKeyInf, -kKeyInf, -kKeyInf, 0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    // the extent is needed on open axes only (periodic axes take the box)
-    if (!prm.periodic[0]) {
-      const double x = in.x[i];
-      v[0] = fmin(v[0], x);
-      v[3] = fmax(v[3], x);
+    const double* xyz[3] = {in.x, in.y, in.z};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      if (!open[ax]) continue;
+      const double q = xyz[ax][i];
+      v[ax] = min(v[ax], okey(q, kKeyInf));
+      v[3 + ax] = max(v[3 + ax], okey(q, -kKeyInf));
     }
-    if (!prm.periodic[1]) {
-      const double y = in.y[i];
-      v[1] = fmin(v[1], y);
-      v[4] = fmax(v[4], y);
-    }
-    if (!prm.periodic[2]) {
-      const double z = in.z[i];
-      v[2] = fmin(v[2], z);
-      v[5] = fmax(v[5], z);
-    }
-    v[6] = fmax(v[6], in.h[i]);
+    v[6] = max(v[6], okey(in.h[i], 0));
   }
-  for (int k = 0; k < 3; ++k) v[k] = warp_min(v[k]);
-  for (int k = 3; k < 7; ++k) v[k] = warp_max(v[k]);
-  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    if (!open[ax]) continue;
+    v[ax] = warp_min_ll(v[ax]);
+    v[3 + ax] = warp_max_ll(v[3 + ax]);
+  }
+  v[6] = warp_max_ll(v[6]);
   if (l == 0)
     for (int k = 0; k < 7; ++k) sh[w][k] = v[k];
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) {
-      for (int k = 0; k < 3; ++k) v[k] = fmin(v[k], sh[ww][k]);
-      for (int k = 3; k < 7; ++k) v[k] = fmax(v[k], sh[ww][k]);
+      for (int k = 0; k < 3; ++k) v[k] = min(v[k], sh[ww][k]);
+      for (int k = 3; k < 7; ++k) v[k] = max(v[k], sh[ww][k]);
     }
     for (int k = 0; k < 7; ++k) part[blockIdx.x * 8 + k] = v[k];
     __threadfence();
@@ -73,25 +86,27 @@ __global__ void k_grid_reduce(StateView in, int64_t n, sph_params prm, Grid* g, 
   // last block: every thread folds a strided subset of the block partials
   // (read from L2), then warp and block trees (min/max: order-free)
   __threadfence();
-  double r[7] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0};
+  long long r[7] = {kKeyInf, kKeyInf, kKeyInf, -kKeyInf, -kKeyInf, -kKeyInf, 0};
   for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
-    const double* pb = part + b * 8;
-    for (int k = 0; k < 3; ++k) r[k] = fmin(r[k], __ldcg(pb + k));
-    for (int k = 3; k < 7; ++k) r[k] = fmax(r[k], __ldcg(pb + k));
+    const long long* pb = part + b * 8;
+    for (int k = 0; k < 3; ++k) r[k] = min(r[k], __ldcg(pb + k));
+    for (int k = 3; k < 7; ++k) r[k] = max(r[k], __ldcg(pb + k));
   }
-  for (int k = 0; k < 3; ++k) r[k] = warp_min(r[k]);
-  for (int k = 3; k < 7; ++k) r[k] = warp_max(r[k]);
+  for (int k = 0; k < 3; ++k) r[k] = warp_min_ll(r[k]);
+  for (int k = 3; k < 7; ++k) r[k] = warp_max_ll(r[k]);
   if (l == 0)
     for (int k = 0; k < 7; ++k) sh[w][k] = r[k];
   __syncthreads();
   if (threadIdx.x != 0) return;
   for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) {
-    for (int k = 0; k < 3; ++k) r[k] = fmin(r[k], sh[ww][k]);
-    for (int k = 3; k < 7; ++k) r[k] = fmax(r[k], sh[ww][k]);
+    for (int k = 0; k < 3; ++k) r[k] = min(r[k], sh[ww][k]);
+    for (int k = 3; k < 7; ++k) r[k] = max(r[k], sh[ww][k]);
   }
+  double rd[7];
+  for (int k = 0; k < 7; ++k) rd[k] = from_okey(r[k]);
   *counter = 0;
   Grid G;
-  double hmax = r[6];
+  double hmax = rd[6];
   G.hmax = hmax;
   int maxnc = 1;
   for (int ax = 0; ax < 3; ++ax) {
@@ -102,8 +117,8 @@ __global__ void k_grid_reduce(StateView in, int64_t n, sph_params prm, Grid* g, 
       L = prm.box_hi[ax] - prm.box_lo[ax];
       if (!(2.0 * hmax < 0.5 * L)) raise_flag(err, SPH_FLAG_BAD_BOX);
     } else {
-      lo = n > 0 ? r[ax] : 0.0;
-      L = n > 0 ? r[3 + ax] - r[ax] : 0.0;
+      lo = n > 0 ? rd[ax] : 0.0;
+      L = n > 0 ? rd[3 + ax] - rd[ax] : 0.0;
     }
     int nc = 1;
     if (hmax > 0.0 && L > 0.0) {
@@ -135,10 +150,32 @@ __global__ void k_grid_reduce(StateView in, int64_t n, sph_params prm, Grid* g, 
   *g = G;
 }
 
-__global__ void k_zero_table(const Grid* g, uint32_t* count) {
+__global__ void k_zero_table(const Grid* g, uint32_t* count, double* org) {
   uint32_t size = g->tbl_size;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < size; i += gridDim.x * blockDim.x)
     count[i] = 0u;
+  // cell origins lo + i cs, one table per axis (read by k_gather_a)
+  constexpr int kRow = 1 << kMaxCellBits;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 3 * kRow) {
+    const int ax = i / kRow, c = i % kRow;
+    if (c < g->nc[ax]) org[i] = g->lo[ax] + c * g->cs[ax];
+  }
+}
+
+// Double to float rounded to nearest even, by integer arithmetic when the
+// result is a normal float (FP64 conversions run on the FP64 pipe, at 1/64 of
+// the FP32 rate on this part); zero, float-subnormal, overflowing and NaN
+// inputs take the FP64 conversion.  Equal to (float)d for every d.
+__device__ __forceinline__ float f32_rn(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e - 897u >= 254u) return (float)d;  // float exponent field outside [1, 254]
+  unsigned f = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1fffffffu;  // the 29 bits dropped
+  f += (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u))) ? 1u : 0u;  // carries into
+  return __int_as_float(f | (hi & 0x80000000u));                             // the exponent
 }
 
 __device__ __forceinline__ void cell_coords(const Grid& g, double x, double y, double z, int& ix,
@@ -147,9 +184,10 @@ __device__ __forceinline__ void cell_coords(const Grid& g, double x, double y, d
   int c[3];
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
-    double q = floor((p[ax] - g.lo[ax]) * g.inv_cs[ax]);
-    int v = q < 0.0 ? 0 : (q >= (double)g.nc[ax] ? g.nc[ax] - 1 : (int)q);
-    c[ax] = v;
+    // floor((p - lo) / cs) clamped to [0, nc - 1]: the round-down conversion
+    // saturates (NaN gives 0), so the clamp runs on integers
+    const int v = __double2int_rd((p[ax] - g.lo[ax]) * g.inv_cs[ax]);
+    c[ax] = v < 0 ? 0 : (v >= g.nc[ax] ? g.nc[ax] - 1 : v);
   }
   ix = c[0];
   iy = c[1];
@@ -353,10 +391,10 @@ __device__ __forceinline__ uint32_t compact3(uint32_t v) {
 
 // Gather, first part: what the search, density and IAD read (positions, h,
 // m, u, id and the FP32 cell-relative positions).
-__global__ void k_gather_a(StateView in, StateView out, int64_t n, const Grid* gp,
+__global__ void k_gather_a(StateView in, StateView out, int64_t n, const double* org,
                            const int32_t* perm, const uint32_t* code, float4* pos32,
                            int32_t* cell3, float4* rec_d) {
-  const Grid g = *gp;
+  constexpr int kRow = 1 << kMaxCellBits;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     int64_t s = perm[p];
@@ -371,12 +409,12 @@ __global__ void k_gather_a(StateView in, StateView out, int64_t n, const Grid* g
     out.id[p] = in.id[s];
     uint32_t c = code[s];
     int ix = compact3(c), iy = compact3(c >> 1), iz = compact3(c >> 2);
-    float ox = (float)(x - (g.lo[0] + ix * g.cs[0]));
-    float oy = (float)(y - (g.lo[1] + iy * g.cs[1]));
-    float oz = (float)(z - (g.lo[2] + iz * g.cs[2]));
-    pos32[p] = make_float4(ox, oy, oz, (float)h);
+    const float ox = f32_rn(x - __ldg(org + ix));
+    const float oy = f32_rn(y - __ldg(org + kRow + iy));
+    const float oz = f32_rn(z - __ldg(org + 2 * kRow + iz));
+    pos32[p] = make_float4(ox, oy, oz, f32_rn(h));
     cell3[p] = pack_cell(ix, iy, iz);
-    rec_d[p] = make_float4(ox, oy, oz, (float)m);
+    rec_d[p] = make_float4(ox, oy, oz, f32_rn(m));
   }
 }
 
@@ -396,7 +434,7 @@ __global__ void k_gather_b(StateView in, StateView out, int64_t n, const int32_t
     out.vyh[p] = in.vyh[s];
     out.vzh[p] = in.vzh[s];
     out.du_prev[p] = in.du_prev[s];
-    const float4 vm = make_float4((float)vx, (float)vy, (float)vz, (float)out.m[p]);
+    const float4 vm = make_float4(f32_rn(vx), f32_rn(vy), f32_rn(vz), f32_rn(out.m[p]));
     if (recV)
       recV[p] = vm;  // the staged pair passes' velocity plane
     else
@@ -417,9 +455,10 @@ inline int grid_for(int64_t n, int threads, int sm) {
 void launch_grid(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st) {
   int blocks = grid_for(n, kRedThreads, ctx->sm_count);
   if (blocks > kReduceBlocks) blocks = kReduceBlocks;
-  k_grid_reduce<<<blocks, kRedThreads, 0, st>>>(in, n, ctx->prm, ctx->grid, ctx->red.part,
+  k_grid_reduce<<<blocks, kRedThreads, 0, st>>>(in, n, ctx->prm, ctx->grid,
+                                                reinterpret_cast<long long*>(ctx->red.part),
                                                 ctx->red.counter + 0, ctx->err);
-  k_zero_table<<<ctx->sm_count * 8, 256, 0, st>>>(ctx->grid, ctx->tbl_count);
+  k_zero_table<<<ctx->sm_count * 8, 256, 0, st>>>(ctx->grid, ctx->tbl_count, ctx->cell_org);
   ctx->launches += 2;
 }
 
@@ -437,7 +476,7 @@ void launch_sort(sph_ctx* ctx, const StateView& in, int64_t n, cudaStream_t st,
                                                   ctx->tbl_count, ctx->perm_tmp, ctx->perm,
                                                   ctx->cell_of);
   if (wait_gather) cudaStreamWaitEvent(st, wait_gather, 0);
-  k_gather_a<<<pb, 256, 0, st>>>(in, ctx->s, n, ctx->grid, ctx->perm, ctx->code, ctx->pos32,
+  k_gather_a<<<pb, 256, 0, st>>>(in, ctx->s, n, ctx->cell_org, ctx->perm, ctx->code, ctx->pos32,
                                  ctx->cell3, ctx->rec_d);
   ctx->launches += 7;
 }

@@ -9,9 +9,9 @@
 // k_update    section 4.1's second-order integrators, read as a variable-step
 //             leapfrog for x and v and Adams-Bashforth for u; smoothing length
 //             adapted toward the target neighbour count; periodic wrap; block
-//             partial sums of momentum, energies, angular momentum and
-//             neighbour-count statistics of the new state (section 4.2: the
-//             optional conservation reduction)
+//             partial sums of momentum, energies, neighbour-count statistics
+//             and (when angular_sums is set) angular momentum of the new state
+//             (section 4.2: the optional conservation reduction)
 // k_diag      the same sums for any state
 // Cross-block totals are combined by the last block in a fixed-shape tree, so
 // every reduction here is deterministic.
@@ -97,6 +97,23 @@ __device__ void finalize_block(const double* part, int nblocks, const Op (&op)[N
   __syncthreads();
 }
 
+// FP32 value of a positive double whose exponent lies in [-60, 60], taken from
+// its high word by integer arithmetic (no FP64 instruction: FP64 runs at 1/64
+// of the FP32 rate on this part).  The 20 mantissa bits of the high word are
+// kept and the rest truncated, so the result is in [v (1 - 2^-20), v].  NaN
+// for any other input (zero, negative, subnormal, outside the range, NaN).
+__device__ __forceinline__ float f32_of_hi(double v) {
+  const int hi = __double2hiint(v);
+  const unsigned e = ((unsigned)hi >> 20) - (1023u - 60u);  // sign bit set: huge
+  return e <= 120u ? __int_as_float((hi - ((1023 - 127) << 20)) << 3) : __int_as_float(0x7fc00000);
+}
+
+// Screen of the exact minimum of h/c: q32 approximates the quotient within
+// 2^-18 relative (the two truncations above and __fdividef's 2 ulp), so a
+// quotient whose q32 exceeds the running minimum's FP32 value by the factor
+// 1 + 2^-16 is larger than that minimum and needs no FP64 division.
+constexpr float kScreen = 1.0f + 0x1p-16f;
+
 __global__ void __launch_bounds__(kThreads) k_timestep(const double* h, const double* c,
                                                        const double* u, const double* du,
                                                        int64_t n, double courant, double growth,
@@ -104,10 +121,32 @@ __global__ void __launch_bounds__(kThreads) k_timestep(const double* h, const do
                                                        double* diag, double* part,
                                                        unsigned int* counter, uint32_t* err) {
   double mn = INFINITY, mu = INFINITY;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    mn = fmin(mn, h[i] / c[i]);
-    if (energy_dt > 0.0 && du[i] != 0.0) mu = fmin(mu, u[i] / fabs(du[i]));
+  float lim = INFINITY;  // FP32 screen value of mn
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int kU = 4;  // particles per thread and pass: their loads overlap
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += kU * stride) {
+    double hv[kU], cv[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+      const int64_t i = i0 + k * stride;
+      hv[k] = i < n ? h[i] : 0.0;
+      cv[k] = i < n ? c[i] : 1.0;
+    }
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+      // exact division only where the screen cannot rule the quotient out
+      // (NaN screen values: inputs outside the range of f32_of_hi)
+      if (i0 + k * stride < n && !(__fdividef(f32_of_hi(hv[k]), f32_of_hi(cv[k])) > lim)) {
+        mn = fmin(mn, hv[k] / cv[k]);
+        lim = (float)mn * kScreen;
+      }
+    }
+    if (energy_dt > 0.0) {
+      for (int k = 0; k < kU; ++k) {
+        const int64_t i = i0 + k * stride;
+        if (i < n && du[i] != 0.0) mu = fmin(mu, u[i] / fabs(du[i]));
+      }
+    }
   }
   mn = warp_min(mn);
   mu = warp_min(mu);
@@ -157,6 +196,9 @@ __global__ void k_hfac_table(double* tab, int ng) {
     tab[k] = hfac_of(ng, k);
 }
 
+// kAngular: also sum the angular momentum m (x x v) of the new state (12 more
+// FP64 operations per particle; momentum and energy are always summed)
+template <bool kAngular>
 __global__ void __launch_bounds__(kThreads) k_update(StateView s, OutView o, StateView d,
                                                      const int32_t* nn, int64_t n,
                                                      sph_params prm, const double* hfac,
@@ -167,6 +209,14 @@ __global__ void __launch_bounds__(kThreads) k_update(StateView s, OutView o, Sta
   const double delta = 0.5 * (dt + dt_prev);
   const double q = dt_prev > 0.0 ? dt / (2.0 * dt_prev) : 0.0;
   double acc[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  // periodic wrap tests on ordered integer keys of the box corners (a NaN
+  // position takes the key of box_lo: no wrap, as in the FP comparison)
+  long long klo[3], khi[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    klo[k] = okey(prm.box_lo[k], 0);
+    khi[k] = okey(prm.box_hi[k], 0);
+  }
   // neighbour-count statistics in integer arithmetic (FP64 runs at 1/64 of the
   // FP32 rate on this part); converted once per thread below
   long long csum = 0;
@@ -183,9 +233,10 @@ __global__ void __launch_bounds__(kThreads) k_update(StateView s, OutView o, Sta
       double xk = x3[k] + dt * vhn[k];
       if (prm.periodic[k]) {
         const double L = prm.box_hi[k] - prm.box_lo[k];
-        if (xk >= prm.box_hi[k])
+        const long long kx = okey(xk, klo[k]);
+        if (kx >= khi[k])
           xk -= L;
-        else if (xk < prm.box_lo[k])
+        else if (kx < klo[k])
           xk += L;
       }
       xn[k] = xk;
@@ -216,11 +267,15 @@ __global__ void __launch_bounds__(kThreads) k_update(StateView s, OutView o, Sta
     acc[0] += m * vn[0];
     acc[1] += m * vn[1];
     acc[2] += m * vn[2];
-    acc[3] += 0.5 * m * (vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
+    // m |v|^2, halved once at the end: scaling by 0.5 is exact, so the sum
+    // equals that of 0.5 m |v|^2 bit for bit
+    acc[3] += m * (vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
     acc[4] += m * un;
-    acc[5] += m * (xn[1] * vn[2] - xn[2] * vn[1]);
-    acc[6] += m * (xn[2] * vn[0] - xn[0] * vn[2]);
-    acc[7] += m * (xn[0] * vn[1] - xn[1] * vn[0]);
+    if (kAngular) {
+      acc[5] += m * (xn[1] * vn[2] - xn[2] * vn[1]);
+      acc[6] += m * (xn[2] * vn[0] - xn[0] * vn[2]);
+      acc[7] += m * (xn[0] * vn[1] - xn[1] * vn[0]);
+    }
     csum += cnt;
     cmin = min(cmin, cnt);
     cmax = max(cmax, cnt);
@@ -255,6 +310,8 @@ __global__ void __launch_bounds__(kThreads) k_update(StateView s, OutView o, Sta
   finalize_block<11>(part, gridDim.x, ops, res);
   if (threadIdx.x == 0) {
     for (int k = 0; k < 8; ++k) diag[k] = res[k];
+    diag[3] = 0.5 * res[3];
+    if (!kAngular) diag[5] = diag[6] = diag[7] = NAN;
     diag[9] = res[8];
     diag[10] = res[9];
     diag[11] = res[10];
@@ -320,7 +377,8 @@ void launch_update(sph_ctx* ctx, const StateView& s, const OutView& o, const Sta
                    int64_t n, const double* dt_io, cudaStream_t st) {
   (void)dt_io;
   if (ctx->hfac_ng != ctx->prm.ng_target) launch_hfac_table(ctx, st);
-  k_update<<<red_blocks(n, ctx->sm_count), kThreads, 0, st>>>(
+  auto kern = ctx->prm.angular_sums ? k_update<true> : k_update<false>;
+  kern<<<red_blocks(n, ctx->sm_count), kThreads, 0, st>>>(
       s, o, dst, ctx->nn, n, ctx->prm, ctx->hfac, ctx->diag, ctx->red.part,
       ctx->red.counter + 2, ctx->stats);
   ctx->launches += 1;

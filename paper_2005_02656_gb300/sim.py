@@ -35,6 +35,7 @@ class Params:
     pair_mode: str = "staged"   # FP32-mixed pair sums: "staged" (cell-staged candidates
                                 # and hit masks) | "lists" (int32 neighbour lists)
     energy_dt: float = 0.0      # > 0: dt <= energy_dt * min u / |du| (opt-in energy-rate limit)
+    angular_sums: int = 0       # 1: each step also sums the angular momentum (last_diagnostics()[5:8])
 
     def c(self) -> SphParams:
         p = SphParams()
@@ -49,6 +50,7 @@ class Params:
         p.gradh = int(self.gradh)
         p.pair_mode = {"staged": _lib.SPH_PAIRS_STAGED, "lists": _lib.SPH_PAIRS_LISTS}[self.pair_mode]
         p.energy_dt = float(self.energy_dt)
+        p.angular_sums = int(self.angular_sums)
         return p
 
 

@@ -32,7 +32,8 @@ def run(side: int = 100, t_end: float = 0.5, precision: str = "fp64", max_steps:
     import sph_inputs
     from .sim import Params, SphSim
     s = sph_inputs.square_patch(side)
-    prm = Params(box_lo=s["lo"], box_hi=s["hi"], periodic=s["periodic"], precision=precision)
+    prm = Params(box_lo=s["lo"], box_hi=s["hi"], periodic=s["periodic"], precision=precision,
+                 angular_sums=1)
     for k, v in params.items():
         setattr(prm, k, v)
     sim = SphSim(s, prm, device=device)

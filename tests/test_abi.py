@@ -39,13 +39,14 @@ def test_default_params_and_layout(lib, tmp_path):
     lib.sph_default_params(C.byref(p))
     assert p.max_nb == 160 and p.ng_target == 100 and p.sinc_n == 6.0
     assert p.pair_mode == 0      # SPH_PAIRS_STAGED
+    assert p.energy_dt == 0.0 and p.angular_sums == 0
     assert abs(p.gamma - 5.0 / 3.0) < 1e-15 and p.alpha == 1.0 and p.courant == 0.2
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "sph.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(sph_state), sizeof(sph_params),'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sph_state), sizeof(sph_params),'
         ' offsetof(sph_state, n), offsetof(sph_params, sinc_n), offsetof(sph_params, gradh),'
-        ' offsetof(sph_params, pair_mode));'
+        ' offsetof(sph_params, pair_mode), offsetof(sph_params, angular_sums));'
         'return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
@@ -53,7 +54,8 @@ def test_default_params_and_layout(lib, tmp_path):
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
                                            check=True).stdout.split()]
     assert vals == [C.sizeof(SphState), C.sizeof(SphParams), SphState.n.offset,
-                    SphParams.sinc_n.offset, SphParams.gradh.offset, SphParams.pair_mode.offset]
+                    SphParams.sinc_n.offset, SphParams.gradh.offset, SphParams.pair_mode.offset,
+                    SphParams.angular_sums.offset]
 
 
 def test_null_arguments_are_rejected(lib):
@@ -76,7 +78,8 @@ def _params(lib, **kw):
 @pytest.mark.parametrize("field,value", [
     ("gamma", 1.0), ("alpha", -0.1), ("courant", 0.0), ("dt_growth", 0.9), ("ng_target", -1),
     ("max_nb", 0), ("max_nb", 162), ("max_nb", 4100), ("sinc_n", 0.5), ("sinc_n", 6.5),
-    ("sinc_n", 13.0), ("precision", 7), ("kernel_mode", 3), ("gradh", 2), ("pair_mode", 2)])
+    ("sinc_n", 13.0), ("precision", 7), ("kernel_mode", 3), ("gradh", 2), ("pair_mode", 2),
+    ("energy_dt", -1.0), ("angular_sums", 2)])
 def test_invalid_params_are_rejected_before_any_device_work(lib, field, value):
     # sph_init validates its parameters on the host and returns before any
     # CUDA call, so this runs without a GPU

@@ -273,6 +273,27 @@ def test_energy_rate_limited_time_step(precision, cu):
         assert abs(dt_gpu - dt) <= 1e-2 * dt     # du in FP32: the limiting ratio u/|du|
 
 
+@pytest.mark.parametrize("precision,span", [("fp64", 240.0), ("fp64", 0.5), ("fp32_mixed", 8.0)])
+def test_time_step_is_the_exact_minimum(precision, span):
+    """dt = courant * min_a h_a / c_a bit for bit, with c from the step's own
+    EOS and h of the state before the update.  u is spread log-uniformly over
+    10^(+-span) (c ~ sqrt(u)), so some quotients fall outside the range of the
+    kernel's FP32 screen and must take the exact FP64 path, and (span 0.5)
+    many lie within the screen's margin of one another."""
+    from paper_2005_02656_gb300 import SphSim
+    s = sph_inputs.jittered_box(12, seed_index=51)
+    rng = np.random.default_rng(51)
+    s["u"] = 10.0 ** rng.uniform(-span, span, s["u"].shape[0])
+    sim = SphSim(s, precision=precision, ng_target=0)
+    sim.step()
+    sim.error_word()                     # extreme u may raise flags; dt is still written
+    dt_gpu = float(sim.dt.cpu()[0])
+    got = sim.to_numpy()
+    sim.close()
+    h0 = by_id(s)["h"]
+    assert dt_gpu == 0.2 * np.min(h0 / got["c"])
+
+
 def test_empty_and_single_particle():
     from paper_2005_02656_gb300 import SphSim
     s = sph_inputs.jittered_box(10)
