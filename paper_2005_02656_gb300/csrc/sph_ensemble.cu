@@ -198,24 +198,31 @@ __device__ void ph_extent(const Args& A) {
     const int b0 = __shfl_sync(0xffffffffu, b, 0);
     if (__all_sync(0xffffffffu, b == b0 || b < 0) && b0 >= 0) {
       // one box for the whole warp: reduce only the open axes' extents (the
-      // box decides, so the branches are uniform; FP64 min/max run at 1/64 of
-      // the FP32 rate on this part)
+      // box decides, so the branches are uniform), on ordered integer keys
+      // (FP64 min/max run at 1/64 of the FP32 rate on this part); NaN takes
+      // the neutral key, as fmin/fmax would ignore it
       const Box& Bw = A.boxes[b0];
+      long long kh = okey(h, 0);
+      long long kv[6];
+      for (int k = 0; k < 3; ++k) {
+        kv[k] = okey(v[k], kKeyInf);
+        kv[3 + k] = okey(v[3 + k], -kKeyInf);
+      }
       for (int o = 16; o > 0; o >>= 1) {
-        h = fmax(h, __shfl_xor_sync(0xffffffffu, h, o));
+        kh = max(kh, __shfl_xor_sync(0xffffffffu, kh, o));
         for (int k = 0; k < 3; ++k) {
           if (Bw.periodic[k]) continue;
-          v[k] = fmin(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
-          v[3 + k] = fmax(v[3 + k], __shfl_xor_sync(0xffffffffu, v[3 + k], o));
+          kv[k] = min(kv[k], __shfl_xor_sync(0xffffffffu, kv[k], o));
+          kv[3 + k] = max(kv[3 + k], __shfl_xor_sync(0xffffffffu, kv[3 + k], o));
         }
       }
       if (lane == 0) {
         Box& B = A.boxes[b0];
-        atomicMax(&B.hmax_o, ord(h));
+        atomicMax(&B.hmax_o, ord(from_okey(kh)));
         for (int k = 0; k < 3; ++k) {  // the extent is needed on open axes only
           if (B.periodic[k]) continue;
-          atomicMin(&B.xmin_o[k], ord(v[k]));
-          atomicMax(&B.xmax_o[k], ord(v[3 + k]));
+          atomicMin(&B.xmin_o[k], ord(from_okey(kv[k])));
+          atomicMax(&B.xmax_o[k], ord(from_okey(kv[3 + k])));
         }
       }
     } else if (on) {
@@ -294,8 +301,10 @@ __device__ __forceinline__ void cell_of(const Grid& g, double x, double y, doubl
   int c[3];
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
-    const double q = floor((p[ax] - g.lo[ax]) * g.inv_cs[ax]);
-    c[ax] = q < 0.0 ? 0 : (q >= (double)g.nc[ax] ? g.nc[ax] - 1 : (int)q);
+    // floor((p - lo) / cs) clamped to [0, nc - 1]: the round-down conversion
+    // saturates (NaN gives 0), so the clamp runs on integers
+    const int v = __double2int_rd((p[ax] - g.lo[ax]) * g.inv_cs[ax]);
+    c[ax] = v < 0 ? 0 : (v >= g.nc[ax] ? g.nc[ax] - 1 : v);
   }
   ix = c[0];
   iy = c[1];
@@ -444,12 +453,14 @@ __device__ void ph_gather(const Args& A) {
     A.s.id[p] = A.in.id[s];
     const uint32_t c = A.code[s];
     const int ix = compact3_bits(c), iy = compact3_bits(c >> 1), iz = compact3_bits(c >> 2);
-    const float ox = (float)(x - (g.lo[0] + ix * g.cs[0]));
-    const float oy = (float)(y - (g.lo[1] + iy * g.cs[1]));
-    const float oz = (float)(z - (g.lo[2] + iz * g.cs[2]));
-    A.pos32[p] = make_float4(ox, oy, oz, (float)h);
-    A.rec_d[p] = make_float4(ox, oy, oz, (float)m);
-    A.rec_m[5 * p + 1] = make_float4((float)vx, (float)vy, (float)vz, (float)m);
+    // f32_rn equals the FP64 conversion bit for bit, on the integer pipes
+    const float ox = f32_rn(x - (g.lo[0] + ix * g.cs[0]));
+    const float oy = f32_rn(y - (g.lo[1] + iy * g.cs[1]));
+    const float oz = f32_rn(z - (g.lo[2] + iz * g.cs[2]));
+    const float m32 = f32_rn(m);
+    A.pos32[p] = make_float4(ox, oy, oz, f32_rn(h));
+    A.rec_d[p] = make_float4(ox, oy, oz, m32);
+    A.rec_m[5 * p + 1] = make_float4(f32_rn(vx), f32_rn(vy), f32_rn(vz), m32);
   }
 }
 
@@ -517,9 +528,10 @@ __device__ void ph_density_t(const Args& A) {
     const int bq = own ? b : -1;
     const int b0 = __shfl_sync(0xffffffffu, b, 0);
     if (__all_sync(0xffffffffu, b == b0 || b < 0) && b0 >= 0) {
-      double m = q;
-      for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (lane == 0) atomicMin(&A.boxes[b0].qmin_o, ord(m));
+      // the warp's minimum on ordered integer keys (NaN ignored, as by fmin)
+      long long km = okey(q, kKeyInf);
+      for (int o = 16; o > 0; o >>= 1) km = min(km, __shfl_xor_sync(0xffffffffu, km, o));
+      if (lane == 0) atomicMin(&A.boxes[b0].qmin_o, ord(from_okey(km)));
     } else if (bq >= 0) {
       atomicMin(&A.boxes[bq].qmin_o, ord(q));
     }
@@ -615,10 +627,13 @@ __device__ void ph_update(const Args& A) {
       vhn[k] = vh3[k] + a3[k] * delta;
       double xk = x3[k] + dt * vhn[k];
       if (B.periodic[k]) {
+        // the tests on ordered integer keys (a NaN position takes the key of
+        // lo: no wrap, as in the FP comparison)
         const double L = B.hi[k] - B.lo[k];
-        if (xk >= B.hi[k])
+        const long long klo = okey(B.lo[k], 0), kx = okey(xk, klo);
+        if (kx >= okey(B.hi[k], 0))
           xk -= L;
-        else if (xk < B.lo[k])
+        else if (kx < klo)
           xk += L;
       }
       xn[k] = xk;

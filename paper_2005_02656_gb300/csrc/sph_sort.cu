@@ -163,21 +163,6 @@ __global__ void k_zero_table(const Grid* g, uint32_t* count, double* org) {
   }
 }
 
-// Double to float rounded to nearest even, by integer arithmetic when the
-// result is a normal float (FP64 conversions run on the FP64 pipe, at 1/64 of
-// the FP32 rate on this part); zero, float-subnormal, overflowing and NaN
-// inputs take the FP64 conversion.  Equal to (float)d for every d.
-__device__ __forceinline__ float f32_rn(double d) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-  const unsigned e = (hi >> 20) & 0x7ffu;
-  if (e - 897u >= 254u) return (float)d;  // float exponent field outside [1, 254]
-  unsigned f = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-  const unsigned rest = lo & 0x1fffffffu;  // the 29 bits dropped
-  f += (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u))) ? 1u : 0u;  // carries into
-  return __int_as_float(f | (hi & 0x80000000u));                             // the exponent
-}
-
 __device__ __forceinline__ void cell_coords(const Grid& g, double x, double y, double z, int& ix,
                                             int& iy, int& iz) {
   double p[3] = {x, y, z};
