@@ -145,8 +145,9 @@ struct sph_ctx {
   float4* recC;
   float2* recC2;
   int find_mask_blocks;   // persistent CTAs of the mask-writing search
-  int pass_blocks[6];     // persistent CTAs of the density, IAD, momentum passes (general
-                          // kernels, then pipelined ones at +3)
+  int pass_blocks[12];    // persistent CTAs of the density, IAD, momentum passes (general
+                          // kernels, then pipelined ones at +3; the plain-configuration
+                          // kernels at +6)
 
   // reductions
   sph::Reduce red;

@@ -451,14 +451,26 @@ __device__ __forceinline__ float wrap32(float d, const Grid& g, int ax) {
   return d;
 }
 
+// Pair-pass configurations.  kCfgAny decides at run time (per pair) whether
+// separations take the FP32 minimum image, which kernel form is used and
+// whether the grad-h sum is formed; kCfgPlain fixes the default case at
+// compile time: no minimum image (every periodic axis has at least 3 cells),
+// the series kernel with n = 6 and no grad-h terms.  The two give the same
+// results bit for bit where both apply; a plain launch runs only when the
+// grid needs no minimum image (Grid::wrap32 = 0), so the launcher starts both
+// and each returns at once unless the grid is its case.
+constexpr int kCfgAny = 0;
+constexpr int kCfgPlain = 1;
+
 // Separation b - a of two positions relative to the target's cell; the FP32
 // minimum image is needed only on periodic axes with fewer than 3 cells.
+template <int CFG>
 __device__ __forceinline__ void sep(const Grid& g, float bx, float by, float bz, float ax_,
                                     float ay, float az, float& dx, float& dy, float& dz) {
   dx = bx - ax_;
   dy = by - ay;
   dz = bz - az;
-  if (g.wrap32) {
+  if (CFG == kCfgAny && g.wrap32) {
     if (g.periodic[0]) dx = wrap32(dx, g, 0);
     if (g.periodic[1]) dy = wrap32(dy, g, 1);
     if (g.periodic[2]) dz = wrap32(dz, g, 2);
@@ -467,7 +479,9 @@ __device__ __forceinline__ void sep(const Grid& g, float bx, float by, float bz,
 
 // S(t)^n (t = v^2; the exact kernel's polynomial, or the table), B_n / h^3
 // factored out of the sums.
+template <int CFG>
 __device__ __forceinline__ float s_pow(float t, int n, const float2* tab) {
+  if (CFG == kCfgPlain) return kernel_w32(t, 1.0f, 6);
   return tab ? kernel_w32_tab(t, 1.0f, tab) : kernel_w32(t, 1.0f, n);
 }
 
@@ -477,14 +491,16 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 // s_pow for two arguments: the polynomial and the powers in paired FP32.
+template <int CFG>
 __device__ __forceinline__ float2 s_pow2(float2 t, int n, const float2* tab) {
-  if (tab) return make_float2(kernel_w32_tab(t.x, 1.0f, tab), kernel_w32_tab(t.y, 1.0f, tab));
+  if (CFG == kCfgAny && tab)
+    return make_float2(kernel_w32_tab(t.x, 1.0f, tab), kernel_w32_tab(t.y, 1.0f, tab));
   t = make_float2(fminf(t.x, 4.0f), fminf(t.y, 4.0f));
   constexpr SincCoefs<kSincTerms32> C{};
   float2 s = f2((float)C.c[kSincTerms32 - 1]);
 #pragma unroll
   for (int k = kSincTerms32 - 2; k >= 0; --k) s = __ffma2_rn(s, t, f2((float)C.c[k]));
-  if (n == 6) {
+  if (CFG == kCfgPlain || n == 6) {
     const float2 s2 = __fmul2_rn(s, s);
     return __fmul2_rn(__fmul2_rn(s2, s2), s2);
   }
@@ -493,12 +509,13 @@ __device__ __forceinline__ float2 s_pow2(float2 t, int n, const float2* tab) {
 
 // Separations b - a of two neighbours (paired), with the FP32 minimum image
 // on periodic axes of fewer than 3 cells.
+template <int CFG>
 __device__ __forceinline__ void sep2(const Grid& g, float4 b0, float4 b1, float ax_, float ay,
                                      float az, float2& dx, float2& dy, float2& dz) {
   dx = __fadd2_rn(f2(b0.x, b1.x), f2(-ax_));
   dy = __fadd2_rn(f2(b0.y, b1.y), f2(-ay));
   dz = __fadd2_rn(f2(b0.z, b1.z), f2(-az));
-  if (g.wrap32) {
+  if (CFG == kCfgAny && g.wrap32) {
     if (g.periodic[0]) dx = make_float2(wrap32(dx.x, g, 0), wrap32(dx.y, g, 0));
     if (g.periodic[1]) dy = make_float2(wrap32(dy.x, g, 1), wrap32(dy.y, g, 1));
     if (g.periodic[2]) dz = make_float2(wrap32(dz.x, g, 2), wrap32(dz.y, g, 2));
@@ -539,7 +556,8 @@ __device__ __forceinline__ void add_shift(float4* rec, int j, uint32_t e, const 
 }
 
 // --- density + EOS (Eq. 1, self term included) ---
-struct DensityPass {
+template <int CFG>
+struct DensityPassT {
   static constexpr int kWin = 1024;   // staged slots held in shared memory
   static constexpr int kRecBytes = 16;
   static constexpr int kV = 2;        // reduced values: sum m S^n, grad-h sum
@@ -566,6 +584,13 @@ struct DensityPass {
   double gamma;
   int gradh;
   uint32_t* err;
+  __device__ bool has_gradh() const { return CFG == kCfgAny && gradh; }
+  // kCfgAny launched beside a kCfgPlain launch: runs only on grids that need
+  // the minimum image
+  int only_wrap;
+  __device__ bool runs(const Grid& g) const {
+    return CFG == kCfgPlain ? !g.wrap32 : (!only_wrap || g.wrap32);
+  }
 
   struct Target {
     float x, y, z, hinv2;
@@ -594,20 +619,20 @@ struct DensityPass {
   __device__ void pair(const Target& T, const Rec& R, const Grid& g, float* acc) const {
     const float4 r = R.r;
     float dx, dy, dz;
-    sep(g, r.x, r.y, r.z, T.x, T.y, T.z, dx, dy, dz);
+    sep<CFG>(g, r.x, r.y, r.z, T.x, T.y, T.z, dx, dy, dz);
     const float tt = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) * T.hinv2;
-    acc[0] = fmaf(r.w, s_pow(tt, sinc_n, ktab), acc[0]);
-    if (gradh) acc[1] = fmaf(r.w, kernel_tdw32(tt, 1.0f, sinc_n), acc[1]);
+    acc[0] = fmaf(r.w, s_pow<CFG>(tt, sinc_n, ktab), acc[0]);
+    if (has_gradh()) acc[1] = fmaf(r.w, kernel_tdw32(tt, 1.0f, sinc_n), acc[1]);
   }
   __device__ void pair2(const Target& T, const Rec& R0, const Rec& R1, const Grid& g,
                         float2* acc) const {
     float2 dx, dy, dz;
-    sep2(g, R0.r, R1.r, T.x, T.y, T.z, dx, dy, dz);
+    sep2<CFG>(g, R0.r, R1.r, T.x, T.y, T.z, dx, dy, dz);
     const float2 tt =
         __fmul2_rn(__ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx))), f2(T.hinv2));
     const float2 m = f2(R0.r.w, R1.r.w);
-    acc[0] = __ffma2_rn(m, s_pow2(tt, sinc_n, ktab), acc[0]);
-    if (gradh)
+    acc[0] = __ffma2_rn(m, s_pow2<CFG>(tt, sinc_n, ktab), acc[0]);
+    if (has_gradh())
       acc[1] = __ffma2_rn(m, make_float2(kernel_tdw32(tt.x, 1.0f, sinc_n),
                                          kernel_tdw32(tt.y, 1.0f, sinc_n)), acc[1]);
   }
@@ -640,7 +665,7 @@ struct DensityPass {
     o.c[a] = (double)c;
     rec_i[a] = make_float4(p.x, p.y, p.z, ma * inv_rho);
     recA[a] = make_float4(p.x, p.y, p.z, hinv2);
-    if (gradh) {
+    if (has_gradh()) {
       const float omega = -2.0f * norm * acc[1] * inv_rho * (1.0f / 3.0f);
       X /= omega;
       if (o.omega) o.omega[a] = (double)omega;
@@ -651,7 +676,8 @@ struct DensityPass {
 };
 
 // --- IAD: tau_a and C_a = tau_a^{-1} ---
-struct IadPass {
+template <int CFG>
+struct IadPassT {
   static constexpr int kWin = 1024;
   static constexpr int kRecBytes = 16;
   static constexpr int kV = 6;
@@ -674,6 +700,12 @@ struct IadPass {
   const float2* ktab;
   int sinc_n;
   uint32_t* err;
+  // kCfgAny launched beside a kCfgPlain launch: runs only on grids that need
+  // the minimum image
+  int only_wrap;
+  __device__ bool runs(const Grid& g) const {
+    return CFG == kCfgPlain ? !g.wrap32 : (!only_wrap || g.wrap32);
+  }
 
   struct Target {
     float x, y, z, hinv2, inv_h;
@@ -703,13 +735,13 @@ struct IadPass {
   __device__ void pair(const Target& T, const Rec& R, const Grid& g, float* acc) const {
     const float4 r = R.r;
     float dx, dy, dz;
-    sep(g, r.x, r.y, r.z, T.x, T.y, T.z, dx, dy, dz);
+    sep<CFG>(g, r.x, r.y, r.z, T.x, T.y, T.z, dx, dy, dz);
     const float tt = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) * T.hinv2;
     // separation scaled by 1/h_a keeps tau of order one in FP32
     dx *= T.inv_h;
     dy *= T.inv_h;
     dz *= T.inv_h;
-    const float w = r.w * s_pow(tt, sinc_n, ktab);
+    const float w = r.w * s_pow<CFG>(tt, sinc_n, ktab);
     const float wx = w * dx, wy = w * dy, wz = w * dz;
     acc[0] = fmaf(wx, dx, acc[0]);
     acc[1] = fmaf(wx, dy, acc[1]);
@@ -721,14 +753,14 @@ struct IadPass {
   __device__ void pair2(const Target& T, const Rec& R0, const Rec& R1, const Grid& g,
                         float2* acc) const {
     float2 dx, dy, dz;
-    sep2(g, R0.r, R1.r, T.x, T.y, T.z, dx, dy, dz);
+    sep2<CFG>(g, R0.r, R1.r, T.x, T.y, T.z, dx, dy, dz);
     const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
     const float2 tt = __fmul2_rn(r2, f2(T.hinv2));
     const float2 ih = f2(T.inv_h);
     dx = __fmul2_rn(dx, ih);
     dy = __fmul2_rn(dy, ih);
     dz = __fmul2_rn(dz, ih);
-    const float2 w = __fmul2_rn(f2(R0.r.w, R1.r.w), s_pow2(tt, sinc_n, ktab));
+    const float2 w = __fmul2_rn(f2(R0.r.w, R1.r.w), s_pow2<CFG>(tt, sinc_n, ktab));
     const float2 wx = __fmul2_rn(w, dx), wy = __fmul2_rn(w, dy), wz = __fmul2_rn(w, dz);
     acc[0] = __ffma2_rn(wx, dx, acc[0]);
     acc[1] = __ffma2_rn(wx, dy, acc[1]);
@@ -779,7 +811,8 @@ struct IadPass {
 };
 
 // --- momentum and energy with artificial viscosity (Eqs. 2-5) ---
-struct MomentumPass {
+template <int CFG>
+struct MomentumPassT {
   static constexpr int kWin = 768;  // staged slots (plane stride): three CTAs of 73 KB per SM
   static constexpr int kRecBytes = 72;  // four float4 planes and one float2 plane
   static constexpr int kV = 4;
@@ -806,6 +839,12 @@ struct MomentumPass {
   int sinc_n;
   float alpha;
   uint32_t* err;
+  // kCfgAny launched beside a kCfgPlain launch: runs only on grids that need
+  // the minimum image
+  int only_wrap;
+  __device__ bool runs(const Grid& g) const {
+    return CFG == kCfgPlain ? !g.wrap32 : (!only_wrap || g.wrap32);
+  }
 
   struct Target {
     float4 p, v, q;
@@ -859,13 +898,13 @@ struct MomentumPass {
     // one pair of Eqs. 2-5 (x_ab = -d, d = x_b - x_a)
     const float4 b0 = R.p;
     float dx, dy, dz;
-    sep(g, b0.x, b0.y, b0.z, T.p.x, T.p.y, T.p.z, dx, dy, dz);
+    sep<CFG>(g, b0.x, b0.y, b0.z, T.p.x, T.p.y, T.p.z, dx, dy, dz);
     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
     const float4 b2 = R.q;
     // W_a and W_b together in paired FP32 (each component rounded as the
     // scalar operation), clamped at t = 4 (S = 0)
     const float2 Wab = __fmul2_rn(f2(T.q.x, b2.x),
-                                  s_pow2(__fmul2_rn(f2(r2), f2(T.p.w, b0.w)), sinc_n, ktab));
+                                  s_pow2<CFG>(__fmul2_rn(f2(r2), f2(T.p.w, b0.w)), sinc_n, ktab));
     const float Wa = Wab.x, Wb = Wab.y;
     const float Cadx = fmaf(T.c02, dz, fmaf(T.c01, dy, T.c00 * dx));
     const float Cady = fmaf(T.c12, dz, fmaf(T.c11, dy, T.c01 * dx));
@@ -898,11 +937,12 @@ struct MomentumPass {
                         float2* acc) const {
     // two pairs of Eqs. 2-5, the operations of pair() in paired FP32
     float2 dx, dy, dz;
-    sep2(g, R0.p, R1.p, T.p.x, T.p.y, T.p.z, dx, dy, dz);
+    sep2<CFG>(g, R0.p, R1.p, T.p.x, T.p.y, T.p.z, dx, dy, dz);
     const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-    const float2 Wa = __fmul2_rn(f2(T.q.x), s_pow2(__fmul2_rn(r2, f2(T.p.w)), sinc_n, ktab));
+    const float2 Wa =
+        __fmul2_rn(f2(T.q.x), s_pow2<CFG>(__fmul2_rn(r2, f2(T.p.w)), sinc_n, ktab));
     const float2 Wb = __fmul2_rn(f2(R0.q.x, R1.q.x),
-                                 s_pow2(__fmul2_rn(r2, f2(R0.p.w, R1.p.w)), sinc_n, ktab));
+                                 s_pow2<CFG>(__fmul2_rn(r2, f2(R0.p.w, R1.p.w)), sinc_n, ktab));
     const float2 Cadx = __ffma2_rn(f2(T.c02), dz, __ffma2_rn(f2(T.c01), dy, __fmul2_rn(f2(T.c00), dx)));
     const float2 Cady = __ffma2_rn(f2(T.c12), dz, __ffma2_rn(f2(T.c11), dy, __fmul2_rn(f2(T.c01), dx)));
     const float2 Cadz = __ffma2_rn(f2(T.c22), dz, __ffma2_rn(f2(T.c12), dy, __fmul2_rn(f2(T.c02), dx)));
@@ -1064,6 +1104,7 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
   float* part = reinterpret_cast<float*>(smem_raw + SM::kRec);
   int* tot = reinterpret_cast<int*>(smem_raw + SM::oTot);
   const Grid g = *gp;
+  if (!pass.runs(g)) return;
   Tabs tb(smem_raw + SM::oTab);
   tb.fill<kPT>(g);
   const uint32_t n_cells = (uint32_t)*src.ncells;
@@ -1264,6 +1305,7 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
     return reinterpret_cast<float*>(smem_raw + SM::oPart + h * SM::kPart);
   };
   const Grid g = *gp;
+  if (!pass.runs(g)) return;
   const int tid = threadIdx.x;
   Tabs tb(smem_raw + SM::oTab);
   tb.fill<PT>(g);
@@ -1650,59 +1692,84 @@ void launch_find_masks(sph_ctx* ctx, const StateView& s, int64_t n, cudaStream_t
   ctx->launches += 2;
 }
 
+// The pair passes run in the plain configuration (kCfgPlain) when the
+// parameters allow it: the exact kernel with n = 6 (and, for the density, no
+// grad-h terms).  The general kernels are launched too and take over on grids
+// that need the FP32 minimum image; one of the two returns at once.
+inline bool plain_kernel(const sph_ctx* ctx) {
+  return ctx->prm.kernel_mode == SPH_KERNEL_EXACT && ctx->prm.sinc_n == 6.0;
+}
+
+template <template <int> class PassT, class Fill>
+void launch_cfg(sph_ctx* ctx, bool plain, int slot, Fill fill, cudaStream_t st) {
+  if (plain) {
+    PassT<kCfgPlain> q;
+    fill(q);
+    q.only_wrap = 0;
+    launch_pass(ctx, q, &ctx->pass_blocks[6 + slot], st);
+  }
+  PassT<kCfgAny> p;
+  fill(p);
+  p.only_wrap = plain ? 1 : 0;
+  launch_pass(ctx, p, &ctx->pass_blocks[slot], st);
+}
+
 void launch_density_staged(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
                            cudaStream_t st) {
   (void)n;
-  DensityPass p;
-  p.rec_d = ctx->rec_d;
-  p.pos32 = ctx->pos32;
-  p.u = s.u;
-  p.o = outs_with_omega(o, ctx->prm.gradh);
-  p.rec_i = ctx->rec_i;
-  p.recA = ctx->recA;
-  p.recQ = ctx->recQ;
-  p.ktab = ctx->prm.kernel_mode == SPH_KERNEL_TABLE ? ctx->ktab32 : nullptr;
-  p.Bn = (float)ctx->Bn;
-  p.sinc_n = (int)ctx->prm.sinc_n;
-  p.gamma = ctx->prm.gamma;
-  p.gradh = ctx->prm.gradh;
-  p.err = ctx->err;
-  launch_pass(ctx, p, &ctx->pass_blocks[0], st);
+  auto fill = [&](auto& p) {
+    p.rec_d = ctx->rec_d;
+    p.pos32 = ctx->pos32;
+    p.u = s.u;
+    p.o = outs_with_omega(o, ctx->prm.gradh);
+    p.rec_i = ctx->rec_i;
+    p.recA = ctx->recA;
+    p.recQ = ctx->recQ;
+    p.ktab = ctx->prm.kernel_mode == SPH_KERNEL_TABLE ? ctx->ktab32 : nullptr;
+    p.Bn = (float)ctx->Bn;
+    p.sinc_n = (int)ctx->prm.sinc_n;
+    p.gamma = ctx->prm.gamma;
+    p.gradh = ctx->prm.gradh;
+    p.err = ctx->err;
+  };
+  launch_cfg<DensityPassT>(ctx, plain_kernel(ctx) && !ctx->prm.gradh, 0, fill, st);
 }
 
 void launch_iad_staged(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
                        cudaStream_t st) {
   (void)s;
   (void)n;
-  IadPass p;
-  p.rec_i = ctx->rec_i;
-  p.recA = ctx->recA;
-  p.recQ = ctx->recQ;
-  p.o = o;
-  p.recC = ctx->recC;
-  p.recC2 = ctx->recC2;
-  p.ktab = ctx->prm.kernel_mode == SPH_KERNEL_TABLE ? ctx->ktab32 : nullptr;
-  p.sinc_n = (int)ctx->prm.sinc_n;
-  p.err = ctx->err;
-  launch_pass(ctx, p, &ctx->pass_blocks[1], st);
+  auto fill = [&](auto& p) {
+    p.rec_i = ctx->rec_i;
+    p.recA = ctx->recA;
+    p.recQ = ctx->recQ;
+    p.o = o;
+    p.recC = ctx->recC;
+    p.recC2 = ctx->recC2;
+    p.ktab = ctx->prm.kernel_mode == SPH_KERNEL_TABLE ? ctx->ktab32 : nullptr;
+    p.sinc_n = (int)ctx->prm.sinc_n;
+    p.err = ctx->err;
+  };
+  launch_cfg<IadPassT>(ctx, plain_kernel(ctx), 1, fill, st);
 }
 
 void launch_momentum_staged(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
                             cudaStream_t st) {
   (void)s;
   (void)n;
-  MomentumPass p;
-  p.recA = ctx->recA;
-  p.recV = ctx->recV;
-  p.recQ = ctx->recQ;
-  p.recC = ctx->recC;
-  p.recC2 = ctx->recC2;
-  p.o = o;
-  p.ktab = ctx->prm.kernel_mode == SPH_KERNEL_TABLE ? ctx->ktab32 : nullptr;
-  p.sinc_n = (int)ctx->prm.sinc_n;
-  p.alpha = (float)ctx->prm.alpha;
-  p.err = ctx->err;
-  launch_pass(ctx, p, &ctx->pass_blocks[2], st);
+  auto fill = [&](auto& p) {
+    p.recA = ctx->recA;
+    p.recV = ctx->recV;
+    p.recQ = ctx->recQ;
+    p.recC = ctx->recC;
+    p.recC2 = ctx->recC2;
+    p.o = o;
+    p.ktab = ctx->prm.kernel_mode == SPH_KERNEL_TABLE ? ctx->ktab32 : nullptr;
+    p.sinc_n = (int)ctx->prm.sinc_n;
+    p.alpha = (float)ctx->prm.alpha;
+    p.err = ctx->err;
+  };
+  launch_cfg<MomentumPassT>(ctx, plain_kernel(ctx), 2, fill, st);
 }
 
 void launch_export_masks(sph_ctx* ctx, const StateView& s, int64_t n, int32_t* counts,
