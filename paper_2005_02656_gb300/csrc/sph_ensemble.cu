@@ -509,7 +509,9 @@ __device__ __forceinline__ pairs32::Lists lists_of(const Args& A) {
 // since the pair loop reads it for every pair.
 
 // density + EOS, and the per-box minimum of h / c for the time step
-template <int NSUB>
+// N > 0: the kernel exponent fixed at compile time (sinc_n = N, and for the
+// density no grad-h terms); N = 0: both taken from the parameters.
+template <int NSUB, int N>
 __device__ void ph_density_t(const Args& A) {
   const pairs32::F32 f = f32_of(A);
   const pairs32::Lists L = lists_of(A);
@@ -521,8 +523,8 @@ __device__ void ph_density_t(const Args& A) {
     const int64_t p = on ? t / NSUB : 0;
     const int b = on ? A.box_of[p] : -1;
     const Grid g = A.boxes[on ? b : 0].g;
-    pairs32::density_one<NSUB>(p, g, f, A.out, A.s.u, L, A.Bn, (int)A.prm.sinc_n, A.prm.gamma,
-                               A.err, on, sub, A.prm.gradh != 0);
+    pairs32::density_one<NSUB, N>(p, g, f, A.out, A.s.u, L, A.Bn, (int)A.prm.sinc_n,
+                                  A.prm.gamma, A.err, on, sub, N == 0 && A.prm.gradh != 0);
     const bool own = on && sub == 0;
     const double q = own ? A.s.h[p] / A.out.c[p] : INFINITY;
     const int bq = own ? b : -1;
@@ -538,7 +540,7 @@ __device__ void ph_density_t(const Args& A) {
   }
 }
 
-template <int NSUB>
+template <int NSUB, int N>
 __device__ void ph_iad_t(const Args& A) {
   const pairs32::F32 f = f32_of(A);
   const pairs32::Lists L = lists_of(A);
@@ -549,11 +551,11 @@ __device__ void ph_iad_t(const Args& A) {
     const bool on = t < total;
     const int64_t p = on ? t / NSUB : 0;
     const Grid g = A.boxes[on ? A.box_of[p] : 0].g;
-    pairs32::iad_one<NSUB>(p, g, f, A.out, L, (int)A.prm.sinc_n, A.err, on, sub);
+    pairs32::iad_one<NSUB, N>(p, g, f, A.out, L, (int)A.prm.sinc_n, A.err, on, sub);
   }
 }
 
-template <int NSUB>
+template <int NSUB, int N>
 __device__ void ph_momentum_t(const Args& A) {
   const pairs32::F32 f = f32_of(A);
   const pairs32::Lists L = lists_of(A);
@@ -565,35 +567,55 @@ __device__ void ph_momentum_t(const Args& A) {
     const int64_t p = on ? t / NSUB : 0;
     const Box& B = A.boxes[on ? A.box_of[p] : 0];
     const Grid g = B.g;
-    pairs32::momentum_one<NSUB>(p, g, f, A.out, L, (int)A.prm.sinc_n, (float)B.alpha, A.err, on,
-                                sub);
+    pairs32::momentum_one<NSUB, N>(p, g, f, A.out, L, (int)A.prm.sinc_n, (float)B.alpha, A.err,
+                                   on, sub);
   }
 }
 
-__device__ void ph_density(const Args& A) {
+template <int N>
+__device__ void ph_density_n(const Args& A) {
   if (A.tpp == 4)
-    ph_density_t<4>(A);
+    ph_density_t<4, N>(A);
   else if (A.tpp == 2)
-    ph_density_t<2>(A);
+    ph_density_t<2, N>(A);
   else
-    ph_density_t<1>(A);
+    ph_density_t<1, N>(A);
+}
+template <int N>
+__device__ void ph_iad_n(const Args& A) {
+  if (A.tpp == 4)
+    ph_iad_t<4, N>(A);
+  else if (A.tpp == 2)
+    ph_iad_t<2, N>(A);
+  else
+    ph_iad_t<1, N>(A);
+}
+template <int N>
+__device__ void ph_momentum_n(const Args& A) {
+  if (A.tpm == 4)
+    ph_momentum_t<4, N>(A);
+  else if (A.tpm == 2)
+    ph_momentum_t<2, N>(A);
+  else
+    ph_momentum_t<1, N>(A);
+}
+// density and IAD: the default kernel (n = 6, no grad-h terms) with its
+// exponent fixed at compile time, any other with the parameters' values;
+// momentum keeps the run-time exponent (its fixed-exponent body spilled at
+// the kernel's 80-register cap)
+__device__ void ph_density(const Args& A) {
+  if (A.prm.sinc_n == 6.0 && !A.prm.gradh)
+    ph_density_n<6>(A);
+  else
+    ph_density_n<0>(A);
 }
 __device__ void ph_iad(const Args& A) {
-  if (A.tpp == 4)
-    ph_iad_t<4>(A);
-  else if (A.tpp == 2)
-    ph_iad_t<2>(A);
+  if (A.prm.sinc_n == 6.0)
+    ph_iad_n<6>(A);
   else
-    ph_iad_t<1>(A);
+    ph_iad_n<0>(A);
 }
-__device__ void ph_momentum(const Args& A) {
-  if (A.tpm == 4)
-    ph_momentum_t<4>(A);
-  else if (A.tpm == 2)
-    ph_momentum_t<2>(A);
-  else
-    ph_momentum_t<1>(A);
-}
+__device__ void ph_momentum(const Args& A) { ph_momentum_n<0>(A); }
 
 // dt_n = min(courant * min h/c, dt_growth * dt_{n-1}) per box (section 4.2)
 __device__ void ph_dt(const Args& A) {

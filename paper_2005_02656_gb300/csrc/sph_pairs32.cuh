@@ -122,7 +122,8 @@ __device__ __forceinline__ float group_sum(float v) {
 
 // The functions below compute target a with NSUB lanes (NSUB = 1, 2 or 4;
 // `sub` is the lane's index in its group, `on` false for lanes past the last
-// target).  With NSUB > 1 every lane of the warp must call them; lane sub = 0
+// target).  N > 0 fixes the kernel exponent n at compile time (the caller
+// passes sinc_n = N), N = 0 takes sinc_n at run time.  With NSUB > 1 every lane of the warp must call them; lane sub = 0
 // writes the results.
 
 // ---------------------------------------------------------------- density --
@@ -131,12 +132,13 @@ __device__ __forceinline__ float group_sum(float v) {
 // grad-h terms Omega_a = -(2 / (3 rho_a)) sum_{b != a} m_b t dW/dt (the form
 // of 1 + h/(3 rho) sum m dW/dh for this kernel, t = v^2), folded into the
 // record's X = P / (Omega rho^2).
-template <int NSUB = 1>
+template <int NSUB = 1, int N = 0>
 __device__ __forceinline__ void density_one(int64_t a, const Grid& g, const F32& f,
                                             const OutView& o, const double* u, const Lists& L,
                                             float Bn, int sinc_n, double gamma, uint32_t* err,
                                             bool on = true, int sub = 0, bool gradh = false) {
   const bool wrap = g.wrap32 != 0;
+  if (N > 0) sinc_n = N;
   float4 pa = make_float4(0.f, 0.f, 0.f, 1.f);
   float hinv2 = 0.f, norm = 0.f, acc = 0.0f, gsum = 0.0f;
   if (on) {
@@ -181,11 +183,12 @@ __device__ __forceinline__ void density_one(int64_t a, const Grid& g, const F32&
 // -------------------------------------------------------------------- IAD --
 // tau_a and C_a = tau_a^{-1} for particle a (separations scaled by 1/h_a so
 // that tau is of order one in FP32).
-template <int NSUB = 1>
+template <int NSUB = 1, int N = 0>
 __device__ __forceinline__ void iad_one(int64_t a, const Grid& g, const F32& f, const OutView& o,
                                         const Lists& L, int sinc_n, uint32_t* err,
                                         bool on = true, int sub = 0) {
   const bool wrap = g.wrap32 != 0;
+  if (N > 0) sinc_n = N;
   float t00 = 0, t01 = 0, t02 = 0, t11 = 0, t12 = 0, t22 = 0;
   float hinv2 = 0.f;
   if (on) {
@@ -251,12 +254,13 @@ __device__ __forceinline__ void iad_one(int64_t a, const Grid& g, const F32& f, 
 
 // ------------------------------------------------------- momentum/energy --
 // Eqs. 2-5 for particle a with viscosity coefficient alpha.
-template <int NSUB = 1>
+template <int NSUB = 1, int N = 0>
 __device__ __forceinline__ void momentum_one(int64_t a, const Grid& g, const F32& f,
                                              const OutView& o, const Lists& L, int sinc_n,
                                              float alpha, uint32_t* err, bool on = true,
                                              int sub = 0) {
   const bool wrap = g.wrap32 != 0;
+  if (N > 0) sinc_n = N;
   float accx = 0, accy = 0, accz = 0, du = 0;
   if (on) {
     const float4* ra = f.rec_m + 5 * a;
