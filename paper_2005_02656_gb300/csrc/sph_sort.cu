@@ -376,54 +376,68 @@ __device__ __forceinline__ uint32_t compact3(uint32_t v) {
 
 // Gather, first part: what the search, density and IAD read (positions, h,
 // m, u, id and the FP32 cell-relative positions).
+// Every load of a particle (and the next particle's source index) is issued
+// before its first store: the compiler cannot tell that the output arrays
+// alias none of the inputs, so a load written after a store would wait for a
+// memory round trip of its own.
 __global__ void k_gather_a(StateView in, StateView out, int64_t n, const double* org,
                            const int32_t* perm, const uint32_t* code, float4* pos32,
                            int32_t* cell3, float4* rec_d) {
   constexpr int kRow = 1 << kMaxCellBits;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    int64_t s = perm[p];
-    double x = in.x[s], y = in.y[s], z = in.z[s], h = in.h[s];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t s = p < n ? perm[p] : 0;
+  for (; p < n; p += stride) {
+    const double x = in.x[s], y = in.y[s], z = in.z[s], h = in.h[s];
+    const double m = in.m[s], u = in.u[s];
+    const int64_t id = in.id[s];
+    const uint32_t c = code[s];
+    const int64_t s_next = p + stride < n ? perm[p + stride] : 0;
+    const int ix = compact3(c), iy = compact3(c >> 1), iz = compact3(c >> 2);
+    const float ox = f32_rn(x - __ldg(org + ix));
+    const float oy = f32_rn(y - __ldg(org + kRow + iy));
+    const float oz = f32_rn(z - __ldg(org + 2 * kRow + iz));
     out.x[p] = x;
     out.y[p] = y;
     out.z[p] = z;
     out.h[p] = h;
-    const double m = in.m[s];
     out.m[p] = m;
-    out.u[p] = in.u[s];
-    out.id[p] = in.id[s];
-    uint32_t c = code[s];
-    int ix = compact3(c), iy = compact3(c >> 1), iz = compact3(c >> 2);
-    const float ox = f32_rn(x - __ldg(org + ix));
-    const float oy = f32_rn(y - __ldg(org + kRow + iy));
-    const float oz = f32_rn(z - __ldg(org + 2 * kRow + iz));
+    out.u[p] = u;
+    out.id[p] = id;
     pos32[p] = make_float4(ox, oy, oz, f32_rn(h));
     cell3[p] = pack_cell(ix, iy, iz);
     rec_d[p] = make_float4(ox, oy, oz, f32_rn(m));
+    s = s_next;
   }
 }
 
 // Gather, second part: velocities and the integrator history, first read by
 // the momentum pass (so a caller may still be copying them in while the
-// search runs).
+// search runs).  Loads before stores, as in k_gather_a.
 __global__ void k_gather_b(StateView in, StateView out, int64_t n, const int32_t* perm,
                            float4* rec_m, float4* recV) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    int64_t s = perm[p];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t s = p < n ? perm[p] : 0;
+  for (; p < n; p += stride) {
     const double vx = in.vx[s], vy = in.vy[s], vz = in.vz[s];
+    const double vxh = in.vxh[s], vyh = in.vyh[s], vzh = in.vzh[s];
+    const double dup = in.du_prev[s];
+    const double m = out.m[p];
+    const int64_t s_next = p + stride < n ? perm[p + stride] : 0;
     out.vx[p] = vx;
     out.vy[p] = vy;
     out.vz[p] = vz;
-    out.vxh[p] = in.vxh[s];
-    out.vyh[p] = in.vyh[s];
-    out.vzh[p] = in.vzh[s];
-    out.du_prev[p] = in.du_prev[s];
-    const float4 vm = make_float4(f32_rn(vx), f32_rn(vy), f32_rn(vz), f32_rn(out.m[p]));
+    out.vxh[p] = vxh;
+    out.vyh[p] = vyh;
+    out.vzh[p] = vzh;
+    out.du_prev[p] = dup;
+    const float4 vm = make_float4(f32_rn(vx), f32_rn(vy), f32_rn(vz), f32_rn(m));
     if (recV)
       recV[p] = vm;  // the staged pair passes' velocity plane
     else
       rec_m[5 * p + 1] = vm;
+    s = s_next;
   }
 }
 

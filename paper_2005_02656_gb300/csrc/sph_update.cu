@@ -250,6 +250,9 @@ __global__ void __launch_bounds__(kThreads) k_update(StateView s, OutView o, Sta
     if (prm.ng_target > 0)
       h = h * (cnt >= 0 && cnt < kHTab ? __ldg(hfac + cnt) : hfac_of(prm.ng_target, cnt));
     const double m = s.m[p];
+    // loaded before the first store (the compiler cannot tell that d aliases
+    // none of the inputs, and a load after a store waits for its own round trip)
+    const int64_t id = d.id ? s.id[p] : 0;
     d.x[p] = xn[0];
     d.y[p] = xn[1];
     d.z[p] = xn[2];
@@ -263,7 +266,7 @@ __global__ void __launch_bounds__(kThreads) k_update(StateView s, OutView o, Sta
     if (d.du_prev) d.du_prev[p] = du;  // NULL: the caller takes du_prev, m and id elsewhere
     d.h[p] = h;
     if (d.m) d.m[p] = m;
-    if (d.id) d.id[p] = s.id[p];
+    if (d.id) d.id[p] = id;
     acc[0] += m * vn[0];
     acc[1] += m * vn[1];
     acc[2] += m * vn[2];
