@@ -917,21 +917,23 @@ struct MomentumPassT {
     const float4 vb = R.v;
     const float vabx = T.v.x - vb.x, vaby = T.v.y - vb.y, vabz = T.v.z - vb.z;
     const float xv = -fmaf(dz, vabz, fmaf(dy, vaby, dx * vabx));
-    // Eq. 5 without a branch: w_ab = x_ab.v_ab / r, Pi = 0 unless approaching
+    // Eq. 5 without a branch: w_ab = x_ab.v_ab / r, Pi = 0 unless approaching;
+    // hP = Pi / 2 and qP = Pi / 4 (exact: scalings by powers of two)
     const float w = xv * rsqrtf(r2);
     const float vsig = T.q.z + b2.z - 3.0f * w;
-    const float Pi = xv < 0.0f ? -0.5f * alpha * vsig * w : 0.0f;
+    const float hP = xv < 0.0f ? -0.25f * alpha * vsig * w : 0.0f;
+    const float qP = 0.5f * hP;
     const float ira = T.q.w, irb = b2.w;
     const float mb = vb.w;
-    const float fa = mb * Wa * fmaf(0.5f * Pi, ira, T.q.y);
-    const float fb = mb * Wb * fmaf(0.5f * Pi, irb, b2.y);
-    acc[0] -= fmaf(fa, Cadx, fb * Cbdx);
-    acc[1] -= fmaf(fa, Cady, fb * Cbdy);
-    acc[2] -= fmaf(fa, Cadz, fb * Cbdz);
+    const float fa = mb * Wa * fmaf(hP, ira, T.q.y);
+    const float fb = mb * Wb * fmaf(hP, irb, b2.y);
+    // a -= fa C_a d + fb C_b d as two fused steps
+    acc[0] = fmaf(-fb, Cbdx, fmaf(-fa, Cadx, acc[0]));
+    acc[1] = fmaf(-fb, Cbdy, fmaf(-fa, Cady, acc[1]));
+    acc[2] = fmaf(-fb, Cbdz, fmaf(-fa, Cadz, acc[2]));
     const float vCa = fmaf(vabz, Cadz, fmaf(vaby, Cady, vabx * Cadx));
     const float vCb = fmaf(vabz, Cbdz, fmaf(vaby, Cbdy, vabx * Cbdx));
-    acc[3] = fmaf(mb, fmaf(Wa * fmaf(0.25f * Pi, ira, T.q.y), vCa, 0.25f * Pi * irb * Wb * vCb),
-                  acc[3]);
+    acc[3] = fmaf(mb, fmaf(Wa * fmaf(qP, ira, T.q.y), vCa, qP * irb * Wb * vCb), acc[3]);
   }
   __device__ void pair2(const Target& T, const Rec& R0, const Rec& R1, const Grid& g,
                         float2* acc) const {
