@@ -708,7 +708,7 @@ struct IadPassT {
   }
 
   struct Target {
-    float x, y, z, hinv2, inv_h;
+    float x, y, z, hinv2;
   };
   struct Rec {
     float4 r;  // position relative to the target's cell, m / rho
@@ -730,18 +730,14 @@ struct IadPassT {
     T.y = p.y;
     T.z = p.z;
     T.hinv2 = p.w;
-    T.inv_h = sqrtf(p.w);
   }
   __device__ void pair(const Target& T, const Rec& R, const Grid& g, float* acc) const {
     const float4 r = R.r;
     float dx, dy, dz;
     sep<CFG>(g, r.x, r.y, r.z, T.x, T.y, T.z, dx, dy, dz);
     const float tt = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) * T.hinv2;
-    // separation scaled by 1/h_a keeps tau of order one in FP32
-    dx *= T.inv_h;
-    dy *= T.inv_h;
-    dz *= T.inv_h;
-    const float w = r.w * s_pow<CFG>(tt, sinc_n, ktab);
+    // the weight divided by h_a^2 (tau / h_a^2 is of order one in FP32)
+    const float w = r.w * s_pow<CFG>(tt, sinc_n, ktab) * T.hinv2;
     const float wx = w * dx, wy = w * dy, wz = w * dz;
     acc[0] = fmaf(wx, dx, acc[0]);
     acc[1] = fmaf(wx, dy, acc[1]);
@@ -756,11 +752,8 @@ struct IadPassT {
     sep2<CFG>(g, R0.r, R1.r, T.x, T.y, T.z, dx, dy, dz);
     const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
     const float2 tt = __fmul2_rn(r2, f2(T.hinv2));
-    const float2 ih = f2(T.inv_h);
-    dx = __fmul2_rn(dx, ih);
-    dy = __fmul2_rn(dy, ih);
-    dz = __fmul2_rn(dz, ih);
-    const float2 w = __fmul2_rn(f2(R0.r.w, R1.r.w), s_pow2<CFG>(tt, sinc_n, ktab));
+    const float2 w = __fmul2_rn(__fmul2_rn(f2(R0.r.w, R1.r.w), s_pow2<CFG>(tt, sinc_n, ktab)),
+                                f2(T.hinv2));
     const float2 wx = __fmul2_rn(w, dx), wy = __fmul2_rn(w, dy), wz = __fmul2_rn(w, dz);
     acc[0] = __ffma2_rn(wx, dx, acc[0]);
     acc[1] = __ffma2_rn(wx, dy, acc[1]);
