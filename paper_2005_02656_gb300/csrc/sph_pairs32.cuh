@@ -195,18 +195,14 @@ __device__ __forceinline__ void iad_one(int64_t a, const Grid& g, const F32& f, 
     const float4 pa = f.pos[a];
     hinv2 = f.rec_m[5 * a].w;
     const float norm = f.rec_m[5 * a + 2].x;
-    const float inv_h = 1.0f / pa.w;
     const int cnt = min(L.nn[a], L.max_nb);
     for_entries_part<NSUB>(L.nbr + a * L.max_nb, cnt, sub, [&](uint32_t e) {
       const float4 rb = f.rec_i[entry_index(e)];
       float dx, dy, dz;
       rel(g, wrap, e, rb, pa, dx, dy, dz);
       const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-      // separation scaled by 1/h_a keeps tau of order one in FP32
-      dx *= inv_h;
-      dy *= inv_h;
-      dz *= inv_h;
-      const float w = rb.w * kw32(r2 * hinv2, norm, sinc_n, f.ktab);
+      // the weight divided by h_a^2 keeps tau / h_a^2 of order one in FP32
+      const float w = rb.w * kw32(r2 * hinv2, norm, sinc_n, f.ktab) * hinv2;
       const float wx = w * dx, wy = w * dy, wz = w * dz;
       t00 = fmaf(wx, dx, t00);
       t01 = fmaf(wx, dy, t01);
@@ -294,19 +290,22 @@ __device__ __forceinline__ void momentum_one(int64_t a, const Grid& g, const F32
       const float vabx = va.x - vb.x, vaby = va.y - vb.y, vabz = va.z - vb.z;
       const float xv = -fmaf(dz, vabz, fmaf(dy, vaby, dx * vabx));
       // Eq. 5 without a branch: w_ab = x_ab.v_ab / r, Pi = 0 unless approaching
+      // hP = Pi / 2 and qP = Pi / 4 (exact: scalings by powers of two)
       const float w = xv * rsqrtf(r2);
       const float vsig = csa + b2.z - 3.0f * w;
-      const float Pi = xv < 0.0f ? -0.5f * alpha * vsig * w : 0.0f;
+      const float hP = xv < 0.0f ? -0.25f * alpha * vsig * w : 0.0f;
+      const float qP = 0.5f * hP;
       const float irb = b2.w;
       const float mb = vb.w;
-      const float fa = mb * Wa * fmaf(0.5f * Pi, ira, Xa);
-      const float fb = mb * Wb * fmaf(0.5f * Pi, irb, b2.y);
-      accx -= fmaf(fa, Cadx, fb * Cbdx);
-      accy -= fmaf(fa, Cady, fb * Cbdy);
-      accz -= fmaf(fa, Cadz, fb * Cbdz);
+      const float fa = mb * Wa * fmaf(hP, ira, Xa);
+      const float fb = mb * Wb * fmaf(hP, irb, b2.y);
+      // a -= fa C_a d + fb C_b d as two fused steps
+      accx = fmaf(-fb, Cbdx, fmaf(-fa, Cadx, accx));
+      accy = fmaf(-fb, Cbdy, fmaf(-fa, Cady, accy));
+      accz = fmaf(-fb, Cbdz, fmaf(-fa, Cadz, accz));
       const float vCa = fmaf(vabz, Cadz, fmaf(vaby, Cady, vabx * Cadx));
       const float vCb = fmaf(vabz, Cbdz, fmaf(vaby, Cbdy, vabx * Cbdx));
-      du = fmaf(mb, fmaf(Wa * fmaf(0.25f * Pi, ira, Xa), vCa, 0.25f * Pi * irb * Wb * vCb), du);
+      du = fmaf(mb, fmaf(Wa * fmaf(qP, ira, Xa), vCa, qP * irb * Wb * vCb), du);
     });
   }
   accx = group_sum<NSUB>(accx);
