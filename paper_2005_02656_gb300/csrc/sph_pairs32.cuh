@@ -181,8 +181,8 @@ __device__ __forceinline__ void density_one(int64_t a, const Grid& g, const F32&
 }
 
 // -------------------------------------------------------------------- IAD --
-// tau_a and C_a = tau_a^{-1} for particle a (separations scaled by 1/h_a so
-// that tau is of order one in FP32).
+// tau_a and C_a = tau_a^{-1} for particle a (each pair weight divided by
+// h_a^2, so that the sum tau_a / h_a^2 is of order one in FP32).
 template <int NSUB = 1, int N = 0>
 __device__ __forceinline__ void iad_one(int64_t a, const Grid& g, const F32& f, const OutView& o,
                                         const Lists& L, int sinc_n, uint32_t* err,
