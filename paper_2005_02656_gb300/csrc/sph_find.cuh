@@ -179,40 +179,49 @@ __device__ __forceinline__ void find_cell(const Grid& g, uint32_t code, const St
   const uint32_t lt = (1u << lane) - 1u;
   for (;;) {
     // stage candidates within reach, cell by cell in stencil order, until the
-    // window cannot take another 32 or the stencil is exhausted
+    // window cannot take another 32 or the stencil is exhausted (the targets'
+    // box and the reach in registers for this pass, each cell's values read
+    // once for all its batches of 32)
+    const float blx = S.box_lo[0], bly = S.box_lo[1], blz = S.box_lo[2];
+    const float bhx = S.box_hi[0], bhy = S.box_hi[1], bhz = S.box_hi[2];
+    const float reach2 = S.reach2;
     while (sc < S.ncell && wn + 32 <= WIN) {
       const int cnt = S.off[sc + 1] - S.off[sc];
       const bool own = sc == S.self_cell;
       if (own && j0 == 0) gself = wbase + wn;
       const int st = S.start[sc];
-      const int j = j0 + lane;
-      bool keep = false;
-      float cx = 0.f, cy = 0.f, cz = 0.f;
-      if (j < cnt) {
-        const float4 p = pos32[st + j];
-        cx = p.x + S.shift[sc][0];
-        cy = p.y + S.shift[sc][1];
-        cz = p.z + S.shift[sc][2];
-        if (WRAP || own) {
-          keep = true;
-        } else {
-          const float dx = fmaxf(fmaxf(S.box_lo[0] - cx, cx - S.box_hi[0]), 0.0f);
-          const float dy = fmaxf(fmaxf(S.box_lo[1] - cy, cy - S.box_hi[1]), 0.0f);
-          const float dz = fmaxf(fmaxf(S.box_lo[2] - cz, cz - S.box_hi[2]), 0.0f);
-          keep = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < S.reach2;
+      const float shx = S.shift[sc][0], shy = S.shift[sc][1], shz = S.shift[sc][2];
+      const uint32_t ecode = entry_make(S.scode[sc], 0);
+      do {
+        const int j = j0 + lane;
+        bool keep = false;
+        float cx = 0.f, cy = 0.f, cz = 0.f;
+        if (j < cnt) {
+          const float4 p = pos32[st + j];
+          cx = p.x + shx;
+          cy = p.y + shy;
+          cz = p.z + shz;
+          if (WRAP || own) {
+            keep = true;
+          } else {
+            const float dx = fmaxf(fmaxf(blx - cx, cx - bhx), 0.0f);
+            const float dy = fmaxf(fmaxf(bly - cy, cy - bhy), 0.0f);
+            const float dz = fmaxf(fmaxf(blz - cz, cz - bhz), 0.0f);
+            keep = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < reach2;
+          }
         }
-      }
-      const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-      if (keep) {
-        const int q = wn + __popc(bal & lt);
-        const int pq = pair_index(q);
-        W.cx[pq] = cx;
-        W.cy[pq] = cy;
-        W.cz[pq] = cz;
-        W.entry[q] = entry_make(S.scode[sc], st + j);
-      }
-      wn += __popc(bal);
-      j0 += 32;
+        const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+          const int q = wn + __popc(bal & lt);
+          const int pq = pair_index(q);
+          W.cx[pq] = cx;
+          W.cy[pq] = cy;
+          W.cz[pq] = cz;
+          W.entry[q] = ecode | (uint32_t)(st + j);
+        }
+        wn += __popc(bal);
+        j0 += 32;
+      } while (j0 < cnt && wn + 32 <= WIN);
       if (j0 >= cnt) {
         ++sc;
         j0 = 0;

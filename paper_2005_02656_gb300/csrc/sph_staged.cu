@@ -236,41 +236,50 @@ __device__ __forceinline__ void find_cell_masks(const Grid& g, uint32_t cell, ui
   int sc = 0, j0 = 0;  // next source: stencil cell and particle within it
   const uint32_t lt = (1u << lane) - 1u;
   for (;;) {
+    // the targets' box and the reach, in registers for this staging pass
+    const float blx = S.box_lo[0], bly = S.box_lo[1], blz = S.box_lo[2];
+    const float bhx = S.box_hi[0], bhy = S.box_hi[1], bhz = S.box_hi[2];
+    const float reach2 = S.reach2;
     while (sc < S.ncell && wn + 32 <= WIN) {
+      // this stencil cell's values, read once for all its batches of 32
       const int cnt = S.off[sc + 1] - S.off[sc];
       const bool own = sc == S.self_cell;
       if (own && j0 == 0) gself = 64 * (int)gb + wn;
       const int st = S.start[sc];
-      const int j = j0 + lane;
-      bool keep = false;
-      float cx = 0.f, cy = 0.f, cz = 0.f;
-      if (j < cnt) {
-        const float4 p = pos32[st + j];
-        cx = p.x + S.shift[sc][0];
-        cy = p.y + S.shift[sc][1];
-        cz = p.z + S.shift[sc][2];
-        if (WRAP || own) {
-          keep = true;
-        } else {
-          const float dx = fmaxf(fmaxf(S.box_lo[0] - cx, cx - S.box_hi[0]), 0.0f);
-          const float dy = fmaxf(fmaxf(S.box_lo[1] - cy, cy - S.box_hi[1]), 0.0f);
-          const float dz = fmaxf(fmaxf(S.box_lo[2] - cz, cz - S.box_hi[2]), 0.0f);
-          keep = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < S.reach2;
+      const float shx = S.shift[sc][0], shy = S.shift[sc][1], shz = S.shift[sc][2];
+      const uint32_t ecode = entry_make(S.scode[sc], 0);
+      do {
+        const int j = j0 + lane;
+        bool keep = false;
+        float cx = 0.f, cy = 0.f, cz = 0.f;
+        if (j < cnt) {
+          const float4 p = pos32[st + j];
+          cx = p.x + shx;
+          cy = p.y + shy;
+          cz = p.z + shz;
+          if (WRAP || own) {
+            keep = true;
+          } else {
+            const float dx = fmaxf(fmaxf(blx - cx, cx - bhx), 0.0f);
+            const float dy = fmaxf(fmaxf(bly - cy, cy - bhy), 0.0f);
+            const float dz = fmaxf(fmaxf(blz - cz, cz - bhz), 0.0f);
+            keep = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < reach2;
+          }
         }
-      }
-      const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-      if (keep) {
-        const int q = wn + __popc(bal & lt);
-        const int pq = pair_index(q);
-        W.cx[pq] = cx;
-        W.cy[pq] = cy;
-        W.cz[pq] = cz;
-        const uint32_t e = entry_make(S.scode[sc], st + j);
-        W.entry[q] = e;
-        mo.sent[slot_base + 64u * gb + (uint32_t)q] = e;
-      }
-      wn += __popc(bal);
-      j0 += 32;
+        const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+          const int q = wn + __popc(bal & lt);
+          const int pq = pair_index(q);
+          W.cx[pq] = cx;
+          W.cy[pq] = cy;
+          W.cz[pq] = cz;
+          const uint32_t e = ecode | (uint32_t)(st + j);
+          W.entry[q] = e;
+          mo.sent[slot_base + 64u * gb + (uint32_t)q] = e;
+        }
+        wn += __popc(bal);
+        j0 += 32;
+      } while (j0 < cnt && wn + 32 <= WIN);
       if (j0 >= cnt) {
         ++sc;
         j0 = 0;
