@@ -690,7 +690,8 @@ struct IadPassT {
   static constexpr int kWin = 1024;
   static constexpr int kRecBytes = 16;
   static constexpr int kV = 6;
-  static constexpr int kMinBlocks = 4;
+  static constexpr int kMinBlocks = 3;  // general kernel (the few cells outside the pipelined
+                                        // lists): no register spills at this bound
   static constexpr int kStageU = 4;
   static constexpr bool kPaired = true;
   static constexpr int kPipeThreads = 256;
@@ -1167,9 +1168,11 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
             const int tt = i / (kLC / 4), k4 = 4 * (i - tt * (kLC / 4));
             const int kk = lp * kLC + k4;
             if (kk < tot[tt])  // 8-byte chunks: max_nb and kLC are multiples of 4
-              *reinterpret_cast<uint2*>(lists + tt * kLS + k4) = __ldg(reinterpret_cast<const uint2*>(
-                  slot_row(const_cast<uint16_t*>(src.slist), (int64_t)a0 + r0 + tt, src.max_nb) + kk));
+              cp_async8(lists + tt * kLS + k4,
+                        slot_row(const_cast<uint16_t*>(src.slist), (int64_t)a0 + r0 + tt,
+                                 src.max_nb) + kk);
           }
+          cp_async_commit();
           const int nl = active ? min(tot[t] - lp * kLC, kLC) : 0;
           int k = sub;
           for (int w0 = 0; w0 < S; w0 += Pass::kWin) {
@@ -1178,21 +1181,48 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
               if (w0 > 0) __syncthreads();  // the previous window's readers are done
               const uint32_t* es = src.sent + slot_base + (uint32_t)w0;
               const bool pre = w0 == 0 && r0 == 0 && lp == 0;  // entries already loaded
-              for (int j0 = 0; j0 < wn; j0 += U * kPT) {
-                uint32_t e[U];
+              // the window's records by cp.async (no register staging, one round
+              // trip), then the cell shifts added to the records this thread copied
+              constexpr int NB = (Pass::kWin + U * kPT - 1) / (U * kPT);
+              uint32_t e[NB][U];
+#pragma unroll
+              for (int bq = 0; bq < NB; ++bq)
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                  const int j = j0 + u * kPT + tid;
-                  e[u] = (pre && j0 == 0) ? cur.e[u] : (j < wn ? __ldg(es + j) : 0u);
+                  const int j = bq * U * kPT + u * kPT + tid;
+                  e[bq][u] = (pre && bq == 0) ? cur.e[u] : (j < wn ? __ldg(es + j) : 0u);
                 }
+              // the entries' shift codes (5 bits each) kept packed across the wait
+              static_assert(NB * U <= 6, "shift codes packed into one register");
+              uint32_t codes = 0;
 #pragma unroll
-                for (int u = 0; u < U; ++u)
-                  if (j0 + u * kPT + tid < wn)
-                    Pass::template store<Pass::kWin>(rec, j0 + u * kPT + tid, pass.load(e[u], tb.shift));
-              }
+              for (int bq = 0; bq < NB; ++bq)
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                  const int j = bq * U * kPT + u * kPT + tid;
+                  if (j < wn) pass.template copy_async<Pass::kWin>(rec, j, entry_index(e[bq][u]));
+                  codes |= (e[bq][u] >> kIndexBits) << (5 * (bq * U + u));
+                }
+              cp_async_commit();
+              cp_async_wait_all();
+#pragma unroll
+              for (int bq = 0; bq < NB; ++bq)
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                  const int j = bq * U * kPT + u * kPT + tid;
+                  if (j < wn) {
+                    const float4 sh = tb.shift[(codes >> (5 * (bq * U + u))) & 31u];
+                    float4 r = rec[j];
+                    r.x += sh.x;
+                    r.y += sh.y;
+                    r.z += sh.z;
+                    rec[j] = r;
+                  }
+                }
               staged_w0 = w0;
             }
-            __syncthreads();  // lists copied, records staged
+            cp_async_wait_all();  // the list chunks have landed
+            __syncthreads();      // lists copied, records staged
             const uint16_t* row = lists + t * kLS;
             const int wend = w0 + wn;
             for (; Pass::kPaired && k + nsub < nl; k += 2 * nsub) {  // two entries at a time
