@@ -553,17 +553,6 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Adds the cell shift of entry e to the position of staged record j (plane 0).
-__device__ __forceinline__ void add_shift(float4* rec, int j, uint32_t e, const Grid& g) {
-  float sx, sy, sz;
-  entry_shift(e, g, sx, sy, sz);
-  float4 r = rec[j];
-  r.x += sx;
-  r.y += sy;
-  r.z += sz;
-  rec[j] = r;
-}
-
 // --- density + EOS (Eq. 1, self term included) ---
 template <int CFG>
 struct DensityPassT {
@@ -571,7 +560,6 @@ struct DensityPassT {
   static constexpr int kRecBytes = 16;
   static constexpr int kV = 2;        // reduced values: sum m S^n, grad-h sum
   static constexpr int kMinBlocks = 4;
-  static constexpr int kStageU = 4;   // staged records loaded per thread at once
   static constexpr bool kPaired = true;  // two pairs per iteration in paired FP32
   static constexpr int kPipeThreads = 256;
   static constexpr int kPipeMinBlocks = 3;
@@ -692,7 +680,6 @@ struct IadPassT {
   static constexpr int kV = 6;
   static constexpr int kMinBlocks = 3;  // general kernel (the few cells outside the pipelined
                                         // lists): no register spills at this bound
-  static constexpr int kStageU = 4;
   static constexpr bool kPaired = true;
   static constexpr int kPipeThreads = 256;
   static constexpr int kPipeMinBlocks = 3;
@@ -831,7 +818,6 @@ struct MomentumPassT {
   static constexpr bool kSmemLists = false;  // lists read through L1
   static constexpr bool kTargetSmem = true;  // target records from the staged window
   static constexpr bool kPipePaired = false;
-  static constexpr int kStageU = 2;
   const float4* recA;    // (offset, 1 / h^2)
   const float4* recV;    // (v, m)
   const float4* recQ;    // (B_n / h^3, X = P / (Omega rho^2), c, 1 / rho)
@@ -1075,26 +1061,32 @@ struct Src {
 };
 
 // Values of the next cell loaded while the current one is computed: the
-// neighbour counts of its first targets and its first staged entries.
-template <int U>
+// neighbour counts of its first targets and the staged entries of its first
+// window (slots tid + i kPT, i < J).
+template <int J>
 struct Prefetch {
   int nn;          // thread tid < kTR: count of target tid of the first round
-  uint32_t e[U];   // staged entries tid + u kPT of the first window
+  uint32_t e[J];
 };
+
+// staged slots per thread in a window of the general kernel
+template <class Pass>
+constexpr int window_slots() {
+  return (Pass::kWin + kPT - 1) / kPT;
+}
 
 template <class Pass>
 __device__ __forceinline__ void prefetch_cell(const Src& src, uint4 md,
-                                              Prefetch<Pass::kStageU>& pf) {
+                                              Prefetch<window_slots<Pass>()>& pf) {
   const int tid = threadIdx.x;
   const int S = cell_S(md), na = cell_na(md);
   const bool staged = md.y != kListForm;
   pf.nn = (staged && tid < kTR && tid < na) ? __ldg(src.nn + md.z + tid) : 0;
-  (void)S;
   const int wn = min(Pass::kWin, S);
 #pragma unroll
-  for (int u = 0; u < Pass::kStageU; ++u) {
-    const int j = tid + u * kPT;
-    pf.e[u] = (staged && j < wn) ? __ldg(src.sent + md.x + (uint32_t)j) : 0u;
+  for (int i = 0; i < window_slots<Pass>(); ++i) {
+    const int j = tid + i * kPT;
+    pf.e[i] = (staged && j < wn) ? __ldg(src.sent + md.x + (uint32_t)j) : 0u;
   }
 }
 
@@ -1102,7 +1094,6 @@ template <class Pass>
 __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, const Grid* gp,
                                                                     Src src) {
   using SM = PassSmem<Pass>;
-  constexpr int U = Pass::kStageU;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* rec = reinterpret_cast<float4*>(smem_raw);
   uint16_t* lists = reinterpret_cast<uint16_t*>(smem_raw + SM::kRec);
@@ -1122,11 +1113,12 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
   uint4 md_next = meta_of(blockIdx.x);
   uint4 md_after = meta_of(blockIdx.x + G);
   uint32_t c_ahead = cell_at(blockIdx.x + 2 * G);  // meta loaded one cell later
-  Prefetch<U> pf;
+  constexpr int NJ = window_slots<Pass>();
+  Prefetch<NJ> pf;
   prefetch_cell<Pass>(src, md_next, pf);
   for (uint32_t q = blockIdx.x; q < n_cells; q += G) {
     const uint4 md = md_next;
-    const Prefetch<U> cur = pf;
+    const Prefetch<NJ> cur = pf;
     md_next = md_after;
     md_after = meta_at(c_ahead);
     c_ahead = cell_at(q + 3 * G);
@@ -1183,42 +1175,35 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
               const bool pre = w0 == 0 && r0 == 0 && lp == 0;  // entries already loaded
               // the window's records by cp.async (no register staging, one round
               // trip), then the cell shifts added to the records this thread copied
-              constexpr int NB = (Pass::kWin + U * kPT - 1) / (U * kPT);
-              uint32_t e[NB][U];
+              uint32_t e[NJ];
 #pragma unroll
-              for (int bq = 0; bq < NB; ++bq)
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                  const int j = bq * U * kPT + u * kPT + tid;
-                  e[bq][u] = (pre && bq == 0) ? cur.e[u] : (j < wn ? __ldg(es + j) : 0u);
-                }
+              for (int i = 0; i < NJ; ++i) {
+                const int j = i * kPT + tid;
+                e[i] = pre ? cur.e[i] : (j < wn ? __ldg(es + j) : 0u);
+              }
               // the entries' shift codes (5 bits each) kept packed across the wait
-              static_assert(NB * U <= 6, "shift codes packed into one register");
+              static_assert(NJ <= 6, "shift codes packed into one register");
               uint32_t codes = 0;
 #pragma unroll
-              for (int bq = 0; bq < NB; ++bq)
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                  const int j = bq * U * kPT + u * kPT + tid;
-                  if (j < wn) pass.template copy_async<Pass::kWin>(rec, j, entry_index(e[bq][u]));
-                  codes |= (e[bq][u] >> kIndexBits) << (5 * (bq * U + u));
-                }
+              for (int i = 0; i < NJ; ++i) {
+                const int j = i * kPT + tid;
+                if (j < wn) pass.template copy_async<Pass::kWin>(rec, j, entry_index(e[i]));
+                codes |= (e[i] >> kIndexBits) << (5 * i);
+              }
               cp_async_commit();
               cp_async_wait_all();
 #pragma unroll
-              for (int bq = 0; bq < NB; ++bq)
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                  const int j = bq * U * kPT + u * kPT + tid;
-                  if (j < wn) {
-                    const float4 sh = tb.shift[(codes >> (5 * (bq * U + u))) & 31u];
-                    float4 r = rec[j];
-                    r.x += sh.x;
-                    r.y += sh.y;
-                    r.z += sh.z;
-                    rec[j] = r;
-                  }
+              for (int i = 0; i < NJ; ++i) {
+                const int j = i * kPT + tid;
+                if (j < wn) {
+                  const float4 sh = tb.shift[(codes >> (5 * i)) & 31u];
+                  float4 r = rec[j];
+                  r.x += sh.x;
+                  r.y += sh.y;
+                  r.z += sh.z;
+                  rec[j] = r;
                 }
+              }
               staged_w0 = w0;
             }
             cp_async_wait_all();  // the list chunks have landed
@@ -1237,6 +1222,8 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
               pass.pair(T, Pass::template fetch<Pass::kWin>(rec, slot - w0), g, acc);
             }
           }
+          // a cell of a pipelined list has no list longer than kLC: one pass
+          if (md.w & 0x8000u) break;
           const int more = __syncthreads_or(active && sub == 0 && tot[t] > (lp + 1) * kLC);
           if (!more) break;
         }
