@@ -1361,19 +1361,6 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
     }
   };
   // the next cell's lists (shared-memory lists): 16-byte chunks of each row
-  auto issue_lists = [&](uint4 md, const int* cnt, uint16_t* lst) {
-    const int na = cell_na(md);
-    for (int i = tid; i < na * (kLC / 8); i += PT) {
-      const int tt = i / (kLC / 8), k8 = 8 * (i - tt * (kLC / 8));
-      if (k8 >= cnt[tt]) continue;
-      const uint16_t* grow =
-          slot_row(const_cast<uint16_t*>(src.slist), (int64_t)md.z + tt, src.max_nb) + k8;
-      if (k8 + 8 <= src.max_nb)
-        cp_async16(lst + tt * kLS + k8, grow);
-      else  // the last 4 entries of a row of max_nb = 4 mod 8
-        cp_async8(lst + tt * kLS + k8, grow);
-    }
-  };
   // this thread's target in a cell (nsub threads per target)
   auto target_of = [&](uint4 md, int& t, int& sub, int& nsub) {
     const int na = present(md) ? cell_na(md) : 0;
@@ -1410,6 +1397,21 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
                   128 * (i - t * lines));
     }
   };
+  // the next cell's lists (shared-memory lists): thread (t, s) copies the
+  // 16-byte chunks s, s + nsub, ... of target t's row that hold entries
+  auto issue_lists = [&](uint4 md, const Share& sh, const int* cnt, uint16_t* lst) {
+    if (sh.t < 0) return;
+    const int c = cnt[sh.t];
+    const uint16_t* row =
+        slot_row(const_cast<uint16_t*>(src.slist), (int64_t)md.z + sh.t, src.max_nb);
+    uint16_t* dst = lst + sh.t * kLS;
+    for (int k8 = 8 * sh.sub; k8 < c; k8 += 8 * sh.nsub) {
+      if (k8 + 8 <= src.max_nb)
+        cp_async16(dst + k8, row + k8);
+      else  // the last 4 entries of a row of max_nb = 4 mod 8
+        cp_async8(dst + k8, row + k8);
+    }
+  };
   // prologue: the first cell's copies, registers of the next two cells
   uint4 md_cur = meta_at(cell_at(q)), md_nxt = meta_at(cell_at(q + G));
   uint4 md_nn = meta_at(cell_at(q + 2 * G));
@@ -1418,16 +1420,16 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
   load_entries(md_cur, e_cur);
   const int c_cur0 = count_of(md_cur);
   issue_records(md_cur, e_cur, rbuf(0));
+  Share sh_cur = share_of(md_cur, c_cur0);
   if (kLists) {
     if (tid < kTR) tcnt(0)[tid] = c_cur0;
     __syncthreads();
-    issue_lists(md_cur, tcnt(0), lbuf(0));
+    issue_lists(md_cur, sh_cur, tcnt(0), lbuf(0));
   } else {
     prefetch_rows(md_cur);
   }
   cp_async_commit();
   load_entries(md_nxt, e_nxt);
-  Share sh_cur = share_of(md_cur, c_cur0);
   int cnt_nxt = count_of(md_nxt);
   typename Pass::Target T_cur, T_nxt;
   if (!Pass::kTargetSmem && sh_cur.t >= 0) pass.load_target((int64_t)md_cur.z + sh_cur.t, T_cur);
@@ -1479,9 +1481,13 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
     if (kLists && has_nxt && tid < kTR) tcnt(cb_nxt)[tid] = cnt_nxt;
     __syncthreads();  // this cell's data published; the previous cell computed
     finish_prev(buf ^ 1, fin_prv);
+    // the next cell's thread shares: needed here by the list copies, after the
+    // next loads otherwise
+    Share sh_nxt;
+    if (kLists) sh_nxt = share_of(md_nxt, cnt_nxt);
     if (has_nxt) {
       issue_records(md_nxt, e_nxt, rbuf(buf ^ 1));
-      if (kLists) issue_lists(md_nxt, tcnt(cb_nxt), lbuf(buf ^ 1));
+      if (kLists) issue_lists(md_nxt, sh_nxt, tcnt(cb_nxt), lbuf(buf ^ 1));
     }
     cp_async_commit();
     // registers for the next cells
@@ -1490,8 +1496,10 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
     const int cnt_nn = count_of(md_nn);
     const uint4 md_nnn = meta_at(c_nnn);
     c_nnn = cell_at(q + 4 * G);
-    const Share sh_nxt = share_of(md_nxt, cnt_nxt);
-    if (!kLists) prefetch_rows(md_nxt);
+    if (!kLists) {
+      sh_nxt = share_of(md_nxt, cnt_nxt);
+      prefetch_rows(md_nxt);
+    }
     if (!Pass::kTargetSmem && sh_nxt.t >= 0)
       pass.load_target((int64_t)md_nxt.z + sh_nxt.t, T_nxt);
     // compute this cell
