@@ -573,8 +573,8 @@ struct DensityPassT {
   const double* u;
   OutView o;
   float4* rec_i;         // out: (offset, m / rho)
-  float4* recA;          // out: (offset, 1 / h^2)
-  float4* recQ;          // out: (B_n / h^3, X, c, 1 / rho)
+  float4* recA;          // out: (offset, 1 / h^2); plain configuration (offset, 1 / h)
+  float4* recQ;          // out: (B_n / h^3, X, c, 1 / rho); plain configuration (c, 1 / rho, -, -)
   const float2* ktab;
   float Bn;
   int sinc_n;
@@ -600,8 +600,6 @@ struct DensityPassT {
     const float4 r = rec_d[entry_index(e)];
     return {make_float4(r.x + sh.x, r.y + sh.y, r.z + sh.z, r.w)};
   }
-  template <int W>
-  static __device__ void store(float4* rec, int j, const Rec& r) { rec[j] = r.r; }
   template <int W>
   static __device__ Rec fetch(const float4* rec, int j) { return {rec[j]}; }
   template <int W>
@@ -644,8 +642,11 @@ struct DensityPassT {
   __device__ void finish(int64_t a, const float* acc) const { finish2(a, acc, prefin(a)); }
   __device__ void finish2(int64_t a, const float* acc, const FinishIn& fin) const {
     const float4 p = fin.p;
-    const float hinv2 = 1.0f / (p.w * p.w);
-    const float norm = Bn * hinv2 / p.w;
+    // the plain configuration keeps 1/h in the records and forms 1/h^2 and
+    // B_n / h^3 from it as the momentum pass does
+    const float hinv = CFG == kCfgPlain ? 1.0f / p.w : 0.0f;
+    const float hinv2 = CFG == kCfgPlain ? hinv * hinv : 1.0f / (p.w * p.w);
+    const float norm = CFG == kCfgPlain ? Bn * hinv * hinv2 : Bn * hinv2 / p.w;
     const float ma = fin.m;
     const float rho = norm * (ma + acc[0]);  // self term: S(0)^n = 1
     // the ideal-gas equation of state in FP32 (from the FP32 density; FP64
@@ -661,13 +662,16 @@ struct DensityPassT {
     o.p[a] = (double)pr;
     o.c[a] = (double)c;
     rec_i[a] = make_float4(p.x, p.y, p.z, ma * inv_rho);
-    recA[a] = make_float4(p.x, p.y, p.z, hinv2);
+    recA[a] = make_float4(p.x, p.y, p.z, CFG == kCfgPlain ? hinv : hinv2);
     if (has_gradh()) {
       const float omega = -2.0f * norm * acc[1] * inv_rho * (1.0f / 3.0f);
       X /= omega;
       if (o.omega) o.omega[a] = (double)omega;
     }
-    recQ[a] = make_float4(norm, X, c, inv_rho);
+    // (plain: X = P / rho^2 = c^2 / (gamma rho) is formed by the momentum pass;
+    // the IAD pass writes C12 and C22 into the last two components)
+    recQ[a] = CFG == kCfgPlain ? make_float4(c, inv_rho, 0.0f, 0.0f)
+                               : make_float4(norm, X, c, inv_rho);
     if (!isfinite(rho) || !isfinite(c)) raise_flag(err, SPH_FLAG_NONFINITE);
   }
 };
@@ -689,12 +693,13 @@ struct IadPassT {
   static constexpr bool kTargetSmem = false;
   static constexpr bool kPipePaired = true;
   const float4* rec_i;   // (offset, m / rho)
-  const float4* recA;    // (offset, 1 / h^2)
-  const float4* recQ;    // (B_n / h^3, ...)
+  const float4* recA;    // (offset, 1 / h^2); plain configuration (offset, 1 / h)
+  float4* recQ;          // (B_n / h^3, ...); plain configuration: out (-, -, C12, C22)
   OutView o;
   float4* recC;          // out: (C00, C01, C02, C11)
-  float2* recC2;         // out: (C12, C22)
+  float2* recC2;         // out: (C12, C22) (general configuration)
   const float2* ktab;
+  float Bn;
   int sinc_n;
   uint32_t* err;
   // kCfgAny launched beside a kCfgPlain launch: runs only on grids that need
@@ -716,8 +721,6 @@ struct IadPassT {
     return {make_float4(r.x + sh.x, r.y + sh.y, r.z + sh.z, r.w)};
   }
   template <int W>
-  static __device__ void store(float4* rec, int j, const Rec& r) { rec[j] = r.r; }
-  template <int W>
   static __device__ Rec fetch(const float4* rec, int j) { return {rec[j]}; }
   template <int W>
   static __device__ void target_from(float4*, int, Target&) {}
@@ -726,7 +729,7 @@ struct IadPassT {
     T.x = p.x;
     T.y = p.y;
     T.z = p.z;
-    T.hinv2 = p.w;
+    T.hinv2 = CFG == kCfgPlain ? p.w * p.w : p.w;
   }
   __device__ void pair(const Target& T, const Rec& R, const Grid& g, float* acc) const {
     const float4 r = R.r;
@@ -764,7 +767,13 @@ struct IadPassT {
   struct FinishIn {
     float hinv2, norm;
   };
-  __device__ FinishIn prefin(int64_t a) const { return {recA[a].w, recQ[a].x}; }
+  __device__ FinishIn prefin(int64_t a) const {
+    if (CFG == kCfgPlain) {
+      const float hinv = recA[a].w, hinv2 = hinv * hinv;
+      return {hinv2, Bn * hinv * hinv2};
+    }
+    return {recA[a].w, recQ[a].x};
+  }
   __device__ void finish(int64_t a, const float* acc) const { finish2(a, acc, prefin(a)); }
   __device__ void finish2(int64_t a, const float* acc, const FinishIn& fin) const {
     const float hinv2 = fin.hinv2;
@@ -794,7 +803,10 @@ struct IadPassT {
       Cm[5] = c22 * sc;
     }
     recC[a] = make_float4(Cm[0], Cm[1], Cm[2], Cm[3]);
-    recC2[a] = make_float2(Cm[4], Cm[5]);
+    if (CFG == kCfgPlain)
+      reinterpret_cast<float2*>(recQ + a)[1] = make_float2(Cm[4], Cm[5]);
+    else
+      recC2[a] = make_float2(Cm[4], Cm[5]);
     double* out = o.iad + 6 * a;
     for (int q = 0; q < 6; ++q) out[q] = (double)Cm[q];
   }
@@ -803,8 +815,11 @@ struct IadPassT {
 // --- momentum and energy with artificial viscosity (Eqs. 2-5) ---
 template <int CFG>
 struct MomentumPassT {
-  static constexpr int kWin = 768;  // staged slots (plane stride): three CTAs of 73 KB per SM
-  static constexpr int kRecBytes = 72;  // four float4 planes and one float2 plane
+  static constexpr int kWin = 768;  // staged slots (plane stride): three CTAs of <= 73 KB per SM
+  // four float4 planes and one float2 plane; the plain configuration keeps
+  // four float4 planes (1/h, c and 1/rho stored; 1/h^2, B_n / h^3 and X
+  // formed per record read): 8 bytes fewer per pair from shared memory
+  static constexpr int kRecBytes = CFG == kCfgPlain ? 64 : 72;
   static constexpr int kV = 4;
   static constexpr int kMinBlocks = 3;
   static constexpr bool kPaired = false;  // the paired body needs ~120 registers: scalar pairs
@@ -818,15 +833,18 @@ struct MomentumPassT {
   static constexpr bool kSmemLists = false;  // lists read through L1
   static constexpr bool kTargetSmem = true;  // target records from the staged window
   static constexpr bool kPipePaired = false;
-  const float4* recA;    // (offset, 1 / h^2)
+  const float4* recA;    // (offset, 1 / h^2); plain configuration (offset, 1 / h)
   const float4* recV;    // (v, m)
-  const float4* recQ;    // (B_n / h^3, X = P / (Omega rho^2), c, 1 / rho)
+  const float4* recQ;    // (B_n / h^3, X = P / (Omega rho^2), c, 1 / rho);
+                         // plain configuration (c, 1 / rho, C12, C22)
   const float4* recC;    // (C00, C01, C02, C11)
-  const float2* recC2;   // (C12, C22)
+  const float2* recC2;   // (C12, C22) (general configuration)
   OutView o;
   const float2* ktab;
   int sinc_n;
   float alpha;
+  float Bn;              // kernel normalisation (plain configuration: B_n / h^3 from 1/h)
+  float inv_gamma;       // 1 / gamma (plain configuration: X = c^2 / (gamma rho))
   uint32_t* err;
   // kCfgAny launched beside a kCfgPlain launch: runs only on grids that need
   // the minimum image
@@ -850,38 +868,48 @@ struct MomentumPassT {
     float4 p, v, q, c;  // (position relative to the target's cell, 1/h^2), (v, m), Q, C
     float2 c2;
   };
+  // a plain-configuration record (A: offset, 1/h; V; Q: c, 1/rho, C12, C22; C)
+  // in the general form (A: offset, 1/h^2; Q: B_n / h^3, X, c, 1/rho; C2), with
+  // X = P / rho^2 = c^2 / (gamma rho) for the ideal gas
+  __device__ __forceinline__ Rec widen(float4 p, float4 v, float4 q, float4 c) const {
+    const float hinv2 = p.w * p.w;
+    const float norm = Bn * p.w * hinv2;
+    const float X = q.x * q.x * (q.y * inv_gamma);
+    return {make_float4(p.x, p.y, p.z, hinv2), v, make_float4(norm, X, q.x, q.y), c,
+            make_float2(q.z, q.w)};
+  }
   __device__ Rec load(uint32_t e, const float4* shtab) const {
     const float4 sh = shtab[e >> kIndexBits];
     const int b = entry_index(e);
     const float4 p = recA[b];
-    return {make_float4(p.x + sh.x, p.y + sh.y, p.z + sh.z, p.w), recV[b], recQ[b], recC[b],
-            recC2[b]};
+    const float4 ps = make_float4(p.x + sh.x, p.y + sh.y, p.z + sh.z, p.w);
+    if (CFG == kCfgPlain) return widen(ps, recV[b], recQ[b], recC[b]);
+    return {ps, recV[b], recQ[b], recC[b], recC2[b]};
   }
   template <int W>
-  static __device__ void store(float4* rec, int j, const Rec& r) {
-    plane<W>(rec, 0)[j] = r.p;
-    plane<W>(rec, 1)[j] = r.v;
-    plane<W>(rec, 2)[j] = r.q;
-    plane<W>(rec, 3)[j] = r.c;
-    plane2<W>(rec)[j] = r.c2;
-  }
-  template <int W>
-  static __device__ Rec fetch(float4* rec, int j) {
+  __device__ Rec fetch(float4* rec, int j) const {
+    if (CFG == kCfgPlain)
+      return widen(plane<W>(rec, 0)[j], plane<W>(rec, 1)[j], plane<W>(rec, 2)[j],
+                   plane<W>(rec, 3)[j]);
     return {plane<W>(rec, 0)[j], plane<W>(rec, 1)[j], plane<W>(rec, 2)[j], plane<W>(rec, 3)[j],
             plane2<W>(rec)[j]};
   }
+  static __device__ void to_target(const Rec& R, Target& T) {
+    T.p = R.p;
+    T.v = R.v;
+    T.q = R.q;
+    T.c00 = R.c.x;
+    T.c01 = R.c.y;
+    T.c02 = R.c.z;
+    T.c11 = R.c.w;
+    T.c12 = R.c2.x;
+    T.c22 = R.c2.y;
+  }
   __device__ void load_target(int64_t a, Target& T) const {
-    T.p = recA[a];
-    T.v = recV[a];
-    T.q = recQ[a];
-    const float4 c = recC[a];
-    const float2 c2 = recC2[a];
-    T.c00 = c.x;
-    T.c01 = c.y;
-    T.c02 = c.z;
-    T.c11 = c.w;
-    T.c12 = c2.x;
-    T.c22 = c2.y;
+    if (CFG == kCfgPlain)
+      to_target(widen(recA[a], recV[a], recQ[a], recC[a]), T);
+    else
+      to_target({recA[a], recV[a], recQ[a], recC[a], recC2[a]}, T);
   }
   __device__ void pair(const Target& T, const Rec& R, const Grid& g, float* acc) const {
     // one pair of Eqs. 2-5 (x_ab = -d, d = x_b - x_a)
@@ -973,21 +1001,12 @@ struct MomentumPassT {
     cp_async16(plane<W>(rec, 1) + j, recV + b);
     cp_async16(plane<W>(rec, 2) + j, recQ + b);
     cp_async16(plane<W>(rec, 3) + j, recC + b);
-    cp_async8(plane2<W>(rec) + j, recC2 + b);
+    if (CFG != kCfgPlain) cp_async8(plane2<W>(rec) + j, recC2 + b);
   }
   // The target's data is its own staged record (its cell's shift is zero).
   template <int W>
-  static __device__ void target_from(float4* rec, int j, Target& T) {
-    const Rec R = fetch<W>(rec, j);
-    T.p = R.p;
-    T.v = R.v;
-    T.q = R.q;
-    T.c00 = R.c.x;
-    T.c01 = R.c.y;
-    T.c02 = R.c.z;
-    T.c11 = R.c.w;
-    T.c12 = R.c2.x;
-    T.c22 = R.c2.y;
+  __device__ void target_from(float4* rec, int j, Target& T) const {
+    to_target(fetch<W>(rec, j), T);
   }
   struct FinishIn {};
   __device__ FinishIn prefin(int64_t) const { return {}; }
@@ -1213,13 +1232,13 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
             for (; Pass::kPaired && k + nsub < nl; k += 2 * nsub) {  // two entries at a time
               const int s0 = row[k], s1 = row[k + nsub];
               if (s1 >= wend) break;                 // ascending: s0 < s1
-              pass.pair2(T, Pass::template fetch<Pass::kWin>(rec, s0 - w0),
-                         Pass::template fetch<Pass::kWin>(rec, s1 - w0), g, acc2);
+              pass.pair2(T, pass.template fetch<Pass::kWin>(rec, s0 - w0),
+                         pass.template fetch<Pass::kWin>(rec, s1 - w0), g, acc2);
             }
             for (; k < nl; k += nsub) {
               const int slot = row[k];
               if (slot >= wend) break;
-              pass.pair(T, Pass::template fetch<Pass::kWin>(rec, slot - w0), g, acc);
+              pass.pair(T, pass.template fetch<Pass::kWin>(rec, slot - w0), g, acc);
             }
           }
           // a cell of a pipelined list has no list longer than kLC: one pass
@@ -1515,7 +1534,7 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
     if (sh_cur.t >= 0) {
       float4* rec = rbuf(buf);
       if (Pass::kTargetSmem)
-        Pass::template target_from<W>(rec, (int)md_cur.y + sh_cur.t, T_cur);
+        pass.template target_from<W>(rec, (int)md_cur.y + sh_cur.t, T_cur);
       const int ns = sh_cur.nsub;
       int k = sh_cur.sub;
       if (kLists) {
@@ -1523,22 +1542,22 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
         const int c = tcnt(cb)[sh_cur.t];
         if (Pass::kPipePaired)
           for (; k + ns < c; k += 2 * ns)
-            pass.pair2(T_cur, Pass::template fetch<W>(rec, row[k]),
-                       Pass::template fetch<W>(rec, row[k + ns]), g, acc2);
-        for (; k < c; k += ns) pass.pair(T_cur, Pass::template fetch<W>(rec, row[k]), g, acc);
+            pass.pair2(T_cur, pass.template fetch<W>(rec, row[k]),
+                       pass.template fetch<W>(rec, row[k + ns]), g, acc2);
+        for (; k < c; k += ns) pass.pair(T_cur, pass.template fetch<W>(rec, row[k]), g, acc);
       } else {
         const uint16_t* row =
             slot_row(const_cast<uint16_t*>(src.slist), (int64_t)a0 + sh_cur.t, src.max_nb);
         const int c = sh_cur.cnt;
         if (Pass::kPipePaired)
           for (; k + ns < c; k += 2 * ns)
-            pass.pair2(T_cur, Pass::template fetch<W>(rec, __ldg(row + k)),
-                       Pass::template fetch<W>(rec, __ldg(row + k + ns)), g, acc2);
+            pass.pair2(T_cur, pass.template fetch<W>(rec, __ldg(row + k)),
+                       pass.template fetch<W>(rec, __ldg(row + k + ns)), g, acc2);
         // the next entry's slot is loaded (through L1) while this pair is summed
         int slot = k < c ? __ldg(row + k) : 0;
         for (; k < c; k += ns) {
           const int nxt = k + ns < c ? __ldg(row + k + ns) : 0;
-          pass.pair(T_cur, Pass::template fetch<W>(rec, slot), g, acc);
+          pass.pair(T_cur, pass.template fetch<W>(rec, slot), g, acc);
           slot = nxt;
         }
       }
@@ -1722,9 +1741,11 @@ void launch_find_masks(sph_ctx* ctx, const StateView& s, int64_t n, cudaStream_t
 }
 
 // The pair passes run in the plain configuration (kCfgPlain) when the
-// parameters allow it: the exact kernel with n = 6 (and, for the density, no
-// grad-h terms).  The general kernels are launched too and take over on grids
-// that need the FP32 minimum image; one of the two returns at once.
+// parameters allow it: the exact kernel with n = 6 and no grad-h terms.  The
+// three passes take the same configuration, since the plain one also lays out
+// the momentum records differently.  The general kernels are launched too and
+// take over on grids that need the FP32 minimum image; one of the two returns
+// at once.
 inline bool plain_kernel(const sph_ctx* ctx) {
   return ctx->prm.kernel_mode == SPH_KERNEL_EXACT && ctx->prm.sinc_n == 6.0;
 }
@@ -1776,10 +1797,11 @@ void launch_iad_staged(sph_ctx* ctx, const StateView& s, const OutView& o, int64
     p.recC = ctx->recC;
     p.recC2 = ctx->recC2;
     p.ktab = ctx->prm.kernel_mode == SPH_KERNEL_TABLE ? ctx->ktab32 : nullptr;
+    p.Bn = (float)ctx->Bn;
     p.sinc_n = (int)ctx->prm.sinc_n;
     p.err = ctx->err;
   };
-  launch_cfg<IadPassT>(ctx, plain_kernel(ctx), 1, fill, st);
+  launch_cfg<IadPassT>(ctx, plain_kernel(ctx) && !ctx->prm.gradh, 1, fill, st);
 }
 
 void launch_momentum_staged(sph_ctx* ctx, const StateView& s, const OutView& o, int64_t n,
@@ -1796,9 +1818,11 @@ void launch_momentum_staged(sph_ctx* ctx, const StateView& s, const OutView& o, 
     p.ktab = ctx->prm.kernel_mode == SPH_KERNEL_TABLE ? ctx->ktab32 : nullptr;
     p.sinc_n = (int)ctx->prm.sinc_n;
     p.alpha = (float)ctx->prm.alpha;
+    p.Bn = (float)ctx->Bn;
+    p.inv_gamma = (float)(1.0 / ctx->prm.gamma);
     p.err = ctx->err;
   };
-  launch_cfg<MomentumPassT>(ctx, plain_kernel(ctx), 2, fill, st);
+  launch_cfg<MomentumPassT>(ctx, plain_kernel(ctx) && !ctx->prm.gradh, 2, fill, st);
 }
 
 void launch_export_masks(sph_ctx* ctx, const StateView& s, int64_t n, int32_t* counts,
