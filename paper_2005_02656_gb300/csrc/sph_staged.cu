@@ -464,10 +464,12 @@ __device__ __forceinline__ float wrap32(float d, const Grid& g, int ax) {
 // separations take the FP32 minimum image, which kernel form is used and
 // whether the grad-h sum is formed; kCfgPlain fixes the default case at
 // compile time: no minimum image (every periodic axis has at least 3 cells),
-// the series kernel with n = 6 and no grad-h terms.  Where both apply they
-// evaluate the same expressions in the same order; a plain launch runs only
-// when the grid needs no minimum image (Grid::wrap32 = 0), so the launcher
-// starts both and each returns at once unless the grid is its case.
+// the series kernel with n = 6 and no grad-h terms.  The plain configuration
+// also keeps 64-byte momentum records (1/h, c and 1/rho stored; 1/h^2, B_n/h^3
+// and P/rho^2 formed per read), so the two agree to FP32 rounding, not bit for
+// bit.  A plain launch runs only when the grid needs no minimum image
+// (Grid::wrap32 = 0), so the launcher starts both and each returns at once
+// unless the grid is its case.
 constexpr int kCfgAny = 0;
 constexpr int kCfgPlain = 1;
 
