@@ -496,6 +496,11 @@ __device__ __forceinline__ float s_pow(float t, int n, const float2* tab) {
   return tab ? kernel_w32_tab(t, 1.0f, tab) : kernel_w32(t, 1.0f, n);
 }
 
+// L1 prefetch of the line holding p.
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // Paired FP32: two pairs per instruction (f32x2 arithmetic of sm_100+), each
 // component rounded exactly as the scalar operation.
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
@@ -641,6 +646,12 @@ struct DensityPassT {
     double u;
   };
   __device__ FinishIn prefin(int64_t a) const { return {pos32[a], rec_d[a].w, u[a]}; }
+  // L1 prefetch of prefin's lines, one iteration before prefin reads them
+  __device__ void prefetch_fin(int64_t a) const {
+    prefetch_l1(pos32 + a);
+    prefetch_l1(rec_d + a);
+    prefetch_l1(u + a);
+  }
   __device__ void finish(int64_t a, const float* acc) const { finish2(a, acc, prefin(a)); }
   __device__ void finish2(int64_t a, const float* acc, const FinishIn& fin) const {
     const float4 p = fin.p;
@@ -769,6 +780,10 @@ struct IadPassT {
   struct FinishIn {
     float hinv2, norm;
   };
+  __device__ void prefetch_fin(int64_t a) const {
+    prefetch_l1(recA + a);
+    if (CFG != kCfgPlain) prefetch_l1(recQ + a);
+  }
   __device__ FinishIn prefin(int64_t a) const {
     if (CFG == kCfgPlain) {
       const float hinv = recA[a].w, hinv2 = hinv * hinv;
@@ -1012,6 +1027,7 @@ struct MomentumPassT {
   }
   struct FinishIn {};
   __device__ FinishIn prefin(int64_t) const { return {}; }
+  __device__ void prefetch_fin(int64_t) const {}
   __device__ void finish2(int64_t a, const float* acc, const FinishIn&) const { finish(a, acc); }
   __device__ void finish(int64_t a, const float* acc) const {
     o.ax[a] = acc[0];
@@ -1324,9 +1340,6 @@ struct Share {
   int t, sub, nsub, cnt;
 };
 
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
 
 template <class Pass>
 __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_cellpipe(
@@ -1526,6 +1539,7 @@ __global__ void __launch_bounds__(Pass::kPipeThreads, Pass::kPipeMinBlocks) k_ce
     // compute this cell
     const int na = cell_na(md_cur);
     const uint32_t a0 = md_cur.z;
+    if (tid < na) pass.prefetch_fin((int64_t)a0 + tid);  // read by its finish next iteration
     float acc[kV];
     float2 acc2[kV];
 #pragma unroll
