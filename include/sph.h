@@ -94,7 +94,8 @@ enum { SPH_KERNEL_EXACT = 0, SPH_KERNEL_TABLE = 1 };
  *    64-bit hit mask per 64 staged candidates (bit set: r^2 < (2 h_a)^2
  *    decided exactly as by sph_find_neighbors).  Density, IAD and momentum
  *    then work cell by cell: the cell's staged candidate records are copied
- *    into shared memory once and each target's sum runs over its hit bits.
+ *    into shared memory once and each target's sum runs over the staged slots
+ *    of its hit bits (slot lists the search writes from the masks).
  *    The masks and staged entries live in the list buffer and a 108-byte-per-
  *    particle entry buffer; a state whose masks do not fit (more than
  *    max_nb / 2 mask words per particle on average) raises
@@ -103,8 +104,9 @@ enum { SPH_KERNEL_EXACT = 0, SPH_KERNEL_TABLE = 1 };
  *    particle) and every pair kernel gathers its neighbours' records from
  *    global memory; the batched ensemble uses this form, and a single box
  *    run with it equals the ensemble's result for that box bit for bit.
- * Both give the same neighbour sets and the same sums up to FP32 summation
- * order. */
+ * Both give the same neighbour sets and the same sums up to FP32 rounding
+ * (summation order, and the order in which per-particle factors such as
+ * 1/h^2 and P/rho^2 are formed). */
 enum { SPH_PAIRS_STAGED = 0, SPH_PAIRS_LISTS = 1 };
 
 /* Particle state: structure of arrays of caller-owned device memory.
