@@ -25,13 +25,14 @@
 // Pair passes (k_cellpass, one CTA of kPT threads per occupied cell at a time).
 // The cell's staged candidate records are copied once into shared memory,
 // with their cell shift applied, so separations are FP32 differences of
-// positions relative to the target cell.  Each target's hit masks are
-// expanded into a list of staged slots in shared memory; the target's sum is
-// split over nsub = kPT / (targets) threads, thread s taking entries s,
-// s + nsub, ..., and the nsub partial sums are added in a fixed order, so the
-// result does not depend on scheduling.  Cells whose staged set or target set
-// exceeds the shared-memory window are processed in windows and rounds; a
-// target with more than kLC hits in a window is expanded in several passes.
+// positions relative to the target cell.  Each target's staged-slot list
+// (written by the search from its hit masks) is copied into shared memory;
+// the target's sum is split over nsub = kPT / (targets) threads, thread s
+// taking entries s, s + nsub, ..., and the nsub partial sums are added in a
+// fixed order, so the result does not depend on scheduling.  Cells whose
+// staged set or target set exceeds the shared-memory window are processed in
+// windows and rounds; a target with more than kLC entries is read in several
+// list passes.
 #include <cuda_runtime.h>
 
 #include "sph_device.cuh"
@@ -57,7 +58,7 @@ using find::pair_index;
 constexpr int kTR = 64;         // targets per round of the pair passes
 constexpr int kLC = 128;        // list entries per target and list pass
 constexpr int kPipeWin = 832;   // staged candidates of a cell the pipelined passes take
-constexpr int kPipeWinM = 448;  // ... the pipelined momentum pass takes (72-byte records)
+constexpr int kPipeWinM = 448;  // ... the pipelined momentum pass takes (64/72-byte records)
 
 // A cell is staged (hit masks) when its stencil holds at most kStagedMaxP
 // particles, so a target's mask row is at most kStagedMaxP / 64 words and the
@@ -1298,7 +1299,7 @@ __global__ void __launch_bounds__(kPT, Pass::kMinBlocks) k_cellpass(Pass pass, c
 // list, so the threads of a warp step through their lists in lockstep.  The
 // lists come from shared memory (passes with 16-byte records: the next cell's
 // lists are copied by cp.async with its records) or from global memory
-// through L1 (momentum, whose 72-byte records leave no room for list buffers:
+// through L1 (momentum, whose 64/72-byte records leave no room for list buffers:
 // the next cell's list rows are prefetched into L1).
 
 template <class Pass>
